@@ -1,0 +1,178 @@
+/*
+ * radarsim — GB300 (sm_103a) FMCW radar data from ray-tracer output and meta data.
+ *
+ * C ABI of libradarsim.so.  It turns the per-ray output of a radar ray tracer
+ * (round-trip path length, amplitude, radial velocity, azimuth/elevation,
+ * start phase) and its meta data (object id, material id) into
+ *   1. the complex beat-signal cube s[k][m][n] of every virtual channel k,
+ *      chirp m and fast-time sample n (arXiv 2305.14176, Sec. II-A, Eqs. 1-3,
+ *      with the far-field antenna adjustment of Sec. II-E, Eq. 7),
+ *   2. its windowed range-Doppler-angle spectrum (Sec. II-A, Eq. 4, extended
+ *      along the virtual channels), and
+ *   3. a per-cell object label: the id whose rays deposit the most energy in
+ *      the cell (Sec. II-C, Eq. 5 decomposition by meta data, and the automatic
+ *      annotation that follows it).
+ *
+ * Signal model (separable reading of Eq. 2):
+ *   s[k][m][n] = sum_i a_i exp(2 pi j (phi_i + k nu_a,i + m nu_d,i + n nu_r,i))
+ *   phi_i  = f_c d_i / c + phase0_i / 2pi           carrier phase (Eq. 2, f_c tau)
+ *   nu_r,i = B d_i / (c N_s)                        Eq. 2 mu t tau, t = n T_c / N_s, Eq. 3
+ *   nu_d,i = 2 v_i f_c T_d / c                      Eq. 2 f_c tau_i(j), d grows 2 v T_d per chirp
+ *   nu_a,i = s f_c sin(az_i) cos(el_i) / c          Eq. 7 in the far field, ULA spacing s
+ * with c = 299792458 m/s.  Virtual channel k = tx * n_rx + rx sits at k * s.
+ *
+ * Spectrum X[a][p][q] = sum_{k<N_v, m<N_c, n<N_s} w_a[k] w_d[m] w_r[n] s[k][m][n]
+ *                        e^{-2 pi j (k a / N_a + m p / N_c + n q / N_s)}
+ * forward, unnormalised, natural order (bin 0 = DC); the angle axis is zero
+ * padded from N_v to N_a.
+ *
+ * Labels: each ray's cell is (q_a, q_d, q_r) with q_x = floor(x + 0.5) mod N_x,
+ *   x_r = (B d) / c, x_d = ((((2 v) f_c) T_d) N_c) / c,
+ *   x_a = (N_a s f_c / c) (sin(az) cos(el)),
+ * in FP64 in exactly this order (sin, cos by Cody-Waite reduction and Taylor
+ * series in a fixed fused-multiply-add order); its energy is
+ * min(rint(a^2 2^32), 2^41) as int64.  A cell's label is the object id with the
+ * largest summed energy, ties to the smallest id, -1 for a cell no ray falls in.
+ *
+ * Layouts (row-major, last index fastest, complex = interleaved float re, im):
+ *   signal    complex64[N_v][N_c][N_s]
+ *   spectrum  complex64[N_a][N_c][N_s]
+ *   labels    int32[N_a][N_c][N_s]
+ *
+ * Errors: every call returns an int status (SIM_OK or a negative SIM_E_*);
+ * nothing aborts or throws across the ABI.  All calls are thread-safe.
+ */
+#ifndef RADARSIM_H
+#define RADARSIM_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RADARSIM_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define SIM_API __attribute__((visibility("default")))
+#else
+#define SIM_API
+#endif
+
+/* status codes */
+#define SIM_OK 0
+#define SIM_E_INVALID (-1)        /* bad parameters or ray values */
+#define SIM_E_NOMEM (-2)          /* device or host allocation failed */
+#define SIM_E_BUSY (-3)           /* admission refused: memory budget or queue full */
+#define SIM_E_TIMEOUT (-4)        /* sim_fetch timed out; the ticket stays valid */
+#define SIM_E_NOT_READY (-5)      /* ticket not finished (timeout_ms == 0) */
+#define SIM_E_UNKNOWN_TICKET (-6) /* ticket never issued, already fetched or for another context */
+#define SIM_E_CUDA (-7)           /* a CUDA runtime call failed */
+#define SIM_E_DEVICE (-8)         /* a kernel reported an internal limit (status word) */
+
+/* window codes */
+#define SIM_WIN_NONE 0
+#define SIM_WIN_HANN_PERIODIC 1   /* w[t] = (1 - cos(2 pi t / L)) / 2 */
+#define SIM_WIN_HANN_SYMMETRIC 2  /* w[t] = (1 - cos(2 pi t / (L - 1))) / 2 */
+#define SIM_WIN_HANN_NOZERO 3     /* w[t] = (1 - cos(2 pi (t + 1) / (L + 1))) / 2 */
+
+/* ray-sum arithmetic */
+#define SIM_PREC_FP32_DIRECT 0    /* one FP32 sin/cos per ray and output sample */
+#define SIM_PREC_BF16 1           /* tensor-core GEMM, BF16 operands, FP32 accumulation */
+#define SIM_PREC_BF16_SPLIT 2     /* BF16 hi + lo operands, three MMAs */
+#define SIM_PREC_FP16 3
+#define SIM_PREC_FP16_SPLIT 4
+
+/* outputs bitmask */
+#define SIM_OUT_SIGNAL 1
+#define SIM_OUT_SPECTRUM 2
+#define SIM_OUT_LABELS 4
+
+typedef struct sim_ctx sim_ctx; /* opaque: one radar configuration */
+
+typedef struct {
+  uint32_t struct_size;      /* sizeof(sim_radar_params) of the caller's header */
+  double carrier_hz;         /* f_c > 0 */
+  double bandwidth_hz;       /* B > 0 */
+  double sweep_time_s;       /* T_c > 0: sweep and sampling window */
+  double chirp_period_s;     /* T_d > 0: chirp repetition period */
+  int32_t n_samples;         /* N_s: power of two, 16 .. 4096 */
+  int32_t n_chirps;          /* N_c: power of two, 2 .. 4096 */
+  int32_t n_tx, n_rx;        /* >= 1 each; N_v = n_tx * n_rx <= 1024 */
+  double element_spacing_m;  /* virtual ULA spacing s >= 0; 0 means lambda / 2 */
+  int32_t n_angle;           /* N_a: power of two >= N_v, <= 1024; 0 means max(16, nextpow2(N_v)) */
+  int32_t window[3];         /* range, Doppler, angle: SIM_WIN_* */
+  int32_t precision;         /* SIM_PREC_* */
+  int32_t outputs;           /* SIM_OUT_* bitmask, nonzero */
+  int64_t max_rays;          /* 1 .. 2^21 (keeps the int64 energy sums exact) */
+} sim_radar_params;
+
+/* Structure-of-arrays rays.  Each pointer holds n elements; pointers may be
+   host (pageable or pinned) or device memory of the current device. */
+typedef struct {
+  int64_t n;                        /* 0 .. max_rays */
+  const double *range_rt_m;         /* d_i >= 0: Tx -> scatterers -> Rx path length */
+  const float *amplitude;           /* a_i >= 0 */
+  const float *radial_velocity_mps; /* v_i, > 0 receding; finite */
+  const float *azimuth_rad;         /* |az| <= pi */
+  const float *elevation_rad;       /* |el| <= pi/2 */
+  const float *phase0_rad;          /* finite */
+} sim_rays;
+
+typedef struct {
+  const int32_t *object_id;   /* >= 0; required when SIM_OUT_LABELS is requested */
+  const int32_t *material_id; /* may be NULL; carried for filter rules, not used yet */
+} sim_meta;
+
+/* Validate params, derive the radar constants and upload the window and twiddle
+   tables.  *out receives a context owned by the caller until sim_destroy.
+   Errors: SIM_E_INVALID (bad params, *out untouched), SIM_E_NOMEM, SIM_E_CUDA. */
+SIM_API int sim_create(const sim_radar_params *params, sim_ctx **out);
+
+/* Queue one scene.  The ray arrays (and meta arrays) are copied before the call
+   returns; the caller may reuse them at once.  Work starts on the device as soon
+   as the engine admits the scene (free memory budget and free slot); otherwise it
+   waits in a bounded queue and is admitted when an earlier result is fetched.
+   *ticket_out identifies the result for sim_fetch.
+   Errors: SIM_E_INVALID (n out of range, NULL array, a host ray with a bad value),
+   SIM_E_BUSY (queue full, or the scene alone exceeds the memory budget),
+   SIM_E_NOMEM, SIM_E_CUDA.  Invalid values in device-resident rays are reported
+   by sim_fetch as SIM_E_INVALID. */
+SIM_API int sim_submit(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, uint64_t *ticket_out);
+
+/* Wait for a ticket and copy its results out.  spectrum (complex64), signal
+   (complex64) and labels (int32) are caller-owned host or device buffers in the
+   layouts above; each may be NULL if not wanted and must be NULL if the context
+   was created without that output.  timeout_ms < 0 waits forever, 0 polls.
+   On SIM_OK the ticket is consumed and its device memory released.
+   Errors: SIM_E_UNKNOWN_TICKET, SIM_E_TIMEOUT / SIM_E_NOT_READY (ticket kept),
+   SIM_E_INVALID (the scene held an invalid ray; ticket consumed), SIM_E_DEVICE,
+   SIM_E_CUDA. */
+SIM_API int sim_fetch(sim_ctx *ctx, uint64_t ticket, void *spectrum_c64, void *signal_c64,
+              int32_t *labels, int32_t timeout_ms);
+
+/* Release a context.  Unfetched tickets of the context are waited for and dropped. */
+SIM_API int sim_destroy(sim_ctx *ctx);
+
+/* Static string for a status code. */
+SIM_API const char *sim_status_string(int status);
+
+/* ---- engine controls and measurement (not part of the paper's method) ---- */
+
+/* Device-memory budget of the engine in bytes (0 = default: 90 % of the free
+   memory when the engine starts) and the number of concurrent slots (streams).
+   Must be called before the first sim_create; SIM_E_INVALID afterwards. */
+SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int32_t max_queue);
+
+/* Per-stage device time in milliseconds of the most recently fetched ticket of
+   this context: [0] ingest copies, [1] per-ray prep, [2] ray sum, [3] FFTs,
+   [4] labels, [5] whole device pipeline; n is the array length (<= 8).  Stage
+   timing is on by default; entries for stages that did not run are 0. */
+SIM_API int sim_last_stage_ms(sim_ctx *ctx, float *ms, int32_t n);
+
+/* Number of kernels the most recently fetched ticket of this context launched. */
+SIM_API int sim_last_kernel_count(sim_ctx *ctx, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,84 @@
+// Internal declarations shared by the CUDA translation units of libradarsim.
+// Nothing here is part of the C ABI (include/radarsim.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "radarsim.h"
+
+namespace rs {
+
+constexpr double kC = 299792458.0;  // speed of light, m/s
+
+// device status word bits (written by kernels with atomicOr, read at fetch)
+enum : uint32_t {
+  kStatusBadRay = 1u,        // a ray failed validation in the prep kernel
+  kStatusHashFull = 2u,      // a label hash probe ran past its limit
+  kStatusWaitLimit = 4u,     // a tensor-core pipeline wait ran past its limit
+  kStatusBadLaunch = 8u,     // a kernel saw a launch shape it was not built for
+};
+
+// Radar constants derived on the host in FP64 from sim_radar_params.
+struct Derived {
+  double fc, bw, tc, td;
+  int ns, nc, ntx, nrx, nv, na;
+  int log2_ns, log2_nc, log2_na;
+  double spacing_wl;  // antenna spacing in carrier wavelengths: s f_c / c, or exactly 1/2
+  double ka;          // N_a * spacing_wl: angle-bin coordinate per unit sin(az) cos(el)
+  int win[3];
+  int precision, outputs;
+  int64_t max_rays;
+  int64_t n_sig;   // N_v N_c N_s
+  int64_t n_cell;  // N_a N_c N_s
+};
+
+// Rays as handed to the device (structure of arrays)
+struct RaysIn {
+  const double *d;
+  const float *a, *v, *az, *el, *p0;
+  const int32_t *obj;
+};
+
+// Per-ray quantities produced by the prep kernel (Q0.64 phases are fractions of a cycle
+// times 2^64; integer addition wraps exactly modulo one cycle).
+struct RaysPrep {
+  uint64_t *carrier;  // frac(f_c d / c) + phase0 / 2 pi
+  uint64_t *nu_r;     // cycles per fast-time sample
+  uint64_t *nu_d;     // cycles per chirp
+  uint64_t *nu_a;     // cycles per virtual channel
+  float *amp;         // amplitude (0 for an invalid ray)
+  int32_t *cell;      // flat label cell, -1 for an invalid ray
+  uint64_t *energy;   // min(rint(a^2 2^32), 2^41)
+};
+
+// Scratch for the label kernels: two open-addressing hash tables
+struct LabelScratch {
+  uint64_t *pair_key;    // (cell << 32) | object id, ~0 = empty
+  uint64_t *pair_energy;
+  uint32_t *cell_key;    // cell, ~0 = empty
+  uint64_t *cell_max;
+  uint32_t *cell_obj;    // smallest object id at the cell maximum
+  int64_t capacity;      // power of two, >= 2 * rays
+};
+
+int64_t label_capacity(int64_t n_rays);
+
+// window / twiddle tables for one radar configuration (device memory)
+struct Tables {
+  float *win_r, *win_d, *win_a;   // lengths N_s, N_c, N_v
+  float2 *tw_r, *tw_d, *tw_a;     // e^{-2 pi i j / N}, j < N/2
+};
+
+// ---- launchers (each returns the number of kernels it launched) ----
+int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s);
+int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s);
+int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);
+int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
+                  int32_t *labels, uint32_t *status, cudaStream_t s);
+
+// tensor-core ray sum: workspace bytes it needs and its launcher
+int64_t umma_workspace_bytes(const Derived &g, int64_t n);
+int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace,
+                    uint32_t *status, cudaStream_t s);
+
+}  // namespace rs

@@ -1,0 +1,145 @@
+// K_a: per-ray prep in FP64 (arXiv 2305.14176, Sec. II-A Eqs. 1-3, Sec. II-E Eq. 7).
+//
+// For every ray: validate it, range-reduce its phase increments to Q0.64 fixed point
+// (the one step whose accuracy needs FP64: f_c d / c is up to ~1e5 cycles), and compute
+// its label cell and fixed-point energy.  All FP64 arithmetic uses explicit _rn
+// intrinsics so no multiply-add is contracted: the bin coordinates follow a fixed
+// operation order and are reproducible bit for bit.
+#include <math.h>
+
+#include "internal.h"
+
+namespace rs {
+namespace {
+
+// pi/2 as a sum of two doubles (Cody-Waite), and 2/pi, each the nearest double
+__device__ constexpr double kP1 = 0x1.921fb54442d18p+0;
+__device__ constexpr double kP2 = 0x1.1a62633145c07p-54;
+__device__ constexpr double kTwoOverPi = 0x1.45f306dc9c883p-1;
+__device__ constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;  // 1 / (2 pi)
+__device__ constexpr double kTwo64 = 18446744073709551616.0;
+
+// Taylor series of sin on [-pi/4, pi/4] through r^17, Horner in r^2 with fused multiply-adds
+__device__ __forceinline__ double poly_sin(double r) {
+  const double z = __dmul_rn(r, r);
+  double p = 1.0 / 355687428096000.0;
+  p = __fma_rn(p, z, -1.0 / 1307674368000.0);
+  p = __fma_rn(p, z, 1.0 / 6227020800.0);
+  p = __fma_rn(p, z, -1.0 / 39916800.0);
+  p = __fma_rn(p, z, 1.0 / 362880.0);
+  p = __fma_rn(p, z, -1.0 / 5040.0);
+  p = __fma_rn(p, z, 1.0 / 120.0);
+  p = __fma_rn(p, z, -1.0 / 6.0);
+  return __fma_rn(__dmul_rn(r, z), p, r);
+}
+
+// Taylor series of cos on [-pi/4, pi/4] through r^18
+__device__ __forceinline__ double poly_cos(double r) {
+  const double z = __dmul_rn(r, r);
+  double q = -1.0 / 6402373705728000.0;
+  q = __fma_rn(q, z, 1.0 / 20922789888000.0);
+  q = __fma_rn(q, z, -1.0 / 87178291200.0);
+  q = __fma_rn(q, z, 1.0 / 479001600.0);
+  q = __fma_rn(q, z, -1.0 / 3628800.0);
+  q = __fma_rn(q, z, 1.0 / 40320.0);
+  q = __fma_rn(q, z, -1.0 / 720.0);
+  q = __fma_rn(q, z, 1.0 / 24.0);
+  q = __fma_rn(q, z, -1.0 / 2.0);
+  return __fma_rn(z, q, 1.0);
+}
+
+// sin (want_cos = false) or cos of x, |x| <= fl32(pi): quadrant k = rint(x 2/pi) in -2..2,
+// r = (x - k P1) - k P2 (the first subtraction is exact), then the series by quadrant.
+__device__ __forceinline__ double sin_or_cos(double x, bool want_cos) {
+  const double k = rint(__dmul_rn(x, kTwoOverPi));
+  const double r = __dsub_rn(__dsub_rn(x, __dmul_rn(k, kP1)), __dmul_rn(k, kP2));
+  const int q = (static_cast<int>(k) + (want_cos ? 1 : 0)) & 3;
+  switch (q) {
+    case 0: return poly_sin(r);
+    case 1: return poly_cos(r);
+    case 2: return -poly_sin(r);
+    default: return -poly_cos(r);
+  }
+}
+
+__device__ __forceinline__ uint64_t frac_q64(double x) {
+  const double f = __dsub_rn(x, floor(x));  // exact, in [0, 1)
+  return __double2ull_rn(__dmul_rn(f, kTwo64));
+}
+
+__device__ __forceinline__ int64_t bin_of(double x, int64_t n) {
+  int64_t q = static_cast<int64_t>(floor(__dadd_rn(x, 0.5)));
+  q %= n;
+  if (q < 0) q += n;
+  return q;
+}
+
+struct PrepConst {
+  double fc, bw, td, nc_d, ka;
+  double inv_ns, inv_nc, inv_na;
+  int64_t ns, nc, na;
+  int want_labels;
+};
+
+__global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64_t n, RaysPrep out,
+                                                   uint32_t *status) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  const double d = in.d[i];
+  const float a = in.a[i], v = in.v[i], az = in.az[i], el = in.el[i], p0 = in.p0[i];
+  const int32_t obj = k.want_labels ? in.obj[i] : 0;
+  // validation: NaN fails every comparison below
+  const bool ok = (d >= 0.0 && d <= 1.0e7) && (a >= 0.0f && a <= 3.0e38f) &&
+                  (fabsf(v) <= 1.0e5f) && (fabsf(az) <= 3.14159274f) && (fabsf(el) <= 1.57079637f) &&
+                  (fabsf(p0) <= 1.0e6f) && (obj >= 0);
+  if (!ok) {
+    atomicOr(status, kStatusBadRay);
+    out.carrier[i] = 0; out.nu_r[i] = 0; out.nu_d[i] = 0; out.nu_a[i] = 0;
+    out.amp[i] = 0.0f; out.cell[i] = -1; out.energy[i] = 0;
+    return;
+  }
+  const double vd = static_cast<double>(v);
+  // analytic bin coordinates (fixed order, no contraction)
+  const double x_r = __ddiv_rn(__dmul_rn(k.bw, d), kC);
+  const double x_d = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, vd), k.fc), k.td), k.nc_d), kC);
+  const double x_a = __dmul_rn(k.ka, __dmul_rn(sin_or_cos(static_cast<double>(az), false),
+                                               sin_or_cos(static_cast<double>(el), true)));
+  // phase increments per sample / chirp / channel: x_x / N_x (exact scaling by a power of two)
+  out.nu_r[i] = frac_q64(__dmul_rn(x_r, k.inv_ns));
+  out.nu_d[i] = frac_q64(__dmul_rn(x_d, k.inv_nc));
+  out.nu_a[i] = frac_q64(__dmul_rn(x_a, k.inv_na));
+  // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
+  out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +
+                   frac_q64(__dmul_rn(static_cast<double>(p0), kInv2Pi));
+  out.amp[i] = a;
+  const int64_t cell = (bin_of(x_a, k.na) * k.nc + bin_of(x_d, k.nc)) * k.ns + bin_of(x_r, k.ns);
+  out.cell[i] = static_cast<int32_t>(cell);
+  const double aa = static_cast<double>(a);
+  double e = rint(ldexp(__dmul_rn(aa, aa), 32));
+  if (e > 2199023255552.0) e = 2199023255552.0;  // 2^41
+  out.energy[i] = static_cast<uint64_t>(e);
+}
+
+}  // namespace
+
+int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s) {
+  if (n <= 0) return 0;
+  PrepConst k;
+  k.fc = g.fc;
+  k.bw = g.bw;
+  k.td = g.td;
+  k.nc_d = static_cast<double>(g.nc);
+  k.ka = g.ka;
+  k.inv_ns = 1.0 / g.ns;
+  k.inv_nc = 1.0 / g.nc;
+  k.inv_na = 1.0 / g.na;
+  k.ns = g.ns;
+  k.nc = g.nc;
+  k.na = g.na;
+  k.want_labels = in.obj != nullptr;
+  const int64_t blocks = (n + 255) / 256;
+  prep_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(k, in, n, out, status);
+  return 1;
+}
+
+}  // namespace rs

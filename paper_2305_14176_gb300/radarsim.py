@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libradarsim.so (C ABI in include/radarsim.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels.  Functions carry the C names.  Pointers may be host numpy arrays
+or device tensors (anything with ``data_ptr()`` or ``ctypes.data``).
+There is no fallback: if the library is missing, importing raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Dict, Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libradarsim.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "radarsim.h")
+
+SIM_OK = 0
+SIM_E_INVALID = -1
+SIM_E_NOMEM = -2
+SIM_E_BUSY = -3
+SIM_E_TIMEOUT = -4
+SIM_E_NOT_READY = -5
+SIM_E_UNKNOWN_TICKET = -6
+SIM_E_CUDA = -7
+SIM_E_DEVICE = -8
+
+SIM_WIN_NONE, SIM_WIN_HANN_PERIODIC, SIM_WIN_HANN_SYMMETRIC, SIM_WIN_HANN_NOZERO = 0, 1, 2, 3
+SIM_PREC_FP32_DIRECT, SIM_PREC_BF16, SIM_PREC_BF16_SPLIT, SIM_PREC_FP16, SIM_PREC_FP16_SPLIT = 0, 1, 2, 3, 4
+SIM_OUT_SIGNAL, SIM_OUT_SPECTRUM, SIM_OUT_LABELS = 1, 2, 4
+PRECISION_NAMES = {"fp32": SIM_PREC_FP32_DIRECT, "bf16": SIM_PREC_BF16, "bf16_split": SIM_PREC_BF16_SPLIT,
+                   "fp16": SIM_PREC_FP16, "fp16_split": SIM_PREC_FP16_SPLIT}
+
+
+class sim_radar_params(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32),
+                ("carrier_hz", ctypes.c_double), ("bandwidth_hz", ctypes.c_double),
+                ("sweep_time_s", ctypes.c_double), ("chirp_period_s", ctypes.c_double),
+                ("n_samples", ctypes.c_int32), ("n_chirps", ctypes.c_int32),
+                ("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
+                ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
+                ("window", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
+                ("outputs", ctypes.c_int32), ("max_rays", ctypes.c_int64)]
+
+
+class sim_rays(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("range_rt_m", ctypes.c_void_p), ("amplitude", ctypes.c_void_p),
+                ("radial_velocity_mps", ctypes.c_void_p), ("azimuth_rad", ctypes.c_void_p),
+                ("elevation_rad", ctypes.c_void_p), ("phase0_rad", ctypes.c_void_p)]
+
+
+class sim_meta(ctypes.Structure):
+    _fields_ = [("object_id", ctypes.c_void_p), ("material_id", ctypes.c_void_p)]
+
+
+class SimError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {sim_status_string(code)} ({code})" if what else sim_status_string(code))
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libradarsim.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, U64P = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)
+    lib.sim_create.argtypes = [ctypes.POINTER(sim_radar_params), ctypes.POINTER(ctypes.c_void_p)]
+    lib.sim_submit.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), U64P]
+    lib.sim_fetch.argtypes = [P, ctypes.c_uint64, P, P, P, I32]
+    lib.sim_destroy.argtypes = [P]
+    lib.sim_status_string.argtypes = [ctypes.c_int]
+    lib.sim_status_string.restype = ctypes.c_char_p
+    lib.sim_engine_configure.argtypes = [I64, I32, I32]
+    lib.sim_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), I32]
+    lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
+              "sim_last_stage_ms", "sim_last_kernel_count"):
+        getattr(lib, f).restype = ctypes.c_int
+    return lib
+
+
+lib = _load()
+
+
+def header_functions(path: str = HEADER) -> Sequence[str]:
+    """Names of the functions include/radarsim.h declares."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sim_[a-z_0-9]+)\s*\(", src)))
+
+
+def _addr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+# ------------------------------------------------------------------ the C entry points
+
+def sim_status_string(code: int) -> str:
+    return lib.sim_status_string(int(code)).decode()
+
+
+def sim_engine_configure(memory_budget_bytes: int = 0, slots: int = 4, max_queue: int = 64) -> int:
+    return lib.sim_engine_configure(int(memory_budget_bytes), int(slots), int(max_queue))
+
+
+def sim_create(params: sim_radar_params) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    rc = lib.sim_create(ctypes.byref(params), ctypes.byref(ctx))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_create")
+    return ctx
+
+
+def sim_submit(ctx, rays: sim_rays, meta: Optional[sim_meta] = None) -> int:
+    t = ctypes.c_uint64()
+    rc = lib.sim_submit(ctx, ctypes.byref(rays), ctypes.byref(meta) if meta is not None else None,
+                        ctypes.byref(t))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_submit")
+    return int(t.value)
+
+
+def sim_fetch(ctx, ticket: int, spectrum=None, signal=None, labels=None, timeout_ms: int = -1) -> int:
+    """Returns the status code (SIM_OK, SIM_E_TIMEOUT, ...) without raising."""
+    return lib.sim_fetch(ctx, ctypes.c_uint64(ticket), _addr(spectrum), _addr(signal), _addr(labels),
+                         int(timeout_ms))
+
+
+def sim_destroy(ctx) -> int:
+    return lib.sim_destroy(ctx)
+
+
+def sim_last_stage_ms(ctx):
+    buf = (ctypes.c_float * 6)()
+    rc = lib.sim_last_stage_ms(ctx, buf, 6)
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_last_stage_ms")
+    names = ("ingest", "prep", "ray_sum", "fft", "labels", "total")
+    return dict(zip(names, list(buf)))
+
+
+def sim_last_kernel_count(ctx) -> int:
+    c = ctypes.c_int32()
+    rc = lib.sim_last_kernel_count(ctx, ctypes.byref(c))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_last_kernel_count")
+    return int(c.value)
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def make_params(radar, precision: int = SIM_PREC_FP32_DIRECT,
+                outputs: int = SIM_OUT_SIGNAL | SIM_OUT_SPECTRUM | SIM_OUT_LABELS,
+                max_rays: int = 1 << 21) -> sim_radar_params:
+    """sim_radar_params from any object with the radar attribute names of the ABI."""
+    p = sim_radar_params()
+    p.struct_size = ctypes.sizeof(sim_radar_params)
+    p.carrier_hz = radar.carrier_hz
+    p.bandwidth_hz = radar.bandwidth_hz
+    p.sweep_time_s = radar.sweep_time_s
+    p.chirp_period_s = radar.chirp_period_s
+    p.n_samples = radar.n_samples
+    p.n_chirps = radar.n_chirps
+    p.n_tx = radar.n_tx
+    p.n_rx = radar.n_rx
+    p.element_spacing_m = radar.element_spacing_m
+    p.n_angle = radar.n_angle
+    for i in range(3):
+        p.window[i] = int(radar.window[i])
+    p.precision = int(precision)
+    p.outputs = int(outputs)
+    p.max_rays = int(max_rays)
+    return p
+
+
+def make_rays(arrays: Dict[str, object], n: int):
+    """(sim_rays, sim_meta) over arrays keyed by the ABI field names."""
+    r = sim_rays(int(n), _addr(arrays["range_rt_m"]), _addr(arrays["amplitude"]),
+                 _addr(arrays["radial_velocity_mps"]), _addr(arrays["azimuth_rad"]),
+                 _addr(arrays["elevation_rad"]), _addr(arrays["phase0_rad"]))
+    m = sim_meta(_addr(arrays.get("object_id")), _addr(arrays.get("material_id")))
+    return r, m
+
+
+class Context:
+    """Owns one sim_ctx; submit/fetch with numpy (host) or torch (device) arrays."""
+
+    def __init__(self, radar, precision=SIM_PREC_FP32_DIRECT,
+                 outputs=SIM_OUT_SIGNAL | SIM_OUT_SPECTRUM | SIM_OUT_LABELS, max_rays=1 << 21):
+        if isinstance(precision, str):
+            precision = PRECISION_NAMES[precision]
+        self.radar = radar
+        self.outputs = outputs
+        self.ctx = sim_create(make_params(radar, precision, outputs, max_rays))
+        self.nv = radar.n_tx * radar.n_rx
+        na = radar.n_angle or max(16, 1 << (self.nv - 1).bit_length())
+        self.signal_shape = (self.nv, radar.n_chirps, radar.n_samples)
+        self.cube_shape = (na, radar.n_chirps, radar.n_samples)
+
+    def submit(self, arrays: Dict[str, object], n: Optional[int] = None) -> int:
+        if n is None:
+            n = len(arrays["range_rt_m"])
+        r, m = make_rays(arrays, n)
+        return sim_submit(self.ctx, r, m)
+
+    def fetch(self, ticket, spectrum=None, signal=None, labels=None, timeout_ms=-1) -> int:
+        return sim_fetch(self.ctx, ticket, spectrum, signal, labels, timeout_ms)
+
+    def close(self):
+        if self.ctx is not None:
+            sim_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,201 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Signal and spectrum: max |error| / max |oracle| and RMS error within the
+tolerance of the ray-sum arithmetic (1e-5 for FP32 and split precision, 2e-3
+for single-pass BF16/FP16).  Labels and bins: bit exact.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen
+from scenegen import Radar, Rays
+from paper_2305_14176_gb300 import radarsim as rs
+from gpu_helpers import TOL, rel_max, rel_rms, run
+
+pytestmark = pytest.mark.gpu
+
+C = 299792458.0
+PRECISIONS = [rs.SIM_PREC_FP32_DIRECT]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    radar, rays = scenegen.tiny_scene(seed=0)
+    sig = oracle.signal(radar, rays)
+    return radar, rays, sig, oracle.spectrum(radar, sig), oracle.labels(radar, rays)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("device_inputs", [True, False])
+def test_tiny_scene_full_cube(tiny, precision, device_inputs):
+    radar, rays, ref_sig, ref_spec, ref_lab = tiny
+    rc, sig, spec, lab = run(radar, rays, precision, device_inputs)
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    tol = TOL[precision]
+    assert rel_max(sig, ref_sig) <= tol and rel_rms(sig, ref_sig) <= tol
+    assert rel_max(spec, ref_spec) <= tol and rel_rms(spec, ref_spec) <= tol
+    assert np.array_equal(lab, ref_lab)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape,n", [((16, 2, 1, 3, 4), 1), ((32, 4, 1, 3, 4), 255),
+                                     ((64, 8, 2, 3, 8), 257), ((128, 128, 3, 4, 16), 700),
+                                     ((256, 32, 1, 1, 1), 33)])
+def test_ragged_shapes(precision, shape, n):
+    ns, nc, ntx, nrx, na = shape
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na)
+    rays = scenegen.uniform_rays(seed=ns + n, n=n, n_objects=5)
+    ref = oracle.signal(radar, rays)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    tol = TOL[precision]
+    assert rel_max(sig, ref) <= tol
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_empty_scene(precision):
+    radar = scenegen.radar_tiny()
+    rays = scenegen.uniform_rays(seed=0, n=0)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    assert np.all(sig == 0) and np.all(spec == 0) and np.all(lab == -1)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_automotive_radar_subsampled(precision):
+    """The automotive frame's radar (12 x 256 x 512, N_a 16) with 3,000 of its rays:
+    signal at 4,096 sampled points, spectrum at sampled and peak cells, labels whole."""
+    radar, rays = scenegen.automotive_scene(seed=1000, n_rays=3000)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    idx = scenegen.randint(7, 1, 4096, 0, sig.size - 1).astype(np.int64)
+    ref = oracle.signal_at(radar, rays, idx)
+    tol = TOL[precision]
+    assert rel_max(sig.reshape(-1)[idx], ref) <= tol and rel_rms(sig.reshape(-1)[idx], ref) <= tol
+    flat = np.abs(spec.reshape(-1))
+    cells = np.unique(np.concatenate([np.argsort(-flat)[:16],
+                                      scenegen.randint(7, 2, 240, 0, flat.size - 1)])).astype(np.int64)
+    refc = oracle.cell_dtft(radar, rays, cells)
+    assert rel_max(spec.reshape(-1)[cells], refc) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_automotive_frame_full_size(precision):
+    """The full automotive frame (200,000 rays) in the launch configuration the benchmark
+    times: signal at sampled points, four spectrum cells (the peak among them), labels whole."""
+    radar, rays = scenegen.automotive_scene(seed=1000)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    idx = scenegen.randint(8, 1, 256, 0, sig.size - 1).astype(np.int64)
+    ref = oracle.signal_at(radar, rays, idx)
+    tol = TOL[precision]
+    assert rel_rms(sig.reshape(-1)[idx], ref) <= tol
+    assert rel_max(sig.reshape(-1)[idx], ref) <= tol
+    flat = np.abs(spec.reshape(-1))
+    cells = np.array([int(np.argmax(flat)), 12345, 777777, int(flat.size - 1)], np.int64)
+    refc = oracle.cell_dtft(radar, rays, cells)
+    assert rel_max(spec.reshape(-1)[cells], refc, norm=np.abs(refc).max()) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
+def _boundary_rays(radar, seed):
+    """Rays whose range, Doppler or angle coordinate sits within a few ulp of a bin edge."""
+    lam = C / radar.carrier_hz
+    out = []
+    oid = 0
+    rng = np.random.default_rng(seed)
+    for q in (0, 3, 17, radar.n_samples - 1, radar.n_samples + 2):
+        d0 = (q + 0.5) * C / radar.bandwidth_hz
+        for k in range(-3, 4):
+            d = d0
+            for _ in range(abs(k)):
+                d = np.nextafter(d, np.inf if k > 0 else -np.inf)
+            out.append((d, 0.0, 0.0, oid)); oid += 1
+    for q in (-3, 0, 5, radar.n_chirps // 2 - 1):
+        v0 = np.float32((q + 0.5) * lam / (2 * radar.n_chirps * radar.chirp_period_s))
+        for k in range(-3, 4):
+            v = v0
+            for _ in range(abs(k)):
+                v = np.nextafter(v, np.float32(np.inf if k > 0 else -np.inf))
+            out.append((40 * C / radar.bandwidth_hz, float(v), 0.0, oid)); oid += 1
+    for q in (-2, 0, 1, 3):
+        a0 = np.float32(math.asin((q + 0.5) / (radar.n_angle * 0.5)))
+        for k in range(-3, 4):
+            a = a0
+            for _ in range(abs(k)):
+                a = np.nextafter(a, np.float32(np.inf if k > 0 else -np.inf))
+            out.append((80 * C / radar.bandwidth_hz, 0.0, float(a), oid)); oid += 1
+    n = len(out)
+    return Rays(np.array([o[0] for o in out]), rng.uniform(0.1, 1.0, n).astype(np.float32),
+                np.array([o[1] for o in out], np.float32), np.array([o[2] for o in out], np.float32),
+                np.zeros(n, np.float32), np.zeros(n, np.float32), np.array([o[3] for o in out], np.int32))
+
+
+def test_bin_edges_are_bit_exact():
+    radar = scenegen.radar_automotive(n_chirps=64, n_samples=128)
+    rays = _boundary_rays(radar, 3)
+    ref = oracle.labels(radar, rays)
+    rc, _, _, lab = run(radar, rays, rs.SIM_PREC_FP32_DIRECT,
+                        outputs=rs.SIM_OUT_SPECTRUM | rs.SIM_OUT_LABELS)
+    assert rc == rs.SIM_OK
+    assert np.array_equal(lab, ref)
+    # the cells really do straddle edges: both sides occur among the nudged rays
+    b = oracle.bins(radar, rays)
+    assert np.any(np.abs(b["x_r"] - np.round(b["x_r"] - 0.5) - 0.5) < 1e-12)
+
+
+def test_invalid_rays_rejected():
+    radar, rays = scenegen.tiny_scene(seed=1, n_rays=50)
+    bad = rays.take(slice(None))
+    bad.range_rt_m = bad.range_rt_m.copy()
+    bad.range_rt_m[7] = np.nan
+    ctx = rs.Context(radar)
+    try:
+        with pytest.raises(rs.SimError) as e:  # host arrays: rejected at submit
+            ctx.submit(bad.arrays(), bad.n)
+        assert e.value.code == rs.SIM_E_INVALID
+        arr = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in bad.arrays().items()}
+        t = ctx.submit(arr, bad.n)  # device arrays: the prep kernel flags them
+        assert ctx.fetch(t) == rs.SIM_E_INVALID
+        with pytest.raises(rs.SimError):
+            ctx.submit(rays.arrays(), (1 << 21) + 1)
+        neg = rays.take(slice(None))
+        neg.object_id = neg.object_id.copy()
+        neg.object_id[0] = -4
+        with pytest.raises(rs.SimError):
+            ctx.submit(neg.arrays(), neg.n)
+    finally:
+        ctx.close()
+
+
+def test_unknown_ticket_and_poll():
+    radar, rays = scenegen.automotive_scene(seed=5, n_rays=20000)
+    ctx = rs.Context(radar)
+    try:
+        assert ctx.fetch(123456789) == rs.SIM_E_UNKNOWN_TICKET
+        t = ctx.submit(rays.arrays(), rays.n)
+        rc = ctx.fetch(t, timeout_ms=0)
+        assert rc in (rs.SIM_E_NOT_READY, rs.SIM_OK)
+        if rc != rs.SIM_OK:
+            assert ctx.fetch(t, timeout_ms=-1) == rs.SIM_OK
+        assert ctx.fetch(t) == rs.SIM_E_UNKNOWN_TICKET
+    finally:
+        ctx.close()
+
+
+def test_linearity_on_gpu():
+    """Eq. 5: the cube of A and B together equals the sum of their cubes."""
+    radar = scenegen.radar_tiny()
+    A = scenegen.uniform_rays(seed=31, n=600)
+    B = scenegen.uniform_rays(seed=32, n=400)
+    _, sA, _, _ = run(radar, A)
+    _, sB, _, _ = run(radar, B)
+    _, sAB, _, _ = run(radar, Rays.concat([A, B]))
+    assert rel_max(sAB, sA + sB) <= 1e-5
