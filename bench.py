@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark: FMCW ray sum -> windowed range-Doppler-angle FFT -> labels on the GPU.
+
+One step = one automotive frame (3x4 TDM-MIMO = 12 virtual channels, 256 chirps x
+512 samples, 200,000 seeded synthetic rays in 20 object clusters plus 10 % clutter)
+through the whole path of the C ABI: ingest copy, per-ray FP64 prep, ray sum,
+three FFTs, labels, and the copy of signal, spectrum and labels into caller
+buffers.  The metric is ray x sample contributions per second,
+R * N_v * N_c * N_s per frame over the frame's device time (CUDA events recorded
+by the library on the stream the frame runs on).  The L2 cache is flushed (a
+256 MB write) before every timed step.
+
+`e2e` repeats the steps through the same calls with pinned HOST input and output
+buffers, timed on the host around submit + fetch (host-to-device and
+device-to-host copies included).
+
+`--impl reference` times the FP64 CPU oracle (the correctness reference) on the
+host cores, on a bounded sample of the same frame's output points.
+
+Multi-GPU: independent frames per rank (replicas, no collective); the value is
+the contributions of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import scenegen  # noqa: E402
+
+METRIC = "ray-sample contributions/s"
+UNIT = "contributions/s"
+WORKLOAD = "automotive frame: 12 virtual ch x 256 chirps x 512 samples, N_a 16, 200k rays"
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, gpu: int, path: str):
+        self.path = path
+        self.proc = None
+        self.gpu = gpu
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(radar, rays, seconds: float = 10.0, seed: int = 17):
+    """Contributions/s of the FP64 oracle's ray sum, on as many sampled output points of the
+    frame as fill about `seconds` of wall time on the host cores."""
+    import oracle
+    n_out = radar.n_virtual * radar.n_chirps * radar.n_samples
+    probe = scenegen.randint(seed, 1, 64, 0, n_out - 1).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.signal_at(radar, rays, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n_pts = int(max(64, min(n_out, 64 * seconds / dt)))
+    idx = scenegen.randint(seed, 2, n_pts, 0, n_out - 1).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.signal_at(radar, rays, idx)
+    dt = time.perf_counter() - t0
+    rate = n_pts * rays.n / dt
+    return rate, n_pts, dt, oracle.threads()
+
+
+def run_reference(args, world, rank):
+    """The oracle arm: each step is the FP64 ray sum at a bounded sample of output points."""
+    if rank != 0:
+        return 0
+    import oracle
+    radar, rays = scenegen.automotive_scene(seed=1000)
+    n_out = radar.n_virtual * radar.n_chirps * radar.n_samples
+    per_step = max(16, int(args.ref_points))
+    rates, times = [], []
+    for s in range(args.warmup + args.steps):
+        idx = scenegen.randint(2000 + s, 3, per_step, 0, n_out - 1).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.signal_at(radar, rays, idx)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+            rates.append(per_step * rays.n / dt)
+    value = per_step * rays.n * len(times) / sum(times)
+    cores = oracle.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "rays": rays.n, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} output points x {rays.n} rays per step (FP64 direct sum)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16_split",
+                    choices=["fp32", "bf16", "bf16_split", "fp16", "fp16_split"])
+    ap.add_argument("--rays", type=int, default=200_000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-points", type=int, default=2048)
+    ap.add_argument("--clocks-csv", default=os.path.join(ROOT, "gpurun_out", "bench_clocks.csv"))
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2305_14176_gb300 import radarsim as rs
+
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    radar, rays = scenegen.automotive_scene(seed=1000 + rank, n_rays=args.rays)
+    prec = rs.PRECISION_NAMES[args.precision]
+    ctx = rs.Context(radar, precision=prec)
+    n = rays.n
+    contrib = n * radar.n_virtual * radar.n_chirps * radar.n_samples
+    arrays = rays.arrays()
+    dev_in = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in arrays.items()}
+    host_in = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in arrays.items()}
+    spec = torch.empty(ctx.cube_shape + (2,), dtype=torch.float32, device=dev)
+    sig = torch.empty(ctx.signal_shape + (2,), dtype=torch.float32, device=dev)
+    lab = torch.empty(ctx.cube_shape, dtype=torch.int32, device=dev)
+    h_spec = torch.empty(spec.shape, dtype=torch.float32).pin_memory()
+    h_sig = torch.empty(sig.shape, dtype=torch.float32).pin_memory()
+    h_lab = torch.empty(lab.shape, dtype=torch.int32).pin_memory()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(inputs, outs):
+        t = ctx.submit(inputs, n)
+        rc = ctx.fetch(t, *outs)
+        if rc != rs.SIM_OK:
+            raise rs.SimError(rc, "sim_fetch")
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        torch.cuda.synchronize()
+        step(dev_in, (spec, sig, lab))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    totals, mains, kernels = [], [], 0
+    stages_sum = {}
+    with ClockSampler(local, args.clocks_csv) as clk:
+        wall0 = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            step(dev_in, (spec, sig, lab))
+            st = rs.sim_last_stage_ms(ctx.ctx)
+            totals.append(st["total"])
+            mains.append(st["ray_sum"])
+            for k, v in st.items():
+                stages_sum[k] = stages_sum.get(k, 0.0) + v
+            kernels += rs.sim_last_kernel_count(ctx.ctx)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    dev_s = sum(totals) / 1e3
+    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev_s_max = float(t.item())
+    value = contrib * args.steps * world / dev_s_max
+
+    # end to end through the same calls with pinned host buffers
+    e2e_times = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(host_in, (h_spec, h_sig, h_lab))
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            e2e_times.append(dt)
+    e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = contrib * args.steps * world / float(e2e_s.item())
+    h2d = sum(int(v.numel() * v.element_size()) for v in host_in.values())
+    d2h = sum(int(v.numel() * v.element_size()) for v in (h_spec, h_sig, h_lab))
+
+    peaks, peak_src = _peaks()
+    main_s = statistics.mean(mains) / 1e3
+    flops = 8.0 * contrib
+    split = args.precision.endswith("_split")
+    tensor_path = args.precision != "fp32"
+    if tensor_path:
+        achieved = flops / main_s / 1e12
+        peak = float(peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "umma_sum_kernel", "peak_source": f"{peak_src} bf16 dense burst",
+                "executed_tflops": achieved * (3 if split else 1),
+                "executed_frac": achieved * (3 if split else 1) / peak}
+    else:
+        roof = {"bound": "alu", "achieved": contrib / main_s / 1e12, "peak": None, "unit": "Tcontrib/s",
+                "frac": None, "traffic": None, "kernel": "direct_sum_kernel"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, pts, secs, cores = cpu_oracle_rate(radar, rays, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{pts} of {radar.n_virtual * radar.n_chirps * radar.n_samples} output points x "
+                         f"{n} rays, FP64 direct sum, {secs:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dev_s_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32"}.get(args.precision, args.precision),
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays": n, "n_virtual": radar.n_virtual, "n_chirps": radar.n_chirps,
+                   "n_samples": radar.n_samples, "n_angle": radar.n_angle, "precision": args.precision,
+                   "outputs": "signal+spectrum+labels", "l2": "flushed (256 MB write) before each step",
+                   "parallelism": f"replicas x{world}"},
+        "frames_per_s": args.steps * world / dev_s_max,
+        "stage_ms_mean": {k: v / args.steps for k, v in stages_sum.items()},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": 1e3 * float(e2e_s.item()) / args.steps},
+        "gpu_launches": kernels,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+        "wall_s_timed": wall,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -164,13 +164,24 @@ SIM_API const char *sim_status_string(int status);
 SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int32_t max_queue);
 
 /* Per-stage device time in milliseconds of the most recently fetched ticket of
-   this context: [0] ingest copies, [1] per-ray prep, [2] ray sum, [3] FFTs,
-   [4] labels, [5] whole device pipeline; n is the array length (<= 8).  Stage
-   timing is on by default; entries for stages that did not run are 0. */
+   this context, from CUDA events on the stream the scene ran on: [0] ingest
+   copies, [1] per-ray prep, [2] ray-sum main kernel, [3] ray-sum split reduction,
+   [4] FFTs, [5] labels, [6] whole device pipeline; n is the array length (<= 8).
+   Entries for stages that did not run are 0. */
 SIM_API int sim_last_stage_ms(sim_ctx *ctx, float *ms, int32_t n);
 
 /* Number of kernels the most recently fetched ticket of this context launched. */
 SIM_API int sim_last_kernel_count(sim_ctx *ctx, int32_t *count);
+
+/* Self-test of the tensor-core tile path on caller data (not a simulation call):
+   D[M][N] = A[M][K] * B[N][K]^T with A, B row-major 16-bit (f16 != 0: FP16, else
+   BF16) device matrices and D row-major FP32 device memory, through the same shared
+   memory layout, descriptors and tcgen05 pipeline the ray sum uses.  N a multiple of
+   16 in 32 .. 512 (a multiple of 256 above 256), K even, M >= 1.  stream is a
+   cudaStream_t (NULL = default stream); the call synchronizes it.
+   Errors: SIM_E_INVALID, SIM_E_NOMEM, SIM_E_CUDA, SIM_E_DEVICE (a pipeline wait ran out). */
+SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
+                              float *d, void *stream);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,7 @@ using namespace rs;
 
 namespace {
 
-constexpr int kNumEvents = 6;  // start, ingest, prep, ray sum, fft, labels/end
+constexpr int kNumEvents = 7;  // start, ingest, prep, ray-sum main kernel, ray sum done, fft, labels/end
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -40,7 +40,7 @@ struct Slot {
 
 struct Plan {  // byte offsets of one scene's buffers inside its device block
   size_t d, a, v, az, el, p0, obj;
-  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy;
+  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy, step_d, step_r;
   size_t status;
   size_t sig, tmp, spec, labels;
   size_t pk, pe, ck, cm, co;
@@ -124,6 +124,8 @@ Plan make_plan(const Derived &g, int64_t n, bool has_obj) {
   p.amp = take(4 * un);
   p.cell = take(4 * un);
   p.energy = take(8 * un);
+  p.step_d = take(8 * un);
+  p.step_r = take(8 * un);
   p.status = take(256);
   p.sig = take(8 * static_cast<size_t>(g.n_sig));
   const bool spec = g.outputs & SIM_OUT_SPECTRUM;
@@ -196,26 +198,31 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
   RaysPrep rp{reinterpret_cast<uint64_t *>(b + p.carrier), reinterpret_cast<uint64_t *>(b + p.nu_r),
               reinterpret_cast<uint64_t *>(b + p.nu_d), reinterpret_cast<uint64_t *>(b + p.nu_a),
               reinterpret_cast<float *>(b + p.amp), reinterpret_cast<int32_t *>(b + p.cell),
-              reinterpret_cast<uint64_t *>(b + p.energy)};
+              reinterpret_cast<uint64_t *>(b + p.energy), reinterpret_cast<float2 *>(b + p.step_d),
+              reinterpret_cast<float2 *>(b + p.step_r)};
   uint32_t *status = reinterpret_cast<uint32_t *>(b + p.status);
   float2 *sig = reinterpret_cast<float2 *>(b + p.sig);
   int kernels = 0;
   kernels += launch_prep(g, in, j->n, rp, status, s);
   cudaEventRecord(sl.ev[2], s);
-  if (g.precision == SIM_PREC_FP32_DIRECT) kernels += launch_direct_sum(g, rp, j->n, sig, s);
-  else kernels += launch_umma_sum(g, rp, j->n, sig, b + p.ws, status, s);
-  cudaEventRecord(sl.ev[3], s);
+  if (g.precision == SIM_PREC_FP32_DIRECT) {
+    kernels += launch_direct_sum(g, rp, j->n, sig, s);
+    cudaEventRecord(sl.ev[3], s);
+  } else {
+    kernels += launch_umma_sum(g, rp, j->n, sig, b + p.ws, status, s, sl.ev[3]);
+  }
+  cudaEventRecord(sl.ev[4], s);
   if (g.outputs & SIM_OUT_SPECTRUM)
     kernels += launch_fft(g, j->ctx->t, sig, reinterpret_cast<float2 *>(b + p.tmp),
                           reinterpret_cast<float2 *>(b + p.spec), s);
-  cudaEventRecord(sl.ev[4], s);
+  cudaEventRecord(sl.ev[5], s);
   if (g.outputs & SIM_OUT_LABELS) {
     LabelScratch sc{reinterpret_cast<uint64_t *>(b + p.pk), reinterpret_cast<uint64_t *>(b + p.pe),
                     reinterpret_cast<uint32_t *>(b + p.ck), reinterpret_cast<uint64_t *>(b + p.cm),
                     reinterpret_cast<uint32_t *>(b + p.co), p.cap};
     kernels += launch_labels(g, rp, in.obj, j->n, sc, reinterpret_cast<int32_t *>(b + p.labels), status, s);
   }
-  cudaEventRecord(sl.ev[5], s);
+  cudaEventRecord(sl.ev[6], s);
   j->kernels = kernels;
   if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
   return SIM_OK;

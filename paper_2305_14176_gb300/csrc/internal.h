@@ -49,6 +49,8 @@ struct RaysPrep {
   float *amp;         // amplitude (0 for an invalid ray)
   int32_t *cell;      // flat label cell, -1 for an invalid ray
   uint64_t *energy;   // min(rint(a^2 2^32), 2^41)
+  float2 *step_d;     // e^{2 pi j 8 nu_d}: phasor step over eight chirps (FP64-accurate)
+  float2 *step_r;     // e^{2 pi j 8 nu_r}: phasor step over eight samples
 };
 
 // Scratch for the label kernels: two open-addressing hash tables
@@ -78,7 +80,9 @@ int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, L
 
 // tensor-core ray sum: workspace bytes it needs and its launcher
 int64_t umma_workspace_bytes(const Derived &g, int64_t n);
+// `after_main` (may be null) is recorded on `s` right after the GEMM kernel, before the
+// split reduction, so the GEMM can be timed on its own stream.
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace,
-                    uint32_t *status, cudaStream_t s);
+                    uint32_t *status, cudaStream_t s, cudaEvent_t after_main);
 
 }  // namespace rs

@@ -67,6 +67,14 @@ __device__ __forceinline__ uint64_t frac_q64(double x) {
   return __double2ull_rn(__dmul_rn(f, kTwo64));
 }
 
+// e^{2 pi j 8 q} for a Q0.64 phase increment q, from the exact Q0.64 product in FP64
+__device__ __forceinline__ float2 step8(uint64_t q) {
+  const double f = static_cast<double>(static_cast<int64_t>(q * 8ull)) * 0x1p-64;  // cycles in [-1/2, 1/2)
+  double s, c;
+  sincospi(2.0 * f, &s, &c);
+  return make_float2(static_cast<float>(c), static_cast<float>(s));
+}
+
 __device__ __forceinline__ int64_t bin_of(double x, int64_t n) {
   int64_t q = static_cast<int64_t>(floor(__dadd_rn(x, 0.5)));
   q %= n;
@@ -96,6 +104,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
     atomicOr(status, kStatusBadRay);
     out.carrier[i] = 0; out.nu_r[i] = 0; out.nu_d[i] = 0; out.nu_a[i] = 0;
     out.amp[i] = 0.0f; out.cell[i] = -1; out.energy[i] = 0;
+    out.step_d[i] = make_float2(1.f, 0.f); out.step_r[i] = make_float2(1.f, 0.f);
     return;
   }
   const double vd = static_cast<double>(v);
@@ -105,8 +114,12 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   const double x_a = __dmul_rn(k.ka, __dmul_rn(sin_or_cos(static_cast<double>(az), false),
                                                sin_or_cos(static_cast<double>(el), true)));
   // phase increments per sample / chirp / channel: x_x / N_x (exact scaling by a power of two)
-  out.nu_r[i] = frac_q64(__dmul_rn(x_r, k.inv_ns));
-  out.nu_d[i] = frac_q64(__dmul_rn(x_d, k.inv_nc));
+  const uint64_t nu_r = frac_q64(__dmul_rn(x_r, k.inv_ns));
+  const uint64_t nu_d = frac_q64(__dmul_rn(x_d, k.inv_nc));
+  out.nu_r[i] = nu_r;
+  out.nu_d[i] = nu_d;
+  out.step_r[i] = step8(nu_r);
+  out.step_d[i] = step8(nu_d);
   out.nu_a[i] = frac_q64(__dmul_rn(x_a, k.inv_na));
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
   out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +

@@ -1,13 +1,661 @@
-// K_b1: tensor-core ray sum (placeholder until the tcgen05 kernel lands).
+// K_b1: the ray sum as a tensor-core GEMM (arXiv 2305.14176, Sec. II-A, Eq. 2).
+//
+// With the separable phase, the beat cube is a complex product over rays:
+//   S[row, n] = sum_i A[row, i] B[i, n],   row = (k, m) = k N_c + m
+//   A[row, i] = a_i exp(2 pi j (carrier_i + k nu_a,i + m nu_d,i))
+//   B[i, n]   = exp(2 pi j n nu_r,i)
+// made real as D[M, 2 N_s] = A'[M, 2R] B'[2R, 2 N_s] with
+//   A'[row, 2i] = Re A, A'[row, 2i+1] = Im A,
+//   B' (stored K-major, one row per output column):
+//     column 2n   : ( Re B, -Im B)   -> D[row, 2n]   = Re S
+//     column 2n+1 : ( Im B,  Re B)   -> D[row, 2n+1] = Im S
+// so the accumulator columns come out as interleaved complex64.
+//
+// Operands are never stored in HBM: producer warps synthesise A' and B' tiles for a
+// stage of rays straight into shared memory (Q0.64 phases from the prep kernel, one FP32
+// sin/cos each, rounded to BF16 or FP16, optionally split into hi + lo), and one thread
+// issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory).  Split precision
+// accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi into the same accumulator.
+//
+// Work is split over rays (split-K): each CTA sums one chunk of rays for one 128-row x
+// BN-column tile and writes an FP32 partial; a second kernel adds the partials in chunk
+// order.  The decomposition depends only on the scene's own shape, so a scene gives the
+// same bits alone or beside others.
+//
+// Every mbarrier wait is bounded; a wait that runs out sets a status bit, the CTA stops
+// issuing work, drains what it issued, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace rs {
+namespace {
 
-int64_t umma_workspace_bytes(const Derived &, int64_t) { return 0; }
+constexpr int BM = 128;          // tile rows (TMEM lanes)
+constexpr int KS = 32;           // rays per pipeline stage (K = 2 KS real elements)
+constexpr int KELEM = 2 * KS;    // K elements per stage
+constexpr int NPROD = 256;       // producer threads (warps 0..7); warps 0..3 also drain TMEM
+constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s: far above any legitimate wait
 
-int launch_umma_sum(const Derived &, RaysPrep, int64_t, float2 *, void *, uint32_t *status, cudaStream_t s) {
-  cudaMemsetAsync(status, 0xff, 4, s);
-  return 0;
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false if the barrier phase has not completed after kWaitLimitNs
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if ((i & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+// 32 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor, kind::f16: D FP32, A/B BF16 (or FP16), both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc(bool f16, int m, int n) {
+  return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
+         (static_cast<uint32_t>(n >> 3) << 17) | (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, no swizzle: core matrices of 8 rows x 16 bytes,
+// `lbo` bytes between core matrices along K, `sbo` bytes between 8-row groups.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+         (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// ------------------------------------------------------------------ operand packing
+template <bool F16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (F16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+  } else {
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&b);
+  }
+}
+template <bool F16>
+__device__ __forceinline__ float2 unpack2(uint32_t v) {
+  if constexpr (F16) {
+    __half2 h = *reinterpret_cast<__half2 *>(&v);
+    return __half22float2(h);
+  } else {
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162 *>(&v);
+    return __bfloat1622float2(b);
+  }
+}
+// x = hi + lo with hi the rounded value and lo the rounded remainder
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void encode(float x, float y, uint32_t &hi, uint32_t &lo) {
+  hi = pack2<F16>(x, y);
+  if constexpr (SPLIT) {
+    const float2 h = unpack2<F16>(hi);
+    lo = pack2<F16>(x - h.x, y - h.y);
+  } else {
+    lo = 0;
+  }
+}
+
+__device__ __forceinline__ float q64_to_rad(uint64_t p) {
+  return static_cast<float>(static_cast<int32_t>(p >> 32)) * 1.46291807926715968e-09f;  // 2 pi / 2^32
+}
+
+// ------------------------------------------------------------------ kernel
+constexpr int NDRAIN = 128;            // drain threads (warps 9..12): one TMEM lane each
+constexpr int MMA_WARP = NPROD / 32;   // warp 8
+constexpr int NTHREADS_ALL = NPROD + 32 + NDRAIN;
+constexpr int SUBST = 32;              // stages (of KS rays) per tensor-memory accumulation
+constexpr uint32_t kLoCol = 256;       // TMEM column of the lo-part accumulator
+
+struct Args {
+  RaysPrep p;
+  int64_t n_rays;
+  int64_t chunk;       // rays per split (multiple of KS)
+  int nc, ns, m_rows;  // N_c, N_s, M = N_v N_c
+  int bn;              // MMA N (real columns per tile) = min(256, 2 N_s)
+  float *partials;     // [splits][M][2 N_s]
+  const uint32_t *amax_bits;  // scene amplitude maximum (FP16 scaling), may be null
+  uint32_t *status;
+  // self-test mode: operands copied from row-major global matrices instead of synthesised
+  const uint16_t *test_a;  // [M][K] 16-bit
+  const uint16_t *test_b;  // [2 N_s][K] 16-bit
+  int64_t test_k;
+};
+
+template <bool F16>
+__device__ __forceinline__ float amp_scale(const uint32_t *amax_bits) {
+  if constexpr (F16) {
+    // power-of-two scale putting the largest amplitude in [2^13, 2^14)
+    const float amax = __uint_as_float(*amax_bits);
+    if (!(amax > 0.f)) return 1.f;
+    int e;
+    frexpf(amax, &e);  // amax = f 2^e, f in [0.5, 1)
+    return ldexpf(1.f, 14 - e);
+  } else {
+    return 1.f;
+  }
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ void sts32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+
+// Synthesise one stage of operands.  Thread t owns ray i = t / 8 of the stage and
+// phase lane j = t % 8: A rows j, j + 8, ..., and B complex columns j, j + 8, ...; along
+// each it steps the phasor by the FP64-accurate e^{2 pi j 8 nu} of the prep kernel, so a
+// stage costs two hardware sin/cos per thread plus one complex multiply per element.
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void produce_stage(const Args &g, uint8_t *a_hi, uint8_t *b_hi, uint8_t *a_lo,
+                                              uint8_t *b_lo, int64_t ray0, int64_t k_hi, int row0, int col0,
+                                              float scale) {
+  const int t = threadIdx.x;
+  const int i = t >> 3, j = t & 7;
+  const int64_t ray = ray0 + i;
+  const bool valid = ray < k_hi;
+  const int bn = g.bn;
+  const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
+  // ---- A: rows r = j + 8 l
+  {
+    uint32_t off = (i >> 2) * lbo_a + j * 16 + (i & 3) * 4;
+    float2 z = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
+    uint64_t car = 0, nua = 0, nud = 0;
+    float am = 0.f;
+    int grow = row0 + j;
+    int kq = grow / g.nc, mq = grow - kq * g.nc;
+    if (valid) {
+      car = g.p.carrier[ray];
+      nua = g.p.nu_a[ray];
+      nud = g.p.nu_d[ray];
+      am = g.p.amp[ray] * scale;
+      w = g.p.step_d[ray];
+    }
+    bool restart = true;
+#pragma unroll 4
+    for (int l = 0; l < BM / 8; ++l) {
+      if (restart) {
+        // start (or restart in a new channel) from the exact Q0.64 phase of row (kq, mq)
+        float sn, cs;
+        __sincosf(q64_to_rad(car + static_cast<uint64_t>(kq) * nua + static_cast<uint64_t>(mq) * nud), &sn, &cs);
+        z = make_float2(am * cs, am * sn);
+      } else {
+        z = cmulf(z, w);  // eight chirps on in the same channel
+      }
+      const float2 v = (valid && grow < g.m_rows) ? z : make_float2(0.f, 0.f);
+      uint32_t hi, lo;
+      encode<F16, SPLIT>(v.x, v.y, hi, lo);
+      sts32(a_hi + off, hi);
+      if constexpr (SPLIT) sts32(a_lo + off, lo);
+      off += 128;
+      grow += 8;
+      mq += 8;
+      restart = false;
+      if (mq >= g.nc) {
+        kq = grow / g.nc;
+        mq = grow - kq * g.nc;
+        restart = true;
+      }
+    }
+  }
+  // ---- B: complex columns nl = j + 8 l, real rows 2 nl and 2 nl + 1
+  {
+    const int nb = bn / 16;  // columns per thread
+    uint32_t off = (i >> 2) * lbo_b + (j >> 2) * 128 + (j & 3) * 32 + (i & 3) * 4;
+    const bool swap = (j >> 2) != 0;  // half the warp writes its odd row first: no bank conflicts
+    float2 z = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
+    if (valid) {
+      float sn, cs;
+      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * g.p.nu_r[ray]), &sn, &cs);
+      z = make_float2(cs, sn);
+      w = g.p.step_r[ray];
+    }
+    for (int l = 0; l < nb; ++l) {
+      if (l > 0) z = cmulf(z, w);
+      uint32_t h0, l0, h1, l1;
+      encode<F16, SPLIT>(z.x, -z.y, h0, l0);  // row 2n:   ( Re B, -Im B)
+      encode<F16, SPLIT>(z.y, z.x, h1, l1);   // row 2n+1: ( Im B,  Re B)
+      const uint32_t o0 = swap ? off + 16 : off, o1 = swap ? off : off + 16;
+      sts32(b_hi + o0, swap ? h1 : h0);
+      sts32(b_hi + o1, swap ? h0 : h1);
+      if constexpr (SPLIT) {
+        sts32(b_lo + o0, swap ? l1 : l0);
+        sts32(b_lo + o1, swap ? l0 : l1);
+      }
+      off += 256;
+    }
+  }
+}
+
+// Copy one stage of operands from row-major 16-bit matrices (self-test).
+__device__ __forceinline__ void copy_stage(const Args &g, uint8_t *a_hi, uint8_t *b_hi, int64_t ray0, int row0,
+                                           int col0) {
+  const int bn = g.bn;
+  const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
+  for (int item = threadIdx.x; item < BM * (KELEM / 8); item += NPROD) {
+    const int r = item % BM, kc = item / BM;
+    const int grow = row0 + r;
+    uint32_t v[4];
+    for (int q = 0; q < 4; ++q) {
+      const int64_t kk = 2 * ray0 + kc * 8 + 2 * q;
+      v[q] = 0;
+      if (grow < g.m_rows && kk < g.test_k) {
+        const uint16_t *src = g.test_a + static_cast<int64_t>(grow) * g.test_k + kk;
+        v[q] = static_cast<uint32_t>(src[0]) | (static_cast<uint32_t>(src[1]) << 16);
+      }
+    }
+    *reinterpret_cast<uint4 *>(a_hi + kc * lbo_a + r * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+  for (int item = threadIdx.x; item < bn * (KELEM / 8); item += NPROD) {
+    const int r = item % bn, kc = item / bn;
+    const int gcol = col0 + r;
+    uint32_t v[4];
+    for (int q = 0; q < 4; ++q) {
+      const int64_t kk = 2 * ray0 + kc * 8 + 2 * q;
+      v[q] = 0;
+      if (kk < g.test_k) {
+        const uint16_t *src = g.test_b + static_cast<int64_t>(gcol) * g.test_k + kk;
+        v[q] = static_cast<uint32_t>(src[0]) | (static_cast<uint32_t>(src[1]) << 16);
+      }
+    }
+    *reinterpret_cast<uint4 *>(b_hi + kc * lbo_b + r * 16) = make_uint4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <bool F16, bool SPLIT, bool TEST>
+__global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int NST = SPLIT ? 2 : 4;
+  constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+  const int bn = g.bn;
+  const uint32_t a_bytes = BM * KELEM * 2;
+  const uint32_t b_bytes = static_cast<uint32_t>(bn) * KELEM * 2;
+  const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
+  uint8_t *base = smem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
+  // barriers: full[NST], empty[NST], acc_full, acc_empty, mma_done
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * NST + 3);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NST);
+  const uint32_t accf = smem_u32(bars + 2 * NST), acce = smem_u32(bars + 2 * NST + 1);
+  const uint32_t done = smem_u32(bars + 2 * NST + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tile_m = blockIdx.x, tile_n = blockIdx.y, split = blockIdx.z;
+  const int row0 = tile_m * BM;
+  const int col0 = tile_n * bn;  // real column; complex n0 = col0 / 2
+  const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
+  const int64_t k_total = TEST ? g.test_k / 2 : g.n_rays;  // rays (K pairs)
+  const int64_t k_hi = k_lo + g.chunk < k_total ? k_lo + g.chunk : k_total;
+  const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
+  const int n_sub = (n_stages + SUBST - 1) / SUBST;
+  const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(full0 + 8 * s, NPROD);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, NDRAIN);
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) tmem_alloc(smem_u32(tmem_holder), TMEM_COLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+  bool failed = false;
+
+  if (warp < MMA_WARP) {
+    // ---------------- producers
+    const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
+    for (int st = 0; st < n_stages; ++st) {
+      const int s = st % NST;
+      if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
+        failed = true;
+        break;
+      }
+      uint8_t *a_hi = base + s * stage_bytes;
+      uint8_t *b_hi = a_hi + a_bytes;
+      uint8_t *a_lo = b_hi + b_bytes;
+      uint8_t *b_lo = a_lo + a_bytes;
+      const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
+      if constexpr (TEST) copy_stage(g, a_hi, b_hi, ray0, row0, col0);
+      else produce_stage<F16, SPLIT>(g, a_hi, b_hi, a_lo, b_lo, ray0, k_hi, row0, col0, scale);
+      fence_proxy_async();
+      mbar_arrive(full0 + 8 * s);
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = make_idesc(F16, BM, bn);
+      const uint32_t sbase = smem_u32(base);
+      bool open = false;  // issued MMAs not yet committed to acc_full
+      for (int st = 0; st < n_stages; ++st) {
+        const int s = st % NST;
+        const int sub = st / SUBST;
+        const bool first = (st % SUBST) == 0;
+        if (first && sub > 0 && !mbar_wait(acce, (sub - 1) & 1)) {
+          failed = true;
+          break;
+        }
+        if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_hi = sbase + s * stage_bytes, b_hi = a_hi + a_bytes;
+        const uint32_t a_lo = b_hi + b_bytes, b_lo = a_lo + a_bytes;
+#pragma unroll
+        for (int kk = 0; kk < KELEM / 16; ++kk) {
+          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+          const uint64_t da = make_sdesc(a_hi + kk * 2 * lbo_a, lbo_a, 128);
+          const uint64_t db = make_sdesc(b_hi + kk * 2 * lbo_b, lbo_b, 128);
+          mma_f16(tmem, da, db, idesc, acc);
+          if constexpr (SPLIT) {
+            mma_f16(tmem + kLoCol, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, acc);
+            mma_f16(tmem + kLoCol, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
+          }
+        }
+        open = true;
+        mma_commit(empty0 + 8 * s);
+        if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
+          mma_commit(accf);
+          open = false;
+        }
+      }
+      if (open) mma_commit(accf);
+      // every issued MMA has completed once `done` fires
+      mma_commit(done);
+      if (!mbar_wait(done, 0)) failed = true;
+    }
+  } else {
+    // ---------------- drain: TMEM lane quarter (warp % 4), FP32 sums into the split's partial
+    const int q = warp & 3;
+    const int grow = row0 + q * 32 + lane;
+    float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    if (n_stages == 0 && grow < g.m_rows) {
+      for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int sub = 0; sub < n_sub; ++sub) {
+      if (!mbar_wait(accf, sub & 1)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      for (int c = 0; c < bn; c += 32) {
+        uint32_t h[32];
+        tmem_ld32(trow + static_cast<uint32_t>(c), h);
+        if constexpr (SPLIT) {
+          uint32_t l[32];
+          tmem_ld32(trow + kLoCol + static_cast<uint32_t>(c), l);
+#pragma unroll
+          for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(l[x]));
+        }
+        if (grow < g.m_rows) {
+#pragma unroll
+          for (int x = 0; x < 32; x += 4) {
+            float4 v = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
+                                   __uint_as_float(h[x + 3]));
+            float4 *d4 = reinterpret_cast<float4 *>(dst + c + x);
+            if (sub > 0) {
+              const float4 o = *d4;
+              v.x += o.x;
+              v.y += o.y;
+              v.z += o.z;
+              v.w += o.w;
+            }
+            *d4 = v;
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acce);
+    }
+  }
+  if (failed) atomicOr(g.status, kStatusWaitLimit);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// sum the split partials in split order: sig[row][n] = sum_s (D_s[row][2n], D_s[row][2n+1]) / scale
+template <bool F16>
+__global__ void reduce_partials(const float *__restrict__ part, int splits, int64_t n_c, float2 *__restrict__ sig,
+                                const uint32_t *amax_bits) {
+  const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_c;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float2 *p = reinterpret_cast<const float2 *>(part) + i;
+    float2 acc = p[0];
+    for (int s = 1; s < splits; ++s) {
+      const float2 v = p[static_cast<int64_t>(s) * n_c];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    sig[i] = make_float2(acc.x * inv, acc.y * inv);
+  }
+}
+
+__global__ void amax_kernel(const float *__restrict__ amp, int64_t n, uint32_t *amax_bits) {
+  uint32_t m = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    m = max(m, __float_as_uint(amp[i]));  // amplitudes are >= 0: bit order is value order
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, m);
+}
+
+int g_num_sms = 0;
+
+struct Shape {
+  int mt, nt, splits, bn;
+  int64_t chunk;
+};
+
+Shape plan_shape(const Derived &g, int64_t n) {
+  Shape s;
+  const int M = g.nv * g.nc;
+  s.bn = 2 * g.ns < 256 ? 2 * g.ns : 256;
+  s.mt = (M + BM - 1) / BM;
+  s.nt = 2 * g.ns / s.bn;
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
+      g_num_sms = 148;
+  }
+  const int64_t tiles = static_cast<int64_t>(s.mt) * s.nt;
+  int64_t splits = (4 * g_num_sms + tiles - 1) / tiles;  // about four waves of CTAs
+  const int64_t max_splits = (n + KS - 1) / KS;
+  if (splits > max_splits) splits = max_splits;
+  if (splits < 1) splits = 1;
+  if (splits > 65535) splits = 65535;
+  int64_t chunk = (n + splits - 1) / splits;
+  chunk = (chunk + KS - 1) / KS * KS;
+  if (chunk < KS) chunk = KS;
+  s.chunk = chunk;
+  s.splits = static_cast<int>((n + chunk - 1) / chunk);
+  if (s.splits < 1) s.splits = 1;
+  return s;
+}
+
+size_t smem_bytes(bool split, int bn) {
+  const int nst = split ? 2 : 4;
+  const size_t stage = static_cast<size_t>(BM * KELEM * 2 + bn * KELEM * 2) * (split ? 2 : 1);
+  return nst * stage + 8 * (2 * nst + 3) + 16;
+}
+
+constexpr int kMaxDynSmem = 232448;  // 227 KB
+
+template <bool F16, bool SPLIT, bool TEST>
+void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
+  // the self-test reserves the whole shared memory so that every descriptor it builds
+  // points inside the allocation
+  const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256)));
+    attr = true;
+  }
+  dim3 grid(sh.mt, sh.nt, sh.splits);
+  umma_sum_kernel<F16, SPLIT, TEST><<<grid, NTHREADS_ALL, sm, s>>>(a);
+}
+
+}  // namespace
+
+int64_t umma_workspace_bytes(const Derived &g, int64_t n) {
+  const Shape sh = plan_shape(g, n);
+  return 256 + static_cast<int64_t>(sh.splits) * g.nv * g.nc * 2 * g.ns * 4;
+}
+
+int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                    cudaStream_t s, cudaEvent_t after_main) {
+  const Shape sh = plan_shape(g, n);
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  int kernels = 0;
+  cudaMemsetAsync(amax, 0, 4, s);
+  if (f16 && n > 0) {
+    amax_kernel<<<g_num_sms > 0 ? 2 * g_num_sms : 296, 256, 0, s>>>(p.amp, n, amax);
+    ++kernels;
+  }
+  Args a{};
+  a.p = p;
+  a.n_rays = n;
+  a.chunk = sh.chunk;
+  a.nc = g.nc;
+  a.ns = g.ns;
+  a.m_rows = g.nv * g.nc;
+  a.bn = sh.bn;
+  a.partials = partials;
+  a.amax_bits = amax;
+  a.status = status;
+  if (f16) {
+    if (split) launch_gemm<true, true, false>(sh, a, s);
+    else launch_gemm<true, false, false>(sh, a, s);
+  } else {
+    if (split) launch_gemm<false, true, false>(sh, a, s);
+    else launch_gemm<false, false, false>(sh, a, s);
+  }
+  ++kernels;
+  if (after_main) cudaEventRecord(after_main, s);
+  const int64_t n_c = static_cast<int64_t>(g.nv) * g.nc * g.ns;
+  const int rb = g_num_sms > 0 ? 4 * g_num_sms : 592;
+  if (f16) reduce_partials<true><<<rb, 256, 0, s>>>(partials, sh.splits, n_c, sig, amax);
+  else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, n_c, sig, amax);
+  ++kernels;
+  return kernels;
 }
 
 }  // namespace rs
+
+// ------------------------------------------------------------------ self-test entry point
+extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
+                                         float *d, void *stream) {
+  using namespace rs;
+  if (m < 1 || n < 32 || (n & 15) || n > 512 || k < 2 || (k & 1) || !a || !b || !d) return SIM_E_INVALID;
+  Shape sh;
+  sh.bn = n < 256 ? n : 256;
+  if (n % sh.bn) return SIM_E_INVALID;
+  sh.mt = (m + BM - 1) / BM;
+  sh.nt = n / sh.bn;
+  sh.splits = 1;
+  sh.chunk = (k / 2 + KS - 1) / KS * KS;
+  Args args{};
+  args.n_rays = k / 2;
+  args.chunk = sh.chunk;
+  args.nc = m;
+  args.ns = n / 2;
+  args.m_rows = m;
+  args.bn = sh.bn;
+  args.partials = d;
+  args.test_a = static_cast<const uint16_t *>(a);
+  args.test_b = static_cast<const uint16_t *>(b);
+  args.test_k = k;
+  uint32_t *status = nullptr;
+  if (cudaMalloc(&status, 4) != cudaSuccess) return SIM_E_NOMEM;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemsetAsync(status, 0, 4, s);
+  args.status = status;
+  if (f16) launch_gemm<true, false, true>(sh, args, s);
+  else launch_gemm<false, false, true>(sh, args, s);
+  uint32_t st = 0;
+  cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(status);
+  if (e != cudaSuccess) return SIM_E_CUDA;
+  return st ? SIM_E_DEVICE : SIM_OK;
+}

@@ -74,8 +74,9 @@ def _load() -> ctypes.CDLL:
     lib.sim_engine_configure.argtypes = [I64, I32, I32]
     lib.sim_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), I32]
     lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sim_selftest_umma.argtypes = [I32, I32, I32, I64, P, P, P, P]
     for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
-              "sim_last_stage_ms", "sim_last_kernel_count"):
+              "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -133,16 +134,22 @@ def sim_fetch(ctx, ticket: int, spectrum=None, signal=None, labels=None, timeout
                          int(timeout_ms))
 
 
+def sim_selftest_umma(f16: int, m: int, n: int, k: int, a, b, d, stream=None) -> int:
+    """D = A B^T through the tensor-core tile path (see include/radarsim.h)."""
+    return lib.sim_selftest_umma(int(f16), int(m), int(n), int(k), _addr(a), _addr(b), _addr(d),
+                                 _addr(stream) if stream is not None else None)
+
+
 def sim_destroy(ctx) -> int:
     return lib.sim_destroy(ctx)
 
 
 def sim_last_stage_ms(ctx):
-    buf = (ctypes.c_float * 6)()
-    rc = lib.sim_last_stage_ms(ctx, buf, 6)
+    buf = (ctypes.c_float * 7)()
+    rc = lib.sim_last_stage_ms(ctx, buf, 7)
     if rc != SIM_OK:
         raise SimError(rc, "sim_last_stage_ms")
-    names = ("ingest", "prep", "ray_sum", "fft", "labels", "total")
+    names = ("ingest", "prep", "ray_sum", "ray_sum_reduce", "fft", "labels", "total")
     return dict(zip(names, list(buf)))
 
 

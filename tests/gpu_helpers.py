@@ -4,9 +4,16 @@ import torch
 
 from paper_2305_14176_gb300 import radarsim as rs
 
-# normwise tolerance on signal and spectrum per ray-sum arithmetic
+# Normwise tolerances (max |err| / max |ref|, and RMS) per ray-sum arithmetic.
+# FP32 and split precision: 1e-5.  Single-pass operands carry their format's rounding:
+# each real operand component is rounded to 8 (BF16) or 11 (FP16) significand bits,
+# a relative error of at most 2^-9 (2^-12); two operands per term and errors adding in
+# quadrature over incoherent rays give an RMS near 2^-9 (2^-12) and a maximum of about
+# twice that, so the bounds below are 1.5x (RMS) and 3x (max) the unit roundoff.
 TOL = {rs.SIM_PREC_FP32_DIRECT: 1e-5, rs.SIM_PREC_BF16_SPLIT: 1e-5, rs.SIM_PREC_FP16_SPLIT: 1e-5,
-       rs.SIM_PREC_BF16: 2e-3, rs.SIM_PREC_FP16: 2e-3}
+       rs.SIM_PREC_BF16: 3 * 2.0 ** -9, rs.SIM_PREC_FP16: 3 * 2.0 ** -12}
+TOL_RMS = {rs.SIM_PREC_FP32_DIRECT: 1e-5, rs.SIM_PREC_BF16_SPLIT: 1e-5, rs.SIM_PREC_FP16_SPLIT: 1e-5,
+           rs.SIM_PREC_BF16: 1.5 * 2.0 ** -9, rs.SIM_PREC_FP16: 1.5 * 2.0 ** -12}
 
 
 def to_c(x: torch.Tensor) -> np.ndarray:
