@@ -110,6 +110,7 @@ Plan make_plan(const Derived &g, int64_t n, bool has_obj) {
     return o;
   };
   const size_t un = static_cast<size_t>(n);
+  const size_t up = (un + 31) / 32 * 32;  // per-ray prep arrays padded to whole 32-ray stages
   p.d = take(8 * un);
   p.a = take(4 * un);
   p.v = take(4 * un);
@@ -117,15 +118,15 @@ Plan make_plan(const Derived &g, int64_t n, bool has_obj) {
   p.el = take(4 * un);
   p.p0 = take(4 * un);
   p.obj = take(has_obj ? 4 * un : 0);
-  p.carrier = take(8 * un);
-  p.nu_r = take(8 * un);
-  p.nu_d = take(8 * un);
-  p.nu_a = take(8 * un);
-  p.amp = take(4 * un);
-  p.cell = take(4 * un);
-  p.energy = take(8 * un);
-  p.step_d = take(8 * un);
-  p.step_r = take(8 * un);
+  p.carrier = take(8 * up);
+  p.nu_r = take(8 * up);
+  p.nu_d = take(8 * up);
+  p.nu_a = take(8 * up);
+  p.amp = take(4 * up);
+  p.cell = take(4 * up);
+  p.energy = take(8 * up);
+  p.step_d = take(8 * up);
+  p.step_r = take(8 * up);
   p.status = take(256);
   p.sig = take(8 * static_cast<size_t>(g.n_sig));
   const bool spec = g.outputs & SIM_OUT_SPECTRUM;

@@ -49,8 +49,8 @@ struct RaysPrep {
   float *amp;         // amplitude (0 for an invalid ray)
   int32_t *cell;      // flat label cell, -1 for an invalid ray
   uint64_t *energy;   // min(rint(a^2 2^32), 2^41)
-  float2 *step_d;     // e^{2 pi j 8 nu_d}: phasor step over eight chirps (FP64-accurate)
-  float2 *step_r;     // e^{2 pi j 8 nu_r}: phasor step over eight samples
+  float2 *step_d;     // e^{2 pi j 16 nu_d}: phasor step over sixteen chirps (FP64-accurate)
+  float2 *step_r;     // e^{2 pi j 16 nu_r}: phasor step over sixteen samples
 };
 
 // Scratch for the label kernels: two open-addressing hash tables

@@ -67,9 +67,9 @@ __device__ __forceinline__ uint64_t frac_q64(double x) {
   return __double2ull_rn(__dmul_rn(f, kTwo64));
 }
 
-// e^{2 pi j 8 q} for a Q0.64 phase increment q, from the exact Q0.64 product in FP64
-__device__ __forceinline__ float2 step8(uint64_t q) {
-  const double f = static_cast<double>(static_cast<int64_t>(q * 8ull)) * 0x1p-64;  // cycles in [-1/2, 1/2)
+// e^{2 pi j 16 q} for a Q0.64 phase increment q, from the exact Q0.64 product in FP64
+__device__ __forceinline__ float2 step16(uint64_t q) {
+  const double f = static_cast<double>(static_cast<int64_t>(q * 16ull)) * 0x1p-64;  // cycles in [-1/2, 1/2)
   double s, c;
   sincospi(2.0 * f, &s, &c);
   return make_float2(static_cast<float>(c), static_cast<float>(s));
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   const uint64_t nu_d = frac_q64(__dmul_rn(x_d, k.inv_nc));
   out.nu_r[i] = nu_r;
   out.nu_d[i] = nu_d;
-  out.step_r[i] = step8(nu_r);
-  out.step_d[i] = step8(nu_d);
+  out.step_r[i] = step16(nu_r);
+  out.step_d[i] = step16(nu_d);
   out.nu_a[i] = frac_q64(__dmul_rn(x_a, k.inv_na));
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
   out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +

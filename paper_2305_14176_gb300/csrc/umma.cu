@@ -35,7 +35,7 @@ namespace {
 constexpr int BM = 128;          // tile rows (TMEM lanes)
 constexpr int KS = 32;           // rays per pipeline stage (K = 2 KS real elements)
 constexpr int KELEM = 2 * KS;    // K elements per stage
-constexpr int NPROD = 256;       // producer threads (warps 0..7); warps 0..3 also drain TMEM
+constexpr int NPROD = 512;       // producer threads (16 warps)
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s: far above any legitimate wait
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -165,11 +165,12 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
 }
 
 // ------------------------------------------------------------------ kernel
-constexpr int NDRAIN = 128;            // drain threads (warps 9..12): one TMEM lane each
-constexpr int MMA_WARP = NPROD / 32;   // warp 8
+constexpr int NDRAIN = 128;            // drain threads: one TMEM lane each
+constexpr int MMA_WARP = NPROD / 32;   // the warp after the producers
 constexpr int NTHREADS_ALL = NPROD + 32 + NDRAIN;
 constexpr int SUBST = 32;              // stages (of KS rays) per tensor-memory accumulation
 constexpr uint32_t kLoCol = 256;       // TMEM column of the lo-part accumulator
+constexpr int LANES = NPROD / KS;      // producer threads per ray (16): row / column stride
 
 struct Args {
   RaysPrep p;
@@ -177,7 +178,7 @@ struct Args {
   int64_t chunk;       // rays per split (multiple of KS)
   int nc, ns, m_rows;  // N_c, N_s, M = N_v N_c
   int bn;              // MMA N (real columns per tile) = min(256, 2 N_s)
-  float *partials;     // [splits][M][2 N_s]
+  float *partials;     // [splits][M][2 N_s], each bn-column tile as (Re block, Im block)
   const uint32_t *amax_bits;  // scene amplitude maximum (FP16 scaling), may be null
   uint32_t *status;
   // self-test mode: operands copied from row-major global matrices instead of synthesised
@@ -206,85 +207,121 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 
 __device__ __forceinline__ void sts32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
-// Synthesise one stage of operands.  Thread t owns ray i = t / 8 of the stage and
-// phase lane j = t % 8: A rows j, j + 8, ..., and B complex columns j, j + 8, ...; along
-// each it steps the phasor by the FP64-accurate e^{2 pi j 8 nu} of the prep kernel, so a
-// stage costs two hardware sin/cos per thread plus one complex multiply per element.
-template <bool F16, bool SPLIT>
+// bounded wait that sleeps between polls (for waits that last a whole accumulation)
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
+  if (mbar_try(a, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    __nanosleep(256);
+    if (mbar_try(a, parity)) return true;
+    if ((i & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+// Per-ray inputs of one stage for one producer thread (prefetched a stage ahead).
+struct RayRegs {
+  uint64_t car, nua, nud, nur;
+  float amp;
+  float2 wd, wr;
+};
+
+__device__ __forceinline__ void load_ray(const Args &g, int64_t ray, bool valid, RayRegs &r) {
+  if (valid) {
+    r.car = g.p.carrier[ray];
+    r.nua = g.p.nu_a[ray];
+    r.nud = g.p.nu_d[ray];
+    r.nur = g.p.nu_r[ray];
+    r.amp = g.p.amp[ray];
+    r.wd = g.p.step_d[ray];
+    r.wr = g.p.step_r[ray];
+  } else {  // a ray past the chunk: zero amplitude and zero range phasor make its terms 0
+    r.car = r.nua = r.nud = r.nur = 0;
+    r.amp = 0.f;
+    r.wd = make_float2(1.f, 0.f);
+    r.wr = make_float2(0.f, 0.f);
+  }
+}
+
+// Synthesise one stage of operands.
+//   Thread mapping (16 producer warps): warp w serves rays 4 (w/2) .. 4 (w/2) + 3 of the
+//   stage; lane = 4 jl + il picks ray il of the four and phase lane j = 8 (w%2) + jl.
+//   A: rows r = j + 16 l (l < 8); B: complex columns nl = j + 16 l (l < bn/32), written as
+//   row nl of the Re block (B'[., 2i] = Re B, B'[., 2i+1] = -Im B) and row bn/2 + nl of the
+//   Im block ((Im B, Re B)), so the accumulator holds (Re S | Im S) per tile.
+//   Consecutive phasors along rows (chirps) and columns (samples) are one complex multiply
+//   apart: e^{2 pi j 16 nu} comes FP64-accurate from the prep kernel.  Every warp-wide
+//   32-bit store covers 32 distinct banks.
+template <bool F16, bool SPLIT, bool FAST>
 __device__ __forceinline__ void produce_stage(const Args &g, uint8_t *a_hi, uint8_t *b_hi, uint8_t *a_lo,
-                                              uint8_t *b_lo, int64_t ray0, int64_t k_hi, int row0, int col0,
-                                              float scale) {
+                                              uint8_t *b_lo, const RayRegs &r, int row0, int col0, float scale) {
   const int t = threadIdx.x;
-  const int i = t >> 3, j = t & 7;
-  const int64_t ray = ray0 + i;
-  const bool valid = ray < k_hi;
+  const int w = t >> 5, lane = t & 31;
+  const int grp = w >> 1, jh = w & 1, il = lane & 3, jl = lane >> 2;
+  const int j = 8 * jh + jl;
   const int bn = g.bn;
   const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
-  // ---- A: rows r = j + 8 l
+  // ---- A
   {
-    uint32_t off = (i >> 2) * lbo_a + j * 16 + (i & 3) * 4;
-    float2 z = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
-    uint64_t car = 0, nua = 0, nud = 0;
-    float am = 0.f;
+    uint32_t off = grp * lbo_a + jh * 128 + jl * 16 + il * 4;
+    const float am = r.amp * scale;
     int grow = row0 + j;
     int kq = grow / g.nc, mq = grow - kq * g.nc;
-    if (valid) {
-      car = g.p.carrier[ray];
-      nua = g.p.nu_a[ray];
-      nud = g.p.nu_d[ray];
-      am = g.p.amp[ray] * scale;
-      w = g.p.step_d[ray];
+    float2 z;
+    {
+      float sn, cs;
+      __sincosf(q64_to_rad(r.car + static_cast<uint64_t>(kq) * r.nua + static_cast<uint64_t>(mq) * r.nud), &sn, &cs);
+      z = make_float2(am * cs, am * sn);
     }
-    bool restart = true;
-#pragma unroll 4
-    for (int l = 0; l < BM / 8; ++l) {
-      if (restart) {
-        // start (or restart in a new channel) from the exact Q0.64 phase of row (kq, mq)
-        float sn, cs;
-        __sincosf(q64_to_rad(car + static_cast<uint64_t>(kq) * nua + static_cast<uint64_t>(mq) * nud), &sn, &cs);
-        z = make_float2(am * cs, am * sn);
+#pragma unroll
+    for (int l = 0; l < BM / LANES; ++l) {
+      if constexpr (FAST) {
+        if (l > 0) z = cmulf(z, r.wd);  // sixteen chirps on, same channel
       } else {
-        z = cmulf(z, w);  // eight chirps on in the same channel
+        if (l > 0) {
+          grow += LANES;
+          mq += LANES;
+          if (mq >= g.nc) {  // crossed into another channel: restart from the exact phase
+            kq = grow / g.nc;
+            mq = grow - kq * g.nc;
+            float sn, cs;
+            __sincosf(q64_to_rad(r.car + static_cast<uint64_t>(kq) * r.nua + static_cast<uint64_t>(mq) * r.nud),
+                      &sn, &cs);
+            z = make_float2(am * cs, am * sn);
+          } else {
+            z = cmulf(z, r.wd);
+          }
+        }
+        if (grow >= g.m_rows) z = make_float2(0.f, 0.f);
       }
-      const float2 v = (valid && grow < g.m_rows) ? z : make_float2(0.f, 0.f);
       uint32_t hi, lo;
-      encode<F16, SPLIT>(v.x, v.y, hi, lo);
+      encode<F16, SPLIT>(z.x, z.y, hi, lo);
       sts32(a_hi + off, hi);
       if constexpr (SPLIT) sts32(a_lo + off, lo);
-      off += 128;
-      grow += 8;
-      mq += 8;
-      restart = false;
-      if (mq >= g.nc) {
-        kq = grow / g.nc;
-        mq = grow - kq * g.nc;
-        restart = true;
-      }
+      off += 256;
     }
   }
-  // ---- B: complex columns nl = j + 8 l, real rows 2 nl and 2 nl + 1
+  // ---- B
   {
-    const int nb = bn / 16;  // columns per thread
-    uint32_t off = (i >> 2) * lbo_b + (j >> 2) * 128 + (j & 3) * 32 + (i & 3) * 4;
-    const bool swap = (j >> 2) != 0;  // half the warp writes its odd row first: no bank conflicts
-    float2 z = make_float2(0.f, 0.f), w = make_float2(1.f, 0.f);
-    if (valid) {
+    uint32_t off = grp * lbo_b + jh * 128 + jl * 16 + il * 4;
+    const uint32_t im_blk = static_cast<uint32_t>(bn) * 8;  // bn/2 rows = bn/16 core groups
+    float2 z;
+    {
       float sn, cs;
-      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * g.p.nu_r[ray]), &sn, &cs);
-      z = make_float2(cs, sn);
-      w = g.p.step_r[ray];
+      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * r.nur), &sn, &cs);
+      z = make_float2(cs, sn);  // finite for every ray; A is zero for rays past the chunk
     }
+    const int nb = bn / (2 * LANES);
     for (int l = 0; l < nb; ++l) {
-      if (l > 0) z = cmulf(z, w);
-      uint32_t h0, l0, h1, l1;
-      encode<F16, SPLIT>(z.x, -z.y, h0, l0);  // row 2n:   ( Re B, -Im B)
-      encode<F16, SPLIT>(z.y, z.x, h1, l1);   // row 2n+1: ( Im B,  Re B)
-      const uint32_t o0 = swap ? off + 16 : off, o1 = swap ? off : off + 16;
-      sts32(b_hi + o0, swap ? h1 : h0);
-      sts32(b_hi + o1, swap ? h0 : h1);
+      if (l > 0) z = cmulf(z, r.wr);
+      uint32_t hi, lo;
+      encode<F16, SPLIT>(z.x, z.y, hi, lo);  // (Re B, Im B)
+      // Re block row: (Re B, -Im B) = flip the sign of the upper half
+      // Im block row: (Im B, Re B)  = swap the halves
+      sts32(b_hi + off, hi ^ 0x80000000u);
+      sts32(b_hi + off + im_blk, __byte_perm(hi, 0, 0x1032));
       if constexpr (SPLIT) {
-        sts32(b_lo + o0, swap ? l1 : l0);
-        sts32(b_lo + o1, swap ? l0 : l1);
+        sts32(b_lo + off, lo ^ 0x80000000u);
+        sts32(b_lo + off + im_blk, __byte_perm(lo, 0, 0x1032));
       }
       off += 256;
     }
@@ -374,8 +411,17 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
   if (warp < MMA_WARP) {
     // ---------------- producers
     const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
+    const bool fast = (g.nc % BM) == 0;  // rows of a tile share one channel and all exist
+    const int my_ray = ((threadIdx.x >> 6) << 2) + (threadIdx.x & 3);
+    RayRegs cur{}, nxt{};
+    if (!TEST && n_stages > 0) load_ray(g, k_lo + my_ray, k_lo + my_ray < k_hi, cur);
     for (int st = 0; st < n_stages; ++st) {
       const int s = st % NST;
+      const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
+      if (!TEST && st + 1 < n_stages) {  // prefetch the next stage's ray while this one is built
+        const int64_t nr = ray0 + KS + my_ray;
+        load_ray(g, nr, nr < k_hi, nxt);
+      }
       if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
         failed = true;
         break;
@@ -384,9 +430,13 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
       uint8_t *b_hi = a_hi + a_bytes;
       uint8_t *a_lo = b_hi + b_bytes;
       uint8_t *b_lo = a_lo + a_bytes;
-      const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
-      if constexpr (TEST) copy_stage(g, a_hi, b_hi, ray0, row0, col0);
-      else produce_stage<F16, SPLIT>(g, a_hi, b_hi, a_lo, b_lo, ray0, k_hi, row0, col0, scale);
+      if constexpr (TEST) {
+        copy_stage(g, a_hi, b_hi, ray0, row0, col0);
+      } else {
+        if (fast) produce_stage<F16, SPLIT, true>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
+        else produce_stage<F16, SPLIT, false>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
+        cur = nxt;
+      }
       fence_proxy_async();
       mbar_arrive(full0 + 8 * s);
     }
@@ -444,7 +494,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
       for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     for (int sub = 0; sub < n_sub; ++sub) {
-      if (!mbar_wait(accf, sub & 1)) {
+      if (!mbar_wait_sleep(accf, sub & 1)) {
         failed = true;
         break;
       }
@@ -488,21 +538,28 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
   }
 }
 
-// sum the split partials in split order: sig[row][n] = sum_s (D_s[row][2n], D_s[row][2n+1]) / scale
+// Sum the split partials in split order and interleave each tile's (Re block, Im block):
+//   sig[row][n] = sum_s (P_s[row][t bn + nl], P_s[row][t bn + bn/2 + nl]) / scale,
+//   t = n / (bn/2), nl = n % (bn/2).
 template <bool F16>
-__global__ void reduce_partials(const float *__restrict__ part, int splits, int64_t n_c, float2 *__restrict__ sig,
-                                const uint32_t *amax_bits) {
+__global__ void reduce_partials(const float *__restrict__ part, int splits, int64_t m_rows, int ns, int bn,
+                                float2 *__restrict__ sig, const uint32_t *amax_bits) {
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
+  const int64_t n_c = m_rows * ns;
+  const int64_t plane = m_rows * 2 * ns;
+  const int half = bn / 2;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_c;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float2 *p = reinterpret_cast<const float2 *>(part) + i;
-    float2 acc = p[0];
+    const int64_t row = i / ns;
+    const int n = static_cast<int>(i - row * ns);
+    const int t = n / half, nl = n - t * half;
+    const float *p = part + row * 2 * ns + t * bn + nl;
+    float re = p[0], im = p[half];
     for (int s = 1; s < splits; ++s) {
-      const float2 v = p[static_cast<int64_t>(s) * n_c];
-      acc.x += v.x;
-      acc.y += v.y;
+      re += p[s * plane];
+      im += p[s * plane + half];
     }
-    sig[i] = make_float2(acc.x * inv, acc.y * inv);
+    sig[i] = make_float2(re * inv, im * inv);
   }
 }
 
@@ -522,24 +579,45 @@ struct Shape {
   int64_t chunk;
 };
 
-Shape plan_shape(const Derived &g, int64_t n) {
-  Shape s;
-  const int M = g.nv * g.nc;
-  s.bn = 2 * g.ns < 256 ? 2 * g.ns : 256;
-  s.mt = (M + BM - 1) / BM;
-  s.nt = 2 * g.ns / s.bn;
+int num_sms() {
   if (g_num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
       g_num_sms = 148;
   }
+  return g_num_sms;
+}
+
+// Tiles of 128 rows x bn columns; the rays split into `splits` chunks so that the CTAs fill
+// whole waves of the SMs (at least four waves) as evenly as possible.  Depends only on the
+// scene's own shape and ray count.
+Shape plan_shape(const Derived &g, int64_t n) {
+  Shape s;
+  const int M = g.nv * g.nc;
+  s.bn = 2 * g.ns < 256 ? 2 * g.ns : 256;
+  s.mt = (M + BM - 1) / BM;
+  s.nt = 2 * g.ns / s.bn;
+  const int sms = num_sms();
   const int64_t tiles = static_cast<int64_t>(s.mt) * s.nt;
-  int64_t splits = (4 * g_num_sms + tiles - 1) / tiles;  // about four waves of CTAs
-  const int64_t max_splits = (n + KS - 1) / KS;
+  const int64_t max_splits = (n + KS - 1) / KS > 0 ? (n + KS - 1) / KS : 1;
+  const int64_t lo = (4 * sms + tiles - 1) / tiles;
+  // idle fraction of the last wave, waste / (ctas + waste); smallest wins, ties to fewer splits
+  int64_t best = lo, best_waste = -1, best_slots = 1;
+  for (int64_t sp = lo; sp <= 3 * lo; ++sp) {
+    const int64_t ctas = tiles * sp;
+    const int64_t slots = ((ctas + sms - 1) / sms) * sms;
+    const int64_t waste = slots - ctas;
+    if (best_waste < 0 || waste * best_slots < best_waste * slots) {
+      best = sp;
+      best_waste = waste;
+      best_slots = slots;
+    }
+  }
+  int64_t splits = best;
   if (splits > max_splits) splits = max_splits;
-  if (splits < 1) splits = 1;
   if (splits > 65535) splits = 65535;
+  if (splits < 1) splits = 1;
   int64_t chunk = (n + splits - 1) / splits;
   chunk = (chunk + KS - 1) / KS * KS;
   if (chunk < KS) chunk = KS;
@@ -589,7 +667,7 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   int kernels = 0;
   cudaMemsetAsync(amax, 0, 4, s);
   if (f16 && n > 0) {
-    amax_kernel<<<g_num_sms > 0 ? 2 * g_num_sms : 296, 256, 0, s>>>(p.amp, n, amax);
+    amax_kernel<<<2 * num_sms(), 256, 0, s>>>(p.amp, n, amax);
     ++kernels;
   }
   Args a{};
@@ -612,10 +690,10 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   }
   ++kernels;
   if (after_main) cudaEventRecord(after_main, s);
-  const int64_t n_c = static_cast<int64_t>(g.nv) * g.nc * g.ns;
-  const int rb = g_num_sms > 0 ? 4 * g_num_sms : 592;
-  if (f16) reduce_partials<true><<<rb, 256, 0, s>>>(partials, sh.splits, n_c, sig, amax);
-  else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, n_c, sig, amax);
+  const int rb = 4 * num_sms();
+  const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
+  if (f16) reduce_partials<true><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
   ++kernels;
   return kernels;
 }
