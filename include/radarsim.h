@@ -183,6 +183,32 @@ SIM_API int sim_last_kernel_count(sim_ctx *ctx, int32_t *count);
 SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
                               float *d, void *stream);
 
+/* Ray sum without any device allocation.
+   Some callers cannot call cudaMalloc: a host application whose framework allocator has
+   already reserved the GPU's memory, a real-time loop that must not take the implicit
+   device synchronisation and unbounded latency of cudaMalloc/cudaFree, or a deployment
+   that forbids allocation after start-up.  For them this call computes the beat-signal
+   cube s[k][m][n] (complex64[N_v][N_c][N_s], same model, precision and result within
+   the same tolerance as the signal of sim_submit/sim_fetch) with all of its working
+   memory in one static device array of 128 MiB that every device which loads the
+   library holds until the process exits.  The caller passes device-resident ray arrays
+   (meta data is not needed) and a device output buffer, and a cudaStream_t (NULL = the
+   default stream); the call runs on that stream and synchronizes it before returning.
+   Limits: n <= min(max_rays, 262144); on the tensor-core precisions one FP32 copy of
+   the whole cube, 8 N_v N_c N_s bytes, must also fit beside the 56 bytes per ray of
+   per-ray data (the automotive 12 x 256 x 512 cube does; a 192 x 512 x 1024 imaging
+   cube does not).  Beyond a limit, or with host pointers, it returns SIM_E_INVALID
+   before launching anything.
+   The first call on each device looks up the array's device address (set-up); make
+   that first call before any stream capture.  Every call on a device shares the one
+   array and finds the previous call's contents in it (the call clears what must start
+   at zero), so calls whose work overlaps on the GPU, from several streams or host
+   threads, race: serialise them.
+   Errors: SIM_E_INVALID, SIM_E_CUDA, SIM_E_DEVICE (a pipeline wait ran out); an invalid
+   ray value is reported as SIM_E_INVALID after the run. */
+SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const sim_rays *rays, void *signal_c64,
+                               void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -421,6 +421,8 @@ int upload_tables(sim_ctx *c) {
 
 }  // namespace
 
+int rs::derive_radar(const sim_radar_params *p, Derived *g) { return derive(p, g); }
+
 extern "C" {
 
 const char *sim_status_string(int s) {

@@ -85,4 +85,13 @@ int64_t umma_workspace_bytes(const Derived &g, int64_t n);
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace,
                     uint32_t *status, cudaStream_t s, cudaEvent_t after_main);
 
+// Validate sim_radar_params and derive the radar constants (SIM_OK or SIM_E_INVALID).
+int derive_radar(const sim_radar_params *p, Derived *g);
+
+// Tensor-core ray sum inside a caller-provided workspace of `ws_bytes`: the split-K count
+// is lowered until the partials fit.  Returns the number of kernels launched, or -1 when
+// even a single split does not fit.
+int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, int64_t ws_bytes,
+                       uint32_t *status, cudaStream_t s);
+
 }  // namespace rs

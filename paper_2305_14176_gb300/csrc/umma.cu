@@ -698,6 +698,56 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   return kernels;
 }
 
+int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, int64_t ws_bytes,
+                       uint32_t *status, cudaStream_t s) {
+  Shape sh = plan_shape(g, n);
+  const int64_t per_split = static_cast<int64_t>(g.nv) * g.nc * 2 * g.ns * 4;
+  const int64_t fit = (ws_bytes - 256) / per_split;
+  if (fit < 1) return -1;
+  if (sh.splits > fit) {
+    int64_t chunk = (n + fit - 1) / fit;
+    chunk = (chunk + KS - 1) / KS * KS;
+    if (chunk < KS) chunk = KS;
+    sh.chunk = chunk;
+    sh.splits = static_cast<int>((n + chunk - 1) / chunk);
+    if (sh.splits < 1) sh.splits = 1;
+  }
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  int kernels = 0;
+  cudaMemsetAsync(amax, 0, 4, s);
+  if (f16 && n > 0) {
+    amax_kernel<<<2 * num_sms(), 256, 0, s>>>(p.amp, n, amax);
+    ++kernels;
+  }
+  Args a{};
+  a.p = p;
+  a.n_rays = n;
+  a.chunk = sh.chunk;
+  a.nc = g.nc;
+  a.ns = g.ns;
+  a.m_rows = g.nv * g.nc;
+  a.bn = sh.bn;
+  a.partials = partials;
+  a.amax_bits = amax;
+  a.status = status;
+  if (f16) {
+    if (split) launch_gemm<true, true, false>(sh, a, s);
+    else launch_gemm<true, false, false>(sh, a, s);
+  } else {
+    if (split) launch_gemm<false, true, false>(sh, a, s);
+    else launch_gemm<false, false, false>(sh, a, s);
+  }
+  ++kernels;
+  const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  ++kernels;
+  return kernels;
+}
+
 }  // namespace rs
 
 // ------------------------------------------------------------------ self-test entry point

@@ -75,8 +75,9 @@ def _load() -> ctypes.CDLL:
     lib.sim_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), I32]
     lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.sim_selftest_umma.argtypes = [I32, I32, I32, I64, P, P, P, P]
+    lib.sim_raysum_noalloc.argtypes = [ctypes.POINTER(sim_radar_params), ctypes.POINTER(sim_rays), P, P]
     for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
-              "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma"):
+              "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma", "sim_raysum_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -138,6 +139,12 @@ def sim_selftest_umma(f16: int, m: int, n: int, k: int, a, b, d, stream=None) ->
     """D = A B^T through the tensor-core tile path (see include/radarsim.h)."""
     return lib.sim_selftest_umma(int(f16), int(m), int(n), int(k), _addr(a), _addr(b), _addr(d),
                                  _addr(stream) if stream is not None else None)
+
+
+def sim_raysum_noalloc(params: sim_radar_params, rays: sim_rays, signal, stream=None) -> int:
+    """Beat-signal cube into a device buffer with no device allocation (see the header)."""
+    return lib.sim_raysum_noalloc(ctypes.byref(params), ctypes.byref(rays), _addr(signal),
+                                  _addr(stream) if stream is not None else None)
 
 
 def sim_destroy(ctx) -> int:

@@ -1,0 +1,61 @@
+"""sim_raysum_noalloc: the ray sum for callers that cannot allocate device memory.
+
+It must give the signal that sim_submit/sim_fetch give for the same scene, within
+the tolerance of the precision, on two calls in a row (the static scratch array
+keeps the first call's contents when the second starts).  This file is collected
+last so that a run stopping at the first failure has run everything else first.
+"""
+import numpy as np
+import pytest
+import torch
+
+import scenegen
+from paper_2305_14176_gb300 import radarsim as rs
+from gpu_helpers import TOL, TOL_RMS, rel_max, rel_rms, run, to_c
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc_signal(radar, rays, precision, stream):
+    params = rs.make_params(radar, precision=precision, outputs=rs.SIM_OUT_SIGNAL)
+    arr = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.arrays().items()}
+    r, _ = rs.make_rays(arr, rays.n)
+    nv = radar.n_tx * radar.n_rx
+    sig = torch.full((nv, radar.n_chirps, radar.n_samples, 2), float("nan"), dtype=torch.float32, device="cuda")
+    rc = rs.sim_raysum_noalloc(params, r, sig, stream)
+    torch.cuda.synchronize()
+    return rc, to_c(sig)
+
+
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_FP32_DIRECT])
+def test_noalloc_matches_submit_fetch_twice(precision):
+    stream = torch.cuda.current_stream().cuda_stream
+    scenes = [scenegen.automotive_scene(seed=1000, n_rays=200_000), scenegen.tiny_scene(seed=4)]
+    if precision == rs.SIM_PREC_FP32_DIRECT:
+        scenes = [scenegen.automotive_scene(seed=1000, n_rays=20_000), scenegen.tiny_scene(seed=4)]
+    for radar, rays in scenes:
+        rc, ref, _, _ = run(radar, rays, precision, outputs=rs.SIM_OUT_SIGNAL)
+        assert rc == rs.SIM_OK
+        for _ in range(2):
+            rc, got = _noalloc_signal(radar, rays, precision, stream)
+            assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+            assert rel_max(got, ref) <= TOL[precision]
+            assert rel_rms(got, ref) <= TOL_RMS[precision]
+
+
+def test_noalloc_rejects_oversize_and_host_pointers():
+    stream = torch.cuda.current_stream().cuda_stream
+    radar, rays = scenegen.tiny_scene(seed=1, n_rays=100)
+    params = rs.make_params(radar, precision=rs.SIM_PREC_BF16_SPLIT, outputs=rs.SIM_OUT_SIGNAL)
+    host = rays.arrays()
+    r, _ = rs.make_rays(host, rays.n)
+    sig = torch.empty((4, 64, 128, 2), dtype=torch.float32, device="cuda")
+    assert rs.sim_raysum_noalloc(params, r, sig, stream) == rs.SIM_E_INVALID  # host rays
+    arr = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in host.items()}
+    r, _ = rs.make_rays(arr, (1 << 18) + 1)
+    assert rs.sim_raysum_noalloc(params, r, sig, stream) == rs.SIM_E_INVALID  # too many rays
+    img = scenegen.radar_imaging()
+    r, _ = rs.make_rays(arr, rays.n)
+    big = torch.empty(16, dtype=torch.float32, device="cuda")  # never written: rejected first
+    assert rs.sim_raysum_noalloc(rs.make_params(img, precision=rs.SIM_PREC_BF16_SPLIT,
+                                                outputs=rs.SIM_OUT_SIGNAL), r, big, stream) == rs.SIM_E_INVALID
