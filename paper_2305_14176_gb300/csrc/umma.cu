@@ -48,12 +48,15 @@ __device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t a) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(a) : "memory");
 }
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+// One potentially blocking test of a phase: the hardware suspends the thread until the
+// phase completes or about `hint_ns` passes, so a waiting warp does not spin on issue slots.
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity, uint32_t hint_ns = 1000000u) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(a), "r"(parity)
+      : "r"(a), "r"(parity), "r"(hint_ns)
       : "memory");
   return ok != 0;
 }
@@ -66,9 +69,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 1;; ++i) {
+  for (;;) {
     if (mbar_try(a, parity)) return true;
-    if ((i & 255u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
   }
 }
 __device__ __forceinline__ void fence_proxy_async() {
@@ -113,6 +116,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+
+// store 32 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Instruction descriptor, kind::f16: D FP32, A/B BF16 (or FP16), both K-major, M x N.
 __host__ __device__ constexpr uint32_t make_idesc(bool f16, int m, int n) {
@@ -168,8 +184,12 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
 constexpr int NDRAIN = 128;            // drain threads: one TMEM lane each
 constexpr int MMA_WARP = NPROD / 32;   // the warp after the producers
 constexpr int NTHREADS_ALL = NPROD + 32 + NDRAIN;
-constexpr int SUBST = 32;              // stages (of KS rays) per tensor-memory accumulation
-constexpr uint32_t kLoCol = 256;       // TMEM column of the lo-part accumulator
+// Stages (of KS rays) per tensor-core accumulation chain before it is folded into the FP32
+// running sum: the tensor core's accumulate is not IEEE round-to-nearest and its error grows
+// with the chain, so split precision folds every 512 rays; single precision (whose operand
+// rounding is ~1e-3) folds only at the end of its chunk.
+constexpr int SUBST_SPLIT = 16;
+constexpr uint32_t kSumCol = 256;      // TMEM column of the FP32 running sum
 constexpr int LANES = NPROD / KS;      // producer threads per ray (16): row / column stride
 
 struct Args {
@@ -211,10 +231,10 @@ __device__ __forceinline__ void sts32(uint8_t *p, uint32_t v) { *reinterpret_cas
 __device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (uint32_t i = 1;; ++i) {
+  for (;;) {
     __nanosleep(256);
     if (mbar_try(a, parity)) return true;
-    if ((i & 63u) == 0 && global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
   }
 }
 
@@ -367,7 +387,7 @@ template <bool F16, bool SPLIT, bool TEST>
 __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NST = SPLIT ? 2 : 4;
-  constexpr uint32_t TMEM_COLS = SPLIT ? 512 : 256;
+  constexpr uint32_t TMEM_COLS = 512;  // accumulator (0..255) and running sum (256..511)
   const int bn = g.bn;
   const uint32_t a_bytes = BM * KELEM * 2;
   const uint32_t b_bytes = static_cast<uint32_t>(bn) * KELEM * 2;
@@ -388,6 +408,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
   const int64_t k_total = TEST ? g.test_k / 2 : g.n_rays;  // rays (K pairs)
   const int64_t k_hi = k_lo + g.chunk < k_total ? k_lo + g.chunk : k_total;
   const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
+  const int SUBST = SPLIT ? SUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
   const int n_sub = (n_stages + SUBST - 1) / SUBST;
   const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
 
@@ -468,8 +489,8 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
           const uint64_t db = make_sdesc(b_hi + kk * 2 * lbo_b, lbo_b, 128);
           mma_f16(tmem, da, db, idesc, acc);
           if constexpr (SPLIT) {
-            mma_f16(tmem + kLoCol, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, acc);
-            mma_f16(tmem + kLoCol, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
+            mma_f16(tmem, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, 1u);
+            mma_f16(tmem, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
           }
         }
         open = true;
@@ -485,7 +506,9 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
       if (!mbar_wait(done, 0)) failed = true;
     }
   } else {
-    // ---------------- drain: TMEM lane quarter (warp % 4), FP32 sums into the split's partial
+    // ---------------- drain: TMEM lane quarter (warp % 4).  Each finished chain is added in
+    // FP32 (round to nearest) to the running sum kept in tensor memory; after the last chain
+    // the sum goes to this split's partial in global memory.
     const int q = warp & 3;
     const int grow = row0 + q * 32 + lane;
     float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
@@ -499,32 +522,27 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
         break;
       }
       tc_fence_after();
+      const bool last = sub == n_sub - 1;
       for (int c = 0; c < bn; c += 32) {
         uint32_t h[32];
         tmem_ld32(trow + static_cast<uint32_t>(c), h);
-        if constexpr (SPLIT) {
-          uint32_t l[32];
-          tmem_ld32(trow + kLoCol + static_cast<uint32_t>(c), l);
+        if (sub > 0) {
+          uint32_t r[32];
+          tmem_ld32(trow + kSumCol + static_cast<uint32_t>(c), r);
 #pragma unroll
-          for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(l[x]));
+          for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
         }
-        if (grow < g.m_rows) {
+        if (!last) {
+          tmem_st32(trow + kSumCol + static_cast<uint32_t>(c), h);
+        } else if (grow < g.m_rows) {
 #pragma unroll
-          for (int x = 0; x < 32; x += 4) {
-            float4 v = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
-                                   __uint_as_float(h[x + 3]));
-            float4 *d4 = reinterpret_cast<float4 *>(dst + c + x);
-            if (sub > 0) {
-              const float4 o = *d4;
-              v.x += o.x;
-              v.y += o.y;
-              v.z += o.z;
-              v.w += o.w;
-            }
-            *d4 = v;
-          }
+          for (int x = 0; x < 32; x += 4)
+            *reinterpret_cast<float4 *>(dst + c + x) =
+                make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
+                            __uint_as_float(h[x + 3]));
         }
       }
+      if (!last) tmem_wait_st();
       tc_fence_before();
       mbar_arrive(acce);
     }
