@@ -37,6 +37,10 @@ import numpy as np  # noqa: E402
 
 import scenegen  # noqa: E402
 
+# DRAM bytes (read + write) of one ray-sum launch on this workload, from the ncu capture
+# summarised in profiles/umma_sum_kernel_automotive_fp16split.md; None where not captured.
+TRAFFIC_BYTES = {"fp16_split": 195.3e6}
+
 METRIC = "ray-sample contributions/s"
 UNIT = "contributions/s"
 WORKLOAD = "automotive frame: 12 virtual ch x 256 chirps x 512 samples, N_a 16, 200k rays"
@@ -164,7 +168,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="bf16_split",
+    ap.add_argument("--precision", default="fp16_split",
                     choices=["fp32", "bf16", "bf16_split", "fp16", "fp16_split"])
     ap.add_argument("--rays", type=int, default=200_000)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -264,7 +268,8 @@ def main():
         achieved = flops / main_s / 1e12
         peak = float(peaks["bf16_tflops"])
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": TRAFFIC_BYTES.get(args.precision) if n == 200_000 else None,
                 "kernel": "umma_sum_kernel", "peak_source": f"{peak_src} bf16 dense burst",
                 "executed_tflops": achieved * (3 if split else 1),
                 "executed_frac": achieved * (3 if split else 1) / peak}
