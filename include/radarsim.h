@@ -130,8 +130,9 @@ SIM_API int sim_create(const sim_radar_params *params, sim_ctx **out);
 
 /* Queue one scene.  The ray arrays (and meta arrays) are copied before the call
    returns; the caller may reuse them at once.  Work starts on the device as soon
-   as the engine admits the scene (free memory budget and free slot); otherwise it
-   waits in a bounded queue and is admitted when an earlier result is fetched.
+   as the engine admits the scene (free memory budget and a free slot); otherwise it
+   waits in a bounded queue.  A slot (a stream) frees when its scene finishes on the
+   device; memory frees when a result is fetched.  Admitted scenes run concurrently.
    *ticket_out identifies the result for sim_fetch.
    Errors: SIM_E_INVALID (n out of range, NULL array, a host ray with a bad value),
    SIM_E_BUSY (queue full, or the scene alone exceeds the memory budget),
@@ -144,7 +145,10 @@ SIM_API int sim_submit(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta,
    layouts above; each may be NULL if not wanted and must be NULL if the context
    was created without that output.  timeout_ms < 0 waits forever, 0 polls.
    On SIM_OK the ticket is consumed and its device memory released.
-   Errors: SIM_E_UNKNOWN_TICKET, SIM_E_TIMEOUT / SIM_E_NOT_READY (ticket kept),
+   A queued ticket is admitted only when earlier results are fetched (their memory and
+   slots free up): fetching it while no other fetch is under way and the queue head cannot
+   be admitted returns SIM_E_BUSY at once (ticket kept) instead of waiting forever.
+   Errors: SIM_E_UNKNOWN_TICKET, SIM_E_TIMEOUT / SIM_E_NOT_READY / SIM_E_BUSY (ticket kept),
    SIM_E_INVALID (the scene held an invalid ray; ticket consumed), SIM_E_DEVICE,
    SIM_E_CUDA. */
 SIM_API int sim_fetch(sim_ctx *ctx, uint64_t ticket, void *spectrum_c64, void *signal_c64,

@@ -3,7 +3,7 @@
 //   s[k][m][n] = sum_i a_i exp(2 pi j (carrier_i + k nu_a,i + m nu_d,i + n nu_r,i))
 //
 // One FP32 sine and cosine per ray and output sample.  The phase is accumulated
-// exactly in Q0.64 integers (wrap = one cycle) and only its top bits are turned into
+// exactly in Q0.64 integers (wrap = one cycle) and only its top 23 bits are turned into
 // an FP32 angle in [-pi, pi), so the hardware sin/cos sees a small argument.
 //
 // A block owns one (k, m) row and all N_s samples; rays stream through shared memory
@@ -17,23 +17,26 @@ namespace {
 
 constexpr int kChunk = 256;
 
-// top 32 bits of a Q0.64 phase as a signed fraction of a cycle, times 2 pi
+// Top 23 bits of a Q0.64 phase turned into an angle in [-pi, pi) without an integer-to-float
+// conversion: with u' = u + 2^31 (mod 2^32), (u' >> 9) | 0x3F800000 is the float 1 + u'/2^32
+// in [1, 2), and (that - 1.5) = u/2^32 - k for the integer k that lands it in [-1/2, 1/2).
 __device__ __forceinline__ float q64_to_rad(uint64_t p) {
-  const int32_t hi = static_cast<int32_t>(p >> 32);
-  return static_cast<float>(hi) * 1.46291807926715968e-09f;  // 2 pi / 2^32
+  const uint32_t u = static_cast<uint32_t>(p >> 32) ^ 0x80000000u;
+  const float f = __uint_as_float((u >> 9) | 0x3F800000u);
+  return (f - 1.5f) * 6.28318530717958647692f;
 }
 
+// One block per (k, m) row: thread t owns samples n = t + j * T (j < NPT).
 template <int NPT>
-__global__ void __launch_bounds__(256) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
+__global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
                                                          float2 *__restrict__ sig) {
-  __shared__ uint64_t s_base[kChunk];
-  __shared__ uint64_t s_nur[kChunk];
+  __shared__ ulonglong2 s_ph[kChunk];  // (base phase of this row, range step)
   __shared__ float s_amp[kChunk];
   const int row = blockIdx.x;
   const uint64_t k = static_cast<uint64_t>(row / nc);
   const uint64_t m = static_cast<uint64_t>(row % nc);
   const int t = threadIdx.x;
-  const uint64_t stride = blockDim.x;
+  const uint64_t T = blockDim.x;
   float tot_re[NPT], tot_im[NPT];
 #pragma unroll
   for (int j = 0; j < NPT; ++j) { tot_re[j] = 0.f; tot_im[j] = 0.f; }
@@ -43,19 +46,20 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(RaysPrep p, int64_t n_r
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const int64_t r = c0 + i;
-      s_base[i] = p.carrier[r] + k * p.nu_a[r] + m * p.nu_d[r];
-      s_nur[i] = p.nu_r[r];
+      s_ph[i] = make_ulonglong2(p.carrier[r] + k * p.nu_a[r] + m * p.nu_d[r], p.nu_r[r]);
       s_amp[i] = p.amp[r];
     }
     __syncthreads();
+    // per-chunk partial sums, then added to the totals (two-level summation)
     float re[NPT], im[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { re[j] = 0.f; im[j] = 0.f; }
+#pragma unroll 2
     for (int i = 0; i < cnt; ++i) {
-      const uint64_t nr = s_nur[i];
-      uint64_t ph = s_base[i] + static_cast<uint64_t>(t) * nr;
-      const uint64_t step = stride * nr;
+      const ulonglong2 q = s_ph[i];
       const float a = s_amp[i];
+      uint64_t ph = q.x + static_cast<uint64_t>(t) * q.y;
+      const uint64_t step = T * q.y;
 #pragma unroll
       for (int j = 0; j < NPT; ++j) {
         float sn, cs;
@@ -80,14 +84,15 @@ __global__ void __launch_bounds__(256) direct_sum_kernel(RaysPrep p, int64_t n_r
 
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s) {
   const int rows = g.nv * g.nc;
-  const int threads = g.ns < 256 ? g.ns : 256;
+  const int threads = g.ns < 128 ? g.ns : 128;
   const int npt = g.ns / threads;  // N_s is a power of two >= 16
   switch (npt) {
     case 1: direct_sum_kernel<1><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
     case 2: direct_sum_kernel<2><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
     case 4: direct_sum_kernel<4><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
     case 8: direct_sum_kernel<8><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    default: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
+    case 16: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
+    default: direct_sum_kernel<32><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
   }
   return 1;
 }

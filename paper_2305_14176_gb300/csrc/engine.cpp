@@ -32,10 +32,13 @@ namespace {
 
 constexpr int kNumEvents = 7;  // start, ingest, prep, ray-sum main kernel, ray sum done, fft, labels/end
 
+struct Job;
+
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[kNumEvents] = {};
   bool busy = false;
+  Job *job = nullptr;  // the scene running on this slot
 };
 
 struct Plan {  // byte offsets of one scene's buffers inside its device block
@@ -64,6 +67,9 @@ struct sim_ctx {
 
 namespace {
 
+// A scene's life: queued (pending, host copy of its inputs) -> running (a slot: stream and
+// events) -> done on the device (slot released, device block and stage times kept) ->
+// fetched (block freed, ticket gone).
 struct Job {
   uint64_t ticket = 0;
   sim_ctx *ctx = nullptr;
@@ -71,11 +77,15 @@ struct Job {
   bool has_obj = false;
   Plan plan{};
   bool pending = true;
+  bool done = false;
+  bool claimed = false;            // a fetch has taken it
   std::vector<uint8_t> host_copy;  // inputs held while the scene waits in the queue
   uint8_t *block = nullptr;
   int slot = -1;
   int kernels = 0;
   int launch_error = 0;
+  cudaError_t device_error = cudaSuccess;
+  float ms[8] = {};
 };
 
 struct Engine {
@@ -85,9 +95,11 @@ struct Engine {
   int64_t budget = 0, used = 0;
   int max_queue = 64;
   std::vector<Slot> slots;
+  std::vector<cudaStream_t> egress;  // streams for the result copies of sim_fetch
   std::deque<Job *> queue;
   std::unordered_map<uint64_t, Job *> jobs;
   uint64_t next_ticket = 1;
+  int fetching = 0;  // threads inside sim_fetch
   cudaMemPool_t pool = nullptr;
   bool ready = false;
   // configuration requested before start
@@ -229,12 +241,19 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
   return SIM_OK;
 }
 
+// does the queue head fit the memory budget now? (lock held; slots free up on their own)
+bool head_fits_locked(Engine &e) {
+  if (e.queue.empty()) return true;
+  return e.used + static_cast<int64_t>(e.queue.front()->plan.total) <= e.budget;
+}
+
 // try to reserve memory and a slot for `j` (lock held)
 bool try_reserve_locked(Engine &e, Job *j) {
   if (e.used + static_cast<int64_t>(j->plan.total) > e.budget) return false;
   for (size_t i = 0; i < e.slots.size(); ++i) {
     if (!e.slots[i].busy) {
       e.slots[i].busy = true;
+      e.slots[i].job = j;
       j->slot = static_cast<int>(i);
       e.used += static_cast<int64_t>(j->plan.total);
       return true;
@@ -243,12 +262,38 @@ bool try_reserve_locked(Engine &e, Job *j) {
   return false;
 }
 
-void release_locked(Engine &e, Job *j) {
-  if (j->slot >= 0) {
-    e.slots[j->slot].busy = false;
-    e.used -= static_cast<int64_t>(j->plan.total);
-    j->slot = -1;
+// the scene finished on the device: keep its stage times, give its slot to the next scene
+void finish_on_device_locked(Engine &e, Job *j, cudaError_t err) {
+  Slot &sl = e.slots[j->slot];
+  for (int i = 0; i + 1 < kNumEvents; ++i) {
+    j->ms[i] = 0.f;
+    cudaEventElapsedTime(&j->ms[i], sl.ev[i], sl.ev[i + 1]);
   }
+  cudaEventElapsedTime(&j->ms[kNumEvents - 1], sl.ev[0], sl.ev[kNumEvents - 1]);
+  cudaGetLastError();
+  j->device_error = err;
+  j->done = true;
+  sl.busy = false;
+  sl.job = nullptr;
+  j->slot = -1;
+}
+
+// poll the running scenes (lock held); true if any finished
+bool reap_locked(Engine &e) {
+  bool any = false;
+  for (auto &sl : e.slots) {
+    if (!sl.busy || !sl.job || sl.job->pending) continue;
+    const cudaError_t q = cudaEventQuery(sl.ev[kNumEvents - 1]);
+    if (q == cudaErrorNotReady) continue;
+    finish_on_device_locked(e, sl.job, q);
+    any = true;
+  }
+  if (any) cudaGetLastError();
+  return any;
+}
+
+bool any_running_locked(const Engine &e) {
+  return std::any_of(e.slots.begin(), e.slots.end(), [](const Slot &s) { return s.busy; });
 }
 
 sim_rays host_copy_view(Job *j, const int32_t **obj) {
@@ -266,27 +311,32 @@ sim_rays host_copy_view(Job *j, const int32_t **obj) {
   return r;
 }
 
-// worker: admit queued scenes in arrival order as memory and slots free up
+// worker: notice scenes that finished on the device (their slots free up) and admit queued
+// scenes in arrival order as memory and slots allow
 void worker_main() {
   Engine &e = engine();
   cudaSetDevice(e.device);
   std::unique_lock<std::mutex> lk(e.mu);
   for (;;) {
-    e.cv.wait(lk, [&] { return !e.queue.empty() && e.used + static_cast<int64_t>(e.queue.front()->plan.total) <= e.budget &&
-                               std::any_of(e.slots.begin(), e.slots.end(), [](const Slot &s) { return !s.busy; }); });
-    Job *j = e.queue.front();
-    if (!try_reserve_locked(e, j)) continue;
-    e.queue.pop_front();
-    lk.unlock();
-    const int32_t *obj = nullptr;
-    sim_rays src = host_copy_view(j, &obj);
-    const int rc = launch_job(e, j, src, obj);
-    lk.lock();
-    j->launch_error = rc;
-    j->pending = false;
-    j->host_copy.clear();
-    j->host_copy.shrink_to_fit();
-    e.cv.notify_all();
+    if (reap_locked(e)) e.cv.notify_all();
+    while (!e.queue.empty()) {
+      Job *j = e.queue.front();
+      if (!try_reserve_locked(e, j)) break;
+      e.queue.pop_front();
+      lk.unlock();
+      const int32_t *obj = nullptr;
+      sim_rays src = host_copy_view(j, &obj);
+      const int rc = launch_job(e, j, src, obj);
+      lk.lock();
+      j->launch_error = rc;
+      j->pending = false;
+      j->host_copy.clear();
+      j->host_copy.shrink_to_fit();
+      if (rc != SIM_OK) finish_on_device_locked(e, j, cudaSuccess);
+      e.cv.notify_all();
+    }
+    if (any_running_locked(e)) e.cv.wait_for(lk, std::chrono::microseconds(100));
+    else e.cv.wait(lk);
   }
 }
 
@@ -310,6 +360,9 @@ int start_engine_locked(Engine &e) {
     for (auto &ev : s.ev)
       if (cudaEventCreate(&ev) != cudaSuccess) return SIM_E_CUDA;
   }
+  e.egress.resize(4);
+  for (auto &st : e.egress)
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SIM_E_CUDA;
   std::thread(worker_main).detach();
   e.ready = true;
   return SIM_OK;
@@ -551,15 +604,18 @@ int sim_submit(sim_ctx *c, const sim_rays *rays, const sim_meta *meta, uint64_t 
     j->pending = false;
     if (rc != SIM_OK) {
       // undo: the scene never ran
-      if (j->block) cudaFreeAsync(j->block, e.slots[j->slot].stream);
-      cudaStreamSynchronize(e.slots[j->slot].stream);
-      release_locked(e, j);
+      cudaStream_t st = e.slots[j->slot].stream;
+      if (j->block) cudaFreeAsync(j->block, st);
+      cudaStreamSynchronize(st);
+      finish_on_device_locked(e, j, cudaSuccess);
+      e.used -= static_cast<int64_t>(j->plan.total);
       e.jobs.erase(j->ticket);
       c->live--;
       delete j;
       e.cv.notify_all();
       return rc;
     }
+    e.cv.notify_all();  // the worker watches for its completion
   }
   *ticket_out = j->ticket;
   return SIM_OK;
@@ -579,82 +635,71 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
   };
   std::unique_lock<std::mutex> lk(e.mu);
   auto it = e.jobs.find(ticket);
-  if (it == e.jobs.end() || it->second->ctx != c) return SIM_E_UNKNOWN_TICKET;
+  if (it == e.jobs.end() || it->second->ctx != c || it->second->claimed) return SIM_E_UNKNOWN_TICKET;
   Job *j = it->second;
-  // wait until admitted
-  while (j->pending) {
-    if (timeout_ms == 0) return SIM_E_NOT_READY;
-    if (timeout_ms < 0) e.cv.wait(lk);
-    else if (e.cv.wait_until(lk, t0 + std::chrono::milliseconds(timeout_ms)) == std::cv_status::timeout && j->pending)
-      return SIM_E_TIMEOUT;
-    if (e.jobs.find(ticket) == e.jobs.end()) return SIM_E_UNKNOWN_TICKET;
-  }
-  if (j->launch_error != SIM_OK) {
-    const int rc = j->launch_error;
-    if (j->block) cudaFreeAsync(j->block, e.slots[j->slot].stream);
-    release_locked(e, j);
-    e.jobs.erase(ticket);
-    c->live--;
-    delete j;
-    e.cv.notify_all();
-    return rc;
-  }
-  Slot &sl = e.slots[j->slot];
-  e.jobs.erase(ticket);  // claim it: no other fetch can take it now
-  lk.unlock();
-  auto give_back = [&]() {
-    std::lock_guard<std::mutex> g2(e.mu);
-    e.jobs[ticket] = j;
-  };
-  // wait for the device pipeline
+  ++e.fetching;
+  int rc = SIM_OK;
   for (;;) {
-    const cudaError_t q = cudaEventQuery(sl.ev[kNumEvents - 1]);
-    if (q == cudaSuccess) break;
-    if (q != cudaErrorNotReady) {
-      give_back();
-      return SIM_E_CUDA;
+    if (j->done) break;
+    if (!j->pending) {
+      // running: poll its final event here too, without waiting for the worker
+      const cudaError_t q = cudaEventQuery(e.slots[j->slot].ev[kNumEvents - 1]);
+      if (q != cudaErrorNotReady) {
+        finish_on_device_locked(e, j, q);
+        e.cv.notify_all();
+        break;
+      }
+      cudaGetLastError();
+    } else if (j->slot < 0 && e.fetching == 1 && !head_fits_locked(e)) {
+      // still queued, behind memory that only fetches free, and no other fetch is under way
+      rc = SIM_E_BUSY;
+      break;
     }
     if (timeout_ms == 0) {
-      give_back();
-      return SIM_E_NOT_READY;
-    }
-    if (timeout_ms < 0) {
-      cudaEventSynchronize(sl.ev[kNumEvents - 1]);
-      continue;
+      rc = SIM_E_NOT_READY;
+      break;
     }
     if (expired()) {
-      give_back();
-      return SIM_E_TIMEOUT;
+      rc = SIM_E_TIMEOUT;
+      break;
     }
-    std::this_thread::sleep_for(std::chrono::microseconds(20));
+    e.cv.wait_for(lk, std::chrono::microseconds(50));
+    if (e.jobs.find(ticket) == e.jobs.end()) {
+      rc = SIM_E_UNKNOWN_TICKET;
+      break;
+    }
   }
-  const Derived &g = c->g;
-  const Plan &p = j->plan;
+  --e.fetching;
+  if (rc != SIM_OK) return rc;
+  j->claimed = true;
+  e.jobs.erase(ticket);
+  cudaStream_t s = e.egress[ticket % e.egress.size()];
+  lk.unlock();
+
   uint32_t status = 0;
-  cudaStream_t s = sl.stream;
-  if (spectrum) cudaMemcpyAsync(spectrum, j->block + p.spec, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-  if (signal) cudaMemcpyAsync(signal, j->block + p.sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
-  if (labels) cudaMemcpyAsync(labels, j->block + p.labels, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-  cudaMemcpyAsync(&status, j->block + p.status, 4, cudaMemcpyDeviceToHost, s);
-  const cudaError_t sync_rc = cudaStreamSynchronize(s);
-  float ms[kNumEvents - 1];
-  for (int i = 0; i + 1 < kNumEvents; ++i) {
-    ms[i] = 0.f;
-    cudaEventElapsedTime(&ms[i], sl.ev[i], sl.ev[i + 1]);
+  cudaError_t sync_rc = j->device_error;
+  if (j->launch_error == SIM_OK && j->block) {
+    const Derived &g = c->g;
+    const Plan &p = j->plan;
+    if (spectrum) cudaMemcpyAsync(spectrum, j->block + p.spec, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+    if (signal) cudaMemcpyAsync(signal, j->block + p.sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
+    if (labels) cudaMemcpyAsync(labels, j->block + p.labels, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+    cudaMemcpyAsync(&status, j->block + p.status, 4, cudaMemcpyDeviceToHost, s);
+    const cudaError_t cr = cudaStreamSynchronize(s);
+    if (sync_rc == cudaSuccess) sync_rc = cr;
   }
-  float whole = 0.f;
-  cudaEventElapsedTime(&whole, sl.ev[0], sl.ev[kNumEvents - 1]);
-  cudaFreeAsync(j->block, s);
+  if (j->block) cudaFreeAsync(j->block, s);
   {
     std::lock_guard<std::mutex> g2(e.mu);
-    for (int i = 0; i + 1 < kNumEvents; ++i) c->last_ms[i] = ms[i];
-    c->last_ms[kNumEvents - 1] = whole;
+    for (int i = 0; i < kNumEvents; ++i) c->last_ms[i] = j->ms[i];
     c->last_kernels = j->kernels;
-    release_locked(e, j);
+    e.used -= static_cast<int64_t>(j->plan.total);
     c->live--;
     e.cv.notify_all();
   }
+  const int launch_error = j->launch_error;
   delete j;
+  if (launch_error != SIM_OK) return launch_error;
   if (sync_rc != cudaSuccess) return SIM_E_CUDA;
   if (status & kStatusBadRay) return SIM_E_INVALID;
   if (status) return SIM_E_DEVICE;
@@ -668,8 +713,6 @@ int sim_destroy(sim_ctx *c) {
   std::vector<uint64_t> mine;
   {
     std::lock_guard<std::mutex> lk(e.mu);
-    for (auto &kv : e.jobs)
-      if (kv.second->ctx == c) mine.push_back(kv.first);
     // queued scenes of this context never start
     for (auto it = e.queue.begin(); it != e.queue.end();) {
       if ((*it)->ctx == c) {
@@ -682,15 +725,11 @@ int sim_destroy(sim_ctx *c) {
         ++it;
       }
     }
+    for (auto &kv : e.jobs)
+      if (kv.second->ctx == c && !kv.second->claimed) mine.push_back(kv.first);
+    e.cv.notify_all();
   }
-  for (uint64_t t : mine) {
-    bool known;
-    {
-      std::lock_guard<std::mutex> lk(e.mu);
-      known = e.jobs.count(t) != 0;
-    }
-    if (known) sim_fetch(c, t, nullptr, nullptr, nullptr, -1);
-  }
+  for (uint64_t t : mine) sim_fetch(c, t, nullptr, nullptr, nullptr, -1);
   while (c->live.load() > 0) std::this_thread::sleep_for(std::chrono::milliseconds(1));
   if (c->table_mem) cudaFree(c->table_mem);
   delete c;
