@@ -162,6 +162,139 @@ def run_reference(args, world, rank):
     return 0
 
 
+def run_batch_workload(args, rs, torch):
+    """64 uneven scenes (ray counts log-uniform 10k-500k, 128/256/512 chirps, 256/512 samples,
+    4 or 12 channels) as one batched, graph-captured device pipeline per step."""
+    scenes = scenegen.batch_scenes(seed=3000, n_scenes=64)
+    prec = rs.PRECISION_NAMES[args.precision]
+    ctxs = [rs.Context(radar, precision=prec) for radar, _ in scenes]
+    rays_s, metas, keep, outs = [], [], [], []
+    contrib = 0
+    for (radar, rays), ctx in zip(scenes, ctxs):
+        arr = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in rays.arrays().items()}
+        r, m = rs.make_rays(arr, rays.n)
+        rays_s.append(r)
+        metas.append(m)
+        keep.append(arr)
+        outs.append((torch.empty(ctx.cube_shape + (2,), dtype=torch.float32, device="cuda"),
+                     torch.empty(ctx.signal_shape + (2,), dtype=torch.float32, device="cuda"),
+                     torch.empty(ctx.cube_shape, dtype=torch.int32, device="cuda")))
+        contrib += rays.n * radar.n_virtual * radar.n_chirps * radar.n_samples
+    cargs = ([c.ctx for c in ctxs], rays_s, metas, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times, kernels = [], 0
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        rc, ms, kc = rs.sim_run_batch(*cargs)
+        if rc != rs.SIM_OK:
+            raise rs.SimError(rc, "sim_run_batch")
+        if s >= args.warmup:
+            times.append(ms)
+            kernels += kc
+    dev_s = sum(times) / 1e3
+    line = {"metric": METRIC, "value": contrib * len(times) / dev_s, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": "batch: 64 uneven scenes in one persistent graph-captured launch",
+                       "rays_total": int(sum(r.n for _, r in scenes)), "contributions_per_step": contrib,
+                       "precision": args.precision, "l2": "flushed (256 MB write) before each step"},
+            "frames_per_s": 64 * len(times) / dev_s, "gpu_launches": kernels}
+    print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+    return 0
+
+
+def run_serve_workload(args, rs, torch):
+    """Poisson arrivals (seeded trace) of automotive frames and, with probability p_img,
+    imaging frames, through sim_submit/sim_fetch; latency = result ready - arrival."""
+    import threading
+    prec = rs.PRECISION_NAMES[args.precision]
+    auto_radar = scenegen.radar_automotive()
+    auto_pool = [scenegen.automotive_scene(seed=4000 + i, n_rays=args.rays)[1] for i in range(4)]
+    img_radar, img_rays = scenegen.imaging_scene(seed=4100, n_rays=args.imaging_rays)
+    ctx_a = rs.Context(auto_radar, precision=prec)
+    ctx_i = rs.Context(img_radar, precision=prec)
+    pools = [{k: np.ascontiguousarray(v) for k, v in r.arrays().items()} for r in auto_pool]
+    img_arr = {k: np.ascontiguousarray(v) for k, v in img_rays.arrays().items()}
+    c_auto = args.rays * auto_radar.n_virtual * auto_radar.n_chirps * auto_radar.n_samples
+    c_img = img_rays.n * img_radar.n_virtual * img_radar.n_chirps * img_radar.n_samples
+    # seeded arrival trace
+    n_arr = int(args.rate * args.duration * 1.5) + 16
+    gaps = -np.log(1.0 - scenegen.uniform(4200, 1, n_arr)) / args.rate
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < args.duration]
+    is_img = scenegen.uniform(4200, 2, arrivals.shape[0]) < args.p_img
+    # warm-up: one of each kind
+    for ctx, arr, nr in ((ctx_a, pools[0], args.rays), (ctx_i, img_arr, img_rays.n)):
+        t = ctx.submit(arr, nr)
+        assert ctx.fetch(t) == rs.SIM_OK
+    outstanding, lat, done_contrib, refused = [], [], [0], [0]
+    lock = threading.Lock()
+    stop = [False]
+    t0 = time.perf_counter()
+
+    def fetcher():
+        while True:
+            with lock:
+                items = list(outstanding)
+            if not items and stop[0]:
+                return
+            progressed = False
+            for it in items:
+                ticket, ctx, t_arr, contrib = it
+                rc = ctx.fetch(ticket, timeout_ms=0)
+                if rc == rs.SIM_OK:
+                    now = time.perf_counter() - t0
+                    with lock:
+                        outstanding.remove(it)
+                        lat.append(now - t_arr)
+                        done_contrib[0] += contrib
+                    progressed = True
+            if not progressed:
+                time.sleep(0.0001)
+
+    th = threading.Thread(target=fetcher)
+    th.start()
+    for k, ta in enumerate(arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        img = bool(is_img[k])
+        ctx, arr, nr, cc = (ctx_i, img_arr, img_rays.n, c_img) if img else (ctx_a, pools[k % 4], args.rays, c_auto)
+        try:
+            ticket = ctx.submit(arr, nr)
+        except rs.SimError as e:
+            if e.code == rs.SIM_E_BUSY:
+                refused[0] += 1
+                continue
+            raise
+        with lock:
+            outstanding.append((ticket, ctx, float(ta), cc))
+    stop[0] = True
+    th.join()
+    wall = time.perf_counter() - t0
+    lat_ms = np.array(lat) * 1e3
+    line = {"metric": METRIC, "value": done_contrib[0] / wall, "unit": UNIT, "n_gpus": 1,
+            "steps": int(arrivals.shape[0]), "warmup": 2, "ms_per_step": float(np.median(lat_ms)) if lat else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": f"serve: Poisson {args.rate}/s for {args.duration}s, automotive frames "
+                                   f"({args.rays} rays) + imaging frames ({img_rays.n} rays, p={args.p_img})",
+                       "precision": args.precision},
+            "latency_ms": {"p50": float(np.percentile(lat_ms, 50)) if lat else None,
+                           "p99": float(np.percentile(lat_ms, 99)) if lat else None,
+                           "max": float(lat_ms.max()) if lat else None},
+            "completed": len(lat), "refused_busy": refused[0], "imaging_arrivals": int(is_img.sum()),
+            "frames_per_s": len(lat) / wall, "wall_s": wall}
+    print(json.dumps(line), flush=True)
+    ctx_a.close()
+    ctx_i.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,6 +308,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-points", type=int, default=2048)
     ap.add_argument("--clocks-csv", default=os.path.join(ROOT, "gpurun_out", "bench_clocks.csv"))
+    ap.add_argument("--workload", default="automotive", choices=["automotive", "batch", "serve"])
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrivals per second")
+    ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
+    ap.add_argument("--p-img", type=float, default=0.002, help="serve: probability of an imaging frame")
+    ap.add_argument("--imaging-rays", type=int, default=1_000_000)
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
@@ -183,6 +321,11 @@ def main():
     import torch
     import torch.distributed as dist
     from paper_2305_14176_gb300 import radarsim as rs
+
+    if args.workload == "batch":
+        return run_batch_workload(args, rs, torch)
+    if args.workload == "serve":
+        return run_serve_workload(args, rs, torch)
 
     if world > 1:
         dist.init_process_group("nccl")

@@ -177,6 +177,23 @@ SIM_API int sim_last_stage_ms(sim_ctx *ctx, float *ms, int32_t n);
 /* Number of kernels the most recently fetched ticket of this context launched. */
 SIM_API int sim_last_kernel_count(sim_ctx *ctx, int32_t *count);
 
+/* Run a batch of scenes as one device pipeline: per-scene prep, ONE persistent
+   tensor-core launch over the (scene, tile, split) work units of all scenes, longest
+   first, then per-scene split reduction, FFTs and labels.  The pipeline is captured into
+   a CUDA graph the first time a batch shape (every scene's radar constants and ray count,
+   in order) is seen, and replayed on later calls of the same shape (a few shapes are
+   cached).  Each scene gives bit-identical results to sim_submit/sim_fetch of it alone.
+   ctxs[i] may repeat or differ; all must use one tensor-core precision (not FP32_DIRECT).
+   rays[i], meta[i]: as for sim_submit (host or device).  spectra / signals / labels:
+   arrays of n output pointers (host or device, layouts as for sim_fetch), each array or
+   entry may be NULL.  Synchronous.  device_ms (nullable) receives the device time of the
+   pipeline without the input and output copies; kernel_count (nullable) the number of
+   kernels it launched.
+   Errors: SIM_E_INVALID, SIM_E_NOMEM, SIM_E_CUDA, SIM_E_DEVICE. */
+SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_rays *rays, const sim_meta *meta,
+                          void *const *spectra, void *const *signals, int32_t *const *labels, float *device_ms,
+                          int32_t *kernel_count);
+
 /* Self-test of the tensor-core tile path on caller data (not a simulation call):
    D[M][N] = A[M][K] * B[N][K]^T with A, B row-major 16-bit (f16 != 0: FP16, else
    BF16) device matrices and D row-major FP32 device memory, through the same shared

@@ -56,15 +56,6 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 }  // namespace
 
-struct sim_ctx {
-  Derived g;
-  Tables t;
-  void *table_mem = nullptr;
-  float last_ms[8] = {};
-  int last_kernels = 0;
-  std::atomic<int> live{0};
-};
-
 namespace {
 
 // A scene's life: queued (pending, host copy of its inputs) -> running (a slot: stream and
@@ -457,6 +448,7 @@ int upload_tables(sim_ctx *c) {
     }
     off += align256(8 * static_cast<size_t>(ffts[a] / 2));
   }
+  c->table_bytes = bytes;
   if (cudaMalloc(&c->table_mem, bytes) != cudaSuccess) {
     cudaGetLastError();
     return SIM_E_NOMEM;

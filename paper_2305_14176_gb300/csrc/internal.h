@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "radarsim.h"
 
 namespace rs {
@@ -85,6 +87,27 @@ int64_t umma_workspace_bytes(const Derived &g, int64_t n);
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace,
                     uint32_t *status, cudaStream_t s, cudaEvent_t after_main);
 
+// ---- batched tensor-core ray sum (one persistent launch over several scenes)
+struct UmmaBatch {
+  unsigned *counter;  // work-list cursor (device)
+  void *args;         // per-scene kernel arguments (device)
+  void *units;        // work list, longest first (device)
+  int n_units, n_scenes, bn_max;
+  bool f16, split;
+};
+// device bytes of the batch's descriptors and counter
+int64_t umma_batch_scratch_bytes(int n_scenes, int64_t n_units);
+// work units (tiles x splits) of one scene: the same decomposition as a single-scene launch
+int64_t umma_units_of(const Derived &g, int64_t n);
+// upload the descriptors (synchronous, not for stream capture); all scenes share one
+// tensor-core precision, else SIM_E_INVALID
+int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *ps, const int64_t *ns,
+                       void *const *workspaces, uint32_t *const *statuses, void *scratch, cudaStream_t s,
+                       UmmaBatch *out);
+int launch_umma_batch(const UmmaBatch &b, cudaStream_t s);
+int launch_umma_pre(const Derived &g, RaysPrep p, int64_t n, void *workspace, cudaStream_t s);
+int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s);
+
 // Validate sim_radar_params and derive the radar constants (SIM_OK or SIM_E_INVALID).
 int derive_radar(const sim_radar_params *p, Derived *g);
 
@@ -95,3 +118,15 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
                        uint32_t *status, cudaStream_t s);
 
 }  // namespace rs
+
+// One radar configuration (the C ABI's opaque handle).
+struct sim_ctx {
+  rs::Derived g;
+  rs::Tables t;
+  void *table_mem = nullptr;  // window and twiddle tables (device)
+  size_t table_bytes = 0;
+  float last_ms[8] = {};
+  int last_kernels = 0;
+  std::atomic<int> live{0};   // tickets not yet fetched
+};
+

@@ -24,6 +24,9 @@
 //
 // Every mbarrier wait is bounded; a wait that runs out sets a status bit, the CTA stops
 // issuing work, drains what it issued, frees its tensor memory and returns.
+#include <algorithm>
+#include <vector>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -383,14 +386,34 @@ __device__ __forceinline__ void copy_stage(const Args &g, uint8_t *a_hi, uint8_t
   }
 }
 
+// One work unit: a 128-row x bn-column tile of one scene summed over one chunk of its rays.
+struct Unit {
+  int scene, tile_m, tile_n, split;
+};
+
+// A launch of the ray-sum kernel: either one scene whose units are decoded from the CTA
+// index (one unit per CTA), or a persistent batch whose CTAs take units from a work list
+// (longest first) through an atomic counter.
+struct Launch {
+  Args inline_scene;     // used when `scenes` is null
+  const Args *scenes;    // per-scene arguments in device memory, or null
+  const Unit *units;     // work list in device memory, or null (decode from inline_scene)
+  int n_units;
+  int mt, nt;            // tiles of the inline scene (for decoding)
+  unsigned *counter;     // persistent mode: next unit to take (zeroed before the launch)
+  int bn_layout;         // B rows the shared-memory stages are laid out for (max bn)
+};
+
 template <bool F16, bool SPLIT, bool TEST>
-__global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
+__global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ Args s_args;
+  __shared__ Unit s_unit;
+  __shared__ int s_abort;
   constexpr int NST = SPLIT ? 2 : 4;
   constexpr uint32_t TMEM_COLS = 512;  // accumulator (0..255) and running sum (256..511)
-  const int bn = g.bn;
   const uint32_t a_bytes = BM * KELEM * 2;
-  const uint32_t b_bytes = static_cast<uint32_t>(bn) * KELEM * 2;
+  const uint32_t b_bytes = static_cast<uint32_t>(L.bn_layout) * KELEM * 2;
   const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
   uint8_t *base = smem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
@@ -399,18 +422,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NST);
   const uint32_t accf = smem_u32(bars + 2 * NST), acce = smem_u32(bars + 2 * NST + 1);
   const uint32_t done = smem_u32(bars + 2 * NST + 2);
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile_m = blockIdx.x, tile_n = blockIdx.y, split = blockIdx.z;
-  const int row0 = tile_m * BM;
-  const int col0 = tile_n * bn;  // real column; complex n0 = col0 / 2
-  const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
-  const int64_t k_total = TEST ? g.test_k / 2 : g.n_rays;  // rays (K pairs)
-  const int64_t k_hi = k_lo + g.chunk < k_total ? k_lo + g.chunk : k_total;
-  const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
-  const int SUBST = SPLIT ? SUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
-  const int n_sub = (n_stages + SUBST - 1) / SUBST;
-  const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -421,133 +433,187 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Args g) {
     mbar_init(acce, NDRAIN);
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
   if (warp == MMA_WARP) tmem_alloc(smem_u32(tmem_holder), TMEM_COLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
-  bool failed = false;
 
-  if (warp < MMA_WARP) {
-    // ---------------- producers
-    const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
-    const bool fast = (g.nc % BM) == 0;  // rows of a tile share one channel and all exist
-    const int my_ray = ((threadIdx.x >> 6) << 2) + (threadIdx.x & 3);
-    RayRegs cur{}, nxt{};
-    if (!TEST && n_stages > 0) load_ray(g, k_lo + my_ray, k_lo + my_ray < k_hi, cur);
-    for (int st = 0; st < n_stages; ++st) {
-      const int s = st % NST;
-      const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
-      if (!TEST && st + 1 < n_stages) {  // prefetch the next stage's ray while this one is built
-        const int64_t nr = ray0 + KS + my_ray;
-        load_ray(g, nr, nr < k_hi, nxt);
-      }
-      if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
-        failed = true;
-        break;
-      }
-      uint8_t *a_hi = base + s * stage_bytes;
-      uint8_t *b_hi = a_hi + a_bytes;
-      uint8_t *a_lo = b_hi + b_bytes;
-      uint8_t *b_lo = a_lo + a_bytes;
-      if constexpr (TEST) {
-        copy_stage(g, a_hi, b_hi, ray0, row0, col0);
+  // running counters shared by every role: pipeline stages, accumulation chains, units
+  int gst = 0, gsub = 0, gunit = 0;
+  int u = static_cast<int>(blockIdx.x);
+  if (L.counter) {
+    if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
+    __syncthreads();
+    u = s_unit.scene;
+    __syncthreads();
+  }
+  while (u < L.n_units) {
+    if (threadIdx.x == 0) {
+      if (L.units) {
+        s_unit = L.units[u];
       } else {
-        if (fast) produce_stage<F16, SPLIT, true>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
-        else produce_stage<F16, SPLIT, false>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
-        cur = nxt;
+        const int per = L.mt * L.nt;
+        s_unit.scene = 0;
+        s_unit.split = u / per;
+        s_unit.tile_n = (u - s_unit.split * per) / L.mt;
+        s_unit.tile_m = u - s_unit.split * per - s_unit.tile_n * L.mt;
       }
-      fence_proxy_async();
-      mbar_arrive(full0 + 8 * s);
+      s_args = L.scenes ? L.scenes[s_unit.scene] : L.inline_scene;
     }
-  } else if (warp == MMA_WARP) {
-    // ---------------- MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = make_idesc(F16, BM, bn);
-      const uint32_t sbase = smem_u32(base);
-      bool open = false;  // issued MMAs not yet committed to acc_full
+    __syncthreads();
+    const Args &g = s_args;
+    const int bn = g.bn;
+    const int row0 = s_unit.tile_m * BM;
+    const int col0 = s_unit.tile_n * bn;  // real column; complex n0 = col0 / 2
+    const int split = s_unit.split;
+    const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
+    const int64_t k_total = TEST ? g.test_k / 2 : g.n_rays;  // rays (K pairs)
+    const int64_t k_hi = k_lo + g.chunk < k_total ? k_lo + g.chunk : k_total;
+    const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
+    const int SUBST = SPLIT ? SUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
+    const int n_sub = (n_stages + SUBST - 1) / SUBST;
+    const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
+    bool failed = false;
+
+    if (warp < MMA_WARP) {
+      // ---------------- producers
+      const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
+      const bool fast = (g.nc % BM) == 0;  // rows of a tile share one channel and all exist
+      const int my_ray = ((threadIdx.x >> 6) << 2) + (threadIdx.x & 3);
+      RayRegs cur{}, nxt{};
+      if (!TEST && n_stages > 0) load_ray(g, k_lo + my_ray, k_lo + my_ray < k_hi, cur);
       for (int st = 0; st < n_stages; ++st) {
-        const int s = st % NST;
-        const int sub = st / SUBST;
-        const bool first = (st % SUBST) == 0;
-        if (first && sub > 0 && !mbar_wait(acce, (sub - 1) & 1)) {
+        const int gs = gst + st;
+        const int s = gs % NST;
+        const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
+        if (!TEST && st + 1 < n_stages) {  // prefetch the next stage's ray while this one is built
+          const int64_t nr = ray0 + KS + my_ray;
+          load_ray(g, nr, nr < k_hi, nxt);
+        }
+        if (gs >= NST && !mbar_wait(empty0 + 8 * s, ((gs / NST) - 1) & 1)) {
           failed = true;
           break;
         }
-        if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+        uint8_t *a_hi = base + s * stage_bytes;
+        uint8_t *b_hi = a_hi + a_bytes;
+        uint8_t *a_lo = b_hi + b_bytes;
+        uint8_t *b_lo = a_lo + a_bytes;
+        if constexpr (TEST) {
+          copy_stage(g, a_hi, b_hi, ray0, row0, col0);
+        } else {
+          if (fast) produce_stage<F16, SPLIT, true>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
+          else produce_stage<F16, SPLIT, false>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
+          cur = nxt;
+        }
+        fence_proxy_async();
+        mbar_arrive(full0 + 8 * s);
+      }
+    } else if (warp == MMA_WARP) {
+      // ---------------- MMA issuer
+      if (lane == 0) {
+        const uint32_t idesc = make_idesc(F16, BM, bn);
+        const uint32_t sbase = smem_u32(base);
+        bool open = false;  // issued MMAs not yet committed to acc_full
+        for (int st = 0; st < n_stages; ++st) {
+          const int gs = gst + st;
+          const int s = gs % NST;
+          const int gc = gsub + st / SUBST;  // this chain's index across the CTA's life
+          const bool first = (st % SUBST) == 0;
+          if (first && gc > 0 && !mbar_wait(acce, (gc - 1) & 1)) {
+            failed = true;
+            break;
+          }
+          if (!mbar_wait(full0 + 8 * s, (gs / NST) & 1)) {
+            failed = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_hi = sbase + s * stage_bytes, b_hi = a_hi + a_bytes;
+          const uint32_t a_lo = b_hi + b_bytes, b_lo = a_lo + a_bytes;
+#pragma unroll
+          for (int kk = 0; kk < KELEM / 16; ++kk) {
+            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+            const uint64_t da = make_sdesc(a_hi + kk * 2 * lbo_a, lbo_a, 128);
+            const uint64_t db = make_sdesc(b_hi + kk * 2 * lbo_b, lbo_b, 128);
+            mma_f16(tmem, da, db, idesc, acc);
+            if constexpr (SPLIT) {
+              mma_f16(tmem, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, 1u);
+              mma_f16(tmem, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
+            }
+          }
+          open = true;
+          mma_commit(empty0 + 8 * s);
+          if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
+            mma_commit(accf);
+            open = false;
+          }
+        }
+        if (open) mma_commit(accf);
+        // every issued MMA of this unit has completed once `done` fires
+        mma_commit(done);
+        if (!mbar_wait(done, gunit & 1)) failed = true;
+      }
+    } else {
+      // ---------------- drain: TMEM lane quarter (warp % 4).  Each finished chain is added in
+      // FP32 (round to nearest) to the running sum kept in tensor memory; after the last chain
+      // the sum goes to this split's partial in global memory.
+      const int q = warp & 3;
+      const int grow = row0 + q * 32 + lane;
+      float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
+      const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      if (n_stages == 0 && grow < g.m_rows) {
+        for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int sub = 0; sub < n_sub; ++sub) {
+        if (!mbar_wait_sleep(accf, (gsub + sub) & 1)) {
           failed = true;
           break;
         }
         tc_fence_after();
-        const uint32_t a_hi = sbase + s * stage_bytes, b_hi = a_hi + a_bytes;
-        const uint32_t a_lo = b_hi + b_bytes, b_lo = a_lo + a_bytes;
+        const bool last = sub == n_sub - 1;
+        for (int c = 0; c < bn; c += 32) {
+          uint32_t h[32];
+          tmem_ld32(trow + static_cast<uint32_t>(c), h);
+          if (sub > 0) {
+            uint32_t r[32];
+            tmem_ld32(trow + kSumCol + static_cast<uint32_t>(c), r);
 #pragma unroll
-        for (int kk = 0; kk < KELEM / 16; ++kk) {
-          const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-          const uint64_t da = make_sdesc(a_hi + kk * 2 * lbo_a, lbo_a, 128);
-          const uint64_t db = make_sdesc(b_hi + kk * 2 * lbo_b, lbo_b, 128);
-          mma_f16(tmem, da, db, idesc, acc);
-          if constexpr (SPLIT) {
-            mma_f16(tmem, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, 1u);
-            mma_f16(tmem, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
+            for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+          }
+          if (!last) {
+            tmem_st32(trow + kSumCol + static_cast<uint32_t>(c), h);
+          } else if (grow < g.m_rows) {
+#pragma unroll
+            for (int x = 0; x < 32; x += 4)
+              *reinterpret_cast<float4 *>(dst + c + x) =
+                  make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
+                              __uint_as_float(h[x + 3]));
           }
         }
-        open = true;
-        mma_commit(empty0 + 8 * s);
-        if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
-          mma_commit(accf);
-          open = false;
-        }
+        if (!last) tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive(acce);
       }
-      if (open) mma_commit(accf);
-      // every issued MMA has completed once `done` fires
-      mma_commit(done);
-      if (!mbar_wait(done, 0)) failed = true;
     }
-  } else {
-    // ---------------- drain: TMEM lane quarter (warp % 4).  Each finished chain is added in
-    // FP32 (round to nearest) to the running sum kept in tensor memory; after the last chain
-    // the sum goes to this split's partial in global memory.
-    const int q = warp & 3;
-    const int grow = row0 + q * 32 + lane;
-    float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
-    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    if (n_stages == 0 && grow < g.m_rows) {
-      for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (failed) {
+      atomicOr(g.status, kStatusWaitLimit);
+      s_abort = 1;
     }
-    for (int sub = 0; sub < n_sub; ++sub) {
-      if (!mbar_wait_sleep(accf, sub & 1)) {
-        failed = true;
-        break;
-      }
-      tc_fence_after();
-      const bool last = sub == n_sub - 1;
-      for (int c = 0; c < bn; c += 32) {
-        uint32_t h[32];
-        tmem_ld32(trow + static_cast<uint32_t>(c), h);
-        if (sub > 0) {
-          uint32_t r[32];
-          tmem_ld32(trow + kSumCol + static_cast<uint32_t>(c), r);
-#pragma unroll
-          for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
-        }
-        if (!last) {
-          tmem_st32(trow + kSumCol + static_cast<uint32_t>(c), h);
-        } else if (grow < g.m_rows) {
-#pragma unroll
-          for (int x = 0; x < 32; x += 4)
-            *reinterpret_cast<float4 *>(dst + c + x) =
-                make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
-                            __uint_as_float(h[x + 3]));
-        }
-      }
-      if (!last) tmem_wait_st();
-      tc_fence_before();
-      mbar_arrive(acce);
-    }
+    gst += n_stages;
+    gsub += n_sub;
+    ++gunit;
+    tc_fence_before();
+    __syncthreads();  // every role is done with this unit (and with s_args)
+    tc_fence_after();
+    if (!L.counter || s_abort) break;
+    if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
+    __syncthreads();
+    u = s_unit.scene;
+    __syncthreads();
   }
-  if (failed) atomicOr(g.status, kStatusWaitLimit);
   tc_fence_before();
   __syncthreads();
   if (warp == MMA_WARP) {
@@ -651,21 +717,32 @@ size_t smem_bytes(bool split, int bn) {
   return nst * stage + 8 * (2 * nst + 3) + 16;
 }
 
-constexpr int kMaxDynSmem = 232448;  // 227 KB
+constexpr int kMaxDynSmem = 232448 - 2048;  // 227 KB per block, less the kernel's static shared memory
 
 template <bool F16, bool SPLIT, bool TEST>
-void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
-  // the self-test reserves the whole shared memory so that every descriptor it builds
-  // points inside the allocation
-  const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn);
+void set_smem_attr() {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256)));
     attr = true;
   }
-  dim3 grid(sh.mt, sh.nt, sh.splits);
-  umma_sum_kernel<F16, SPLIT, TEST><<<grid, NTHREADS_ALL, sm, s>>>(a);
+}
+
+// one scene, one unit per CTA
+template <bool F16, bool SPLIT, bool TEST>
+void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
+  // the self-test reserves the whole shared memory so that every descriptor it builds
+  // points inside the allocation
+  const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn);
+  set_smem_attr<F16, SPLIT, TEST>();
+  Launch L{};
+  L.inline_scene = a;
+  L.n_units = sh.mt * sh.nt * sh.splits;
+  L.mt = sh.mt;
+  L.nt = sh.nt;
+  L.bn_layout = sh.bn;
+  umma_sum_kernel<F16, SPLIT, TEST><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
 }
 
 }  // namespace
@@ -714,6 +791,128 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
   ++kernels;
   return kernels;
+}
+
+// ---- batch: one persistent launch over the units of several scenes
+int64_t umma_batch_scratch_bytes(int n_scenes, int64_t n_units) {
+  return 256 + static_cast<int64_t>(sizeof(Args)) * n_scenes + static_cast<int64_t>(sizeof(Unit)) * n_units;
+}
+
+int64_t umma_units_of(const Derived &g, int64_t n) {
+  const Shape sh = plan_shape(g, n);
+  return static_cast<int64_t>(sh.mt) * sh.nt * sh.splits;
+}
+
+int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *ps, const int64_t *ns,
+                       void *const *workspaces, uint32_t *const *statuses, void *scratch, cudaStream_t s,
+                       UmmaBatch *out) {
+  std::vector<Args> args(static_cast<size_t>(n_scenes));
+  std::vector<Unit> units;
+  std::vector<int64_t> cost;
+  bool f16 = false, split = false;
+  int bn_max = 32;
+  for (int i = 0; i < n_scenes; ++i) {
+    const Derived &g = *gs[i];
+    const Shape sh = plan_shape(g, ns[i]);
+    const bool fi = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+    const bool si = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+    if (i == 0) {
+      f16 = fi;
+      split = si;
+    } else if (fi != f16 || si != split || g.precision == SIM_PREC_FP32_DIRECT) {
+      return SIM_E_INVALID;
+    }
+    if (g.precision == SIM_PREC_FP32_DIRECT) return SIM_E_INVALID;
+    Args &a = args[static_cast<size_t>(i)];
+    a = Args{};
+    a.p = ps[i];
+    a.n_rays = ns[i];
+    a.chunk = sh.chunk;
+    a.nc = g.nc;
+    a.ns = g.ns;
+    a.m_rows = g.nv * g.nc;
+    a.bn = sh.bn;
+    a.partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspaces[i]) + 256);
+    a.amax_bits = static_cast<const uint32_t *>(workspaces[i]);
+    a.status = statuses[i];
+    if (sh.bn > bn_max) bn_max = sh.bn;
+    for (int sp = 0; sp < sh.splits; ++sp) {
+      const int64_t rays = std::min<int64_t>(sh.chunk, ns[i] - sp * sh.chunk);
+      for (int tn = 0; tn < sh.nt; ++tn)
+        for (int tm = 0; tm < sh.mt; ++tm) {
+          units.push_back(Unit{i, tm, tn, sp});
+          cost.push_back(std::max<int64_t>(rays, 0) * sh.bn);
+        }
+    }
+  }
+  // longest first (stable: ties keep scene, split, tile order)
+  std::vector<size_t> order(units.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+  std::vector<Unit> sorted(units.size());
+  for (size_t k = 0; k < order.size(); ++k) sorted[k] = units[order[k]];
+  uint8_t *scr = static_cast<uint8_t *>(scratch);
+  out->counter = reinterpret_cast<unsigned *>(scr);
+  out->args = scr + 256;
+  out->units = scr + 256 + sizeof(Args) * static_cast<size_t>(n_scenes);
+  out->n_units = static_cast<int>(sorted.size());
+  out->n_scenes = n_scenes;
+  out->f16 = f16;
+  out->split = split;
+  out->bn_max = bn_max;
+  if (cudaMemcpyAsync(out->args, args.data(), sizeof(Args) * args.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(out->units, sorted.data(), sizeof(Unit) * sorted.size(), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return SIM_E_CUDA;
+  set_smem_attr<true, true, false>();
+  set_smem_attr<true, false, false>();
+  set_smem_attr<false, true, false>();
+  set_smem_attr<false, false, false>();
+  return SIM_OK;
+}
+
+int launch_umma_batch(const UmmaBatch &b, cudaStream_t s) {
+  Launch L{};
+  L.scenes = static_cast<const Args *>(b.args);
+  L.units = static_cast<const Unit *>(b.units);
+  L.n_units = b.n_units;
+  L.counter = b.counter;
+  L.bn_layout = b.bn_max;
+  const size_t sm = smem_bytes(b.split, b.bn_max);
+  const int grid = std::min(b.n_units, num_sms());
+  cudaMemsetAsync(b.counter, 0, 4, s);
+  if (b.f16) {
+    if (b.split) umma_sum_kernel<true, true, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+    else umma_sum_kernel<true, false, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+  } else {
+    if (b.split) umma_sum_kernel<false, true, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+    else umma_sum_kernel<false, false, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+  }
+  return 1;
+}
+
+// amax (FP16 scaling) and split reduction of one scene of a batch, around the batched GEMM
+int launch_umma_pre(const Derived &g, RaysPrep p, int64_t n, void *workspace, cudaStream_t s) {
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  cudaMemsetAsync(amax, 0, 4, s);
+  if (f16 && n > 0) {
+    amax_kernel<<<2 * num_sms(), 256, 0, s>>>(p.amp, n, amax);
+    return 1;
+  }
+  return 0;
+}
+
+int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s) {
+  const Shape sh = plan_shape(g, n);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
+  const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  return 1;
 }
 
 int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, int64_t ws_bytes,

@@ -76,6 +76,9 @@ def _load() -> ctypes.CDLL:
     lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.sim_selftest_umma.argtypes = [I32, I32, I32, I64, P, P, P, P]
     lib.sim_raysum_noalloc.argtypes = [ctypes.POINTER(sim_radar_params), ctypes.POINTER(sim_rays), P, P]
+    lib.sim_run_batch.argtypes = [I32, P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), P, P, P,
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]
+    lib.sim_run_batch.restype = ctypes.c_int
     for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
               "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma", "sim_raysum_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
@@ -145,6 +148,27 @@ def sim_raysum_noalloc(params: sim_radar_params, rays: sim_rays, signal, stream=
     """Beat-signal cube into a device buffer with no device allocation (see the header)."""
     return lib.sim_raysum_noalloc(ctypes.byref(params), ctypes.byref(rays), _addr(signal),
                                   _addr(stream) if stream is not None else None)
+
+
+def sim_run_batch(ctxs, rays, metas, spectra=None, signals=None, labels=None):
+    """One batched device pipeline over several scenes (see include/radarsim.h).
+    ctxs: list of sim_ctx handles; rays / metas: lists of sim_rays / sim_meta; spectra,
+    signals, labels: lists of output buffers (or None).  Returns (status, device_ms, kernels)."""
+    n = len(ctxs)
+    carr = (ctypes.c_void_p * n)(*[c.value if hasattr(c, "value") else c for c in ctxs])
+    rarr = (sim_rays * n)(*rays)
+    marr = (sim_meta * n)(*metas)
+
+    def ptrs(bufs):
+        if bufs is None:
+            return None
+        return (ctypes.c_void_p * n)(*[_addr(b) for b in bufs])
+
+    ms = ctypes.c_float()
+    kc = ctypes.c_int32()
+    rc = lib.sim_run_batch(n, carr, rarr, marr, ptrs(spectra), ptrs(signals), ptrs(labels), ctypes.byref(ms),
+                           ctypes.byref(kc))
+    return int(rc), float(ms.value), int(kc.value)
 
 
 def sim_destroy(ctx) -> int:
