@@ -61,6 +61,25 @@ def _dist():
     return world, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """Seed of the frame a rank simulates: replicas run independent frames."""
+    return 1000 + rank
+
+
+def max_over_ranks(seconds: float, world: int, dist, device) -> float:
+    """The slowest rank's time (the only cross-rank exchange; no data-path collective)."""
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(contrib_per_step: int, steps: int, world: int, max_seconds: float) -> float:
+    """Contributions of all ranks over the slowest rank's time."""
+    return contrib_per_step * steps * world / max_seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -331,7 +350,7 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    radar, rays = scenegen.automotive_scene(seed=1000 + rank, n_rays=args.rays)
+    radar, rays = scenegen.automotive_scene(seed=replica_seed(rank), n_rays=args.rays)
     prec = rs.PRECISION_NAMES[args.precision]
     ctx = rs.Context(radar, precision=prec)
     n = rays.n
@@ -379,11 +398,8 @@ def main():
     if world > 1:
         dist.barrier()
     dev_s = sum(totals) / 1e3
-    t = torch.tensor([dev_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    dev_s_max = float(t.item())
-    value = contrib * args.steps * world / dev_s_max
+    dev_s_max = max_over_ranks(dev_s, world, dist, dev)
+    value = whole_job_rate(contrib, args.steps, world, dev_s_max)
 
     # end to end through the same calls with pinned host buffers
     e2e_times = []
@@ -395,10 +411,8 @@ def main():
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             e2e_times.append(dt)
-    e2e_s = torch.tensor([sum(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = contrib * args.steps * world / float(e2e_s.item())
+    e2e_max = max_over_ranks(sum(e2e_times), world, dist, dev)
+    e2e_value = whole_job_rate(contrib, args.steps, world, e2e_max)
     h2d = sum(int(v.numel() * v.element_size()) for v in host_in.values())
     d2h = sum(int(v.numel() * v.element_size()) for v in (h_spec, h_sig, h_lab))
 
@@ -439,7 +453,7 @@ def main():
         "frames_per_s": args.steps * world / dev_s_max,
         "stage_ms_mean": {k: v / args.steps for k, v in stages_sum.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": 1e3 * float(e2e_s.item()) / args.steps},
+                "ms_per_step": 1e3 * e2e_max / args.steps},
         "gpu_launches": kernels,
         "roofline": roof,
         "cpu_baseline": cpu,

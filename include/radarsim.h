@@ -194,6 +194,32 @@ SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_rays *rays,
                           void *const *spectra, void *const *signals, int32_t *const *labels, float *device_ms,
                           int32_t *kernel_count);
 
+/* ---- autotuner ----
+   sim_autotune times, on the device and with synthetic rays of the context's shape,
+   the tensor-core ray sum at several split-K counts and the FFT passes at several tile
+   widths, and stores the fastest choice in a process-wide table keyed by (N_v, N_c,
+   N_s, N_a, precision, ceil(log2 n_rays)).  Every later launch of that shape uses it
+   (single scenes, batches, sim_raysum_noalloc), so tune before serving: results of one
+   shape stay bit-identical for as long as the table does.  out (nullable) receives the
+   choice and its timings.  Errors: SIM_E_INVALID, SIM_E_NOMEM, SIM_E_CUDA. */
+typedef struct {
+  int32_t splits;            /* split-K count of the ray sum (0: FP32 direct, not tuned) */
+  int32_t fft_range_points;  /* points per block of the range FFT (0: built-in choice) */
+  int32_t fft_doppler_strip; /* samples per block of the Doppler FFT (0: built-in) */
+  int32_t fft_angle_strip;   /* (m, n) positions per block of the angle FFT (0: built-in) */
+  float ray_sum_ms;          /* device time of the chosen ray sum */
+  float fft_ms;              /* device time of the chosen FFTs */
+} sim_tuning;
+SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *out);
+/* Write / read the table as a JSON array, one object per line.  Loading adds to the
+   table (entries with out-of-range values are skipped).  The engine loads the file named
+   by the environment variable RADARSIM_TUNE_CACHE when it starts. */
+SIM_API int sim_tuning_save(const char *path);
+SIM_API int sim_tuning_load(const char *path);
+SIM_API int sim_tuning_clear(void);
+/* number of tuned shapes in the table (not a status) */
+SIM_API int sim_tuning_count(void);
+
 /* Self-test of the tensor-core tile path on caller data (not a simulation call):
    D[M][N] = A[M][K] * B[N][K]^T with A, B row-major 16-bit (f16 != 0: FP16, else
    BF16) device matrices and D row-major FP32 device memory, through the same shared

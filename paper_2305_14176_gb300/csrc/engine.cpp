@@ -12,6 +12,7 @@
 // Results stay on the device until sim_fetch copies them out and releases the block.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -356,6 +357,7 @@ int start_engine_locked(Engine &e) {
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SIM_E_CUDA;
   std::thread(worker_main).detach();
   e.ready = true;
+  if (const char *tc = getenv("RADARSIM_TUNE_CACHE")) sim_tuning_load(tc);
   return SIM_OK;
 }
 

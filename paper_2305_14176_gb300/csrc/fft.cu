@@ -123,6 +123,14 @@ bool g_attr_done = false;
 }  // namespace
 
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s) {
+  Tuning tu{};
+  const bool have = tuning_lookup(g, -1, &tu);
+  if (!have) tu = Tuning{};
+  return launch_fft_with(g, t, sig, tmp, spec, s, tu);
+}
+
+int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec,
+                    cudaStream_t s, const Tuning &tu) {
   if (!g_attr_done) {
     cudaFuncSetAttribute(fft_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
     cudaFuncSetAttribute(fft_doppler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
@@ -131,20 +139,24 @@ int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp
   }
   // range: rows of N_s, about 2048 points per block
   const int64_t rows = static_cast<int64_t>(g.nv) * g.nc;
-  const int lpc = g.ns >= 2048 ? 1 : 2048 / g.ns;
+  int points = tu.fft_range_points > 0 ? tu.fft_range_points : 2048;
+  if (points > 4096) points = 4096;
+  const int lpc = g.ns >= points ? 1 : points / g.ns;
   const int64_t rb = (rows + lpc - 1) / lpc;
   fft_range_kernel<<<static_cast<unsigned>(rb), 256, sizeof(float2) * lpc * g.ns, s>>>(
       sig, tmp, t.win_r, t.tw_r, g.ns, g.log2_ns, lpc, rows);
   // Doppler: strips of TW samples, N_c * TW * 8 bytes <= 64 KB
   int twd = 8192 / g.nc;
-  if (twd > 16) twd = 16;
+  const int twd_pref = tu.fft_doppler_strip > 0 ? tu.fft_doppler_strip : 16;
+  if (twd > twd_pref) twd = twd_pref;
   if (twd > g.ns) twd = g.ns;
   dim3 gd(g.ns / twd, g.nv);
   fft_doppler_kernel<<<gd, 256, sizeof(float2) * g.nc * twd, s>>>(tmp, t.win_d, t.tw_d, g.nc, g.log2_nc, g.ns, twd);
   // angle: strips of TW positions of the (m, n) plane
   const int64_t plane = static_cast<int64_t>(g.nc) * g.ns;
   int twa = 8192 / g.na;
-  if (twa > 32) twa = 32;
+  const int twa_pref = tu.fft_angle_strip > 0 ? tu.fft_angle_strip : 32;
+  if (twa > twa_pref) twa = twa_pref;
   const int64_t ab = plane / twa;
   fft_angle_kernel<<<static_cast<unsigned>(ab), 256, sizeof(float2) * g.na * twa, s>>>(
       tmp, spec, t.win_a, t.tw_a, g.nv, g.na, g.log2_na, plane, twa);

@@ -108,6 +108,25 @@ int launch_umma_batch(const UmmaBatch &b, cudaStream_t s);
 int launch_umma_pre(const Derived &g, RaysPrep p, int64_t n, void *workspace, cudaStream_t s);
 int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s);
 
+// ---- autotuned launch shapes (table in tune.cu), keyed by the radar shape, precision and
+// the ray count's power-of-two bucket.  0 in a field means "use the built-in heuristic".
+struct Tuning {
+  int splits;             // tensor-core split-K count
+  int fft_range_points;   // points per block of the range FFT (1024 .. 4096)
+  int fft_doppler_strip;  // samples per block of the Doppler FFT
+  int fft_angle_strip;    // (m, n) positions per block of the angle FFT
+};
+bool tuning_lookup(const Derived &g, int64_t n, Tuning *t);
+// FFTs with explicit tile choices (zeros: heuristic)
+int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec,
+                    cudaStream_t s, const Tuning &tu);
+// tensor-core ray sum with a forced split count (autotuner); workspace sized for it
+int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                           cudaStream_t s, int splits);
+int64_t umma_workspace_bytes_splits(const Derived &g, int splits);
+// the split counts the tuner tries for a shape (heuristic first)
+int umma_split_candidates(const Derived &g, int64_t n, int *out, int max_out);
+
 // Validate sim_radar_params and derive the radar constants (SIM_OK or SIM_E_INVALID).
 int derive_radar(const sim_radar_params *p, Derived *g);
 

@@ -676,7 +676,16 @@ int num_sms() {
 // Tiles of 128 rows x bn columns; the rays split into `splits` chunks so that the CTAs fill
 // whole waves of the SMs (at least four waves) as evenly as possible.  Depends only on the
 // scene's own shape and ray count.
+Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits);
+
 Shape plan_shape(const Derived &g, int64_t n) {
+  Tuning tu{};
+  if (tuning_lookup(g, n, &tu) && tu.splits > 0) return plan_shape_forced(g, n, tu.splits);
+  return plan_shape_forced(g, n, 0);
+}
+
+// forced_splits > 0 replaces the wave-filling choice (autotuned tables, tuner trials)
+Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
   Shape s;
   const int M = g.nv * g.nc;
   s.bn = 2 * g.ns < 256 ? 2 * g.ns : 256;
@@ -698,7 +707,7 @@ Shape plan_shape(const Derived &g, int64_t n) {
       best_slots = slots;
     }
   }
-  int64_t splits = best;
+  int64_t splits = forced_splits > 0 ? forced_splits : best;
   if (splits > max_splits) splits = max_splits;
   if (splits > 65535) splits = 65535;
   if (splits < 1) splits = 1;
@@ -791,6 +800,65 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
   ++kernels;
   return kernels;
+}
+
+// ---- autotuner hooks
+int umma_split_candidates(const Derived &g, int64_t n, int *out, int max_out) {
+  const Shape h = plan_shape_forced(g, n, 0);
+  const int64_t tiles = static_cast<int64_t>(h.mt) * h.nt;
+  const int sms = num_sms();
+  int k = 0;
+  auto add = [&](int64_t sp) {
+    if (sp < 1 || k >= max_out) return;
+    const int64_t mx = (n + KS - 1) / KS;
+    if (sp > mx) sp = mx;
+    for (int i = 0; i < k; ++i)
+      if (out[i] == sp) return;
+    out[k++] = static_cast<int>(sp);
+  };
+  add(h.splits);
+  // whole numbers of waves: 2, 4, 6, 8, 12 waves of CTAs
+  for (int w : {2, 4, 6, 8, 12}) add((static_cast<int64_t>(w) * sms + tiles - 1) / tiles);
+  add(h.splits * 2);
+  add(h.splits / 2);
+  return k;
+}
+
+int64_t umma_workspace_bytes_splits(const Derived &g, int splits) {
+  return 256 + static_cast<int64_t>(splits) * g.nv * g.nc * 2 * g.ns * 4;
+}
+
+int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                           cudaStream_t s, int splits) {
+  const Shape sh = plan_shape_forced(g, n, splits);
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  cudaMemsetAsync(amax, 0, 4, s);
+  if (f16 && n > 0) amax_kernel<<<2 * num_sms(), 256, 0, s>>>(p.amp, n, amax);
+  Args a{};
+  a.p = p;
+  a.n_rays = n;
+  a.chunk = sh.chunk;
+  a.nc = g.nc;
+  a.ns = g.ns;
+  a.m_rows = g.nv * g.nc;
+  a.bn = sh.bn;
+  a.partials = partials;
+  a.amax_bits = amax;
+  a.status = status;
+  if (f16) {
+    if (split) launch_gemm<true, true, false>(sh, a, s);
+    else launch_gemm<true, false, false>(sh, a, s);
+  } else {
+    if (split) launch_gemm<false, true, false>(sh, a, s);
+    else launch_gemm<false, false, false>(sh, a, s);
+  }
+  const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  return sh.splits;
 }
 
 // ---- batch: one persistent launch over the units of several scenes

@@ -54,6 +54,12 @@ class sim_meta(ctypes.Structure):
     _fields_ = [("object_id", ctypes.c_void_p), ("material_id", ctypes.c_void_p)]
 
 
+class sim_tuning(ctypes.Structure):
+    _fields_ = [("splits", ctypes.c_int32), ("fft_range_points", ctypes.c_int32),
+                ("fft_doppler_strip", ctypes.c_int32), ("fft_angle_strip", ctypes.c_int32),
+                ("ray_sum_ms", ctypes.c_float), ("fft_ms", ctypes.c_float)]
+
+
 class SimError(RuntimeError):
     def __init__(self, code: int, what: str = ""):
         self.code = code
@@ -79,6 +85,11 @@ def _load() -> ctypes.CDLL:
     lib.sim_run_batch.argtypes = [I32, P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), P, P, P,
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]
     lib.sim_run_batch.restype = ctypes.c_int
+    lib.sim_autotune.argtypes = [P, I64, ctypes.POINTER(sim_tuning)]
+    lib.sim_tuning_save.argtypes = [ctypes.c_char_p]
+    lib.sim_tuning_load.argtypes = [ctypes.c_char_p]
+    for f in ("sim_autotune", "sim_tuning_save", "sim_tuning_load", "sim_tuning_clear", "sim_tuning_count"):
+        getattr(lib, f).restype = ctypes.c_int
     for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
               "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma", "sim_raysum_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
@@ -169,6 +180,30 @@ def sim_run_batch(ctxs, rays, metas, spectra=None, signals=None, labels=None):
     rc = lib.sim_run_batch(n, carr, rarr, marr, ptrs(spectra), ptrs(signals), ptrs(labels), ctypes.byref(ms),
                            ctypes.byref(kc))
     return int(rc), float(ms.value), int(kc.value)
+
+
+def sim_autotune(ctx, n_rays: int) -> sim_tuning:
+    t = sim_tuning()
+    rc = lib.sim_autotune(ctx, int(n_rays), ctypes.byref(t))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_autotune")
+    return t
+
+
+def sim_tuning_save(path: str) -> int:
+    return lib.sim_tuning_save(path.encode())
+
+
+def sim_tuning_load(path: str) -> int:
+    return lib.sim_tuning_load(path.encode())
+
+
+def sim_tuning_clear() -> int:
+    return lib.sim_tuning_clear()
+
+
+def sim_tuning_count() -> int:
+    return lib.sim_tuning_count()
 
 
 def sim_destroy(ctx) -> int:
