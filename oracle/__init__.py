@@ -24,13 +24,16 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+# RADAR_ORACLE_LIB points at another build of oracle.c (the pin-sensitivity test's mutants)
+_LIB_PATH = os.environ.get("RADAR_ORACLE_LIB", os.path.join(_HERE, "liboracle.so"))
 _lock = threading.Lock()
 _lib = None
 
 
 def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (FP64, no contraction, no fast-math)."""
+    if "RADAR_ORACLE_LIB" in os.environ:
+        return _LIB_PATH
     src = os.path.join(_HERE, "oracle.c")
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(src),

@@ -59,6 +59,20 @@ static void ray_cycles_of(const orc_radar *p, const orc_rays *r, int64_t i, ray_
   o->nu_r = mu * dt * tau;                                        /* mu t_n tau per n */
   o->nu_d = p->carrier_hz * (2.0 * v * p->chirp_period_s) / ORC_C; /* f_c dtau per chirp */
   o->nu_a = spacing_wl(p) * sin(az) * cos(el);                   /* far-field Eq. 7 */
+#if defined(ORC_MUTATION)
+  /* planted mistakes, compiled only by the pin-sensitivity test */
+#if ORC_MUTATION == 1
+  o->nu_a = spacing_wl(p) * sin(az);                              /* drops cos(el) */
+#elif ORC_MUTATION == 2
+  o->nu_d = -o->nu_d;                                             /* Doppler sign */
+#elif ORC_MUTATION == 3
+  o->nu_d = p->carrier_hz * (2.0 * v * p->sweep_time_s) / ORC_C;  /* T_c for T_d */
+#elif ORC_MUTATION == 4
+  o->nu_r = mu * dt * tau / 2.0;                                  /* one-way range */
+#elif ORC_MUTATION == 5
+  o->carrier = frac(p->carrier_hz * tau);                         /* drops phi0 */
+#endif
+#endif
   o->amp = (double)r->amplitude[i];
 }
 
@@ -260,6 +274,9 @@ void orc_spectrum(const orc_radar *p, const double *signal, double *out, int nth
   orc_window(p, 1, wd);
   orc_window(p, 2, wa);
   double *tr = twiddles(ns), *td = twiddles(nc), *ta = twiddles(na);
+#if defined(ORC_MUTATION) && ORC_MUTATION == 8
+  for (int64_t t = 0; t < ns; ++t) wr[t] = 1.0;                   /* range window left out */
+#endif
   dft_ctx c0 = {p, signal, t1, wr, tr, 0};
   parallel_for(nv * nc, nthreads, dft_lines, &c0); /* range: along n */
   dft_ctx c1 = {p, t1, t2, wd, td, 1};
@@ -409,7 +426,11 @@ double orc_cos_rep(double x) {
    q_x = floor(x + 0.5) reduced into [0, N_x); cell = (q_a N_c + q_d) N_s + q_r;
    energy = min(rint(a^2 2^32), 2^41). */
 static int64_t bin_of(double x, int64_t n) {
+#if defined(ORC_MUTATION) && ORC_MUTATION == 6
+  int64_t q = (int64_t)floor(x);                                  /* truncating bins */
+#else
   int64_t q = (int64_t)floor(x + 0.5);
+#endif
   q %= n;
   if (q < 0) q += n;
   return q;
@@ -494,7 +515,11 @@ void orc_labels(const orc_radar *p, const orc_rays *r, const int32_t *object_id,
   int64_t best_e = -1;
   for (int64_t t = 0; t < m; ++t) {
     if (t == 0 || cell[t] != cell[t - 1]) best_e = -1;
+#if defined(ORC_MUTATION) && ORC_MUTATION == 7
+    if (e[t] >= best_e) {                                         /* ties to the largest id */
+#else
     if (e[t] > best_e) {
+#endif
       best_e = e[t];
       labels[cell[t]] = obj[t];
     }
