@@ -221,8 +221,8 @@ SIM_API int sim_tuning_clear(void);
 SIM_API int sim_tuning_count(void);
 
 /* Self-test of the tensor-core tile path on caller data (not a simulation call):
-   D[M][N] = A[M][K] * B[N][K]^T with A, B row-major 16-bit (f16 != 0: FP16, else
-   BF16) device matrices and D row-major FP32 device memory, through the same shared
+   D[M][N] = A[M][K] * B[N][K]^T with A, B row-major 16-bit (f16 bit 0 set: FP16, else
+   BF16; bit 1 set: the instruction descriptor's negate-B bit, D = -A B^T) device matrices and D row-major FP32 device memory, through the same shared
    memory layout, descriptors and tcgen05 pipeline the ray sum uses.  N a multiple of
    16 in 32 .. 512 (a multiple of 256 above 256), K even, M >= 1.  stream is a
    cudaStream_t (NULL = default stream); the call synchronizes it.

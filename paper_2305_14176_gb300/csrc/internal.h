@@ -93,7 +93,7 @@ struct UmmaBatch {
   void *args;         // per-scene kernel arguments (device)
   void *units;        // work list, longest first (device)
   int n_units, n_scenes, bn_max;
-  bool f16, split;
+  bool f16, split, fast;
 };
 // device bytes of the batch's descriptors and counter
 int64_t umma_batch_scratch_bytes(int n_scenes, int64_t n_units);

@@ -38,7 +38,7 @@ namespace {
 constexpr int BM = 128;          // tile rows (TMEM lanes)
 constexpr int KS = 32;           // rays per pipeline stage (K = 2 KS real elements)
 constexpr int KELEM = 2 * KS;    // K elements per stage
-constexpr int NPROD = 512;       // producer threads (16 warps)
+constexpr int NPROD = 384;       // producer threads (12 warps, 3 groups)
 constexpr uint64_t kWaitLimitNs = 4000000000ull;  // 4 s: far above any legitimate wait
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -106,31 +106,25 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
 }
-// 32 consecutive FP32 columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 16 consecutive FP32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr)
       : "memory");
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-
-// store 32 consecutive FP32 columns of this warp's 32 TMEM lanes
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
-      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
-      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
-      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
       : "memory");
 }
+
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Instruction descriptor, kind::f16: D FP32, A/B BF16 (or FP16), both K-major, M x N.
@@ -193,7 +187,9 @@ constexpr int NTHREADS_ALL = NPROD + 32 + NDRAIN;
 // rounding is ~1e-3) folds only at the end of its chunk.
 constexpr int SUBST_SPLIT = 16;
 constexpr uint32_t kSumCol = 256;      // TMEM column of the FP32 running sum
-constexpr int LANES = NPROD / KS;      // producer threads per ray (16): row / column stride
+constexpr int NGROUP = 3;              // producer groups; group g builds stages g, g + 3, ...
+constexpr int GSIZE = NPROD / NGROUP;  // 128 threads (4 warps) per group
+constexpr int OCT = 8;                 // rays per 16-byte core-matrix row (one K chunk)
 
 struct Args {
   RaysPrep p;
@@ -208,6 +204,7 @@ struct Args {
   const uint16_t *test_a;  // [M][K] 16-bit
   const uint16_t *test_b;  // [2 N_s][K] 16-bit
   int64_t test_k;
+  int test_negate_b;       // self-test: set the instruction descriptor's negate-B bit
 };
 
 template <bool F16>
@@ -228,7 +225,6 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-__device__ __forceinline__ void sts32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
 // bounded wait that sleeps between polls (for waits that last a whole accumulation)
 __device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
@@ -241,122 +237,189 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
   }
 }
 
-// Per-ray inputs of one stage for one producer thread (prefetched a stage ahead).
-struct RayRegs {
-  uint64_t car, nua, nud, nur;
-  float amp;
-  float2 wd, wr;
+// Per-ray inputs of one stage, staged in shared memory by the producer group that builds it.
+// base = carrier + k0 nu_a + m0 nu_d is the phase at the tile's first row (k0, m0).
+struct StageRays {
+  uint64_t base[KS], car[KS], nua[KS], nud[KS], nur[KS];
+  float2 wd[KS], wr[KS];
+  float amp[KS];
 };
 
-__device__ __forceinline__ void load_ray(const Args &g, int64_t ray, bool valid, RayRegs &r) {
-  if (valid) {
-    r.car = g.p.carrier[ray];
-    r.nua = g.p.nu_a[ray];
-    r.nud = g.p.nu_d[ray];
-    r.nur = g.p.nu_r[ray];
-    r.amp = g.p.amp[ray];
-    r.wd = g.p.step_d[ray];
-    r.wr = g.p.step_r[ray];
-  } else {  // a ray past the chunk: zero amplitude and zero range phasor make its terms 0
-    r.car = r.nua = r.nud = r.nur = 0;
-    r.amp = 0.f;
-    r.wd = make_float2(1.f, 0.f);
-    r.wr = make_float2(0.f, 0.f);
+// Group threads fetch the stage's per-ray words one group-stage ahead: thread (f, q) with
+// f = gt / 32 takes field set f of ray q.  Rays past the chunk read as 0.
+struct RayWords {
+  uint64_t v0, v1, v2, v3;
+};
+
+__device__ __forceinline__ RayWords fetch_ray_words(const Args &g, int64_t ray0, int64_t k_hi, int gt) {
+  const int f = gt >> 5, q = gt & 31;
+  const int64_t ray = ray0 + q;
+  RayWords w{0, 0, 0, 0};
+  if (ray < k_hi) {
+    if (f == 0) {
+      w.v0 = g.p.carrier[ray];
+      w.v1 = g.p.nu_a[ray];
+      w.v2 = g.p.nu_d[ray];
+      w.v3 = *reinterpret_cast<const uint64_t *>(g.p.step_d + ray);
+    } else if (f == 1) {
+      w.v0 = g.p.nu_r[ray];
+      w.v1 = *reinterpret_cast<const uint64_t *>(g.p.step_r + ray);
+      w.v2 = __float_as_uint(g.p.amp[ray]);
+    }
+  }
+  return w;
+}
+
+__device__ __forceinline__ void store_ray_words(StageRays &sr, int gt, const RayWords &w, uint64_t k0, uint64_t m0) {
+  const int f = gt >> 5, q = gt & 31;
+  if (f == 0) {
+    sr.car[q] = w.v0;
+    sr.nua[q] = w.v1;
+    sr.nud[q] = w.v2;
+    sr.base[q] = w.v0 + k0 * w.v1 + m0 * w.v2;
+    sr.wd[q] = *reinterpret_cast<const float2 *>(&w.v3);
+  } else if (f == 1) {
+    sr.nur[q] = w.v0;
+    sr.wr[q] = *reinterpret_cast<const float2 *>(&w.v1);
+    sr.amp[q] = __uint_as_float(static_cast<uint32_t>(w.v2));
   }
 }
 
-// Synthesise one stage of operands.
-//   Thread mapping (16 producer warps): warp w serves rays 4 (w/2) .. 4 (w/2) + 3 of the
-//   stage; lane = 4 jl + il picks ray il of the four and phase lane j = 8 (w%2) + jl.
-//   A: rows r = j + 16 l (l < 8); B: complex columns nl = j + 16 l (l < bn/32), written as
-//   row nl of the Re block (B'[., 2i] = Re B, B'[., 2i+1] = -Im B) and row bn/2 + nl of the
-//   Im block ((Im B, Re B)), so the accumulator holds (Re S | Im S) per tile.
-//   Consecutive phasors along rows (chirps) and columns (samples) are one complex multiply
-//   apart: e^{2 pi j 16 nu} comes FP64-accurate from the prep kernel.  Every warp-wide
-//   32-bit store covers 32 distinct banks.
-template <bool F16, bool SPLIT, bool FAST>
-__device__ __forceinline__ void produce_stage(const Args &g, uint8_t *a_hi, uint8_t *b_hi, uint8_t *a_lo,
-                                              uint8_t *b_lo, const RayRegs &r, int row0, int col0, float scale) {
-  const int t = threadIdx.x;
-  const int w = t >> 5, lane = t & 31;
-  const int grp = w >> 1, jh = w & 1, il = lane & 3, jl = lane >> 2;
-  const int j = 8 * jh + jl;
-  const int bn = g.bn;
-  const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
-  // ---- A
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(GSIZE) : "memory");
+}
+
+__device__ __forceinline__ void sts128(uint8_t *p, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  *reinterpret_cast<uint4 *>(p) = make_uint4(a, b, c, d);
+}
+
+// Eight phasors of eight rays (one K chunk) -> the 16-byte core-matrix rows of their real
+// and imaginary parts (hi, and lo for split precision).
+template <bool F16, bool SPLIT>
+__device__ __forceinline__ void put_octet(const float2 (&z)[OCT], uint8_t *re_hi, uint8_t *im_hi, uint8_t *re_lo,
+                                          uint8_t *im_lo) {
   {
-    uint32_t off = grp * lbo_a + jh * 128 + jl * 16 + il * 4;
-    const float am = r.amp * scale;
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) encode<F16, SPLIT>(z[2 * p].x, z[2 * p + 1].x, h[p], l[p]);
+    sts128(re_hi, h[0], h[1], h[2], h[3]);
+    if constexpr (SPLIT) sts128(re_lo, l[0], l[1], l[2], l[3]);
+  }
+  {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) encode<F16, SPLIT>(z[2 * p].y, z[2 * p + 1].y, h[p], l[p]);
+    sts128(im_hi, h[0], h[1], h[2], h[3]);
+    if constexpr (SPLIT) sts128(im_lo, l[0], l[1], l[2], l[3]);
+  }
+}
+
+// Synthesise one stage of operands in planar K order: within each 16-ray K step, the first
+// K chunk of the A tile holds Re A of eight rays and the next Im A, likewise for B.
+//   Shared layout of a stage: A_re | A_im (128 rows x 32 rays each, core matrices of 8 rows x
+//   8 rays, 2048 bytes per K chunk) | B_re | B_im (NC = bn/2 rows each) | the same four for lo.
+//   Threads 0..63 of the group build A (ray octet o = t/16, rows j, j+16, ... with j = t%16),
+//   threads 64..127 build B (complex columns j, j+16, ...).  Each holds eight independent
+//   phasor chains stepped by the FP64-accurate e^{2 pi j 16 nu} of the prep kernel.
+template <bool F16, bool SPLIT, bool FAST>
+__device__ __forceinline__ void produce_planar(const Args &g, const StageRays &sr, uint8_t *stage, int gt, int row0,
+                                               int col0, float scale) {
+  const int NC = g.bn >> 1;
+  const uint32_t a_half = BM * KS * 2;                 // bytes of A_re (or A_im)
+  const uint32_t x_half = static_cast<uint32_t>(NC) * KS * 2;
+  const uint32_t hi_bytes = 2 * a_half + 2 * x_half;
+  uint8_t *a_re = stage, *a_im = stage + a_half, *x_re = stage + 2 * a_half, *x_im = x_re + x_half;
+  const uint32_t lo = SPLIT ? hi_bytes : 0;
+  if (gt < 64) {
+    const int o = gt >> 4, j = gt & 15;
+    uint32_t off = o * (BM * 16) + (j >> 3) * 128 + (j & 7) * 16;
+    float2 z[OCT], w[OCT];
     int grow = row0 + j;
     int kq = grow / g.nc, mq = grow - kq * g.nc;
-    float2 z;
-    {
-      float sn, cs;
-      __sincosf(q64_to_rad(r.car + static_cast<uint64_t>(kq) * r.nua + static_cast<uint64_t>(mq) * r.nud), &sn, &cs);
-      z = make_float2(am * cs, am * sn);
+    auto start = [&]() {  // exact phases of row (kq, mq)
+#pragma unroll 2
+      for (int q = 0; q < OCT; ++q) {
+        const int i = o * OCT + q;
+        float sn, cs;
+        __sincosf(q64_to_rad(sr.car[i] + static_cast<uint64_t>(kq) * sr.nua[i] + static_cast<uint64_t>(mq) * sr.nud[i]),
+                  &sn, &cs);
+        const float am = sr.amp[i] * scale;
+        z[q] = make_float2(am * cs, am * sn);
+      }
+    };
+    if constexpr (FAST) {
+      // the tile's rows share channel k0 and rows are m0 + r: phase = base + r nu_d
+#pragma unroll
+      for (int q = 0; q < OCT; ++q) {
+        const int i = o * OCT + q;
+        float sn, cs;
+        __sincosf(q64_to_rad(sr.base[i] + static_cast<uint64_t>(j) * sr.nud[i]), &sn, &cs);
+        const float am = sr.amp[i] * scale;
+        z[q] = make_float2(am * cs, am * sn);
+      }
+    } else {
+      start();
     }
 #pragma unroll
-    for (int l = 0; l < BM / LANES; ++l) {
-      if constexpr (FAST) {
-        if (l > 0) z = cmulf(z, r.wd);  // sixteen chirps on, same channel
-      } else {
-        if (l > 0) {
-          grow += LANES;
-          mq += LANES;
-          if (mq >= g.nc) {  // crossed into another channel: restart from the exact phase
+    for (int q = 0; q < OCT; ++q) w[q] = sr.wd[o * OCT + q];
+#pragma unroll 1
+    for (int l = 0; l < BM / 16; ++l) {
+      if (l > 0) {
+        if constexpr (FAST) {
+#pragma unroll
+          for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // sixteen chirps on
+        } else {
+          grow += 16;
+          mq += 16;
+          if (mq >= g.nc) {  // crossed into another channel: restart from the exact phases
             kq = grow / g.nc;
             mq = grow - kq * g.nc;
-            float sn, cs;
-            __sincosf(q64_to_rad(r.car + static_cast<uint64_t>(kq) * r.nua + static_cast<uint64_t>(mq) * r.nud),
-                      &sn, &cs);
-            z = make_float2(am * cs, am * sn);
+            start();
           } else {
-            z = cmulf(z, r.wd);
+#pragma unroll
+            for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);
           }
         }
-        if (grow >= g.m_rows) z = make_float2(0.f, 0.f);
       }
-      uint32_t hi, lo;
-      encode<F16, SPLIT>(z.x, z.y, hi, lo);
-      sts32(a_hi + off, hi);
-      if constexpr (SPLIT) sts32(a_lo + off, lo);
+      if (!FAST && grow >= g.m_rows) {
+#pragma unroll
+        for (int q = 0; q < OCT; ++q) z[q] = make_float2(0.f, 0.f);
+      }
+      put_octet<F16, SPLIT>(z, a_re + off, a_im + off, a_re + lo + off, a_im + lo + off);
       off += 256;
     }
-  }
-  // ---- B
-  {
-    uint32_t off = grp * lbo_b + jh * 128 + jl * 16 + il * 4;
-    const uint32_t im_blk = static_cast<uint32_t>(bn) * 8;  // bn/2 rows = bn/16 core groups
-    float2 z;
-    {
+  } else {
+    const int t = gt - 64;
+    const int o = t >> 4, j = t & 15;
+    uint32_t off = o * static_cast<uint32_t>(NC * 16) + (j >> 3) * 128 + (j & 7) * 16;
+    float2 z[OCT], w[OCT];
+#pragma unroll
+    for (int q = 0; q < OCT; ++q) {
+      const int i = o * OCT + q;
       float sn, cs;
-      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * r.nur), &sn, &cs);
-      z = make_float2(cs, sn);  // finite for every ray; A is zero for rays past the chunk
+      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * sr.nur[i]), &sn, &cs);
+      z[q] = make_float2(cs, sn);
+      w[q] = sr.wr[i];
     }
-    const int nb = bn / (2 * LANES);
-    for (int l = 0; l < nb; ++l) {
-      if (l > 0) z = cmulf(z, r.wr);
-      uint32_t hi, lo;
-      encode<F16, SPLIT>(z.x, z.y, hi, lo);  // (Re B, Im B)
-      // Re block row: (Re B, -Im B) = flip the sign of the upper half
-      // Im block row: (Im B, Re B)  = swap the halves
-      sts32(b_hi + off, hi ^ 0x80000000u);
-      sts32(b_hi + off + im_blk, __byte_perm(hi, 0, 0x1032));
-      if constexpr (SPLIT) {
-        sts32(b_lo + off, lo ^ 0x80000000u);
-        sts32(b_lo + off + im_blk, __byte_perm(lo, 0, 0x1032));
+#pragma unroll 1
+    for (int l = 0; l < NC / 16; ++l) {
+      if (l > 0) {
+#pragma unroll
+        for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // sixteen samples on
       }
+      put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
       off += 256;
     }
   }
 }
 
-// Copy one stage of operands from row-major 16-bit matrices (self-test).
+// Copy one stage of operands from row-major 16-bit matrices (self-test), in the interleaved
+// layout: 128 rows x 64 K of A, then bn rows x 64 K of B.
 __device__ __forceinline__ void copy_stage(const Args &g, uint8_t *a_hi, uint8_t *b_hi, int64_t ray0, int row0,
-                                           int col0) {
+                                           int col0, int gt) {
   const int bn = g.bn;
   const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
-  for (int item = threadIdx.x; item < BM * (KELEM / 8); item += NPROD) {
+  for (int item = gt; item < BM * (KELEM / 8); item += GSIZE) {
     const int r = item % BM, kc = item / BM;
     const int grow = row0 + r;
     uint32_t v[4];
@@ -370,7 +433,7 @@ __device__ __forceinline__ void copy_stage(const Args &g, uint8_t *a_hi, uint8_t
     }
     *reinterpret_cast<uint4 *>(a_hi + kc * lbo_a + r * 16) = make_uint4(v[0], v[1], v[2], v[3]);
   }
-  for (int item = threadIdx.x; item < bn * (KELEM / 8); item += NPROD) {
+  for (int item = gt; item < bn * (KELEM / 8); item += GSIZE) {
     const int r = item % bn, kc = item / bn;
     const int gcol = col0 + r;
     uint32_t v[4];
@@ -404,17 +467,28 @@ struct Launch {
   int bn_layout;         // B rows the shared-memory stages are laid out for (max bn)
 };
 
-template <bool F16, bool SPLIT, bool TEST>
+template <bool SPLIT, bool TEST>
+__host__ __device__ constexpr int num_stages() {
+  return TEST ? 4 : (SPLIT ? 3 : 6);
+}
+
+// bytes of one pipeline stage
+template <bool SPLIT, bool TEST>
+__host__ __device__ constexpr uint32_t stage_size(int bn) {
+  return TEST ? static_cast<uint32_t>(BM * KELEM * 2 + bn * KELEM * 2)
+              : static_cast<uint32_t>(BM * KELEM * 2 + bn * KS * 2) * (SPLIT ? 2u : 1u);
+}
+
+template <bool F16, bool SPLIT, bool TEST, bool FAST>
 __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Args s_args;
   __shared__ Unit s_unit;
   __shared__ int s_abort;
-  constexpr int NST = SPLIT ? 2 : 4;
+  __shared__ StageRays s_rays[NGROUP];
+  constexpr int NST = num_stages<SPLIT, TEST>();
   constexpr uint32_t TMEM_COLS = 512;  // accumulator (0..255) and running sum (256..511)
-  const uint32_t a_bytes = BM * KELEM * 2;
-  const uint32_t b_bytes = static_cast<uint32_t>(L.bn_layout) * KELEM * 2;
-  const uint32_t stage_bytes = (a_bytes + b_bytes) * (SPLIT ? 2 : 1);
+  const uint32_t stage_bytes = stage_size<SPLIT, TEST>(L.bn_layout);
   uint8_t *base = smem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
   // barriers: full[NST], empty[NST], acc_full, acc_empty, mma_done
@@ -426,7 +500,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      mbar_init(full0 + 8 * s, NPROD);
+      mbar_init(full0 + 8 * s, GSIZE);
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accf, 1);
@@ -466,6 +540,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
     __syncthreads();
     const Args &g = s_args;
     const int bn = g.bn;
+    const int NC = bn >> 1;
     const int row0 = s_unit.tile_m * BM;
     const int col0 = s_unit.tile_n * bn;  // real column; complex n0 = col0 / 2
     const int split = s_unit.split;
@@ -475,46 +550,41 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
     const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
     const int SUBST = SPLIT ? SUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
     const int n_sub = (n_stages + SUBST - 1) / SUBST;
-    const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
     bool failed = false;
 
     if (warp < MMA_WARP) {
-      // ---------------- producers
+      // ---------------- producers: group grp builds stages grp, grp + NGROUP, ...
+      const int grp = warp / (GSIZE / 32), gt = threadIdx.x % GSIZE;
       const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
-      const bool fast = (g.nc % BM) == 0;  // rows of a tile share one channel and all exist
-      const int my_ray = ((threadIdx.x >> 6) << 2) + (threadIdx.x & 3);
-      RayRegs cur{}, nxt{};
-      if (!TEST && n_stages > 0) load_ray(g, k_lo + my_ray, k_lo + my_ray < k_hi, cur);
-      for (int st = 0; st < n_stages; ++st) {
+      const uint64_t k0 = static_cast<uint64_t>(row0 / g.nc), m0 = static_cast<uint64_t>(row0 % g.nc);
+      RayWords nxt{0, 0, 0, 0};
+      if (!TEST && grp < n_stages) nxt = fetch_ray_words(g, k_lo + static_cast<int64_t>(grp) * KS, k_hi, gt);
+      for (int st = grp; st < n_stages; st += NGROUP) {
         const int gs = gst + st;
         const int s = gs % NST;
         const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
-        if (!TEST && st + 1 < n_stages) {  // prefetch the next stage's ray while this one is built
-          const int64_t nr = ray0 + KS + my_ray;
-          load_ray(g, nr, nr < k_hi, nxt);
+        if constexpr (!TEST) {
+          store_ray_words(s_rays[grp], gt, nxt, k0, m0);
+          if (st + NGROUP < n_stages) nxt = fetch_ray_words(g, ray0 + NGROUP * KS, k_hi, gt);
+          group_sync(grp);
         }
         if (gs >= NST && !mbar_wait(empty0 + 8 * s, ((gs / NST) - 1) & 1)) {
           failed = true;
           break;
         }
-        uint8_t *a_hi = base + s * stage_bytes;
-        uint8_t *b_hi = a_hi + a_bytes;
-        uint8_t *a_lo = b_hi + b_bytes;
-        uint8_t *b_lo = a_lo + a_bytes;
+        uint8_t *st_base = base + s * stage_bytes;
         if constexpr (TEST) {
-          copy_stage(g, a_hi, b_hi, ray0, row0, col0);
+          copy_stage(g, st_base, st_base + BM * KELEM * 2, ray0, row0, col0, gt);
         } else {
-          if (fast) produce_stage<F16, SPLIT, true>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
-          else produce_stage<F16, SPLIT, false>(g, a_hi, b_hi, a_lo, b_lo, cur, row0, col0, scale);
-          cur = nxt;
+          produce_planar<F16, SPLIT, FAST>(g, s_rays[grp], st_base, gt, row0, col0, scale);
         }
         fence_proxy_async();
         mbar_arrive(full0 + 8 * s);
+        if constexpr (!TEST) group_sync(grp);  // s_rays[grp] is rewritten next round
       }
     } else if (warp == MMA_WARP) {
       // ---------------- MMA issuer
       if (lane == 0) {
-        const uint32_t idesc = make_idesc(F16, BM, bn);
         const uint32_t sbase = smem_u32(base);
         bool open = false;  // issued MMAs not yet committed to acc_full
         for (int st = 0; st < n_stages; ++st) {
@@ -531,17 +601,48 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
             break;
           }
           tc_fence_after();
-          const uint32_t a_hi = sbase + s * stage_bytes, b_hi = a_hi + a_bytes;
-          const uint32_t a_lo = b_hi + b_bytes, b_lo = a_lo + a_bytes;
+          const uint32_t sb = sbase + s * stage_bytes;
+          if constexpr (TEST) {
+            // interleaved layout: D = A B^T over 4 K steps of 16
+            const uint32_t idesc = make_idesc(F16, BM, bn) | (g.test_negate_b ? (1u << 14) : 0u);
+            const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
+            const uint32_t b0 = sb + BM * KELEM * 2;
 #pragma unroll
-          for (int kk = 0; kk < KELEM / 16; ++kk) {
-            const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
-            const uint64_t da = make_sdesc(a_hi + kk * 2 * lbo_a, lbo_a, 128);
-            const uint64_t db = make_sdesc(b_hi + kk * 2 * lbo_b, lbo_b, 128);
-            mma_f16(tmem, da, db, idesc, acc);
-            if constexpr (SPLIT) {
-              mma_f16(tmem, da, make_sdesc(b_lo + kk * 2 * lbo_b, lbo_b, 128), idesc, 1u);
-              mma_f16(tmem, make_sdesc(a_lo + kk * 2 * lbo_a, lbo_a, 128), db, idesc, 1u);
+            for (int kk = 0; kk < KELEM / 16; ++kk)
+              mma_f16(tmem, make_sdesc(sb + kk * 2 * lbo_a, lbo_a, 128), make_sdesc(b0 + kk * 2 * lbo_b, lbo_b, 128),
+                      idesc, (!first || kk > 0) ? 1u : 0u);
+          } else {
+            // planar layout: per 16-ray K step, Re S += A_re B_re - A_im B_im and
+            // Im S += A_re B_im + A_im B_re (the minus by the descriptor's negate-B bit)
+            const uint32_t idesc = make_idesc(F16, BM, NC);
+            const uint32_t ineg = idesc | (1u << 14);
+            const uint32_t lbo_a = BM * 16, lbo_x = static_cast<uint32_t>(NC) * 16;
+            const uint32_t a_half = BM * KS * 2, x_half = static_cast<uint32_t>(NC) * KS * 2;
+            const uint32_t ar = sb, ai = sb + a_half, xr = sb + 2 * a_half, xi = xr + x_half;
+            const uint32_t lo = 2 * a_half + 2 * x_half;
+            const uint32_t t_re = tmem, t_im = tmem + static_cast<uint32_t>(NC);
+#pragma unroll
+            for (int kh = 0; kh < KS / 16; ++kh) {
+              const uint32_t acc = (!first || kh > 0) ? 1u : 0u;
+              const uint32_t oa = kh * 2 * lbo_a, ox = kh * 2 * lbo_x;
+              const uint64_t dar = make_sdesc(ar + oa, lbo_a, 128), dai = make_sdesc(ai + oa, lbo_a, 128);
+              const uint64_t dxr = make_sdesc(xr + ox, lbo_x, 128), dxi = make_sdesc(xi + ox, lbo_x, 128);
+              mma_f16(t_re, dar, dxr, idesc, acc);
+              mma_f16(t_re, dai, dxi, ineg, 1u);
+              mma_f16(t_im, dar, dxi, idesc, acc);
+              mma_f16(t_im, dai, dxr, idesc, 1u);
+              if constexpr (SPLIT) {
+                const uint64_t lar = make_sdesc(ar + lo + oa, lbo_a, 128), lai = make_sdesc(ai + lo + oa, lbo_a, 128);
+                const uint64_t lxr = make_sdesc(xr + lo + ox, lbo_x, 128), lxi = make_sdesc(xi + lo + ox, lbo_x, 128);
+                mma_f16(t_re, dar, lxr, idesc, 1u);
+                mma_f16(t_re, lar, dxr, idesc, 1u);
+                mma_f16(t_re, dai, lxi, ineg, 1u);
+                mma_f16(t_re, lai, dxi, ineg, 1u);
+                mma_f16(t_im, dar, lxi, idesc, 1u);
+                mma_f16(t_im, lar, dxi, idesc, 1u);
+                mma_f16(t_im, dai, lxr, idesc, 1u);
+                mma_f16(t_im, lai, dxr, idesc, 1u);
+              }
             }
           }
           open = true;
@@ -574,20 +675,20 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         }
         tc_fence_after();
         const bool last = sub == n_sub - 1;
-        for (int c = 0; c < bn; c += 32) {
-          uint32_t h[32];
-          tmem_ld32(trow + static_cast<uint32_t>(c), h);
+        for (int c = 0; c < bn; c += 16) {
+          uint32_t h[16];
+          tmem_ld16(trow + static_cast<uint32_t>(c), h);
           if (sub > 0) {
-            uint32_t r[32];
-            tmem_ld32(trow + kSumCol + static_cast<uint32_t>(c), r);
+            uint32_t r[16];
+            tmem_ld16(trow + kSumCol + static_cast<uint32_t>(c), r);
 #pragma unroll
-            for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+            for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
           }
           if (!last) {
-            tmem_st32(trow + kSumCol + static_cast<uint32_t>(c), h);
+            tmem_st16(trow + kSumCol + static_cast<uint32_t>(c), h);
           } else if (grow < g.m_rows) {
 #pragma unroll
-            for (int x = 0; x < 32; x += 4)
+            for (int x = 0; x < 16; x += 4)
               *reinterpret_cast<float4 *>(dst + c + x) =
                   make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
                               __uint_as_float(h[x + 3]));
@@ -721,37 +822,49 @@ Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
 }
 
 size_t smem_bytes(bool split, int bn) {
-  const int nst = split ? 2 : 4;
-  const size_t stage = static_cast<size_t>(BM * KELEM * 2 + bn * KELEM * 2) * (split ? 2 : 1);
+  const int nst = split ? num_stages<true, false>() : num_stages<false, false>();
+  const size_t stage = split ? stage_size<true, false>(bn) : stage_size<false, false>(bn);
   return nst * stage + 8 * (2 * nst + 3) + 16;
 }
 
-constexpr int kMaxDynSmem = 232448 - 2048;  // 227 KB per block, less the kernel's static shared memory
+constexpr int kMaxDynSmem = 232448 - 8192;  // 227 KB per block, less the kernel's static shared memory
 
-template <bool F16, bool SPLIT, bool TEST>
+template <bool F16, bool SPLIT, bool TEST, bool FAST>
 void set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256)));
     attr = true;
   }
 }
 
 // one scene, one unit per CTA
-template <bool F16, bool SPLIT, bool TEST>
+template <bool F16, bool SPLIT, bool TEST, bool FAST>
 void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
   // the self-test reserves the whole shared memory so that every descriptor it builds
   // points inside the allocation
   const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn);
-  set_smem_attr<F16, SPLIT, TEST>();
+  set_smem_attr<F16, SPLIT, TEST, FAST>();
   Launch L{};
   L.inline_scene = a;
   L.n_units = sh.mt * sh.nt * sh.splits;
   L.mt = sh.mt;
   L.nt = sh.nt;
   L.bn_layout = sh.bn;
-  umma_sum_kernel<F16, SPLIT, TEST><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
+  umma_sum_kernel<F16, SPLIT, TEST, FAST><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
+}
+
+// FAST: every tile's 128 rows lie in one channel (N_c a multiple of 128); the general kernel
+// gives the same bits on such scenes, only with more work per row
+void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, const Args &a, cudaStream_t s) {
+  if (f16) {
+    if (split) fast ? launch_gemm<true, true, false, true>(sh, a, s) : launch_gemm<true, true, false, false>(sh, a, s);
+    else fast ? launch_gemm<true, false, false, true>(sh, a, s) : launch_gemm<true, false, false, false>(sh, a, s);
+  } else {
+    if (split) fast ? launch_gemm<false, true, false, true>(sh, a, s) : launch_gemm<false, true, false, false>(sh, a, s);
+    else fast ? launch_gemm<false, false, false, true>(sh, a, s) : launch_gemm<false, false, false, false>(sh, a, s);
+  }
 }
 
 }  // namespace
@@ -785,13 +898,7 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   a.partials = partials;
   a.amax_bits = amax;
   a.status = status;
-  if (f16) {
-    if (split) launch_gemm<true, true, false>(sh, a, s);
-    else launch_gemm<true, false, false>(sh, a, s);
-  } else {
-    if (split) launch_gemm<false, true, false>(sh, a, s);
-    else launch_gemm<false, false, false>(sh, a, s);
-  }
+  launch_gemm_dispatch(f16, split, (g.nc % BM) == 0, sh, a, s);
   ++kernels;
   if (after_main) cudaEventRecord(after_main, s);
   const int rb = 4 * num_sms();
@@ -848,13 +955,7 @@ int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig,
   a.partials = partials;
   a.amax_bits = amax;
   a.status = status;
-  if (f16) {
-    if (split) launch_gemm<true, true, false>(sh, a, s);
-    else launch_gemm<true, false, false>(sh, a, s);
-  } else {
-    if (split) launch_gemm<false, true, false>(sh, a, s);
-    else launch_gemm<false, false, false>(sh, a, s);
-  }
+  launch_gemm_dispatch(f16, split, (g.nc % BM) == 0, sh, a, s);
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
   if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
   else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
@@ -933,10 +1034,17 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
           cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return SIM_E_CUDA;
-  set_smem_attr<true, true, false>();
-  set_smem_attr<true, false, false>();
-  set_smem_attr<false, true, false>();
-  set_smem_attr<false, false, false>();
+  bool all_fast = true;
+  for (int i = 0; i < n_scenes; ++i) all_fast = all_fast && (gs[i]->nc % BM) == 0;
+  out->fast = all_fast;
+  set_smem_attr<true, true, false, true>();
+  set_smem_attr<true, false, false, true>();
+  set_smem_attr<false, true, false, true>();
+  set_smem_attr<false, false, false, true>();
+  set_smem_attr<true, true, false, false>();
+  set_smem_attr<true, false, false, false>();
+  set_smem_attr<false, true, false, false>();
+  set_smem_attr<false, false, false, false>();
   return SIM_OK;
 }
 
@@ -950,13 +1058,15 @@ int launch_umma_batch(const UmmaBatch &b, cudaStream_t s) {
   const size_t sm = smem_bytes(b.split, b.bn_max);
   const int grid = std::min(b.n_units, num_sms());
   cudaMemsetAsync(b.counter, 0, 4, s);
+#define RS_BATCH_LAUNCH(F, SP, FA) umma_sum_kernel<F, SP, false, FA><<<grid, NTHREADS_ALL, sm, s>>>(L)
   if (b.f16) {
-    if (b.split) umma_sum_kernel<true, true, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
-    else umma_sum_kernel<true, false, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+    if (b.split) b.fast ? RS_BATCH_LAUNCH(true, true, true) : RS_BATCH_LAUNCH(true, true, false);
+    else b.fast ? RS_BATCH_LAUNCH(true, false, true) : RS_BATCH_LAUNCH(true, false, false);
   } else {
-    if (b.split) umma_sum_kernel<false, true, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
-    else umma_sum_kernel<false, false, false><<<grid, NTHREADS_ALL, sm, s>>>(L);
+    if (b.split) b.fast ? RS_BATCH_LAUNCH(false, true, true) : RS_BATCH_LAUNCH(false, true, false);
+    else b.fast ? RS_BATCH_LAUNCH(false, false, true) : RS_BATCH_LAUNCH(false, false, false);
   }
+#undef RS_BATCH_LAUNCH
   return 1;
 }
 
@@ -1018,13 +1128,7 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
   a.partials = partials;
   a.amax_bits = amax;
   a.status = status;
-  if (f16) {
-    if (split) launch_gemm<true, true, false>(sh, a, s);
-    else launch_gemm<true, false, false>(sh, a, s);
-  } else {
-    if (split) launch_gemm<false, true, false>(sh, a, s);
-    else launch_gemm<false, false, false>(sh, a, s);
-  }
+  launch_gemm_dispatch(f16, split, (g.nc % BM) == 0, sh, a, s);
   ++kernels;
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
   if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
@@ -1039,7 +1143,9 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
 extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
                                          float *d, void *stream) {
   using namespace rs;
-  if (m < 1 || n < 32 || (n & 15) || n > 512 || k < 2 || (k & 1) || !a || !b || !d) return SIM_E_INVALID;
+  if (m < 1 || n < 32 || (n & 15) || n > 512 || k < 2 || (k & 1) || !a || !b || !d || (f16 & ~3)) return SIM_E_INVALID;
+  const bool negate = (f16 & 2) != 0;
+  f16 &= 1;
   Shape sh;
   sh.bn = n < 256 ? n : 256;
   if (n % sh.bn) return SIM_E_INVALID;
@@ -1058,13 +1164,14 @@ extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int6
   args.test_a = static_cast<const uint16_t *>(a);
   args.test_b = static_cast<const uint16_t *>(b);
   args.test_k = k;
+  args.test_negate_b = negate ? 1 : 0;
   uint32_t *status = nullptr;
   if (cudaMalloc(&status, 4) != cudaSuccess) return SIM_E_NOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(status, 0, 4, s);
   args.status = status;
-  if (f16) launch_gemm<true, false, true>(sh, args, s);
-  else launch_gemm<false, false, true>(sh, args, s);
+  if (f16) launch_gemm<true, false, true, true>(sh, args, s);
+  else launch_gemm<false, false, true, true>(sh, args, s);
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);

@@ -16,13 +16,17 @@ pytestmark = pytest.mark.gpu
     (0, 300, 64, 2048),    # ragged rows, many stages
     (0, 256, 512, 4096),   # two column tiles
     (1, 130, 512, 1002),   # ragged K tail
+    (2, 128, 256, 64),     # BF16 with the descriptor's negate-B bit: D = -A B^T
+    (3, 200, 64, 512),     # FP16, negate-B
 ])
 def test_tile_matches_fp64_matmul(f16, m, n, k):
     g = torch.Generator().manual_seed(m * 7 + n * 3 + k)
-    dt = torch.float16 if f16 else torch.bfloat16
+    dt = torch.float16 if f16 & 1 else torch.bfloat16
     A = torch.randn(m, k, generator=g).to(dt)
     B = torch.randn(n, k, generator=g).to(dt)
     ref = A.double() @ B.double().T
+    if f16 & 2:
+        ref = -ref
     D = torch.full((m, n), float("nan"), dtype=torch.float32, device="cuda")
     Ad, Bd = A.cuda(), B.cuda()
     rc = rs.sim_selftest_umma(f16, m, n, k, Ad, Bd, D, torch.cuda.current_stream().cuda_stream)
