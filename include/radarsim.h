@@ -82,6 +82,11 @@ extern "C" {
 #define SIM_PREC_FP16 3
 #define SIM_PREC_FP16_SPLIT 4
 
+/* signal model */
+#define SIM_MODEL_SEPARABLE 0     /* Eq. 2 without the range-migration product (a GEMM) */
+#define SIM_MODEL_EXACT 1         /* Eq. 2 with mu t (tau_i(j) - tau_i(0)): phase + n m eps_i,
+                                     eps_i = B 2 v_i T_d / (c N_s); FP32_DIRECT precision only */
+
 /* outputs bitmask */
 #define SIM_OUT_SIGNAL 1
 #define SIM_OUT_SPECTRUM 2
@@ -104,6 +109,8 @@ typedef struct {
   int32_t precision;         /* SIM_PREC_* */
   int32_t outputs;           /* SIM_OUT_* bitmask, nonzero */
   int64_t max_rays;          /* 1 .. 2^21 (keeps the int64 energy sums exact) */
+  int32_t model;             /* SIM_MODEL_SEPARABLE or SIM_MODEL_EXACT */
+  int32_t reserved;          /* must be 0 */
 } sim_radar_params;
 
 /* Structure-of-arrays rays.  Each pointer holds n elements; pointers may be
@@ -120,7 +127,8 @@ typedef struct {
 
 typedef struct {
   const int32_t *object_id;   /* >= 0; required when SIM_OUT_LABELS is requested */
-  const int32_t *material_id; /* may be NULL; carried for filter rules, not used yet */
+  const int32_t *material_id; /* may be NULL; used by sim_decompose's span rules */
+  const int32_t *n_hits;      /* may be NULL; number of scatterer hits on the ray's path */
 } sim_meta;
 
 /* Validate params, derive the radar constants and upload the window and twiddle
@@ -159,6 +167,38 @@ SIM_API int sim_destroy(sim_ctx *ctx);
 
 /* Static string for a status code. */
 SIM_API const char *sim_status_string(int status);
+
+/* ---- decomposition by ray meta data (Sec. II-C, Eq. 5) ----
+   A span rule selects rays by meta data; a ray belongs to the span when every set field
+   matches (then `exclude` complements the result):
+     object_id >= 0    : object (mesh) id equals it (needs meta.object_id)
+     material_id >= 0  : material id equals it (needs meta.material_id)
+     min_hits > 0 or max_hits >= 0 : min_hits <= n_hits <= max_hits, max_hits -1 = no upper
+                         bound (needs meta.n_hits)
+   e.g. "any hit on the pedestrian", "more than one hit" (ghosts: min_hits 2), "line of
+   sight of object 7" (object_id 7, min_hits 1, max_hits 1). */
+typedef struct {
+  int32_t object_id;
+  int32_t material_id;
+  int32_t min_hits;
+  int32_t max_hits;
+  int32_t exclude;
+} sim_span_rule;
+
+/* Split one scene into n_spans parts s^h by the rules (1 <= n_spans <= 64), each summed over
+   its rays only with the context's ray-sum arithmetic and model, and transformed like the
+   spectrum.  span_spectra[h] (nullable array / entries): complex64[N_a][N_c][N_s] per span.
+   span_labels (nullable): int32[N_a][N_c][N_s], per cell the span h with the largest
+   |X_h|^2 among spans with |X_h|^2 >= threshold^2 * max_{h, cells} |X_h|^2 (a binary
+   segmentation of each span image; ties to the lower h), -1 if none passes.  0 <= threshold
+   <= 1.  Rays and meta: host or device, as for sim_submit.  Synchronous; allocates its own
+   working memory outside the engine's budget.  The parts of spans that partition the rays
+   add up to the whole scene (Eq. 5).
+   Errors: SIM_E_INVALID (bad rule, missing meta a rule needs, bad ray), SIM_E_NOMEM,
+   SIM_E_CUDA, SIM_E_DEVICE. */
+SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, int32_t n_spans,
+                          const sim_span_rule *rules, void *const *span_spectra, int32_t *span_labels,
+                          float threshold);
 
 /* ---- engine controls and measurement (not part of the paper's method) ---- */
 

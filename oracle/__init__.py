@@ -52,7 +52,7 @@ class _Radar(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("n_chirps", ctypes.c_int32),
                 ("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
-                ("window", ctypes.c_int32 * 3)]
+                ("window", ctypes.c_int32 * 3), ("model", ctypes.c_int32)]
 
 
 class _Rays(ctypes.Structure):
@@ -100,6 +100,7 @@ def _radar(radar) -> _Radar:
     r.n_angle = radar.n_angle
     for i in range(3):
         r.window[i] = int(radar.window[i])
+    r.model = int(getattr(radar, "model", 0))
     return r
 
 
@@ -216,3 +217,38 @@ def sin_rep(x: float) -> float:
 
 def cos_rep(x: float) -> float:
     return float(_load().orc_cos_rep(float(x)))
+
+
+def span_mask(rule, object_id=None, material_id=None, n_hits=None) -> np.ndarray:
+    """Rays of a span (Sec. II-C filter rules): every set field of the rule must match."""
+    n = len(object_id) if object_id is not None else len(n_hits)
+    m = np.ones(n, bool)
+    if rule["object_id"] >= 0:
+        m &= np.asarray(object_id) == rule["object_id"]
+    if rule["material_id"] >= 0:
+        m &= np.asarray(material_id) == rule["material_id"]
+    if rule["min_hits"] > 0 or rule["max_hits"] >= 0:
+        h = np.asarray(n_hits)
+        m &= h >= rule["min_hits"]
+        if rule["max_hits"] >= 0:
+            m &= h <= rule["max_hits"]
+    if rule.get("exclude", 0):
+        m = ~m
+    return m
+
+
+def span_labels(spectra, threshold: float) -> np.ndarray:
+    """Per cell the span with the largest |X_h|^2 among spans whose |X_h|^2 is at least
+    threshold^2 times the largest |X|^2 of all spans and cells (ties to the lower span),
+    -1 where none passes.  `spectra` is [H, ...]; powers are (x*x) + (y*y) in the spectra's
+    own real dtype, each operation rounded separately, so complex64 spectra give FP32
+    decisions."""
+    x, y = np.ascontiguousarray(spectra.real), np.ascontiguousarray(spectra.imag)
+    ft = x.dtype.type
+    p = (x * x) + (y * y)
+    floor = (ft(threshold) * ft(threshold)) * p.max()
+    ok = (p >= floor) & (p > 0)
+    masked = np.where(ok, p, -1.0)
+    lab = np.argmax(masked, axis=0).astype(np.int32)
+    lab[~ok.any(axis=0)] = -1
+    return lab

@@ -44,6 +44,7 @@ typedef struct {
   double nu_r;    /* cycles per fast-time sample: B d / (c N_s)  (mu t tau, t = n T_c/N_s) */
   double nu_d;    /* cycles per chirp: 2 v f_c T_d / c             (f_c dtau per T_d) */
   double nu_a;    /* cycles per virtual channel: s sin(az) cos(el) / lambda */
+  double eps;     /* exact model: cycles per (sample x chirp), mu dt (2 v T_d / c); else 0 */
   double amp;
 } ray_cycles;
 
@@ -59,6 +60,8 @@ static void ray_cycles_of(const orc_radar *p, const orc_rays *r, int64_t i, ray_
   o->nu_r = mu * dt * tau;                                        /* mu t_n tau per n */
   o->nu_d = p->carrier_hz * (2.0 * v * p->chirp_period_s) / ORC_C; /* f_c dtau per chirp */
   o->nu_a = spacing_wl(p) * sin(az) * cos(el);                   /* far-field Eq. 7 */
+  /* exact Eq. 2 keeps mu t_n (tau_i(j) - tau_i(0)) = n j mu dt 2 v T_d / c */
+  o->eps = p->model == 1 ? mu * dt * (2.0 * v * p->chirp_period_s) / ORC_C : 0.0;
 #if defined(ORC_MUTATION)
   /* planted mistakes, compiled only by the pin-sensitivity test */
 #if ORC_MUTATION == 1
@@ -141,7 +144,7 @@ static void signal_rows(void *vctx, int64_t lo, int64_t hi) {
       const double base = q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d);
       for (int n = 0; n < ns; ++n) {
         double re, im;
-        cis_cycles(base + frac(n * q->nu_r), &re, &im);
+        cis_cycles(base + frac(n * q->nu_r) + frac((double)n * m * q->eps), &re, &im);
         o[2 * n] += q->amp * re;
         o[2 * n + 1] += q->amp * im;
       }
@@ -172,7 +175,8 @@ static void signal_points(void *vctx, int64_t lo, int64_t hi) {
     for (int64_t i = 0; i < c->r->n; ++i) {
       const ray_cycles *q = &c->rc[i];
       double re, im;
-      cis_cycles(q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d) + frac(n * q->nu_r), &re, &im);
+      cis_cycles(q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d) + frac(n * q->nu_r) +
+                     frac((double)n * m * q->eps), &re, &im);
       sr += q->amp * re;
       si += q->amp * im;
     }

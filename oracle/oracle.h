@@ -40,6 +40,7 @@ typedef struct {
   int32_t n_angle;          /* angle DFT length N_a >= N_v (zero padded) */
   int32_t window[3];        /* range, Doppler, angle: 0 none, 1 periodic Hann,
                                2 symmetric Hann, 3 Hann without zero end points */
+  int32_t model;            /* 0: separable Eq. 2; 1: Eq. 2 with mu t (tau_i(j) - tau_i(0)) */
 } orc_radar;
 
 typedef struct {

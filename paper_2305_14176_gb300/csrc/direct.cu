@@ -46,7 +46,9 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const int64_t r = c0 + i;
-      s_ph[i] = make_ulonglong2(p.carrier[r] + k * p.nu_a[r] + m * p.nu_d[r], p.nu_r[r]);
+      // exact Eq. 2 adds n m eps: on row m the per-sample increment is nu_r + m eps
+      const uint64_t nur = p.eps ? p.nu_r[r] + m * p.eps[r] : p.nu_r[r];
+      s_ph[i] = make_ulonglong2(p.carrier[r] + k * p.nu_a[r] + m * p.nu_d[r], nur);
       s_amp[i] = p.amp[r];
     }
     __syncthreads();

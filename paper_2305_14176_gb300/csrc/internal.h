@@ -28,7 +28,7 @@ struct Derived {
   double spacing_wl;  // antenna spacing in carrier wavelengths: s f_c / c, or exactly 1/2
   double ka;          // N_a * spacing_wl: angle-bin coordinate per unit sin(az) cos(el)
   int win[3];
-  int precision, outputs;
+  int precision, outputs, model;
   int64_t max_rays;
   int64_t n_sig;   // N_v N_c N_s
   int64_t n_cell;  // N_a N_c N_s
@@ -53,6 +53,7 @@ struct RaysPrep {
   uint64_t *energy;   // min(rint(a^2 2^32), 2^41)
   float2 *step_d;     // e^{2 pi j 16 nu_d}: phasor step over sixteen chirps (FP64-accurate)
   float2 *step_r;     // e^{2 pi j 16 nu_r}: phasor step over sixteen samples
+  uint64_t *eps;      // exact Eq. 2 only (else null): range-migration cycles per sample x chirp
 };
 
 // Scratch for the label kernels: two open-addressing hash tables

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
     out.carrier[i] = 0; out.nu_r[i] = 0; out.nu_d[i] = 0; out.nu_a[i] = 0;
     out.amp[i] = 0.0f; out.cell[i] = -1; out.energy[i] = 0;
     out.step_d[i] = make_float2(1.f, 0.f); out.step_r[i] = make_float2(1.f, 0.f);
+    if (out.eps) out.eps[i] = 0;
     return;
   }
   const double vd = static_cast<double>(v);
@@ -121,6 +122,10 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   out.step_r[i] = step16(nu_r);
   out.step_d[i] = step16(nu_d);
   out.nu_a[i] = frac_q64(__dmul_rn(x_a, k.inv_na));
+  if (out.eps) {
+    // exact Eq. 2: mu t_n (tau_i(j) - tau_i(0)) = n j B (2 v T_d) / (c N_s) cycles
+    out.eps[i] = frac_q64(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(k.bw, __dmul_rn(2.0, vd)), k.td), kC), k.inv_ns));
+  }
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
   out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +
                    frac_q64(__dmul_rn(static_cast<double>(p0), kInv2Pi));

@@ -140,6 +140,7 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   rp.energy = reinterpret_cast<uint64_t *>(take(8 * un));
   rp.step_d = reinterpret_cast<float2 *>(take(8 * un));
   rp.step_r = reinterpret_cast<float2 *>(take(8 * un));
+  rp.eps = nullptr;
   float2 *sig = reinterpret_cast<float2 *>(take(sig_bytes));
   float2 *tmp = reinterpret_cast<float2 *>(take(sig_bytes));
   float2 *spec = reinterpret_cast<float2 *>(take(spec_bytes));

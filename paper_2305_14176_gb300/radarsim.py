@@ -29,6 +29,7 @@ SIM_E_DEVICE = -8
 SIM_WIN_NONE, SIM_WIN_HANN_PERIODIC, SIM_WIN_HANN_SYMMETRIC, SIM_WIN_HANN_NOZERO = 0, 1, 2, 3
 SIM_PREC_FP32_DIRECT, SIM_PREC_BF16, SIM_PREC_BF16_SPLIT, SIM_PREC_FP16, SIM_PREC_FP16_SPLIT = 0, 1, 2, 3, 4
 SIM_OUT_SIGNAL, SIM_OUT_SPECTRUM, SIM_OUT_LABELS = 1, 2, 4
+SIM_MODEL_SEPARABLE, SIM_MODEL_EXACT = 0, 1
 PRECISION_NAMES = {"fp32": SIM_PREC_FP32_DIRECT, "bf16": SIM_PREC_BF16, "bf16_split": SIM_PREC_BF16_SPLIT,
                    "fp16": SIM_PREC_FP16, "fp16_split": SIM_PREC_FP16_SPLIT}
 
@@ -41,7 +42,8 @@ class sim_radar_params(ctypes.Structure):
                 ("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
                 ("window", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
-                ("outputs", ctypes.c_int32), ("max_rays", ctypes.c_int64)]
+                ("outputs", ctypes.c_int32), ("max_rays", ctypes.c_int64),
+                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sim_rays(ctypes.Structure):
@@ -51,7 +53,12 @@ class sim_rays(ctypes.Structure):
 
 
 class sim_meta(ctypes.Structure):
-    _fields_ = [("object_id", ctypes.c_void_p), ("material_id", ctypes.c_void_p)]
+    _fields_ = [("object_id", ctypes.c_void_p), ("material_id", ctypes.c_void_p), ("n_hits", ctypes.c_void_p)]
+
+
+class sim_span_rule(ctypes.Structure):
+    _fields_ = [("object_id", ctypes.c_int32), ("material_id", ctypes.c_int32), ("min_hits", ctypes.c_int32),
+                ("max_hits", ctypes.c_int32), ("exclude", ctypes.c_int32)]
 
 
 class sim_tuning(ctypes.Structure):
@@ -86,6 +93,9 @@ def _load() -> ctypes.CDLL:
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]
     lib.sim_run_batch.restype = ctypes.c_int
     lib.sim_autotune.argtypes = [P, I64, ctypes.POINTER(sim_tuning)]
+    lib.sim_decompose.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), I32,
+                                  ctypes.POINTER(sim_span_rule), P, P, ctypes.c_float]
+    lib.sim_decompose.restype = ctypes.c_int
     lib.sim_tuning_save.argtypes = [ctypes.c_char_p]
     lib.sim_tuning_load.argtypes = [ctypes.c_char_p]
     for f in ("sim_autotune", "sim_tuning_save", "sim_tuning_load", "sim_tuning_clear", "sim_tuning_count"):
@@ -182,6 +192,20 @@ def sim_run_batch(ctxs, rays, metas, spectra=None, signals=None, labels=None):
     return int(rc), float(ms.value), int(kc.value)
 
 
+def span_rule(object_id=-1, material_id=-1, min_hits=0, max_hits=-1, exclude=False) -> sim_span_rule:
+    return sim_span_rule(int(object_id), int(material_id), int(min_hits), int(max_hits), int(bool(exclude)))
+
+
+def sim_decompose(ctx, rays: sim_rays, meta: sim_meta, rules, span_spectra=None, span_labels=None,
+                  threshold: float = 0.0) -> int:
+    """Per-span spectra and span labels (see include/radarsim.h); returns the status."""
+    n = len(rules)
+    rarr = (sim_span_rule * n)(*rules)
+    sp = None if span_spectra is None else (ctypes.c_void_p * n)(*[_addr(x) for x in span_spectra])
+    return lib.sim_decompose(ctx, ctypes.byref(rays), ctypes.byref(meta) if meta is not None else None, n, rarr,
+                             sp, _addr(span_labels), float(threshold))
+
+
 def sim_autotune(ctx, n_rays: int) -> sim_tuning:
     t = sim_tuning()
     rc = lib.sim_autotune(ctx, int(n_rays), ctypes.byref(t))
@@ -231,7 +255,7 @@ def sim_last_kernel_count(ctx) -> int:
 
 def make_params(radar, precision: int = SIM_PREC_FP32_DIRECT,
                 outputs: int = SIM_OUT_SIGNAL | SIM_OUT_SPECTRUM | SIM_OUT_LABELS,
-                max_rays: int = 1 << 21) -> sim_radar_params:
+                max_rays: int = 1 << 21, model: int = SIM_MODEL_SEPARABLE) -> sim_radar_params:
     """sim_radar_params from any object with the radar attribute names of the ABI."""
     p = sim_radar_params()
     p.struct_size = ctypes.sizeof(sim_radar_params)
@@ -250,6 +274,8 @@ def make_params(radar, precision: int = SIM_PREC_FP32_DIRECT,
     p.precision = int(precision)
     p.outputs = int(outputs)
     p.max_rays = int(max_rays)
+    p.model = int(model)
+    p.reserved = 0
     return p
 
 
@@ -258,7 +284,7 @@ def make_rays(arrays: Dict[str, object], n: int):
     r = sim_rays(int(n), _addr(arrays["range_rt_m"]), _addr(arrays["amplitude"]),
                  _addr(arrays["radial_velocity_mps"]), _addr(arrays["azimuth_rad"]),
                  _addr(arrays["elevation_rad"]), _addr(arrays["phase0_rad"]))
-    m = sim_meta(_addr(arrays.get("object_id")), _addr(arrays.get("material_id")))
+    m = sim_meta(_addr(arrays.get("object_id")), _addr(arrays.get("material_id")), _addr(arrays.get("n_hits")))
     return r, m
 
 
@@ -266,12 +292,13 @@ class Context:
     """Owns one sim_ctx; submit/fetch with numpy (host) or torch (device) arrays."""
 
     def __init__(self, radar, precision=SIM_PREC_FP32_DIRECT,
-                 outputs=SIM_OUT_SIGNAL | SIM_OUT_SPECTRUM | SIM_OUT_LABELS, max_rays=1 << 21):
+                 outputs=SIM_OUT_SIGNAL | SIM_OUT_SPECTRUM | SIM_OUT_LABELS, max_rays=1 << 21,
+                 model=SIM_MODEL_SEPARABLE):
         if isinstance(precision, str):
             precision = PRECISION_NAMES[precision]
         self.radar = radar
         self.outputs = outputs
-        self.ctx = sim_create(make_params(radar, precision, outputs, max_rays))
+        self.ctx = sim_create(make_params(radar, precision, outputs, max_rays, model))
         self.nv = radar.n_tx * radar.n_rx
         na = radar.n_angle or max(16, 1 << (self.nv - 1).bit_length())
         self.signal_shape = (self.nv, radar.n_chirps, radar.n_samples)

@@ -88,6 +88,7 @@ class Radar:
     element_spacing_m: float = 0.0        # 0 means half a carrier wavelength
     n_angle: int = 16
     window: tuple = (WIN_HANN_PERIODIC, WIN_HANN_PERIODIC, WIN_HANN_NOZERO)
+    model: int = 0                        # 0 separable signal model, 1 exact (range migration)
 
     @property
     def n_virtual(self) -> int:

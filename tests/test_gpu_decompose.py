@@ -1,0 +1,91 @@
+"""Decomposition by ray meta data (Sec. II-C, Eq. 5): per-span spectra against the oracle on
+the span's rays, parts of a partition adding up to the whole scene, and span labels equal to
+the oracle's segmentation rule applied in the same precision."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import scenegen
+from paper_2305_14176_gb300 import radarsim as rs
+from gpu_helpers import TOL, rel_max, to_c
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene(seed, n):
+    radar, rays = scenegen.tiny_scene(seed=seed, n_rays=n)
+    rays.object_id = scenegen.randint(seed, 50, n, 0, 3)
+    mat = scenegen.randint(seed, 51, n, 0, 2)
+    hits = scenegen.randint(seed, 52, n, 1, 3)
+    return radar, rays, mat, hits
+
+
+RULES = [dict(object_id=1, material_id=-1, min_hits=0, max_hits=-1, exclude=0),      # "the pedestrian"
+         dict(object_id=-1, material_id=-1, min_hits=2, max_hits=-1, exclude=0),     # multi-path ghosts
+         dict(object_id=2, material_id=-1, min_hits=1, max_hits=1, exclude=0),       # line of sight of 2
+         dict(object_id=-1, material_id=0, min_hits=0, max_hits=-1, exclude=1)]      # not material 0
+
+
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT])
+def test_span_spectra_and_labels(precision):
+    radar, rays, mat, hits = _scene(21, 1500)
+    ctx = rs.Context(radar, precision=precision)
+    try:
+        arr = dict(rays.arrays(), material_id=mat, n_hits=hits)
+        arr = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in arr.items()}
+        r, m = rs.make_rays(arr, rays.n)
+        spans = [torch.full(ctx.cube_shape + (2,), float("nan"), dtype=torch.float32, device="cuda")
+                 for _ in RULES]
+        labels = torch.full(ctx.cube_shape, -7, dtype=torch.int32, device="cuda")
+        rc = rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(**q) for q in RULES], spans, labels, 0.05)
+        assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+        torch.cuda.synchronize()
+        got = np.stack([to_c(x) for x in spans])
+        refs = []
+        for q, x in zip(RULES, got):
+            mask = oracle.span_mask(q, rays.object_id, mat, hits)
+            ref = oracle.spectrum(radar, oracle.signal(radar, rays.take(mask)))
+            refs.append(ref)
+            assert rel_max(x, ref, norm=max(np.abs(ref).max(), 1e-30)) <= TOL[precision]
+        lab = labels.cpu().numpy()
+        spans32 = np.stack([x.cpu().numpy()[..., 0] + 1j * x.cpu().numpy()[..., 1] for x in spans]).astype(np.complex64)
+        assert np.array_equal(lab, oracle.span_labels(spans32, 0.05))
+        agree = np.mean(lab == oracle.span_labels(np.stack(refs), 0.05))
+        assert agree >= 0.999
+        assert (lab >= 0).any() and (lab < 0).any()
+    finally:
+        ctx.close()
+
+
+def test_partition_parts_add_up_to_the_scene():
+    """Eq. 5: spans that partition the rays (object 1 and its complement) sum to the full spectrum."""
+    radar, rays, mat, hits = _scene(22, 1200)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
+    try:
+        arr = {k: np.ascontiguousarray(v) for k, v in dict(rays.arrays(), material_id=mat, n_hits=hits).items()}
+        r, m = rs.make_rays(arr, rays.n)
+        rules = [rs.span_rule(object_id=1), rs.span_rule(object_id=1, exclude=True)]
+        spans = [np.zeros(ctx.cube_shape + (2,), np.float32) for _ in rules]
+        assert rs.sim_decompose(ctx.ctx, r, m, rules, spans, None, 0.0) == rs.SIM_OK
+        whole = np.zeros(ctx.cube_shape + (2,), np.float32)
+        t = ctx.submit(arr, rays.n)
+        assert ctx.fetch(t, whole) == rs.SIM_OK
+        parts = sum(x[..., 0].astype(np.float64) + 1j * x[..., 1] for x in spans)
+        full = whole[..., 0].astype(np.float64) + 1j * whole[..., 1]
+        assert rel_max(parts, full) <= 1e-5
+    finally:
+        ctx.close()
+
+
+def test_rules_needing_missing_meta_are_rejected():
+    radar, rays, mat, hits = _scene(23, 100)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
+    try:
+        r, m = rs.make_rays(rays.arrays(), rays.n)  # no material or hit arrays
+        assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(min_hits=2)]) == rs.SIM_E_INVALID
+        assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(material_id=1)]) == rs.SIM_E_INVALID
+        assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(min_hits=3, max_hits=2)]) == rs.SIM_E_INVALID
+        assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(object_id=1)], threshold=2.0) == rs.SIM_E_INVALID
+    finally:
+        ctx.close()

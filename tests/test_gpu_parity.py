@@ -200,3 +200,30 @@ def test_linearity_on_gpu():
     _, sB, _, _ = run(radar, B)
     _, sAB, _, _ = run(radar, Rays.concat([A, B]))
     assert rel_max(sAB, sA + sB) <= 1e-5
+
+
+def test_exact_model_direct_sum():
+    """Eq. 2 with the range-migration product, on the direct-sum path."""
+    radar, rays = scenegen.tiny_scene(seed=6, n_rays=800)
+    radar = radar.replace(model=1)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, spec, lab = run(radar, rays, rs.SIM_PREC_FP32_DIRECT, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK
+    assert rel_max(sig, ref) <= 1e-5 and rel_rms(sig, ref) <= 1e-5
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= 1e-5
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+    # a moving automotive scene at full radar size, sampled
+    radar2, rays2 = scenegen.automotive_scene(seed=44, n_rays=5000)
+    radar2 = radar2.replace(model=1)
+    ctx = rs.Context(radar2, precision=rs.SIM_PREC_FP32_DIRECT, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig2, _, _ = run(radar2, rays2, rs.SIM_PREC_FP32_DIRECT, ctx=ctx)
+    finally:
+        ctx.close()
+    idx = scenegen.randint(44, 3, 2048, 0, sig2.size - 1).astype(np.int64)
+    ref2 = oracle.signal_at(radar2, rays2, idx)
+    assert rel_max(sig2.reshape(-1)[idx], ref2) <= 1e-5

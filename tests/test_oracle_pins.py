@@ -64,6 +64,44 @@ def brute_signal(radar, rays):
     return out
 
 
+def brute_signal_exact(radar, rays):
+    """Eq. 2 written out in physical time with nothing dropped: mu t_n tau_i(j) + f_c tau_i(j),
+    tau_i(j) = (d + 2 v j T_d) / c, plus the far-field channel term and phi0."""
+    lam = C / radar.carrier_hz
+    s_m = radar.element_spacing_m or lam / 2
+    mu = radar.bandwidth_hz / radar.sweep_time_s
+    out = np.zeros((radar.n_virtual, radar.n_chirps, radar.n_samples), np.complex128)
+    t = np.arange(radar.n_samples) * radar.sweep_time_s / radar.n_samples
+    for i in range(rays.n):
+        d = float(rays.range_rt_m[i])
+        v = float(rays.radial_velocity_mps[i])
+        az, el = float(rays.azimuth_rad[i]), float(rays.elevation_rad[i])
+        for k in range(radar.n_virtual):
+            for j in range(radar.n_chirps):
+                tauj = (d + 2.0 * v * j * radar.chirp_period_s) / C
+                ph = (2 * math.pi * (mu * t * tauj + radar.carrier_hz * tauj) + float(rays.phase0_rad[i])
+                      + 2 * math.pi * k * s_m * math.sin(az) * math.cos(el) / lam)
+                out[k, j] += float(rays.amplitude[i]) * np.exp(1j * ph)
+    return out
+
+
+def test_exact_model_matches_eq2_brute_force():
+    """The exact signal model keeps the range-migration product of Eq. 2."""
+    radar = small_radar(n_samples=16, n_chirps=8, n_tx=2, n_rx=2, model=1)
+    rays = scenegen.uniform_rays(seed=13, n=5, v_max=40.0)
+    ref = brute_signal_exact(radar, rays)
+    got = oracle.signal(radar, rays)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    # it differs from the separable model exactly when rays move
+    sep = oracle.signal(radar.replace(model=0), rays)
+    assert np.abs(got - sep).max() > 1e-3 * np.abs(ref).max()
+    still = rays.take(slice(None))
+    still.radial_velocity_mps = np.zeros_like(rays.radial_velocity_mps)
+    assert np.array_equal(oracle.signal(radar, still), oracle.signal(radar.replace(model=0), still))
+    idx = np.arange(0, ref.size, 7)
+    assert np.array_equal(oracle.signal_at(radar, rays, idx), got.reshape(-1)[idx])
+
+
 def test_signal_matches_eq2_brute_force():
     radar = small_radar(n_samples=16, n_chirps=8, n_tx=2, n_rx=2)
     rays = scenegen.uniform_rays(seed=11, n=6)
@@ -375,3 +413,19 @@ def test_sin_cos_rep_within_two_ulp_of_exact():
             ulp = math.ulp(float(ref)) if float(ref) != 0 else 5e-324
             assert abs(mpmath.mpf(got) - ref) <= 2.0 * ulp + 1e-300, (x, got)
     assert oracle.sin_rep(0.0) == 0.0 and oracle.cos_rep(0.0) == 1.0
+
+
+def test_span_selection_and_segmentation_rules():
+    """Sec. II-C filter rules select exactly the rays they name; the segmentation labels the
+    strongest span above the threshold and nothing below it."""
+    obj = np.array([1, 1, 2, 3, 2, 0], np.int32)
+    mat = np.array([0, 1, 0, 1, 2, 0], np.int32)
+    hits = np.array([1, 2, 1, 3, 2, 1], np.int32)
+    rule = lambda **kw: dict(dict(object_id=-1, material_id=-1, min_hits=0, max_hits=-1, exclude=0), **kw)
+    assert oracle.span_mask(rule(object_id=1), obj, mat, hits).tolist() == [1, 1, 0, 0, 0, 0]
+    assert oracle.span_mask(rule(min_hits=2), obj, mat, hits).tolist() == [0, 1, 0, 1, 1, 0]
+    assert oracle.span_mask(rule(object_id=2, min_hits=1, max_hits=1), obj, mat, hits).tolist() == [0, 0, 1, 0, 0, 0]
+    assert oracle.span_mask(rule(material_id=0, exclude=1), obj, mat, hits).tolist() == [0, 1, 0, 1, 1, 0]
+    spectra = np.array([[3.0, 0.1, 0.0, 2.0], [1.0, 0.2, 0.0, 2.0]], np.complex128)
+    assert oracle.span_labels(spectra, 0.2).tolist() == [0, -1, -1, 0]  # 0.2 floor: 0.36 of power 9
+    assert oracle.span_labels(spectra, 0.0).tolist() == [0, 1, -1, 0]
