@@ -31,7 +31,8 @@
  *   x_a = (N_a s f_c / c) (sin(az) cos(el)),
  * in FP64 in exactly this order (sin, cos by Cody-Waite reduction and Taylor
  * series in a fixed fused-multiply-add order); its energy is
- * min(rint(a^2 2^32), 2^41) as int64.  A cell's label is the object id with the
+ * min(rint(a'^2 2^32), 2^41) as int64, a' = a (cos(az) cos(el))^q the amplitude after the
+ * antenna pattern (q = pattern_exp; the same cos polynomial, q multiplications in order).  A cell's label is the object id with the
  * largest summed energy, ties to the smallest id, -1 for a cell no ray falls in.
  *
  * Layouts (row-major, last index fastest, complex = interleaved float re, im):
@@ -110,7 +111,7 @@ typedef struct {
   int32_t outputs;           /* SIM_OUT_* bitmask, nonzero */
   int64_t max_rays;          /* 1 .. 2^21 (keeps the int64 energy sums exact) */
   int32_t model;             /* SIM_MODEL_SEPARABLE or SIM_MODEL_EXACT */
-  int32_t reserved;          /* must be 0 */
+  int32_t pattern_exp;       /* antenna pattern A = (cos(az) cos(el))^q, q = 0 .. 16 (0: isotropic) */
 } sim_radar_params;
 
 /* Structure-of-arrays rays.  Each pointer holds n elements; pointers may be

@@ -52,7 +52,7 @@ class _Radar(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("n_chirps", ctypes.c_int32),
                 ("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
-                ("window", ctypes.c_int32 * 3), ("model", ctypes.c_int32)]
+                ("window", ctypes.c_int32 * 3), ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32)]
 
 
 class _Rays(ctypes.Structure):
@@ -101,6 +101,7 @@ def _radar(radar) -> _Radar:
     for i in range(3):
         r.window[i] = int(radar.window[i])
     r.model = int(getattr(radar, "model", 0))
+    r.pattern_exp = int(getattr(radar, "pattern_exp", 0))
     return r
 
 

@@ -38,6 +38,23 @@ static double spacing_wl(const orc_radar *p) {
 
 static double frac(double x) { return x - floor(x); }
 
+double orc_sin_rep(double x);
+double orc_cos_rep(double x);
+
+/* amplitude after the antenna pattern of Eq. 2, A(az, el) = (cos az cos el)^q: the labels'
+   fixed-point energies follow it too, so it uses the same polynomial cosine and q products
+   in order */
+static double pattern_amp(const orc_radar *p, double a, double az, double el) {
+  if (p->pattern_exp <= 0) return a;
+#if defined(ORC_MUTATION) && ORC_MUTATION == 9
+  const double c = orc_cos_rep(az) * orc_sin_rep(el);
+#else
+  const double c = orc_cos_rep(az) * orc_cos_rep(el);
+#endif
+  for (int e = 0; e < p->pattern_exp; ++e) a = a * c;
+  return a;
+}
+
 /* --------------------------------------------------------------- per-ray cycle counts */
 typedef struct {
   double carrier; /* frac(f_c d / c) + phi0 / 2pi, cycles */
@@ -76,7 +93,7 @@ static void ray_cycles_of(const orc_radar *p, const orc_rays *r, int64_t i, ray_
   o->carrier = frac(p->carrier_hz * tau);                         /* drops phi0 */
 #endif
 #endif
-  o->amp = (double)r->amplitude[i];
+  o->amp = pattern_amp(p, (double)r->amplitude[i], az, el);
 }
 
 /* e^{2 pi i x} for a cycle count x */
@@ -455,7 +472,8 @@ void orc_bins(const orc_radar *p, const orc_rays *r, double *xr, double *xd, dou
     if (xa) xa[i] = x_a;
     if (cell) cell[i] = (bin_of(x_a, na) * nc + bin_of(x_d, nc)) * ns + bin_of(x_r, ns);
     if (energy) {
-      const double a = (double)r->amplitude[i];
+      const double a = pattern_amp(p, (double)r->amplitude[i], (double)r->azimuth_rad[i],
+                                   (double)r->elevation_rad[i]);
       double e = nearbyint(ldexp(a * a, 32));
       if (e > 2199023255552.0) e = 2199023255552.0; /* 2^41 */
       energy[i] = (int64_t)e;

@@ -41,6 +41,7 @@ typedef struct {
   int32_t window[3];        /* range, Doppler, angle: 0 none, 1 periodic Hann,
                                2 symmetric Hann, 3 Hann without zero end points */
   int32_t model;            /* 0: separable Eq. 2; 1: Eq. 2 with mu t (tau_i(j) - tau_i(0)) */
+  int32_t pattern_exp;      /* antenna pattern A(az, el) = (cos az cos el)^q; 0: isotropic */
 } orc_radar;
 
 typedef struct {

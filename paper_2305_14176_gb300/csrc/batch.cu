@@ -53,7 +53,7 @@ struct BatchPlan {
 
 // shape key: the radar constants that select kernels and layouts, and the ray count
 using Key = std::vector<std::tuple<double, double, double, double, int, int, int, int, double, int, int, int,
-                                   int, int, int, int64_t>>;
+                                   int, int, int, int, int, int64_t>>;
 
 std::mutex g_mu;
 std::map<Key, std::unique_ptr<BatchPlan>> g_plans;
@@ -66,7 +66,7 @@ Key key_of(int n, sim_ctx *const *ctxs, const sim_rays *rays) {
   for (int i = 0; i < n; ++i) {
     const Derived &g = ctxs[i]->g;
     k.emplace_back(g.fc, g.bw, g.tc, g.td, g.ns, g.nc, g.ntx, g.nrx, g.spacing_wl, g.na, g.win[0], g.win[1],
-                   g.win[2], g.precision, g.outputs, rays[i].n);
+                   g.win[2], g.precision, g.outputs, g.model, g.pattern_exp, rays[i].n);
   }
   return k;
 }

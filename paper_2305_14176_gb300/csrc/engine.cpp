@@ -395,7 +395,7 @@ int derive(const sim_radar_params *p, Derived *g) {
   if (p->max_rays < 1 || p->max_rays > (int64_t{1} << 21)) return SIM_E_INVALID;
   if (p->model != SIM_MODEL_SEPARABLE && p->model != SIM_MODEL_EXACT) return SIM_E_INVALID;
   if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT) return SIM_E_INVALID;
-  if (p->reserved != 0) return SIM_E_INVALID;
+  if (p->pattern_exp < 0 || p->pattern_exp > 16) return SIM_E_INVALID;
   const int64_t n_cell = static_cast<int64_t>(na) * p->n_chirps * p->n_samples;
   if (n_cell >= (int64_t{1} << 31)) return SIM_E_INVALID;
   g->fc = p->carrier_hz;
@@ -417,6 +417,7 @@ int derive(const sim_radar_params *p, Derived *g) {
   g->precision = p->precision;
   g->outputs = p->outputs;
   g->model = p->model;
+  g->pattern_exp = p->pattern_exp;
   g->max_rays = p->max_rays;
   g->n_sig = static_cast<int64_t>(nv) * g->nc * g->ns;
   g->n_cell = n_cell;

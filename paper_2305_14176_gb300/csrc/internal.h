@@ -28,7 +28,7 @@ struct Derived {
   double spacing_wl;  // antenna spacing in carrier wavelengths: s f_c / c, or exactly 1/2
   double ka;          // N_a * spacing_wl: angle-bin coordinate per unit sin(az) cos(el)
   int win[3];
-  int precision, outputs, model;
+  int precision, outputs, model, pattern_exp;
   int64_t max_rays;
   int64_t n_sig;   // N_v N_c N_s
   int64_t n_cell;  // N_a N_c N_s

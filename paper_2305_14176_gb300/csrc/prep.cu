@@ -83,6 +83,7 @@ __device__ __forceinline__ int64_t bin_of(double x, int64_t n) {
 }
 
 struct PrepConst {
+  int pattern_exp;
   double fc, bw, td, nc_d, ka;
   double inv_ns, inv_nc, inv_na;
   int64_t ns, nc, na;
@@ -112,8 +113,14 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   // analytic bin coordinates (fixed order, no contraction)
   const double x_r = __ddiv_rn(__dmul_rn(k.bw, d), kC);
   const double x_d = __ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, vd), k.fc), k.td), k.nc_d), kC);
-  const double x_a = __dmul_rn(k.ka, __dmul_rn(sin_or_cos(static_cast<double>(az), false),
-                                               sin_or_cos(static_cast<double>(el), true)));
+  const double cos_el = sin_or_cos(static_cast<double>(el), true);
+  const double x_a = __dmul_rn(k.ka, __dmul_rn(sin_or_cos(static_cast<double>(az), false), cos_el));
+  // antenna pattern A(az, el) = (cos(az) cos(el))^q (Eq. 2), q products in order
+  double aa = static_cast<double>(a);
+  if (k.pattern_exp > 0) {
+    const double c = __dmul_rn(sin_or_cos(static_cast<double>(az), true), cos_el);
+    for (int e = 0; e < k.pattern_exp; ++e) aa = __dmul_rn(aa, c);
+  }
   // phase increments per sample / chirp / channel: x_x / N_x (exact scaling by a power of two)
   const uint64_t nu_r = frac_q64(__dmul_rn(x_r, k.inv_ns));
   const uint64_t nu_d = frac_q64(__dmul_rn(x_d, k.inv_nc));
@@ -129,10 +136,9 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
   out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +
                    frac_q64(__dmul_rn(static_cast<double>(p0), kInv2Pi));
-  out.amp[i] = a;
+  out.amp[i] = static_cast<float>(aa);
   const int64_t cell = (bin_of(x_a, k.na) * k.nc + bin_of(x_d, k.nc)) * k.ns + bin_of(x_r, k.ns);
   out.cell[i] = static_cast<int32_t>(cell);
-  const double aa = static_cast<double>(a);
   double e = rint(ldexp(__dmul_rn(aa, aa), 32));
   if (e > 2199023255552.0) e = 2199023255552.0;  // 2^41
   out.energy[i] = static_cast<uint64_t>(e);
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
 int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s) {
   if (n <= 0) return 0;
   PrepConst k;
+  k.pattern_exp = g.pattern_exp;
   k.fc = g.fc;
   k.bw = g.bw;
   k.td = g.td;

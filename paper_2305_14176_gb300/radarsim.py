@@ -43,7 +43,7 @@ class sim_radar_params(ctypes.Structure):
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
                 ("window", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
                 ("outputs", ctypes.c_int32), ("max_rays", ctypes.c_int64),
-                ("model", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32)]
 
 
 class sim_rays(ctypes.Structure):
@@ -275,7 +275,7 @@ def make_params(radar, precision: int = SIM_PREC_FP32_DIRECT,
     p.outputs = int(outputs)
     p.max_rays = int(max_rays)
     p.model = int(model)
-    p.reserved = 0
+    p.pattern_exp = int(getattr(radar, "pattern_exp", 0))
     return p
 
 

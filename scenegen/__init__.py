@@ -89,6 +89,7 @@ class Radar:
     n_angle: int = 16
     window: tuple = (WIN_HANN_PERIODIC, WIN_HANN_PERIODIC, WIN_HANN_NOZERO)
     model: int = 0                        # 0 separable signal model, 1 exact (range migration)
+    pattern_exp: int = 0                  # antenna pattern (cos az cos el)^q; 0 isotropic
 
     @property
     def n_virtual(self) -> int:

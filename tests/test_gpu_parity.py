@@ -227,3 +227,27 @@ def test_exact_model_direct_sum():
     idx = scenegen.randint(44, 3, 2048, 0, sig2.size - 1).astype(np.int64)
     ref2 = oracle.signal_at(radar2, rays2, idx)
     assert rel_max(sig2.reshape(-1)[idx], ref2) <= 1e-5
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_antenna_pattern(precision):
+    """Eq. 2's antenna gain (cos az cos el)^q scales every ray on every path; the labels,
+    decided on the weighted energies, stay bit exact."""
+    radar, rays = scenegen.tiny_scene(seed=9, n_rays=900)
+    radar = radar.replace(pattern_exp=6)
+    ref = oracle.signal(radar, rays)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+    # a crowded cube where the gain moves 27 of 323 labels
+    crowded = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=32, n_chirps=4, n_tx=1, n_rx=3, n_angle=4,
+                    pattern_exp=6)
+    rays = scenegen.uniform_rays(seed=77, n=700, n_objects=5)
+    rc, _, _, lab = run(crowded, rays, precision)
+    assert rc == rs.SIM_OK
+    ref_lab = oracle.labels(crowded, rays)
+    assert np.array_equal(lab, ref_lab)
+    assert np.sum(ref_lab != oracle.labels(crowded.replace(pattern_exp=0), rays)) == 27

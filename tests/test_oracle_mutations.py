@@ -19,6 +19,7 @@ MUTATIONS = {
     6: "truncates instead of rounding bin coordinates",
     7: "breaks label ties toward the largest id",
     8: "leaves the range window out of the spectrum",
+    9: "uses sin(elevation) in the antenna pattern",
 }
 
 

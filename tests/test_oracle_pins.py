@@ -102,6 +102,41 @@ def test_exact_model_matches_eq2_brute_force():
     assert np.array_equal(oracle.signal_at(radar, rays, idx), got.reshape(-1)[idx])
 
 
+def test_antenna_pattern_matches_eq2_brute_force():
+    """The antenna gain A(az, el) of Eq. 2, modelled as (cos az cos el)^q, scales each
+    ray's amplitude; the brute force applies it with the library cosine."""
+    for q in (1, 4, 16):
+        radar = small_radar(n_samples=16, n_chirps=8, n_tx=2, n_rx=2, pattern_exp=q)
+        rays = scenegen.uniform_rays(seed=17 + q, n=6)
+        rays.elevation_rad[:] = scenegen.uniform(5, q, 6, -0.4, 0.4).astype(np.float32)
+        gain = (np.cos(rays.azimuth_rad.astype(np.float64)) * np.cos(rays.elevation_rad.astype(np.float64))) ** q
+        # brute_signal reads float32 amplitudes: scale its per-ray terms in FP64
+        ref = sum(gain[i] * brute_signal(radar, rays.take(slice(i, i + 1))) for i in range(rays.n))
+        got = oracle.signal(radar, rays)
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max(), q
+        assert np.array_equal(oracle.signal(radar.replace(pattern_exp=0), rays),
+                              oracle.signal(small_radar(n_samples=16, n_chirps=8, n_tx=2, n_rx=2), rays))
+
+
+def test_antenna_pattern_weights_the_labels():
+    """Two rays in one cell (az = 0, so elevation leaves the angle bin alone): the stronger
+    raw ray at a steep elevation wins without the pattern and loses with it."""
+    radar = small_radar(n_samples=32, n_chirps=16, n_angle=4)
+    d = 5 * C / radar.bandwidth_hz
+    rays = Rays.concat([one_ray(d, a=0.5, el=0.0, obj=1), one_ray(d, a=1.0, el=1.2, obj=2)])
+    assert oracle.labels(radar, rays)[0, 0, 5] == 2
+    q = 4
+    pr = radar.replace(pattern_exp=q)
+    L = oracle.labels(pr, rays)
+    assert L[0, 0, 5] == 1 and np.sum(L >= 0) == 1
+    cell, obj, e = oracle.cell_object_energy(pr, rays)
+    got = {int(o): int(x) for o, x in zip(obj, e)}
+    assert got[1] == 2 ** 30                      # boresight: gain exactly 1
+    mpmath.mp.prec = 100
+    g = mpmath.cos(mpmath.mpf(float(np.float32(1.2)))) ** q
+    assert abs(got[2] - g * g * 2 ** 32) <= 1.0
+
+
 def test_signal_matches_eq2_brute_force():
     radar = small_radar(n_samples=16, n_chirps=8, n_tx=2, n_rx=2)
     rays = scenegen.uniform_rays(seed=11, n=6)
