@@ -19,7 +19,8 @@
  *   nu_r,i = B d_i / (c N_s)                        Eq. 2 mu t tau, t = n T_c / N_s, Eq. 3
  *   nu_d,i = 2 v_i f_c T_d / c                      Eq. 2 f_c tau_i(j), d grows 2 v T_d per chirp
  *   nu_a,i = s f_c sin(az_i) cos(el_i) / c          Eq. 7 in the far field, ULA spacing s
- * with c = 299792458 m/s.  Virtual channel k = tx * n_rx + rx sits at k * s.
+ * with c = 299792458 m/s.  Virtual channel k = tx * n_rx + rx sits at k * s.  With a TDM
+ * slot time the phase gains tx nu_t,i (see tdm_slot_s); the labels keep the physical cell.
  *
  * Spectrum X[a][p][q] = sum_{k<N_v, m<N_c, n<N_s} w_a[k] w_d[m] w_r[n] s[k][m][n]
  *                        e^{-2 pi j (k a / N_a + m p / N_c + n q / N_s)}
@@ -112,6 +113,9 @@ typedef struct {
   int64_t max_rays;          /* 1 .. 2^21 (keeps the int64 energy sums exact) */
   int32_t model;             /* SIM_MODEL_SEPARABLE or SIM_MODEL_EXACT */
   int32_t pattern_exp;       /* antenna pattern A = (cos(az) cos(el))^q, q = 0 .. 16 (0: isotropic) */
+  double tdm_slot_s;         /* TDM-MIMO slot time T_slot >= 0: transmitter tx sends chirp m at
+                                m T_d + tx T_slot, adding tx nu_t,i = tx 2 v_i f_c T_slot / c cycles
+                                (and, in the exact model, n tx B 2 v_i T_slot / (c N_s)); 0 = none */
 } sim_radar_params;
 
 /* Structure-of-arrays rays.  Each pointer holds n elements; pointers may be
@@ -283,8 +287,8 @@ SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, cons
    (meta data is not needed) and a device output buffer, and a cudaStream_t (NULL = the
    default stream); the call runs on that stream and synchronizes it before returning.
    Limits: n <= min(max_rays, 262144); on the tensor-core precisions one FP32 copy of
-   the whole cube, 8 N_v N_c N_s bytes, must also fit beside the 56 bytes per ray of
-   per-ray data (the automotive 12 x 256 x 512 cube does; a 192 x 512 x 1024 imaging
+   the whole cube, 8 N_v N_c N_s bytes, must also fit beside the 72 bytes per ray of
+   per-ray data, 88 in the exact model (the automotive 12 x 256 x 512 cube does; a 192 x 512 x 1024 imaging
    cube does not).  Beyond a limit, or with host pointers, it returns SIM_E_INVALID
    before launching anything.
    The first call on each device looks up the array's device address (set-up); make

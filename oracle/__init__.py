@@ -52,7 +52,8 @@ class _Radar(ctypes.Structure):
                 ("n_samples", ctypes.c_int32), ("n_chirps", ctypes.c_int32),
                 ("n_tx", ctypes.c_int32), ("n_rx", ctypes.c_int32),
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
-                ("window", ctypes.c_int32 * 3), ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32)]
+                ("window", ctypes.c_int32 * 3), ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32),
+                ("tdm_slot_s", ctypes.c_double)]
 
 
 class _Rays(ctypes.Structure):
@@ -102,6 +103,7 @@ def _radar(radar) -> _Radar:
         r.window[i] = int(radar.window[i])
     r.model = int(getattr(radar, "model", 0))
     r.pattern_exp = int(getattr(radar, "pattern_exp", 0))
+    r.tdm_slot_s = float(getattr(radar, "tdm_slot_s", 0.0))
     return r
 
 
@@ -158,7 +160,10 @@ def spectrum(radar, sig: np.ndarray, nthreads: int = 0) -> np.ndarray:
 
 
 def cell_dtft(radar, rays, flat_cells, nthreads: int = 0) -> np.ndarray:
-    """complex128[len(flat_cells)]: spectrum cells from the rays directly (windowed DTFT)."""
+    """complex128[len(flat_cells)]: spectrum cells from the rays directly (windowed DTFT).
+    The separable model only: the exact model's n m term does not factor over the axes."""
+    if int(getattr(radar, "model", 0)) != 0:
+        raise ValueError("cell_dtft needs the separable signal model")
     lib = _load()
     rp, rr = _radar(radar), _RayRef(rays)
     cells = np.ascontiguousarray(flat_cells, np.int64)

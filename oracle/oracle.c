@@ -55,6 +55,15 @@ static double pattern_amp(const orc_radar *p, double a, double az, double el) {
   return a;
 }
 
+/* transmitter of virtual channel k = tx N_rx + rx */
+static int64_t tx_of(const orc_radar *p, int64_t k) {
+#if defined(ORC_MUTATION) && ORC_MUTATION == 10
+  return k % p->n_rx;
+#else
+  return k / p->n_rx;
+#endif
+}
+
 /* --------------------------------------------------------------- per-ray cycle counts */
 typedef struct {
   double carrier; /* frac(f_c d / c) + phi0 / 2pi, cycles */
@@ -62,6 +71,8 @@ typedef struct {
   double nu_d;    /* cycles per chirp: 2 v f_c T_d / c             (f_c dtau per T_d) */
   double nu_a;    /* cycles per virtual channel: s sin(az) cos(el) / lambda */
   double eps;     /* exact model: cycles per (sample x chirp), mu dt (2 v T_d / c); else 0 */
+  double nu_t;    /* cycles per transmitter slot: 2 v f_c T_slot / c (TDM-MIMO) */
+  double eps_t;   /* exact model: cycles per (sample x slot), mu dt (2 v T_slot / c); else 0 */
   double amp;
 } ray_cycles;
 
@@ -79,6 +90,11 @@ static void ray_cycles_of(const orc_radar *p, const orc_rays *r, int64_t i, ray_
   o->nu_a = spacing_wl(p) * sin(az) * cos(el);                   /* far-field Eq. 7 */
   /* exact Eq. 2 keeps mu t_n (tau_i(j) - tau_i(0)) = n j mu dt 2 v T_d / c */
   o->eps = p->model == 1 ? mu * dt * (2.0 * v * p->chirp_period_s) / ORC_C : 0.0;
+  /* transmitter t of a TDM-MIMO frame sends chirp j at j T_d + t T_slot: its delays
+     tau_i(j, t) = (d + 2 v (j T_d + t T_slot)) / c add t nu_t to the carrier term of Eq. 2 and,
+     in the exact model, n t eps_t to the range-migration product */
+  o->nu_t = p->carrier_hz * (2.0 * v * p->tdm_slot_s) / ORC_C;
+  o->eps_t = p->model == 1 ? mu * dt * (2.0 * v * p->tdm_slot_s) / ORC_C : 0.0;
 #if defined(ORC_MUTATION)
   /* planted mistakes, compiled only by the pin-sensitivity test */
 #if ORC_MUTATION == 1
@@ -153,15 +169,16 @@ static void signal_rows(void *vctx, int64_t lo, int64_t hi) {
   sig_ctx *c = (sig_ctx *)vctx;
   const int ns = c->p->n_samples, nc = c->p->n_chirps;
   for (int64_t row = lo; row < hi; ++row) {
-    const int k = (int)(row / nc), m = (int)(row % nc);
+    const int k = (int)(row / nc), m = (int)(row % nc), tx = (int)tx_of(c->p, k);
     double *o = c->out + row * (int64_t)ns * 2;
     memset(o, 0, sizeof(double) * 2 * (size_t)ns);
     for (int64_t i = 0; i < c->r->n; ++i) {
       const ray_cycles *q = &c->rc[i];
-      const double base = q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d);
+      const double base = q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d) + frac(tx * q->nu_t);
       for (int n = 0; n < ns; ++n) {
         double re, im;
-        cis_cycles(base + frac(n * q->nu_r) + frac((double)n * m * q->eps), &re, &im);
+        cis_cycles(base + frac(n * q->nu_r) + frac((double)n * m * q->eps) + frac((double)n * tx * q->eps_t),
+                   &re, &im);
         o[2 * n] += q->amp * re;
         o[2 * n + 1] += q->amp * im;
       }
@@ -187,13 +204,13 @@ static void signal_points(void *vctx, int64_t lo, int64_t hi) {
   const int64_t ns = c->p->n_samples, nc = c->p->n_chirps;
   for (int64_t t = lo; t < hi; ++t) {
     const int64_t f = c->idx[t];
-    const int64_t n = f % ns, m = (f / ns) % nc, k = f / (ns * nc);
+    const int64_t n = f % ns, m = (f / ns) % nc, k = f / (ns * nc), tx = tx_of(c->p, k);
     double sr = 0.0, si = 0.0;
     for (int64_t i = 0; i < c->r->n; ++i) {
       const ray_cycles *q = &c->rc[i];
       double re, im;
-      cis_cycles(q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d) + frac(n * q->nu_r) +
-                     frac((double)n * m * q->eps), &re, &im);
+      cis_cycles(q->carrier + frac(k * q->nu_a) + frac(m * q->nu_d) + frac(tx * q->nu_t) + frac(n * q->nu_r) +
+                     frac((double)n * m * q->eps) + frac((double)n * tx * q->eps_t), &re, &im);
       sr += q->amp * re;
       si += q->amp * im;
     }
@@ -332,6 +349,21 @@ static void wdtft(const double *w, int len, double nu, int64_t q, int64_t nfft, 
   *im = si;
 }
 
+/* the angle factor with transmitter slot offsets: sum_k w[k] e^{2 pi i (k nu_a + t(k) nu_t - k q / N)},
+   t(k) = k / N_rx; it is wdtft when nu_t = 0 */
+static void wdtft_tdm(const orc_radar *p, const double *w, int len, double nu, double nu_t, int64_t q,
+                      int64_t nfft, double *re, double *im) {
+  double sr = 0.0, si = 0.0;
+  for (int t = 0; t < len; ++t) {
+    double cr, ci;
+    cis_cycles(frac(t * nu) + frac(tx_of(p, t) * nu_t) - (double)((t * q) % nfft) / (double)nfft, &cr, &ci);
+    sr += w[t] * cr;
+    si += w[t] * ci;
+  }
+  *re = sr;
+  *im = si;
+}
+
 static void dtft_cells(void *vctx, int64_t lo, int64_t hi) {
   dtft_ctx *c = (dtft_ctx *)vctx;
   const int64_t ns = c->p->n_samples, nc = c->p->n_chirps, na = c->p->n_angle;
@@ -343,7 +375,10 @@ static void dtft_cells(void *vctx, int64_t lo, int64_t hi) {
     for (int64_t i = 0; i < c->r->n; ++i) {
       const ray_cycles *q = &c->rc[i];
       double ar, ai, dr, di, rr, ri, cr, ci;
-      wdtft(c->w[2], nv, q->nu_a, qa, na, &ar, &ai);
+      if (q->nu_t != 0.0)
+        wdtft_tdm(c->p, c->w[2], nv, q->nu_a, q->nu_t, qa, na, &ar, &ai);
+      else
+        wdtft(c->w[2], nv, q->nu_a, qa, na, &ar, &ai);
       wdtft(c->w[1], (int)nc, q->nu_d, qd, nc, &dr, &di);
       wdtft(c->w[0], (int)ns, q->nu_r, qr, ns, &rr, &ri);
       cis_cycles(q->carrier, &cr, &ci);

@@ -42,6 +42,7 @@ typedef struct {
                                2 symmetric Hann, 3 Hann without zero end points */
   int32_t model;            /* 0: separable Eq. 2; 1: Eq. 2 with mu t (tau_i(j) - tau_i(0)) */
   int32_t pattern_exp;      /* antenna pattern A(az, el) = (cos az cos el)^q; 0: isotropic */
+  double tdm_slot_s;        /* TDM-MIMO: transmitter t sends chirp j at j T_d + t tdm_slot_s */
 } orc_radar;
 
 typedef struct {

@@ -30,7 +30,7 @@ size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 struct SceneBufs {
   size_t d, a, v, az, el, p0, obj;
-  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy, step_d, step_r;
+  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy, step_d, step_r, nu_tx;
   size_t sig, tmp, spec, labels, pk, pe, ck, cm, co, ws, tables;
   int64_t cap;
 };
@@ -53,7 +53,7 @@ struct BatchPlan {
 
 // shape key: the radar constants that select kernels and layouts, and the ray count
 using Key = std::vector<std::tuple<double, double, double, double, int, int, int, int, double, int, int, int,
-                                   int, int, int, int, int, int64_t>>;
+                                   int, int, int, int, int, double, int64_t>>;
 
 std::mutex g_mu;
 std::map<Key, std::unique_ptr<BatchPlan>> g_plans;
@@ -66,7 +66,7 @@ Key key_of(int n, sim_ctx *const *ctxs, const sim_rays *rays) {
   for (int i = 0; i < n; ++i) {
     const Derived &g = ctxs[i]->g;
     k.emplace_back(g.fc, g.bw, g.tc, g.td, g.ns, g.nc, g.ntx, g.nrx, g.spacing_wl, g.na, g.win[0], g.win[1],
-                   g.win[2], g.precision, g.outputs, g.model, g.pattern_exp, rays[i].n);
+                   g.win[2], g.precision, g.outputs, g.model, g.pattern_exp, g.tslot, rays[i].n);
   }
   return k;
 }
@@ -91,7 +91,8 @@ int enqueue(BatchPlan &p, cudaStream_t s) {
                 reinterpret_cast<uint64_t *>(b + q.nu_d), reinterpret_cast<uint64_t *>(b + q.nu_a),
                 reinterpret_cast<float *>(b + q.amp), reinterpret_cast<int32_t *>(b + q.cell),
                 reinterpret_cast<uint64_t *>(b + q.energy), reinterpret_cast<float2 *>(b + q.step_d),
-                reinterpret_cast<float2 *>(b + q.step_r)};
+                reinterpret_cast<float2 *>(b + q.step_r), nullptr, reinterpret_cast<uint64_t *>(b + q.nu_tx),
+                nullptr};
     preps[static_cast<size_t>(i)] = rp;
     kernels += launch_prep(g, in, p.ns[static_cast<size_t>(i)], rp, status + i, s);
     kernels += launch_umma_pre(g, rp, p.ns[static_cast<size_t>(i)], b + q.ws, s);
@@ -147,6 +148,7 @@ int build_plan(int n, sim_ctx *const *ctxs, const sim_rays *rays, BatchPlan &p) 
     q.energy = take(8 * up);
     q.step_d = take(8 * up);
     q.step_r = take(8 * up);
+    q.nu_tx = take(8 * up);
     q.sig = take(8 * static_cast<size_t>(g.n_sig));
     q.tmp = take(spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
     q.spec = take(spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
@@ -201,7 +203,8 @@ int build_plan(int n, sim_ctx *const *ctxs, const sim_rays *rays, BatchPlan &p) 
                reinterpret_cast<uint64_t *>(p.block + q.nu_d), reinterpret_cast<uint64_t *>(p.block + q.nu_a),
                reinterpret_cast<float *>(p.block + q.amp), reinterpret_cast<int32_t *>(p.block + q.cell),
                reinterpret_cast<uint64_t *>(p.block + q.energy), reinterpret_cast<float2 *>(p.block + q.step_d),
-               reinterpret_cast<float2 *>(p.block + q.step_r)};
+               reinterpret_cast<float2 *>(p.block + q.step_r), nullptr,
+               reinterpret_cast<uint64_t *>(p.block + q.nu_tx), nullptr};
     rp.push_back(r);
     ws.push_back(p.block + q.ws);
     st.push_back(reinterpret_cast<uint32_t *>(p.block + p.status_off) + i);

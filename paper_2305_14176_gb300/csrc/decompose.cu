@@ -112,7 +112,8 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                o_hit = take(4 * un);
   const size_t o_car = take(8 * up), o_nur = take(8 * up), o_nud = take(8 * up), o_nua = take(8 * up),
                o_amp = take(4 * up), o_cell = take(4 * up), o_en = take(8 * up), o_sd = take(8 * up),
-               o_sr = take(8 * up), o_eps = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0), o_mamp = take(4 * up);
+               o_sr = take(8 * up), o_eps = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0), o_mamp = take(4 * up),
+               o_ntx = take(8 * up), o_epst = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0);
   const size_t o_status = take(256), o_max = take(256);
   const size_t o_sig = take(8 * static_cast<size_t>(g.n_sig)), o_tmp = take(8 * static_cast<size_t>(g.n_sig));
   const size_t o_spec = take(8 * static_cast<size_t>(g.n_cell) * static_cast<size_t>(n_spans));
@@ -161,7 +162,9 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
               reinterpret_cast<float *>(b + o_amp), reinterpret_cast<int32_t *>(b + o_cell),
               reinterpret_cast<uint64_t *>(b + o_en), reinterpret_cast<float2 *>(b + o_sd),
               reinterpret_cast<float2 *>(b + o_sr),
-              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + o_eps) : nullptr};
+              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + o_eps) : nullptr,
+              reinterpret_cast<uint64_t *>(b + o_ntx),
+              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + o_epst) : nullptr};
   launch_prep(g, in, n, rp, status, s);
   RaysPrep span = rp;
   span.amp = reinterpret_cast<float *>(b + o_mamp);

@@ -29,12 +29,13 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
 // One block per (k, m) row: thread t owns samples n = t + j * T (j < NPT).
 template <int NPT>
 __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
-                                                         float2 *__restrict__ sig) {
+                                                         int nrx, float2 *__restrict__ sig) {
   __shared__ ulonglong2 s_ph[kChunk];  // (base phase of this row, range step)
   __shared__ float s_amp[kChunk];
   const int row = blockIdx.x;
   const uint64_t k = static_cast<uint64_t>(row / nc);
   const uint64_t m = static_cast<uint64_t>(row % nc);
+  const uint64_t tx = k / static_cast<uint64_t>(nrx), rx = k - tx * static_cast<uint64_t>(nrx);
   const int t = threadIdx.x;
   const uint64_t T = blockDim.x;
   float tot_re[NPT], tot_im[NPT];
@@ -46,9 +47,10 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const int64_t r = c0 + i;
-      // exact Eq. 2 adds n m eps: on row m the per-sample increment is nu_r + m eps
-      const uint64_t nur = p.eps ? p.nu_r[r] + m * p.eps[r] : p.nu_r[r];
-      s_ph[i] = make_ulonglong2(p.carrier[r] + k * p.nu_a[r] + m * p.nu_d[r], nur);
+      // exact Eq. 2 adds n (m eps + tx eps_t): on row (tx, m) the per-sample increment grows by that
+      const uint64_t nur = p.eps ? p.nu_r[r] + m * p.eps[r] + tx * p.eps_t[r] : p.nu_r[r];
+      // channel k = tx N_rx + rx: phase tx nu_tx + rx nu_a (= k nu_a without TDM slots)
+      s_ph[i] = make_ulonglong2(p.carrier[r] + tx * p.nu_tx[r] + rx * p.nu_a[r] + m * p.nu_d[r], nur);
       s_amp[i] = p.amp[r];
     }
     __syncthreads();
@@ -89,12 +91,12 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cuda
   const int threads = g.ns < 128 ? g.ns : 128;
   const int npt = g.ns / threads;  // N_s is a power of two >= 16
   switch (npt) {
-    case 1: direct_sum_kernel<1><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    case 2: direct_sum_kernel<2><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    case 4: direct_sum_kernel<4><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    case 8: direct_sum_kernel<8><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    case 16: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
-    default: direct_sum_kernel<32><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, sig); break;
+    case 1: direct_sum_kernel<1><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+    case 2: direct_sum_kernel<2><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+    case 4: direct_sum_kernel<4><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+    case 8: direct_sum_kernel<8><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+    case 16: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+    default: direct_sum_kernel<32><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
   }
   return 1;
 }

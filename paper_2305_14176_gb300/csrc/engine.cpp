@@ -44,7 +44,7 @@ struct Slot {
 
 struct Plan {  // byte offsets of one scene's buffers inside its device block
   size_t d, a, v, az, el, p0, obj;
-  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy, step_d, step_r, eps;
+  size_t carrier, nu_r, nu_d, nu_a, amp, cell, energy, step_d, step_r, eps, nu_tx, eps_t;
   size_t status;
   size_t sig, tmp, spec, labels;
   size_t pk, pe, ck, cm, co;
@@ -132,6 +132,8 @@ Plan make_plan(const Derived &g, int64_t n, bool has_obj) {
   p.step_d = take(8 * up);
   p.step_r = take(8 * up);
   p.eps = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0);
+  p.nu_tx = take(8 * up);
+  p.eps_t = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0);
   p.status = take(256);
   p.sig = take(8 * static_cast<size_t>(g.n_sig));
   const bool spec = g.outputs & SIM_OUT_SPECTRUM;
@@ -206,7 +208,9 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
               reinterpret_cast<float *>(b + p.amp), reinterpret_cast<int32_t *>(b + p.cell),
               reinterpret_cast<uint64_t *>(b + p.energy), reinterpret_cast<float2 *>(b + p.step_d),
               reinterpret_cast<float2 *>(b + p.step_r),
-              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + p.eps) : nullptr};
+              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + p.eps) : nullptr,
+              reinterpret_cast<uint64_t *>(b + p.nu_tx),
+              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + p.eps_t) : nullptr};
   uint32_t *status = reinterpret_cast<uint32_t *>(b + p.status);
   float2 *sig = reinterpret_cast<float2 *>(b + p.sig);
   int kernels = 0;
@@ -396,6 +400,7 @@ int derive(const sim_radar_params *p, Derived *g) {
   if (p->model != SIM_MODEL_SEPARABLE && p->model != SIM_MODEL_EXACT) return SIM_E_INVALID;
   if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT) return SIM_E_INVALID;
   if (p->pattern_exp < 0 || p->pattern_exp > 16) return SIM_E_INVALID;
+  if (!(isfinite(p->tdm_slot_s) && p->tdm_slot_s >= 0.0 && p->tdm_slot_s <= 1.0)) return SIM_E_INVALID;
   const int64_t n_cell = static_cast<int64_t>(na) * p->n_chirps * p->n_samples;
   if (n_cell >= (int64_t{1} << 31)) return SIM_E_INVALID;
   g->fc = p->carrier_hz;
@@ -418,6 +423,7 @@ int derive(const sim_radar_params *p, Derived *g) {
   g->outputs = p->outputs;
   g->model = p->model;
   g->pattern_exp = p->pattern_exp;
+  g->tslot = p->tdm_slot_s;
   g->max_rays = p->max_rays;
   g->n_sig = static_cast<int64_t>(nv) * g->nc * g->ns;
   g->n_cell = n_cell;

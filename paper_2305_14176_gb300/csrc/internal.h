@@ -29,6 +29,7 @@ struct Derived {
   double ka;          // N_a * spacing_wl: angle-bin coordinate per unit sin(az) cos(el)
   int win[3];
   int precision, outputs, model, pattern_exp;
+  double tslot;  // TDM-MIMO slot time (s), 0 = none
   int64_t max_rays;
   int64_t n_sig;   // N_v N_c N_s
   int64_t n_cell;  // N_a N_c N_s
@@ -54,6 +55,8 @@ struct RaysPrep {
   float2 *step_d;     // e^{2 pi j 16 nu_d}: phasor step over sixteen chirps (FP64-accurate)
   float2 *step_r;     // e^{2 pi j 16 nu_r}: phasor step over sixteen samples
   uint64_t *eps;      // exact Eq. 2 only (else null): range-migration cycles per sample x chirp
+  uint64_t *nu_tx;    // cycles per transmitter: N_rx nu_a + nu_t (nu_t = TDM slot Doppler, 0 = none)
+  uint64_t *eps_t;    // exact Eq. 2 only (else null): range-migration cycles per sample x TDM slot
 };
 
 // Scratch for the label kernels: two open-addressing hash tables

@@ -90,6 +90,8 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   rp.step_d = reinterpret_cast<float2 *>(take(8 * up));
   rp.step_r = reinterpret_cast<float2 *>(take(8 * up));
   rp.eps = g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(take(8 * up)) : nullptr;
+  rp.nu_tx = reinterpret_cast<uint64_t *>(take(8 * up));
+  rp.eps_t = g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(take(8 * up)) : nullptr;
   uint32_t *status = reinterpret_cast<uint32_t *>(take(256));
   uint8_t *ws = scr + off;
   const int64_t ws_bytes = static_cast<int64_t>(kScratchBytes) - static_cast<int64_t>(off);

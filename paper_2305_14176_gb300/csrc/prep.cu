@@ -84,7 +84,8 @@ __device__ __forceinline__ int64_t bin_of(double x, int64_t n) {
 
 struct PrepConst {
   int pattern_exp;
-  double fc, bw, td, nc_d, ka;
+  double fc, bw, td, tslot, nc_d, ka;
+  uint64_t nrx;
   double inv_ns, inv_nc, inv_na;
   int64_t ns, nc, na;
   int want_labels;
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
     out.amp[i] = 0.0f; out.cell[i] = -1; out.energy[i] = 0;
     out.step_d[i] = make_float2(1.f, 0.f); out.step_r[i] = make_float2(1.f, 0.f);
     if (out.eps) out.eps[i] = 0;
+    out.nu_tx[i] = 0;
+    if (out.eps_t) out.eps_t[i] = 0;
     return;
   }
   const double vd = static_cast<double>(v);
@@ -128,10 +131,20 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   out.nu_d[i] = nu_d;
   out.step_r[i] = step16(nu_r);
   out.step_d[i] = step16(nu_d);
-  out.nu_a[i] = frac_q64(__dmul_rn(x_a, k.inv_na));
+  const uint64_t nu_a = frac_q64(__dmul_rn(x_a, k.inv_na));
+  out.nu_a[i] = nu_a;
+  // TDM-MIMO: transmitter t fires chirp j at j T_d + t T_slot, so its phase gains t nu_t with
+  // nu_t = 2 v f_c T_slot / c; channel k = t N_rx + r then has phase t (N_rx nu_a + nu_t) + r nu_a
+  const uint64_t nu_t = k.tslot > 0.0
+                            ? frac_q64(__ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, vd), k.fc), k.tslot), kC))
+                            : 0ull;
+  out.nu_tx[i] = k.nrx * nu_a + nu_t;
   if (out.eps) {
     // exact Eq. 2: mu t_n (tau_i(j) - tau_i(0)) = n j B (2 v T_d) / (c N_s) cycles
     out.eps[i] = frac_q64(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(k.bw, __dmul_rn(2.0, vd)), k.td), kC), k.inv_ns));
+    // and with TDM slots n t B (2 v T_slot) / (c N_s)
+    out.eps_t[i] =
+        frac_q64(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(k.bw, __dmul_rn(2.0, vd)), k.tslot), kC), k.inv_ns));
   }
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
   out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +
@@ -150,6 +163,8 @@ int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *
   if (n <= 0) return 0;
   PrepConst k;
   k.pattern_exp = g.pattern_exp;
+  k.tslot = g.tslot;
+  k.nrx = static_cast<uint64_t>(g.nrx);
   k.fc = g.fc;
   k.bw = g.bw;
   k.td = g.td;

@@ -51,6 +51,7 @@ __global__ void synth_rays(RaysPrep p, int64_t n) {
   p.nu_r[i] = hash64(4 * i + 1) >> 2;
   p.nu_d[i] = hash64(4 * i + 2);
   p.nu_a[i] = hash64(4 * i + 3);
+  p.nu_tx[i] = hash64(4 * i + 3) * 4;
   p.amp[i] = 1.0f;
   p.cell[i] = 0;
   p.energy[i] = 0;
@@ -141,6 +142,8 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   rp.step_d = reinterpret_cast<float2 *>(take(8 * un));
   rp.step_r = reinterpret_cast<float2 *>(take(8 * un));
   rp.eps = nullptr;
+  rp.nu_tx = reinterpret_cast<uint64_t *>(take(8 * un));
+  rp.eps_t = nullptr;
   float2 *sig = reinterpret_cast<float2 *>(take(sig_bytes));
   float2 *tmp = reinterpret_cast<float2 *>(take(sig_bytes));
   float2 *spec = reinterpret_cast<float2 *>(take(spec_bytes));

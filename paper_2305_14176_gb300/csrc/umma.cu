@@ -196,6 +196,7 @@ struct Args {
   int64_t n_rays;
   int64_t chunk;       // rays per split (multiple of KS)
   int nc, ns, m_rows;  // N_c, N_s, M = N_v N_c
+  int nrx;             // N_rx: channel k = tx N_rx + rx
   int bn;              // MMA N (real columns per tile) = min(256, 2 N_s)
   float *partials;     // [splits][M][2 N_s], each bn-column tile as (Re block, Im block)
   const uint32_t *amax_bits;  // scene amplitude maximum (FP16 scaling), may be null
@@ -238,9 +239,10 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
 }
 
 // Per-ray inputs of one stage, staged in shared memory by the producer group that builds it.
-// base = carrier + k0 nu_a + m0 nu_d is the phase at the tile's first row (k0, m0).
+// base = carrier + t0 nu_tx + r0 nu_a + m0 nu_d is the phase at the tile's first row
+// (k0 = t0 N_rx + r0, m0).
 struct StageRays {
-  uint64_t base[KS], car[KS], nua[KS], nud[KS], nur[KS];
+  uint64_t base[KS], car[KS], nua[KS], nud[KS], nur[KS], nutx[KS];
   float2 wd[KS], wr[KS];
   float amp[KS];
 };
@@ -260,28 +262,31 @@ __device__ __forceinline__ RayWords fetch_ray_words(const Args &g, int64_t ray0,
       w.v0 = g.p.carrier[ray];
       w.v1 = g.p.nu_a[ray];
       w.v2 = g.p.nu_d[ray];
-      w.v3 = *reinterpret_cast<const uint64_t *>(g.p.step_d + ray);
+      w.v3 = g.p.nu_tx[ray];
     } else if (f == 1) {
       w.v0 = g.p.nu_r[ray];
       w.v1 = *reinterpret_cast<const uint64_t *>(g.p.step_r + ray);
       w.v2 = __float_as_uint(g.p.amp[ray]);
+      w.v3 = *reinterpret_cast<const uint64_t *>(g.p.step_d + ray);
     }
   }
   return w;
 }
 
-__device__ __forceinline__ void store_ray_words(StageRays &sr, int gt, const RayWords &w, uint64_t k0, uint64_t m0) {
+__device__ __forceinline__ void store_ray_words(StageRays &sr, int gt, const RayWords &w, uint64_t t0, uint64_t r0,
+                                                uint64_t m0) {
   const int f = gt >> 5, q = gt & 31;
   if (f == 0) {
     sr.car[q] = w.v0;
     sr.nua[q] = w.v1;
     sr.nud[q] = w.v2;
-    sr.base[q] = w.v0 + k0 * w.v1 + m0 * w.v2;
-    sr.wd[q] = *reinterpret_cast<const float2 *>(&w.v3);
+    sr.nutx[q] = w.v3;
+    sr.base[q] = w.v0 + t0 * w.v3 + r0 * w.v1 + m0 * w.v2;
   } else if (f == 1) {
     sr.nur[q] = w.v0;
     sr.wr[q] = *reinterpret_cast<const float2 *>(&w.v1);
     sr.amp[q] = __uint_as_float(static_cast<uint32_t>(w.v2));
+    sr.wd[q] = *reinterpret_cast<const float2 *>(&w.v3);
   }
 }
 
@@ -336,12 +341,14 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
     float2 z[OCT], w[OCT];
     int grow = row0 + j;
     int kq = grow / g.nc, mq = grow - kq * g.nc;
-    auto start = [&]() {  // exact phases of row (kq, mq)
+    auto start = [&]() {  // exact phases of row (kq, mq), kq = tq N_rx + rq
+      const int tq = kq / g.nrx, rq = kq - tq * g.nrx;
 #pragma unroll 2
       for (int q = 0; q < OCT; ++q) {
         const int i = o * OCT + q;
         float sn, cs;
-        __sincosf(q64_to_rad(sr.car[i] + static_cast<uint64_t>(kq) * sr.nua[i] + static_cast<uint64_t>(mq) * sr.nud[i]),
+        __sincosf(q64_to_rad(sr.car[i] + static_cast<uint64_t>(tq) * sr.nutx[i] + static_cast<uint64_t>(rq) * sr.nua[i] +
+                             static_cast<uint64_t>(mq) * sr.nud[i]),
                   &sn, &cs);
         const float am = sr.amp[i] * scale;
         z[q] = make_float2(am * cs, am * sn);
@@ -557,6 +564,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
       const int grp = warp / (GSIZE / 32), gt = threadIdx.x % GSIZE;
       const float scale = TEST ? 1.f : amp_scale<F16>(g.amax_bits);
       const uint64_t k0 = static_cast<uint64_t>(row0 / g.nc), m0 = static_cast<uint64_t>(row0 % g.nc);
+      const uint64_t t0 = k0 / static_cast<uint64_t>(g.nrx), r0 = k0 - t0 * static_cast<uint64_t>(g.nrx);
       RayWords nxt{0, 0, 0, 0};
       if (!TEST && grp < n_stages) nxt = fetch_ray_words(g, k_lo + static_cast<int64_t>(grp) * KS, k_hi, gt);
       for (int st = grp; st < n_stages; st += NGROUP) {
@@ -564,7 +572,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         const int s = gs % NST;
         const int64_t ray0 = k_lo + static_cast<int64_t>(st) * KS;
         if constexpr (!TEST) {
-          store_ray_words(s_rays[grp], gt, nxt, k0, m0);
+          store_ray_words(s_rays[grp], gt, nxt, t0, r0, m0);
           if (st + NGROUP < n_stages) nxt = fetch_ray_words(g, ray0 + NGROUP * KS, k_hi, gt);
           group_sync(grp);
         }
@@ -894,6 +902,7 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   a.nc = g.nc;
   a.ns = g.ns;
   a.m_rows = g.nv * g.nc;
+  a.nrx = g.nrx;
   a.bn = sh.bn;
   a.partials = partials;
   a.amax_bits = amax;
@@ -951,6 +960,7 @@ int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig,
   a.nc = g.nc;
   a.ns = g.ns;
   a.m_rows = g.nv * g.nc;
+  a.nrx = g.nrx;
   a.bn = sh.bn;
   a.partials = partials;
   a.amax_bits = amax;
@@ -1000,6 +1010,7 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
     a.nc = g.nc;
     a.ns = g.ns;
     a.m_rows = g.nv * g.nc;
+    a.nrx = g.nrx;
     a.bn = sh.bn;
     a.partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspaces[i]) + 256);
     a.amax_bits = static_cast<const uint32_t *>(workspaces[i]);
@@ -1124,6 +1135,7 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
   a.nc = g.nc;
   a.ns = g.ns;
   a.m_rows = g.nv * g.nc;
+  a.nrx = g.nrx;
   a.bn = sh.bn;
   a.partials = partials;
   a.amax_bits = amax;
@@ -1159,6 +1171,7 @@ extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int6
   args.nc = m;
   args.ns = n / 2;
   args.m_rows = m;
+  args.nrx = 1;
   args.bn = sh.bn;
   args.partials = d;
   args.test_a = static_cast<const uint16_t *>(a);

@@ -43,7 +43,8 @@ class sim_radar_params(ctypes.Structure):
                 ("element_spacing_m", ctypes.c_double), ("n_angle", ctypes.c_int32),
                 ("window", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
                 ("outputs", ctypes.c_int32), ("max_rays", ctypes.c_int64),
-                ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32)]
+                ("model", ctypes.c_int32), ("pattern_exp", ctypes.c_int32),
+                ("tdm_slot_s", ctypes.c_double)]
 
 
 class sim_rays(ctypes.Structure):
@@ -276,6 +277,7 @@ def make_params(radar, precision: int = SIM_PREC_FP32_DIRECT,
     p.max_rays = int(max_rays)
     p.model = int(model)
     p.pattern_exp = int(getattr(radar, "pattern_exp", 0))
+    p.tdm_slot_s = float(getattr(radar, "tdm_slot_s", 0.0))
     return p
 
 

@@ -90,6 +90,7 @@ class Radar:
     window: tuple = (WIN_HANN_PERIODIC, WIN_HANN_PERIODIC, WIN_HANN_NOZERO)
     model: int = 0                        # 0 separable signal model, 1 exact (range migration)
     pattern_exp: int = 0                  # antenna pattern (cos az cos el)^q; 0 isotropic
+    tdm_slot_s: float = 0.0               # TDM-MIMO: transmitter t's chirp j starts at j T_d + t slot
 
     @property
     def n_virtual(self) -> int:

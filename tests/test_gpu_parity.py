@@ -251,3 +251,38 @@ def test_antenna_pattern(precision):
     ref_lab = oracle.labels(crowded, rays)
     assert np.array_equal(lab, ref_lab)
     assert np.sum(ref_lab != oracle.labels(crowded.replace(pattern_exp=0), rays)) == 27
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape", [(64, 32, 3, 4, 16), (32, 128, 3, 2, 8)])
+def test_tdm_slot_offsets(precision, shape):
+    """TDM-MIMO slot offsets: transmitter t's chirps start t T_slot later, on every path
+    (the second shape fills whole 128-chirp tiles, the tensor core's single-channel tiles)."""
+    ns, nc, ntx, nrx, na = shape
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na,
+                  tdm_slot_s=13.3e-6)
+    rays = scenegen.uniform_rays(seed=ns + nc, n=700, n_objects=4, v_max=30.0)
+    ref = oracle.signal(radar, rays)
+    rc, sig, spec, lab = run(radar, rays, precision)
+    assert rc == rs.SIM_OK
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+    # the offsets change the cube well beyond the tolerance
+    assert rel_max(oracle.signal(radar.replace(tdm_slot_s=0.0), rays), ref) > 100 * tol
+
+
+def test_tdm_exact_model():
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=32, n_tx=3, n_rx=4, n_angle=16,
+                  tdm_slot_s=13.3e-6, model=1)
+    rays = scenegen.uniform_rays(seed=71, n=600, n_objects=4, v_max=30.0)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, spec, lab = run(radar, rays, rs.SIM_PREC_FP32_DIRECT, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK
+    assert rel_max(sig, ref) <= 1e-5 and rel_rms(sig, ref) <= 1e-5
+    assert np.array_equal(lab, oracle.labels(radar, rays))

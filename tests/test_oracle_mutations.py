@@ -20,6 +20,7 @@ MUTATIONS = {
     7: "breaks label ties toward the largest id",
     8: "leaves the range window out of the spectrum",
     9: "uses sin(elevation) in the antenna pattern",
+    10: "takes the receiver index as the TDM transmitter slot",
 }
 
 

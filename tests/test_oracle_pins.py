@@ -464,3 +464,55 @@ def test_span_selection_and_segmentation_rules():
     spectra = np.array([[3.0, 0.1, 0.0, 2.0], [1.0, 0.2, 0.0, 2.0]], np.complex128)
     assert oracle.span_labels(spectra, 0.2).tolist() == [0, -1, -1, 0]  # 0.2 floor: 0.36 of power 9
     assert oracle.span_labels(spectra, 0.0).tolist() == [0, 1, -1, 0]
+
+
+# ------------------------------------------------------------------ TDM-MIMO slot offsets
+
+def brute_signal_tdm(radar, rays, exact):
+    """Eq. 2 in physical time for a TDM-MIMO frame: transmitter t sends chirp j at
+    j T_d + t T_slot, so tau_i(j, t) = (d + 2 v (j T_d + t T_slot)) / c.  The separable model
+    keeps mu t_n tau_i(0) in the beat term, the exact one mu t_n tau_i(j, t)."""
+    lam = C / radar.carrier_hz
+    s_m = radar.element_spacing_m or lam / 2
+    mu = radar.bandwidth_hz / radar.sweep_time_s
+    out = np.zeros((radar.n_virtual, radar.n_chirps, radar.n_samples), np.complex128)
+    t = np.arange(radar.n_samples) * radar.sweep_time_s / radar.n_samples
+    for i in range(rays.n):
+        d = float(rays.range_rt_m[i])
+        v = float(rays.radial_velocity_mps[i])
+        az, el = float(rays.azimuth_rad[i]), float(rays.elevation_rad[i])
+        for k in range(radar.n_virtual):
+            tx = k // radar.n_rx
+            for j in range(radar.n_chirps):
+                tau = (d + 2.0 * v * (j * radar.chirp_period_s + tx * radar.tdm_slot_s)) / C
+                beat = tau if exact else d / C
+                ph = (2 * math.pi * (mu * t * beat + radar.carrier_hz * tau) + float(rays.phase0_rad[i])
+                      + 2 * math.pi * k * s_m * math.sin(az) * math.cos(el) / lam)
+                out[k, j] += float(rays.amplitude[i]) * np.exp(1j * ph)
+    return out
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_tdm_slot_offsets_match_eq2_brute_force(model):
+    radar = small_radar(n_samples=16, n_chirps=8, n_tx=3, n_rx=2, n_angle=8, tdm_slot_s=13.3e-6, model=model)
+    rays = scenegen.uniform_rays(seed=23 + model, n=5, v_max=40.0)
+    ref = brute_signal_tdm(radar, rays, exact=bool(model))
+    got = oracle.signal(radar, rays)
+    assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    idx = np.arange(0, ref.size, 5)
+    assert np.array_equal(oracle.signal_at(radar, rays, idx), got.reshape(-1)[idx])
+    # the offsets only act on moving rays, and only on transmitters t > 0
+    off = oracle.signal(radar.replace(tdm_slot_s=0.0), rays)
+    assert np.array_equal(got[: radar.n_rx], off[: radar.n_rx])
+    assert np.abs(got - off).max() > 1e-2 * np.abs(ref).max()
+
+
+def test_tdm_two_oracle_paths_agree():
+    """The per-cell DTFT path with its own angle sum equals DFT(signal) under TDM offsets."""
+    radar = small_radar(n_samples=16, n_chirps=8, n_tx=3, n_rx=2, n_angle=8, tdm_slot_s=20e-6,
+                        window=(WIN_HANN_PERIODIC, WIN_HANN_PERIODIC, WIN_HANN_NOZERO))
+    rays = scenegen.uniform_rays(seed=29, n=7, v_max=30.0)
+    X = oracle.spectrum(radar, oracle.signal(radar, rays))
+    cells = np.arange(0, X.size, 3)
+    got = oracle.cell_dtft(radar, rays, cells)
+    assert np.abs(got - X.reshape(-1)[cells]).max() <= 1e-12 * np.abs(X).max()
