@@ -83,6 +83,9 @@ def _load():
             lib.orc_cos_rep.argtypes = [ctypes.c_double]
             lib.orc_cos_rep.restype = ctypes.c_double
             lib.orc_default_threads.restype = ctypes.c_int
+            lib.orc_paths.argtypes = [P, P, P, P, ctypes.c_int]
+            lib.orc_signal_geom.argtypes = [P, P, P, P, ctypes.c_int]
+            lib.orc_signal_geom_at.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int]
             _lib = lib
     return _lib
 
@@ -120,6 +123,45 @@ class _RayRef:
         self.obj = np.ascontiguousarray(rays.object_id, np.int32)
         self.s = _Rays(self.d.shape[0], self.d.ctypes.data, self.a.ctypes.data, self.v.ctypes.data,
                        self.az.ctypes.data, self.el.ctypes.data, self.p0.ctypes.data)
+
+
+class _Geometry(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
+                ("tx_pos", ctypes.c_void_p), ("rx_pos", ctypes.c_void_p),
+                ("ref_tx", ctypes.c_double * 3), ("ref_rx", ctypes.c_double * 3),
+                ("hit_offset", ctypes.c_void_p), ("hit_triangle", ctypes.c_void_p),
+                ("hit_u", ctypes.c_void_p), ("hit_v", ctypes.c_void_p)]
+
+
+class _GeomRef:
+    """Contiguous typed copies of a scene's mesh, antennas and hit lists for one C call."""
+
+    def __init__(self, radar, rays, hits, geom):
+        self.vert = np.ascontiguousarray(geom.vertices, np.float64)
+        self.tri = np.ascontiguousarray(geom.triangles, np.int32)
+        self.tx = np.ascontiguousarray(geom.tx_pos, np.float64)
+        self.rx = np.ascontiguousarray(geom.rx_pos, np.float64)
+        self.off = np.ascontiguousarray(hits.offset, np.int64)
+        self.ht = np.ascontiguousarray(hits.triangle, np.int32)
+        self.hu = np.ascontiguousarray(hits.u, np.float32)
+        self.hv = np.ascontiguousarray(hits.v, np.float32)
+        assert self.vert.shape[0] == radar.n_chirps and self.vert.shape[2] == 3
+        assert self.tx.shape == (radar.n_tx, 3) and self.rx.shape == (radar.n_rx, 3)
+        assert self.off.shape[0] == rays.n + 1 and np.all(np.diff(self.off) >= 1)
+        assert np.all((self.tri >= 0) & (self.tri < self.vert.shape[1]))
+        assert np.all((self.ht >= 0) & (self.ht < self.tri.shape[0]))
+        g = _Geometry()
+        g.n_vertices = self.vert.shape[1]
+        g.n_triangles = self.tri.shape[0]
+        g.vertices, g.triangles = self.vert.ctypes.data, self.tri.ctypes.data
+        g.tx_pos, g.rx_pos = self.tx.ctypes.data, self.rx.ctypes.data
+        for c in range(3):
+            g.ref_tx[c] = float(geom.ref_tx[c])
+            g.ref_rx[c] = float(geom.ref_rx[c])
+        g.hit_offset, g.hit_triangle = self.off.ctypes.data, self.ht.ctypes.data
+        g.hit_u, g.hit_v = self.hu.ctypes.data, self.hv.ctypes.data
+        self.s = g
 
 
 def _ptr(a: np.ndarray):
@@ -258,3 +300,32 @@ def span_labels(spectra, threshold: float) -> np.ndarray:
     lab = np.argmax(masked, axis=0).astype(np.int32)
     lab[~ok.any(axis=0)] = -1
     return lab
+
+
+def paths(radar, rays, hits, geom, nthreads: int = 0) -> np.ndarray:
+    """float64[n][N_c][N_v]: path length of each ray at each chirp snapshot and virtual
+    channel (Eq. 6 hit positions, Eq. 7 antenna displacement)."""
+    lib = _load()
+    rp, rr, gr = _radar(radar), _RayRef(rays), _GeomRef(radar, rays, hits, geom)
+    out = np.zeros((rays.n, radar.n_chirps, radar.n_virtual), np.float64)
+    lib.orc_paths(ctypes.byref(rp), ctypes.byref(rr.s), ctypes.byref(gr.s), _ptr(out), nthreads)
+    return out
+
+
+def signal_geom(radar, rays, hits, geom, nthreads: int = 0) -> np.ndarray:
+    """complex128[N_v][N_c][N_s]: Eq. 2 over the per-(ray, chirp, channel) path lengths."""
+    lib = _load()
+    rp, rr, gr = _radar(radar), _RayRef(rays), _GeomRef(radar, rays, hits, geom)
+    out = np.zeros((radar.n_virtual, radar.n_chirps, radar.n_samples, 2), np.float64)
+    lib.orc_signal_geom(ctypes.byref(rp), ctypes.byref(rr.s), ctypes.byref(gr.s), _ptr(out), nthreads)
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def signal_geom_at(radar, rays, hits, geom, flat_idx, nthreads: int = 0) -> np.ndarray:
+    lib = _load()
+    rp, rr, gr = _radar(radar), _RayRef(rays), _GeomRef(radar, rays, hits, geom)
+    idx = np.ascontiguousarray(flat_idx, np.int64)
+    out = np.zeros((idx.shape[0], 2), np.float64)
+    lib.orc_signal_geom_at(ctypes.byref(rp), ctypes.byref(rr.s), ctypes.byref(gr.s), idx.shape[0], _ptr(idx),
+                           _ptr(out), nthreads)
+    return out[:, 0] + 1j * out[:, 1]

@@ -408,6 +408,130 @@ void orc_cell_dtft(const orc_radar *p, const orc_rays *r, int64_t ncells, const 
   free(rc); free(wr); free(wd); free(wa);
 }
 
+/* --------------------------------------------------------------- virtual snapshots (Eq. 6, Eq. 7) */
+/* hit h at chirp snapshot j: the stored barycentric coordinates applied to the triangle's
+   vertices at that snapshot, p = (1 - u - v) v1 + u v2 + v v3 (Eq. 6) */
+static void hit_position(const orc_geometry *g, int64_t j, int64_t h, double out[3]) {
+  const int32_t *tri = g->triangles + 3 * (int64_t)g->hit_triangle[h];
+  const double *V = g->vertices + j * g->n_vertices * 3;
+  const double u = (double)g->hit_u[h], v = (double)g->hit_v[h];
+  const double w = 1.0 - u - v;
+  for (int c = 0; c < 3; ++c) {
+#if defined(ORC_MUTATION) && ORC_MUTATION == 11
+    out[c] = w * V[3 * tri[0] + c] + v * V[3 * tri[1] + c] + u * V[3 * tri[2] + c];  /* u, v swapped */
+#else
+    out[c] = w * V[3 * tri[0] + c] + u * V[3 * tri[1] + c] + v * V[3 * tri[2] + c];
+#endif
+  }
+}
+
+static double distance3(const double a[3], const double b[3]) {
+  const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+  return sqrt(x * x + y * y + z * z);
+}
+
+/* length between the first and the last hit at snapshot j */
+static double inner_length(const orc_geometry *g, int64_t i, int64_t j) {
+  double s = 0.0, prev[3], cur[3];
+  hit_position(g, j, g->hit_offset[i], prev);
+  for (int64_t h = g->hit_offset[i] + 1; h < g->hit_offset[i + 1]; ++h) {
+    hit_position(g, j, h, cur);
+    s += distance3(prev, cur);
+    prev[0] = cur[0]; prev[1] = cur[1]; prev[2] = cur[2];
+  }
+  return s;
+}
+
+/* Eq. 7: the traced length minus the legs to the traced antennas at snapshot 0, plus the legs
+   to transmitter t and receiver r at snapshot j; the path between the first and last hit is
+   re-measured at snapshot j (the hits move with their triangles, Eq. 6) */
+static double path_length(const orc_geometry *g, const orc_rays *r, int64_t i, int64_t j, int t, int rx) {
+  const int64_t f = g->hit_offset[i], l = g->hit_offset[i + 1] - 1;
+  double pf0[3], pl0[3], pfj[3], plj[3];
+  hit_position(g, 0, f, pf0);
+  hit_position(g, 0, l, pl0);
+  hit_position(g, j, f, pfj);
+  hit_position(g, j, l, plj);
+#if defined(ORC_MUTATION) && ORC_MUTATION == 12
+  return r->range_rt_m[i] - distance3(pf0, g->ref_tx) + distance3(pfj, g->tx_pos + 3 * t) -
+         inner_length(g, i, 0) + inner_length(g, i, j) - distance3(pl0, g->ref_rx) +
+         distance3(plj, g->rx_pos + 3 * t);                       /* receiver leg to the transmitter */
+#else
+  return r->range_rt_m[i] - distance3(pf0, g->ref_tx) + distance3(pfj, g->tx_pos + 3 * t) -
+         inner_length(g, i, 0) + inner_length(g, i, j) - distance3(pl0, g->ref_rx) +
+         distance3(plj, g->rx_pos + 3 * rx);
+#endif
+}
+
+typedef struct {
+  const orc_radar *p;
+  const orc_rays *r;
+  const orc_geometry *g;
+  double *out;
+  const int64_t *idx;
+} geom_ctx;
+
+static void paths_rays(void *vctx, int64_t lo, int64_t hi) {
+  geom_ctx *c = (geom_ctx *)vctx;
+  const int nc = c->p->n_chirps, nv = nv_of(c->p);
+  for (int64_t i = lo; i < hi; ++i)
+    for (int j = 0; j < nc; ++j)
+      for (int k = 0; k < nv; ++k)
+        c->out[(i * nc + j) * nv + k] = path_length(c->g, c->r, i, j, k / c->p->n_rx, k % c->p->n_rx);
+}
+
+void orc_paths(const orc_radar *p, const orc_rays *r, const orc_geometry *g, double *out, int nthreads) {
+  geom_ctx c = {p, r, g, out, NULL};
+  parallel_for(r->n, nthreads, paths_rays, &c);
+}
+
+/* one output sample of Eq. 2 with tau = l / c: sum_i a_i e^{2 pi i (f_c tau + mu t_n tau) + i phi0} */
+static void geom_point(const geom_ctx *c, int64_t k, int64_t m, int64_t n, double *sr, double *si) {
+  const orc_radar *p = c->p;
+  const double mu = p->bandwidth_hz / p->sweep_time_s, dt = p->sweep_time_s / p->n_samples;
+  double accr = 0.0, acci = 0.0;
+  for (int64_t i = 0; i < c->r->n; ++i) {
+    const double tau = path_length(c->g, c->r, i, m, (int)(k / p->n_rx), (int)(k % p->n_rx)) / ORC_C;
+    const double amp = pattern_amp(p, (double)c->r->amplitude[i], (double)c->r->azimuth_rad[i],
+                                   (double)c->r->elevation_rad[i]);
+    double re, im;
+    cis_cycles(frac(p->carrier_hz * tau) + frac((double)c->r->phase0_rad[i] / ORC_TWO_PI) +
+                   frac(mu * (double)n * dt * tau), &re, &im);
+    accr += amp * re;
+    acci += amp * im;
+  }
+  *sr = accr;
+  *si = acci;
+}
+
+static void geom_rows(void *vctx, int64_t lo, int64_t hi) {
+  geom_ctx *c = (geom_ctx *)vctx;
+  const int64_t ns = c->p->n_samples, nc = c->p->n_chirps;
+  for (int64_t row = lo; row < hi; ++row)
+    for (int64_t n = 0; n < ns; ++n)
+      geom_point(c, row / nc, row % nc, n, &c->out[2 * (row * ns + n)], &c->out[2 * (row * ns + n) + 1]);
+}
+
+static void geom_points(void *vctx, int64_t lo, int64_t hi) {
+  geom_ctx *c = (geom_ctx *)vctx;
+  const int64_t ns = c->p->n_samples, nc = c->p->n_chirps;
+  for (int64_t t = lo; t < hi; ++t) {
+    const int64_t f = c->idx[t];
+    geom_point(c, f / (ns * nc), (f / ns) % nc, f % ns, &c->out[2 * t], &c->out[2 * t + 1]);
+  }
+}
+
+void orc_signal_geom(const orc_radar *p, const orc_rays *r, const orc_geometry *g, double *out, int nthreads) {
+  geom_ctx c = {p, r, g, out, NULL};
+  parallel_for((int64_t)nv_of(p) * p->n_chirps, nthreads, geom_rows, &c);
+}
+
+void orc_signal_geom_at(const orc_radar *p, const orc_rays *r, const orc_geometry *g, int64_t npts,
+                        const int64_t *idx, double *out, int nthreads) {
+  geom_ctx c = {p, r, g, out, idx};
+  parallel_for(npts, nthreads, geom_points, &c);
+}
+
 /* --------------------------------------------------------------- polynomial sin / cos */
 /* Cody-Waite reduction by pi/2 split into two doubles (P1 + P2), then Taylor series
    of sin and cos on [-pi/4, pi/4] in Horner form with fused multiply-adds in a fixed

@@ -78,6 +78,31 @@ void orc_labels(const orc_radar *p, const orc_rays *r, const int32_t *object_id,
    Returns the number of pairs; arrays must hold r->n entries. */
 int64_t orc_cell_object_energy(const orc_radar *p, const orc_rays *r, const int32_t *object_id,
                                int64_t *cell, int32_t *obj, int64_t *energy);
+/* Moving scene for virtual snapshots (Sec. II-D, Eq. 6) and antenna displacement (Sec. II-E,
+   Eq. 7).  Ray i hit the triangles hit_triangle[h], h = hit_offset[i] .. hit_offset[i+1]-1, in
+   path order (first hit first), at barycentric coordinates (hit_u, hit_v); its traced path
+   length d_i runs from ref_tx over those hits to ref_rx at snapshot 0. */
+typedef struct {
+  int64_t n_vertices, n_triangles;
+  const double *vertices;    /* [N_c][n_vertices][3]: vertex positions at t = j T_d (m) */
+  const int32_t *triangles;  /* [n_triangles][3] vertex indices */
+  const double *tx_pos;      /* [n_tx][3] transmitter positions */
+  const double *rx_pos;      /* [n_rx][3] receiver positions */
+  double ref_tx[3], ref_rx[3];
+  const int64_t *hit_offset; /* [n + 1] */
+  const int32_t *hit_triangle;
+  const float *hit_u, *hit_v;
+} orc_geometry;
+
+/* Path length of every ray at every chirp snapshot and virtual channel k = tx N_rx + rx:
+   out[i][j][k] (Eq. 6 hit positions, Eq. 7 antenna displacement, inner path updated). */
+void orc_paths(const orc_radar *p, const orc_rays *r, const orc_geometry *g, double *out, int nthreads);
+/* Eq. 2 with those path lengths, tau_i(j, k) = l_i(j, k) / c in both the beat and the carrier
+   term: the signal cube, or its values at flat indices (k*N_c + m)*N_s + n. */
+void orc_signal_geom(const orc_radar *p, const orc_rays *r, const orc_geometry *g, double *out, int nthreads);
+void orc_signal_geom_at(const orc_radar *p, const orc_rays *r, const orc_geometry *g, int64_t npts,
+                        const int64_t *idx, double *out, int nthreads);
+
 /* The polynomial sine/cosine used for the angle bin (Cody-Waite + Taylor). |x| <= pi. */
 double orc_sin_rep(double x);
 double orc_cos_rep(double x);

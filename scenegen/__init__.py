@@ -227,6 +227,149 @@ def cluster_rays(seed: int, n_rays: int, n_objects: int = 20, clutter_frac: floa
     return Rays.concat([objects, clutter])
 
 
+# ---------------------------------------------------------------- moving triangle scenes
+
+@dataclasses.dataclass
+class Geometry:
+    """Animated triangle mesh and antenna positions (x forward, y left, z up; metres)."""
+    vertices: np.ndarray   # f64 [N_c][V][3]: vertex positions at t = j T_d
+    triangles: np.ndarray  # i32 [T][3] vertex indices
+    tx_pos: np.ndarray     # f64 [n_tx][3]
+    rx_pos: np.ndarray     # f64 [n_rx][3]
+    ref_tx: np.ndarray     # f64 [3]: antennas the rays were traced between
+    ref_rx: np.ndarray     # f64 [3]
+
+
+@dataclasses.dataclass
+class Hits:
+    """Per-ray hit lists in CSR form, first hit first."""
+    offset: np.ndarray     # i64 [n + 1]
+    triangle: np.ndarray   # i32 [H]
+    u: np.ndarray          # f32 [H] barycentric coordinates
+    v: np.ndarray          # f32 [H]
+
+    @property
+    def n_hits(self) -> np.ndarray:
+        return np.diff(self.offset).astype(np.int32)
+
+
+_BOX_TRIS = np.array([[0, 1, 2], [0, 2, 3], [4, 6, 5], [4, 7, 6], [0, 4, 5], [0, 5, 1],
+                      [1, 5, 6], [1, 6, 2], [2, 6, 7], [2, 7, 3], [3, 7, 4], [3, 4, 0]], np.int32)
+
+
+def _rot_z(angle: np.ndarray, xyz: np.ndarray) -> np.ndarray:
+    c, s = np.cos(angle), np.sin(angle)
+    return np.stack([c * xyz[..., 0] - s * xyz[..., 1], s * xyz[..., 0] + c * xyz[..., 1], xyz[..., 2]], -1)
+
+
+def moving_scene(seed: int, radar: Radar, n_rays: int, n_objects: int = 8, bounce_frac: float = 0.2,
+                 r_range=(3.0, 30.0), v_max: float = 15.0, yaw_max: float = 1.0):
+    """A scene of boxes moving and turning in front of the radar, standing in for the ray
+    tracer's output: rays with their traced path length, hit lists on the boxes (a fraction
+    first bouncing off a static ground plane), and the mesh animated over the N_c chirps.
+
+    The virtual array lies along -y: transmitter t at y = -t N_rx s, receiver r at y = -r s,
+    s the element spacing (lambda / 2 by default); rays were traced between transmitter 0
+    and receiver 0 at the origin.  Box j (id j + 1): size U(0.5, 4.5) x U(0.5, 2) x
+    U(0.5, 1.8) m, centre at range U(r_range), azimuth U(+-60 deg), height U(-0.5, 0.5) m,
+    radial velocity U(+-v_max), tangential U(+-2) m/s, yaw rate U(+-yaw_max) rad/s.  Rays
+    pick a box uniformly, a triangle uniformly and a uniform point on it; with probability
+    bounce_frac the ray first hits the ground (z = -1.5 m) half way to that point.
+    Amplitude sqrt(RCS) / R^2 with R = d / 2, start phase U[0, 2 pi).  The label inputs
+    (v, az, el) are the traced ray's: half the path-length rate between the first two
+    snapshots, and the direction of its first hit at snapshot 0."""
+    lam = 299792458.0 / radar.carrier_hz
+    sp = radar.element_spacing_m or lam / 2
+    tx = np.zeros((radar.n_tx, 3))
+    tx[:, 1] = -np.arange(radar.n_tx) * radar.n_rx * sp
+    rx = np.zeros((radar.n_rx, 3))
+    rx[:, 1] = -np.arange(radar.n_rx) * sp
+    size = np.stack([uniform(seed, 300, n_objects, 0.5, 4.5), uniform(seed, 301, n_objects, 0.5, 2.0),
+                     uniform(seed, 302, n_objects, 0.5, 1.8)], -1)
+    rng = uniform(seed, 303, n_objects, *r_range)
+    azc = uniform(seed, 304, n_objects, -60 * _DEG, 60 * _DEG)
+    zc = uniform(seed, 305, n_objects, -0.5, 0.5)
+    centre = np.stack([rng * np.cos(azc), rng * np.sin(azc), zc], -1)
+    los = centre / np.linalg.norm(centre, axis=1, keepdims=True)
+    side = np.stack([-np.sin(azc), np.cos(azc), np.zeros(n_objects)], -1)
+    vel = los * uniform(seed, 306, n_objects, -v_max, v_max)[:, None] + side * uniform(seed, 307, n_objects, -2, 2)[:, None]
+    yaw0 = uniform(seed, 308, n_objects, -math.pi, math.pi)
+    yaw_rate = uniform(seed, 309, n_objects, -yaw_max, yaw_max)
+    corners = np.array([[-1, -1, -1], [1, -1, -1], [1, 1, -1], [-1, 1, -1],
+                        [-1, -1, 1], [1, -1, 1], [1, 1, 1], [-1, 1, 1]], np.float64) * 0.5
+    offs = corners[None] * size[:, None, :]                                  # [obj][8][3]
+    t = np.arange(radar.n_chirps) * radar.chirp_period_s
+    ang = yaw0[None, :, None] + yaw_rate[None, :, None] * t[:, None, None]   # [j][obj][1]
+    boxes = (centre[None, :, None, :] + vel[None, :, None, :] * t[:, None, None, None]
+             + _rot_z(np.broadcast_to(ang, (radar.n_chirps, n_objects, 8)), np.broadcast_to(offs, (radar.n_chirps, n_objects, 8, 3))))
+    ground = np.array([[0.0, -100.0, -1.5], [150.0, -100.0, -1.5], [150.0, 100.0, -1.5], [0.0, 100.0, -1.5]])
+    verts = np.concatenate([boxes.reshape(radar.n_chirps, -1, 3),
+                            np.broadcast_to(ground, (radar.n_chirps, 4, 3))], 1).astype(np.float64)
+    g0 = 8 * n_objects
+    tris = np.concatenate([(_BOX_TRIS[None] + 8 * np.arange(n_objects)[:, None, None]).reshape(-1, 3),
+                           np.array([[g0, g0 + 1, g0 + 2], [g0, g0 + 2, g0 + 3]])]).astype(np.int32)
+    # object hits
+    obj = randint(seed, 310, n_rays, 0, n_objects - 1)
+    tri = (12 * obj + randint(seed, 311, n_rays, 0, 11)).astype(np.int32)
+    u = uniform(seed, 312, n_rays)
+    v = uniform(seed, 313, n_rays)
+    fold = u + v > 1.0
+    u, v = np.where(fold, 1.0 - u, u), np.where(fold, 1.0 - v, v)
+    u, v = u.astype(np.float32), v.astype(np.float32)
+
+    def on_tri(j, tr, uu, vv):
+        V = verts[j]
+        a, b, c = V[tris[tr, 0]], V[tris[tr, 1]], V[tris[tr, 2]]
+        uu = uu.astype(np.float64)[:, None]
+        vv = vv.astype(np.float64)[:, None]
+        return (1.0 - uu - vv) * a + uu * b + vv * c
+
+    p_obj0 = on_tri(0, tri, u, v)
+    bounce = uniform(seed, 314, n_rays) < bounce_frac
+    # ground point half way (static plane): barycentric coordinates on one of its two triangles
+    gx, gy = 0.5 * p_obj0[:, 0], 0.5 * p_obj0[:, 1]
+    s_, t_ = gx / 150.0, (gy + 100.0) / 200.0                                 # unit-square coordinates
+    lower = s_ >= t_                                                         # triangle (g0, g0+1, g0+2)
+    gtri = np.where(lower, len(tris) - 2, len(tris) - 1).astype(np.int32)
+    gu = np.where(lower, s_ - t_, s_).astype(np.float32)
+    gv = np.where(lower, t_, t_ - s_).astype(np.float32)
+    nh = np.where(bounce, 2, 1)
+    offset = np.concatenate([[0], np.cumsum(nh)]).astype(np.int64)
+    H = int(offset[-1])
+    htri = np.empty(H, np.int32)
+    hu = np.empty(H, np.float32)
+    hv = np.empty(H, np.float32)
+    first = offset[:-1]
+    htri[first] = np.where(bounce, gtri, tri)
+    hu[first] = np.where(bounce, gu, u)
+    hv[first] = np.where(bounce, gv, v)
+    second = first[bounce] + 1
+    htri[second] = tri[bounce]
+    hu[second] = u[bounce]
+    hv[second] = v[bounce]
+    hits = Hits(offset, htri, hu, hv)
+
+    def polyline(j):
+        pts_first = on_tri(j, htri[first], hu[first], hv[first])
+        pts_last = on_tri(j, htri[offset[1:] - 1], hu[offset[1:] - 1], hv[offset[1:] - 1])
+        inner = np.where(bounce, np.linalg.norm(pts_last - pts_first, axis=1), 0.0)
+        return (np.linalg.norm(pts_first - tx[0], axis=1) + inner + np.linalg.norm(pts_last - rx[0], axis=1),
+                pts_first)
+
+    d0, pf = polyline(0)
+    d1, _ = polyline(1) if radar.n_chirps > 1 else (d0, None)
+    az = np.arctan2(pf[:, 1], pf[:, 0])
+    el = np.arctan2(pf[:, 2], np.hypot(pf[:, 0], pf[:, 1]))
+    rays = Rays(range_rt_m=d0.astype(np.float64),
+                amplitude=_amplitude(seed, 315, 0.5 * d0).astype(np.float32),
+                radial_velocity_mps=((d1 - d0) / (2.0 * radar.chirp_period_s)).astype(np.float32),
+                azimuth_rad=az.astype(np.float32), elevation_rad=el.astype(np.float32),
+                phase0_rad=uniform(seed, 317, n_rays, 0.0, 2.0 * math.pi).astype(np.float32),
+                object_id=(obj + 1).astype(np.int32), material_id=nh.astype(np.int32))
+    geom = Geometry(verts, tris, tx, rx, tx[0].copy(), rx[0].copy())
+    return rays, hits, geom
+
+
 # ---------------------------------------------------------------- named workloads
 
 def tiny_scene(seed: int = 0, n_rays: int = 2000):

@@ -21,6 +21,8 @@ MUTATIONS = {
     8: "leaves the range window out of the spectrum",
     9: "uses sin(elevation) in the antenna pattern",
     10: "takes the receiver index as the TDM transmitter slot",
+    11: "swaps the barycentric weights u and v of Eq. 6",
+    12: "measures the receiver leg of Eq. 7 to the transmitter's position",
 }
 
 

@@ -516,3 +516,110 @@ def test_tdm_two_oracle_paths_agree():
     cells = np.arange(0, X.size, 3)
     got = oracle.cell_dtft(radar, rays, cells)
     assert np.abs(got - X.reshape(-1)[cells]).max() <= 1e-12 * np.abs(X).max()
+
+
+# ------------------------------------------------------------------ virtual snapshots (Eq. 6, Eq. 7)
+
+def polyline_paths(radar, hits, geom):
+    """Path of every ray at every snapshot j and channel (t, r), measured directly: transmitter t
+    to the hits at snapshot j (each the barycentric point of its triangle's vertices then) and
+    on to receiver r."""
+    V, T = geom.vertices, geom.triangles
+    n = hits.offset.shape[0] - 1
+    out = np.zeros((n, radar.n_chirps, radar.n_virtual))
+    for i in range(n):
+        hs = range(int(hits.offset[i]), int(hits.offset[i + 1]))
+        for j in range(radar.n_chirps):
+            pts = []
+            for h in hs:
+                a, b, c = (V[j, T[hits.triangle[h], q]] for q in range(3))
+                u, v = float(hits.u[h]), float(hits.v[h])
+                pts.append(np.einsum("q,qc->c", [1.0 - u - v, u, v], np.stack([a, b, c])))
+            inner = sum(np.linalg.norm(pts[q + 1] - pts[q]) for q in range(len(pts) - 1))
+            for k in range(radar.n_virtual):
+                t, r = divmod(k, radar.n_rx)
+                out[i, j, k] = (np.linalg.norm(pts[0] - geom.tx_pos[t]) + inner
+                                + np.linalg.norm(pts[-1] - geom.rx_pos[r]))
+    return out
+
+
+def test_snapshot_paths_match_polylines():
+    """Eq. 6 moves each hit with its triangle and Eq. 7 swaps the antenna legs: with the traced
+    length equal to the snapshot-0 polyline, every path is the polyline at snapshot j between
+    transmitter t and receiver r.  A traced length carrying an extra delta shifts every path
+    by exactly that delta (Eq. 7 only replaces the two antenna legs)."""
+    radar = scenegen.radar_automotive(n_chirps=8, n_samples=16)
+    rays, hits, geom = scenegen.moving_scene(3, radar, 40, bounce_frac=0.4)
+    assert np.any(hits.n_hits == 2) and np.any(hits.n_hits == 1)
+    ref = polyline_paths(radar, hits, geom)
+    got = oracle.paths(radar, rays, hits, geom)
+    assert np.abs(got - ref).max() <= 1e-10
+    assert np.ptp(got[:, :, 0], axis=1).max() > 0.01      # the boxes move over the frame
+    shifted = rays.take(slice(None))
+    shifted.range_rt_m = rays.range_rt_m + 0.37
+    assert np.abs(oracle.paths(radar, shifted, hits, geom) - got - 0.37).max() <= 1e-12
+
+
+def _one_triangle_scene(radar, verts0, vel, hit_uv, d_offset=0.0):
+    tri = np.array([[0, 1, 2]], np.int32)
+    t = np.arange(radar.n_chirps) * radar.chirp_period_s
+    verts = verts0[None] + vel[None, None, :] * t[:, None, None]
+    z = np.zeros(3)
+    geom = scenegen.Geometry(verts, tri, np.zeros((radar.n_tx, 3)), np.zeros((radar.n_rx, 3)), z, z)
+    n = len(hit_uv)
+    hits = scenegen.Hits(np.arange(n + 1, dtype=np.int64), np.zeros(n, np.int32),
+                         np.array([u for u, _ in hit_uv], np.float32), np.array([v for _, v in hit_uv], np.float32))
+    return geom, hits
+
+
+def test_barycentric_corners_are_the_vertices():
+    radar = small_radar(n_samples=16, n_chirps=4, n_tx=1, n_rx=1, n_angle=1)
+    verts0 = np.array([[10.0, 1.0, 0.5], [12.0, -2.0, 0.0], [9.0, 0.0, 3.0]])
+    vel = np.array([3.0, -1.0, 0.5])
+    geom, hits = _one_triangle_scene(radar, verts0, vel, [(0.0, 0.0), (1.0, 0.0), (0.0, 1.0)])
+    rays = Rays(2 * np.linalg.norm(verts0, axis=1), np.ones(3, np.float32), np.zeros(3, np.float32),
+                np.zeros(3, np.float32), np.zeros(3, np.float32), np.zeros(3, np.float32), np.zeros(3, np.int32))
+    P = oracle.paths(radar, rays, hits, geom)[:, :, 0]
+    for q in range(3):
+        for j in range(radar.n_chirps):
+            ref = 2 * np.linalg.norm(verts0[q] + vel * j * radar.chirp_period_s)
+            assert abs(P[q, j] - ref) <= 1e-12 * ref
+
+
+def test_radial_motion_reduces_to_the_exact_model():
+    """A triangle moving along the line of sight of its hit point at speed v, antennas at the
+    origin: the path is d + 2 v j T_d and the signal equals Eq. 2 with tau_i(j) in both terms."""
+    radar = small_radar(n_samples=32, n_chirps=16, n_tx=1, n_rx=1, n_angle=1)
+    verts0 = np.array([[20.0, 3.0, 1.0], [21.0, 2.0, 0.0], [20.5, 4.0, -1.0]])
+    uv = (0.25, 0.35)
+    p0 = (1 - uv[0] - uv[1]) * verts0[0] + uv[0] * verts0[1] + uv[1] * verts0[2]
+    v = 7.5
+    geom, hits = _one_triangle_scene(radar, verts0, v * p0 / np.linalg.norm(p0), [uv])
+    d = 2 * np.linalg.norm(p0)
+    rays = one_ray(d, a=0.7, v=v, phi0=1.1)
+    got = oracle.signal_geom(radar, rays, hits, geom)
+    ref = oracle.signal(radar.replace(model=1), rays)
+    assert np.abs(got - ref).max() <= 1e-8 * np.abs(ref).max()
+    ref_bf = brute_signal_exact(radar, rays)
+    assert np.abs(got - ref_bf).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_far_field_limit_of_eq7():
+    """A static scatterer 2 km away: the channel-to-channel path step of the array along -y is
+    s sin(az) cos(el) to within aperture^2 / R."""
+    radar = scenegen.radar_automotive(n_chirps=2, n_samples=16)
+    lam = C / radar.carrier_hz
+    s = lam / 2
+    az, el = 0.4, -0.1
+    dirv = np.array([math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), math.sin(el)])
+    p0 = 2000.0 * dirv
+    verts0 = p0[None] + np.array([[0.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    geom, hits = _one_triangle_scene(radar, verts0, np.zeros(3), [(0.0, 0.0)])
+    geom.tx_pos[:, 1] = -np.arange(radar.n_tx) * radar.n_rx * s
+    geom.rx_pos[:, 1] = -np.arange(radar.n_rx) * s
+    rays = one_ray(2 * 2000.0)
+    P = oracle.paths(radar, rays, hits, geom)[0, 0]
+    k = np.arange(radar.n_virtual)
+    aperture = radar.n_virtual * s
+    assert np.abs((P - P[0]) - k * s * math.sin(az) * math.cos(el)).max() <= aperture ** 2 / 2000.0
+    assert np.abs((P - P[0]) - k * s * math.sin(az) * math.cos(el)).max() > 0.0
