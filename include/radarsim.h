@@ -173,6 +173,54 @@ SIM_API int sim_destroy(sim_ctx *ctx);
 /* Static string for a status code. */
 SIM_API const char *sim_status_string(int status);
 
+/* ---- virtual snapshots and antenna displacement (Sec. II-D Eq. 6, Sec. II-E Eq. 7) ----
+   A ray traced once (first chirp, one transmitter / receiver pair) keeps its hits as
+   (triangle, u, v).  At chirp j a hit sits at (1 - u - v) v1 + u v2 + v v3 of its triangle's
+   vertices at that snapshot (Eq. 6); the ray's path to transmitter t and receiver r is its
+   traced length d with both antenna legs replaced (Eq. 7) and the stretch between its first
+   and last hit measured again at snapshot j:
+     l(j, t, r) = d + [inner(j) - inner(0)] + |p_f(j) - x_t| - |p_f(0) - ref_tx|
+                    + |p_l(j) - x_r| - |p_l(0) - ref_rx|.
+   Coordinates in metres, FP64. */
+typedef struct {
+  int64_t n_vertices;         /* V, 1 .. 2^31 */
+  int64_t n_triangles;        /* 1 .. 2^31 */
+  const double *vertices;     /* [N_c][V][3]: vertex positions at t = j T_d, one snapshot per chirp */
+  const int32_t *triangles;   /* [n_triangles][3] vertex indices in [0, V) */
+  const double *tx_pos;       /* [n_tx][3] transmitter positions */
+  const double *rx_pos;       /* [n_rx][3] receiver positions */
+  double ref_tx[3];           /* the transmitter and receiver the rays were traced between */
+  double ref_rx[3];
+} sim_geometry;
+
+/* Hit lists in CSR form: ray i hit triangle[h] at (u[h], v[h]) for h = offset[i] ..
+   offset[i+1] - 1, first hit first; offset[0] = 0 and every ray has at least one hit. */
+typedef struct {
+  const int64_t *offset;      /* [n + 1] */
+  const int32_t *triangle;    /* [offset[n]] indices in [0, n_triangles) */
+  const float *u;             /* [offset[n]] barycentric coordinates */
+  const float *v;
+} sim_hits;
+
+/* Path lengths l(j, t, r) of every ray into paths, double[n][N_c][N_v] (k = t N_rx + r), host or
+   device.  The context gives N_c, n_tx, n_rx; it must use SIM_PREC_FP32_DIRECT and no TDM slot
+   time.  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
+   memory.  SIM_E_INVALID for bad arguments, a hit list or index out of range (checked before
+   any access) or a ray failing sim_submit's checks. */
+SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hits *hits, const sim_geometry *geom,
+                               double *paths);
+
+/* The scene through Eq. 2 with tau = l(j, t, r) / c in both the beat and the carrier term
+   (channel k = t N_rx + r, chirp m = j):
+     s[k][m][n] = sum_i a_i' exp(2 pi j (f_c l / c + n B l / (c N_s)) + j phase0_i),
+   a_i' the amplitude after the antenna pattern; then the spectrum and the labels as for
+   sim_fetch (labels from the rays' analytic cells of d, v, az, el).  Any of spectrum,
+   signal, labels may be NULL (not all); spectrum and labels need the context's outputs
+   bit.  Same context limits, memory and errors as sim_snapshot_paths; the direct sum runs
+   in chunks of rays whose phase words fit 1 GiB. */
+SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, const sim_hits *hits,
+                             const sim_geometry *geom, void *spectrum, void *signal, int32_t *labels);
+
 /* ---- decomposition by ray meta data (Sec. II-C, Eq. 5) ----
    A span rule selects rays by meta data; a ray belongs to the span when every set field
    matches (then `exclude` complements the result):

@@ -26,6 +26,28 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
   return (f - 1.5f) * 6.28318530717958647692f;
 }
 
+// Add one staged chunk of rays to the thread's samples n = t + j T (j < NPT): phase words
+// (base of the row, per-sample step) and amplitudes in shared memory.
+template <int NPT>
+__device__ __forceinline__ void sum_chunk(const ulonglong2 *s_ph, const float *s_amp, int cnt, int t, uint64_t T,
+                                          float (&re)[NPT], float (&im)[NPT]) {
+#pragma unroll 2
+  for (int i = 0; i < cnt; ++i) {
+    const ulonglong2 q = s_ph[i];
+    const float a = s_amp[i];
+    uint64_t ph = q.x + static_cast<uint64_t>(t) * q.y;
+    const uint64_t step = T * q.y;
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) {
+      float sn, cs;
+      __sincosf(q64_to_rad(ph), &sn, &cs);
+      re[j] = fmaf(a, cs, re[j]);
+      im[j] = fmaf(a, sn, im[j]);
+      ph += step;
+    }
+  }
+}
+
 // One block per (k, m) row: thread t owns samples n = t + j * T (j < NPT).
 template <int NPT>
 __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
@@ -58,21 +80,7 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
     float re[NPT], im[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { re[j] = 0.f; im[j] = 0.f; }
-#pragma unroll 2
-    for (int i = 0; i < cnt; ++i) {
-      const ulonglong2 q = s_ph[i];
-      const float a = s_amp[i];
-      uint64_t ph = q.x + static_cast<uint64_t>(t) * q.y;
-      const uint64_t step = T * q.y;
-#pragma unroll
-      for (int j = 0; j < NPT; ++j) {
-        float sn, cs;
-        __sincosf(q64_to_rad(ph), &sn, &cs);
-        re[j] = fmaf(a, cs, re[j]);
-        im[j] = fmaf(a, sn, im[j]);
-        ph += step;
-      }
-    }
+    sum_chunk<NPT>(s_ph, s_amp, cnt, t, T, re, im);
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
   }
@@ -81,6 +89,59 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
   for (int j = 0; j < NPT; ++j) {
     const int n = t + j * blockDim.x;
     if (n < ns) o[n] = make_float2(tot_re[j], tot_im[j]);
+  }
+}
+
+// The same sum with phase words per (ray, chirp, transmitter) and (ray, chirp, receiver):
+// row (k = tx N_rx + rx, m) takes base = wt.x + wr.x and step = wt.y + wr.y, wt =
+// w_tx[(m N_tx + tx) stride + i], wr = w_rx[(m N_rx + rx) stride + i] (Q0.64, wrap-exact
+// sums).  With `accumulate` the row is added to what sig holds (rays in several chunks).
+template <int NPT>
+__global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restrict__ w_tx,
+                                                       const ulonglong2 *__restrict__ w_rx,
+                                                       const float *__restrict__ amp, int64_t n_rays, int64_t stride,
+                                                       int nc, int ns, int ntx, int nrx, int accumulate,
+                                                       float2 *__restrict__ sig) {
+  __shared__ ulonglong2 s_ph[kChunk];
+  __shared__ float s_amp[kChunk];
+  const int row = blockIdx.x;
+  const int k = row / nc, m = row % nc;
+  const int tx = k / nrx, rx = k - tx * nrx;
+  const ulonglong2 *wt = w_tx + (static_cast<int64_t>(m) * ntx + tx) * stride;
+  const ulonglong2 *wr = w_rx + (static_cast<int64_t>(m) * nrx + rx) * stride;
+  const int t = threadIdx.x;
+  const uint64_t T = blockDim.x;
+  float tot_re[NPT], tot_im[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) { tot_re[j] = 0.f; tot_im[j] = 0.f; }
+  for (int64_t c0 = 0; c0 < n_rays; c0 += kChunk) {
+    const int cnt = static_cast<int>(n_rays - c0 < kChunk ? n_rays - c0 : kChunk);
+    __syncthreads();
+    for (int i = t; i < cnt; i += blockDim.x) {
+      const ulonglong2 a = wt[c0 + i], b = wr[c0 + i];
+      s_ph[i] = make_ulonglong2(a.x + b.x, a.y + b.y);
+      s_amp[i] = amp[c0 + i];
+    }
+    __syncthreads();
+    float re[NPT], im[NPT];
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) { re[j] = 0.f; im[j] = 0.f; }
+    sum_chunk<NPT>(s_ph, s_amp, cnt, t, T, re, im);
+#pragma unroll
+    for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
+  }
+  float2 *o = sig + static_cast<int64_t>(row) * ns;
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    const int n = t + j * blockDim.x;
+    if (n < ns) {
+      if (accumulate) {
+        const float2 v = o[n];
+        o[n] = make_float2(v.x + tot_re[j], v.y + tot_im[j]);
+      } else {
+        o[n] = make_float2(tot_re[j], tot_im[j]);
+      }
+    }
   }
 }
 
@@ -98,6 +159,25 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cuda
     case 16: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
     default: direct_sum_kernel<32><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
   }
+  return 1;
+}
+
+int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
+                    int64_t stride, bool accumulate, float2 *sig, cudaStream_t s) {
+  const int rows = g.nv * g.nc;
+  const int threads = g.ns < 128 ? g.ns : 128;
+  const int npt = g.ns / threads;
+  const int acc = accumulate ? 1 : 0;
+#define RS_PAIR(N) pair_sum_kernel<N><<<rows, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, g.nc, g.ns, g.ntx, g.nrx, acc, sig)
+  switch (npt) {
+    case 1: RS_PAIR(1); break;
+    case 2: RS_PAIR(2); break;
+    case 4: RS_PAIR(4); break;
+    case 8: RS_PAIR(8); break;
+    case 16: RS_PAIR(16); break;
+    default: RS_PAIR(32); break;
+  }
+#undef RS_PAIR
   return 1;
 }
 

@@ -18,6 +18,7 @@ enum : uint32_t {
   kStatusHashFull = 2u,      // a label hash probe ran past its limit
   kStatusWaitLimit = 4u,     // a tensor-core pipeline wait ran past its limit
   kStatusBadLaunch = 8u,     // a kernel saw a launch shape it was not built for
+  kStatusBadGeometry = 16u,  // a hit list, triangle or vertex index was out of range
 };
 
 // Radar constants derived on the host in FP64 from sim_radar_params.
@@ -80,6 +81,10 @@ struct Tables {
 // ---- launchers (each returns the number of kernels it launched) ----
 int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s);
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s);
+// direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase
+// words (base, per-sample step): w_tx[(m N_tx + t) stride + i], w_rx[(m N_rx + r) stride + i]
+int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
+                    int64_t stride, bool accumulate, float2 *sig, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);
 int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
                   int32_t *labels, uint32_t *status, cudaStream_t s);

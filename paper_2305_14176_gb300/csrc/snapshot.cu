@@ -1,0 +1,379 @@
+// Virtual snapshots and antenna displacement (arXiv 2305.14176, Sec. II-D Eq. 6, Sec. II-E Eq. 7).
+//
+// A ray is traced once, at the first chirp, between one transmitter and one receiver; it keeps
+// its hits as (triangle, u, v).  At chirp j each hit sits at (1 - u - v) v1 + u v2 + v v3 of its
+// triangle's vertices at that snapshot (Eq. 6), and the path to transmitter t and receiver r is
+// the traced length with both antenna legs replaced (Eq. 7) and the stretch between the first
+// and the last hit measured again at snapshot j:
+//
+//   l(j, t, r) = d + [inner(j) - inner(0)] + |p_f(j) - x_t| - |p_f(0) - x_ref,tx|
+//                  + |p_l(j) - x_r| - |p_l(0) - x_ref,rx|          = A_t(j) + B_r(j).
+//
+// Each path enters Eq. 2 with tau = l / c in both the beat and the carrier term, so the sum is
+// not separable over chirps and channels and runs on the direct-sum path.  One thread per
+// (ray, chirp) computes A_t and B_r in FP64 and stores them as Q0.64 phase words (carrier
+// f_c l / c plus the start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m)
+// of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
+// antennas take N_c (N_tx + N_rx) 16 bytes per ray, so rays go through in chunks that keep
+// them within 1 GiB.
+#include <cuda_runtime.h>
+
+#include <math.h>
+
+#include <vector>
+
+#include "internal.h"
+
+using namespace rs;
+
+namespace {
+
+constexpr double kTwo64 = 18446744073709551616.0;
+constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;
+constexpr size_t kWordBudget = size_t{1} << 30;
+
+struct GeomDev {
+  const double *vert;  // [N_c][V][3]
+  const int32_t *tri;  // [T][3]
+  const double *tx;    // [n_tx][3]
+  const double *rx;    // [n_rx][3]
+  double ref_tx[3], ref_rx[3];
+  const int64_t *off;  // [n + 1]
+  const int32_t *htri;
+  const float *hu, *hv;
+  int64_t n_vert, n_tri, n_hits;
+};
+
+struct PhaseConst {
+  double fc_over_c;   // f_c / c: carrier cycles per metre of path
+  double step_per_m;  // B / (c N_s): beat cycles per sample per metre of path
+  int nc, ntx, nrx;
+};
+
+__device__ __forceinline__ uint64_t frac_q64(double x) {
+  const double f = x - floor(x);
+  return __double2ull_rn(f * kTwo64);
+}
+
+// hit h at snapshot j (Eq. 6); false when its triangle or one of the vertex indices is out of range
+__device__ bool hit_at(const GeomDev &g, int64_t j, int64_t h, double p[3]) {
+  const int32_t tr = g.htri[h];
+  if (tr < 0 || tr >= g.n_tri) return false;
+  const int32_t a = g.tri[3 * static_cast<int64_t>(tr)], b = g.tri[3 * static_cast<int64_t>(tr) + 1],
+                c = g.tri[3 * static_cast<int64_t>(tr) + 2];
+  if (a < 0 || a >= g.n_vert || b < 0 || b >= g.n_vert || c < 0 || c >= g.n_vert) return false;
+  const double *V = g.vert + j * g.n_vert * 3;
+  const double u = static_cast<double>(g.hu[h]), v = static_cast<double>(g.hv[h]);
+  const double w = 1.0 - u - v;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) p[q] = w * V[3 * a + q] + u * V[3 * b + q] + v * V[3 * c + q];
+  return true;
+}
+
+__device__ __forceinline__ double dist3(const double *a, const double *b) {
+  const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+  return sqrt(x * x + y * y + z * z);
+}
+
+// One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y).  paths != null:
+// l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the phase words of A_t and B_r.
+__global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double *__restrict__ d,
+                                                       const float *__restrict__ p0, int64_t i0, int64_t cnt,
+                                                       PhaseConst k, double *__restrict__ paths,
+                                                       ulonglong2 *__restrict__ w_tx, ulonglong2 *__restrict__ w_rx,
+                                                       int64_t stride, uint32_t *status) {
+  const int64_t li = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (li >= cnt) return;
+  const int64_t i = i0 + li;
+  const int64_t h0 = g.off[i], h1 = g.off[i + 1];
+  bool ok = h0 >= 0 && h1 > h0 && h1 <= g.n_hits;
+  double pf0[3] = {0, 0, 0}, pfj[3] = {0, 0, 0}, pl0[3] = {0, 0, 0}, plj[3] = {0, 0, 0};
+  double inner0 = 0.0, innerj = 0.0;
+  if (ok) ok = hit_at(g, 0, h0, pf0) && hit_at(g, j, h0, pfj);
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) { pl0[q] = pf0[q]; plj[q] = pfj[q]; }
+    for (int64_t h = h0 + 1; h < h1; ++h) {
+      double c0[3], cj[3];
+      if (!hit_at(g, 0, h, c0) || !hit_at(g, j, h, cj)) {
+        ok = false;
+        break;
+      }
+      inner0 += dist3(pl0, c0);
+      innerj += dist3(plj, cj);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) { pl0[q] = c0[q]; plj[q] = cj[q]; }
+    }
+  }
+  if (!ok) atomicOr(status, kStatusBadGeometry);
+  // Eq. 7: the traced length without its snapshot-0 antenna legs, plus the new legs
+  const double base_a = d[i] + (innerj - inner0) - dist3(pf0, g.ref_tx);
+  const double base_b = -dist3(pl0, g.ref_rx);
+  if (paths) {
+    const int nv = k.ntx * k.nrx;
+    double *o = paths + (i * k.nc + j) * nv;
+    for (int t = 0; t < k.ntx; ++t) {
+      const double a = base_a + dist3(pfj, g.tx + 3 * t);
+      for (int r = 0; r < k.nrx; ++r) o[t * k.nrx + r] = ok ? a + (base_b + dist3(plj, g.rx + 3 * r)) : 0.0;
+    }
+    return;
+  }
+  const uint64_t q0 = frac_q64(static_cast<double>(p0[i]) * kInv2Pi);
+  for (int t = 0; t < k.ntx; ++t) {
+    const double a = base_a + dist3(pfj, g.tx + 3 * t);
+    w_tx[(j * k.ntx + t) * stride + li] =
+        ok ? make_ulonglong2(frac_q64(a * k.fc_over_c) + q0, frac_q64(a * k.step_per_m)) : make_ulonglong2(0, 0);
+  }
+  for (int r = 0; r < k.nrx; ++r) {
+    const double b = base_b + dist3(plj, g.rx + 3 * r);
+    w_rx[(j * k.nrx + r) * stride + li] =
+        ok ? make_ulonglong2(frac_q64(b * k.fc_over_c), frac_q64(b * k.step_per_m)) : make_ulonglong2(0, 0);
+  }
+}
+
+size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+bool finite3(const double *p) { return isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]); }
+
+bool device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// One call's device block: the rays, hits and mesh copied in, per-ray prep, and the outputs.
+struct SnapRun {
+  const Derived *g = nullptr;
+  int64_t n = 0, H = 0, chunk = 0;
+  uint8_t *b = nullptr;
+  cudaStream_t s = nullptr;
+  GeomDev gd{};
+  size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
+  size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
+  size_t o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
+  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0;
+  int64_t cap = 0;
+  ~SnapRun() {
+    if (s) cudaStreamDestroy(s);
+    if (b) cudaFree(b);
+  }
+};
+
+// Checks the arguments, sizes and fills the device block.  mode 0: path lengths only;
+// mode 1: signal (+ spectrum, + labels).
+int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, const sim_hits *hits,
+               const sim_geometry *geom, int mode, bool want_spec, bool want_labels, bool paths_on_device) {
+  if (!ctx || !rays || !hits || !geom) return SIM_E_INVALID;
+  const Derived &g = ctx->g;
+  R.g = &g;
+  if (g.precision != SIM_PREC_FP32_DIRECT || g.tslot != 0.0) return SIM_E_INVALID;
+  const int64_t n = rays->n;
+  if (n < 0 || n > g.max_rays) return SIM_E_INVALID;
+  if (geom->n_vertices < 1 || geom->n_vertices > (int64_t{1} << 31) || geom->n_triangles < 1 ||
+      geom->n_triangles > (int64_t{1} << 31))
+    return SIM_E_INVALID;
+  if (!geom->vertices || !geom->triangles || !geom->tx_pos || !geom->rx_pos || !hits->offset) return SIM_E_INVALID;
+  if (!finite3(geom->ref_tx) || !finite3(geom->ref_rx)) return SIM_E_INVALID;
+  if (n > 0 && (!rays->range_rt_m || !rays->amplitude || !rays->radial_velocity_mps || !rays->azimuth_rad ||
+                !rays->elevation_rad || !rays->phase0_rad || !hits->triangle || !hits->u || !hits->v))
+    return SIM_E_INVALID;
+  if (want_labels && (!meta || !meta->object_id)) return SIM_E_INVALID;
+  // antenna positions and the hit count are read on the host
+  std::vector<double> txp(3 * static_cast<size_t>(g.ntx)), rxp(3 * static_cast<size_t>(g.nrx));
+  int64_t off0 = 0, H = 0;
+  if (cudaMemcpy(txp.data(), geom->tx_pos, 8 * txp.size(), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(rxp.data(), geom->rx_pos, 8 * rxp.size(), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(&off0, hits->offset, 8, cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(&H, hits->offset + n, 8, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return SIM_E_INVALID;
+  }
+  for (int t = 0; t < g.ntx; ++t)
+    if (!finite3(&txp[3 * t])) return SIM_E_INVALID;
+  for (int r = 0; r < g.nrx; ++r)
+    if (!finite3(&rxp[3 * r])) return SIM_E_INVALID;
+  if (off0 != 0 || H < n || H > (int64_t{1} << 32)) return SIM_E_INVALID;
+  R.n = n;
+  R.H = H;
+
+  const size_t un = static_cast<size_t>(n), up = (un + 31) / 32 * 32, uh = static_cast<size_t>(H);
+  const size_t per_ray_words = 16 * static_cast<size_t>(g.nc) * static_cast<size_t>(g.ntx + g.nrx);
+  int64_t chunk = 0;
+  if (mode == 1 && n > 0) {
+    chunk = static_cast<int64_t>(kWordBudget / per_ray_words) / 256 * 256;
+    if (chunk < 256) chunk = 256;
+    if (chunk > n) chunk = n;
+  }
+  R.chunk = chunk;
+  const size_t vbytes = 24 * static_cast<size_t>(g.nc) * static_cast<size_t>(geom->n_vertices);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += round256(bytes > 0 ? bytes : 1);
+    return o;
+  };
+  R.o_d = take(8 * un); R.o_a = take(4 * un); R.o_v = take(4 * un); R.o_az = take(4 * un);
+  R.o_el = take(4 * un); R.o_p0 = take(4 * un); R.o_obj = take(want_labels ? 4 * un : 0);
+  const size_t o_off = take(8 * (un + 1)), o_ht = take(4 * uh), o_hu = take(4 * uh), o_hv = take(4 * uh);
+  const size_t o_vert = take(vbytes), o_tri = take(12 * static_cast<size_t>(geom->n_triangles));
+  const size_t o_tx = take(8 * txp.size()), o_rx = take(8 * rxp.size());
+  R.o_car = take(8 * up); R.o_nur = take(8 * up); R.o_nud = take(8 * up); R.o_nua = take(8 * up);
+  R.o_amp = take(4 * up); R.o_cell = take(4 * up); R.o_en = take(8 * up); R.o_sd = take(8 * up);
+  R.o_sr = take(8 * up); R.o_ntx = take(8 * up);
+  R.o_status = take(256);
+  R.o_wt = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.ntx : 0);
+  R.o_wr = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.nrx : 0);
+  R.o_sig = take(mode == 1 ? 8 * static_cast<size_t>(g.n_sig) : 0);
+  R.o_tmp = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
+  R.o_spec = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
+  R.o_lab = take(want_labels ? 4 * static_cast<size_t>(g.n_cell) : 0);
+  R.cap = want_labels ? label_capacity(n) : 0;
+  const size_t cap = static_cast<size_t>(R.cap);
+  R.o_pk = take(8 * cap); R.o_pe = take(8 * cap); R.o_ck = take(4 * cap); R.o_cm = take(8 * cap);
+  R.o_co = take(4 * cap);
+  R.o_paths = take(mode == 0 && !paths_on_device ? 8 * un * g.nc * g.nv : 0);
+  if (cudaMalloc(&R.b, off) != cudaSuccess) {
+    cudaGetLastError();
+    R.b = nullptr;
+    return SIM_E_NOMEM;
+  }
+  if (cudaStreamCreateWithFlags(&R.s, cudaStreamNonBlocking) != cudaSuccess) {
+    R.s = nullptr;
+    return SIM_E_CUDA;
+  }
+  uint8_t *b = R.b;
+  cudaStream_t s = R.s;
+  if (n > 0) {
+    cudaMemcpyAsync(b + R.o_d, rays->range_rt_m, 8 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + R.o_a, rays->amplitude, 4 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + R.o_v, rays->radial_velocity_mps, 4 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + R.o_az, rays->azimuth_rad, 4 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + R.o_el, rays->elevation_rad, 4 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + R.o_p0, rays->phase0_rad, 4 * un, cudaMemcpyDefault, s);
+    if (want_labels) cudaMemcpyAsync(b + R.o_obj, meta->object_id, 4 * un, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + o_ht, hits->triangle, 4 * uh, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + o_hu, hits->u, 4 * uh, cudaMemcpyDefault, s);
+    cudaMemcpyAsync(b + o_hv, hits->v, 4 * uh, cudaMemcpyDefault, s);
+  }
+  cudaMemcpyAsync(b + o_off, hits->offset, 8 * (un + 1), cudaMemcpyDefault, s);
+  cudaMemcpyAsync(b + o_vert, geom->vertices, vbytes, cudaMemcpyDefault, s);
+  cudaMemcpyAsync(b + o_tri, geom->triangles, 12 * static_cast<size_t>(geom->n_triangles), cudaMemcpyDefault, s);
+  cudaMemcpyAsync(b + o_tx, txp.data(), 8 * txp.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b + o_rx, rxp.data(), 8 * rxp.size(), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(b + R.o_status, 0, 4, s);
+  GeomDev &gd = R.gd;
+  gd.vert = reinterpret_cast<const double *>(b + o_vert);
+  gd.tri = reinterpret_cast<const int32_t *>(b + o_tri);
+  gd.tx = reinterpret_cast<const double *>(b + o_tx);
+  gd.rx = reinterpret_cast<const double *>(b + o_rx);
+  for (int q = 0; q < 3; ++q) {
+    gd.ref_tx[q] = geom->ref_tx[q];
+    gd.ref_rx[q] = geom->ref_rx[q];
+  }
+  gd.off = reinterpret_cast<const int64_t *>(b + o_off);
+  gd.htri = reinterpret_cast<const int32_t *>(b + o_ht);
+  gd.hu = reinterpret_cast<const float *>(b + o_hu);
+  gd.hv = reinterpret_cast<const float *>(b + o_hv);
+  gd.n_vert = geom->n_vertices;
+  gd.n_tri = geom->n_triangles;
+  gd.n_hits = H;
+  // the hosts' copies of the antenna positions must outlive the copies above
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SIM_E_CUDA;
+  return SIM_OK;
+}
+
+PhaseConst phase_const(const Derived &g) {
+  PhaseConst k;
+  k.fc_over_c = g.fc / kC;
+  k.step_per_m = g.bw / (kC * static_cast<double>(g.ns));
+  k.nc = g.nc;
+  k.ntx = g.ntx;
+  k.nrx = g.nrx;
+  return k;
+}
+
+int snap_finish(SnapRun &R) {
+  uint32_t st = 0;
+  cudaMemcpyAsync(&st, R.b + R.o_status, 4, cudaMemcpyDeviceToHost, R.s);
+  const cudaError_t e = cudaStreamSynchronize(R.s);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (st & (kStatusBadRay | kStatusBadGeometry)) return SIM_E_INVALID;
+  return st ? SIM_E_DEVICE : SIM_OK;
+}
+
+}  // namespace
+
+extern "C" SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hits *hits,
+                                          const sim_geometry *geom, double *paths) {
+  if (!paths) return SIM_E_INVALID;
+  SnapRun R;
+  const bool dev = device_ptr(paths);
+  int rc = snap_setup(R, ctx, rays, nullptr, hits, geom, 0, false, false, dev);
+  if (rc != SIM_OK) return rc;
+  const Derived &g = *R.g;
+  if (R.n > 0) {
+    double *out = dev ? paths : reinterpret_cast<double *>(R.b + R.o_paths);
+    const dim3 grid(static_cast<unsigned>((R.n + 127) / 128), static_cast<unsigned>(g.nc));
+    snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const double *>(R.b + R.o_d),
+                                           reinterpret_cast<const float *>(R.b + R.o_p0), 0, R.n, phase_const(g),
+                                           out, nullptr, nullptr, 0, reinterpret_cast<uint32_t *>(R.b + R.o_status));
+    if (!dev)
+      cudaMemcpyAsync(paths, out, 8 * static_cast<size_t>(R.n) * g.nc * g.nv, cudaMemcpyDeviceToHost, R.s);
+  }
+  return snap_finish(R);
+}
+
+extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta,
+                                        const sim_hits *hits, const sim_geometry *geom, void *spectrum,
+                                        void *signal, int32_t *labels) {
+  if (!ctx || (!spectrum && !signal && !labels)) return SIM_E_INVALID;
+  if ((spectrum && !(ctx->g.outputs & SIM_OUT_SPECTRUM)) || (labels && !(ctx->g.outputs & SIM_OUT_LABELS)))
+    return SIM_E_INVALID;
+  SnapRun R;
+  int rc = snap_setup(R, ctx, rays, meta, hits, geom, 1, spectrum != nullptr, labels != nullptr, false);
+  if (rc != SIM_OK) return rc;
+  const Derived &g = *R.g;
+  uint8_t *b = R.b;
+  cudaStream_t s = R.s;
+  uint32_t *status = reinterpret_cast<uint32_t *>(b + R.o_status);
+  RaysIn in{reinterpret_cast<const double *>(b + R.o_d), reinterpret_cast<const float *>(b + R.o_a),
+            reinterpret_cast<const float *>(b + R.o_v), reinterpret_cast<const float *>(b + R.o_az),
+            reinterpret_cast<const float *>(b + R.o_el), reinterpret_cast<const float *>(b + R.o_p0),
+            labels ? reinterpret_cast<const int32_t *>(b + R.o_obj) : nullptr};
+  RaysPrep rp{reinterpret_cast<uint64_t *>(b + R.o_car), reinterpret_cast<uint64_t *>(b + R.o_nur),
+              reinterpret_cast<uint64_t *>(b + R.o_nud), reinterpret_cast<uint64_t *>(b + R.o_nua),
+              reinterpret_cast<float *>(b + R.o_amp), reinterpret_cast<int32_t *>(b + R.o_cell),
+              reinterpret_cast<uint64_t *>(b + R.o_en), reinterpret_cast<float2 *>(b + R.o_sd),
+              reinterpret_cast<float2 *>(b + R.o_sr), nullptr, reinterpret_cast<uint64_t *>(b + R.o_ntx), nullptr};
+  // per-ray validation, antenna-pattern amplitudes, label cells and energies
+  launch_prep(g, in, R.n, rp, status, s);
+  float2 *sig = reinterpret_cast<float2 *>(b + R.o_sig);
+  if (R.n == 0) cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
+  ulonglong2 *wt = reinterpret_cast<ulonglong2 *>(b + R.o_wt), *wr = reinterpret_cast<ulonglong2 *>(b + R.o_wr);
+  const PhaseConst k = phase_const(g);
+  for (int64_t i0 = 0; i0 < R.n; i0 += R.chunk) {
+    const int64_t cnt = R.n - i0 < R.chunk ? R.n - i0 : R.chunk;
+    const dim3 grid(static_cast<unsigned>((cnt + 127) / 128), static_cast<unsigned>(g.nc));
+    snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, in.d, in.p0, i0, cnt, k, nullptr, wt, wr, R.chunk, status);
+    launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, s);
+  }
+  if (signal) cudaMemcpyAsync(signal, sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
+  if (spectrum) {
+    float2 *spec = reinterpret_cast<float2 *>(b + R.o_spec);
+    launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + R.o_tmp), spec, s);
+    cudaMemcpyAsync(spectrum, spec, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+  }
+  if (labels) {
+    LabelScratch sc{reinterpret_cast<uint64_t *>(b + R.o_pk), reinterpret_cast<uint64_t *>(b + R.o_pe),
+                    reinterpret_cast<uint32_t *>(b + R.o_ck), reinterpret_cast<uint64_t *>(b + R.o_cm),
+                    reinterpret_cast<uint32_t *>(b + R.o_co), R.cap};
+    int32_t *dlab = reinterpret_cast<int32_t *>(b + R.o_lab);
+    launch_labels(g, rp, in.obj, R.n, sc, dlab, status, s);
+    cudaMemcpyAsync(labels, dlab, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+  }
+  return snap_finish(R);
+}

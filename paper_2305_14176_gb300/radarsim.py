@@ -62,6 +62,18 @@ class sim_span_rule(ctypes.Structure):
                 ("max_hits", ctypes.c_int32), ("exclude", ctypes.c_int32)]
 
 
+class sim_geometry(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("vertices", ctypes.c_void_p), ("triangles", ctypes.c_void_p),
+                ("tx_pos", ctypes.c_void_p), ("rx_pos", ctypes.c_void_p),
+                ("ref_tx", ctypes.c_double * 3), ("ref_rx", ctypes.c_double * 3)]
+
+
+class sim_hits(ctypes.Structure):
+    _fields_ = [("offset", ctypes.c_void_p), ("triangle", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("v", ctypes.c_void_p)]
+
+
 class sim_tuning(ctypes.Structure):
     _fields_ = [("splits", ctypes.c_int32), ("fft_range_points", ctypes.c_int32),
                 ("fft_doppler_strip", ctypes.c_int32), ("fft_angle_strip", ctypes.c_int32),
@@ -97,6 +109,10 @@ def _load() -> ctypes.CDLL:
     lib.sim_decompose.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), I32,
                                   ctypes.POINTER(sim_span_rule), P, P, ctypes.c_float]
     lib.sim_decompose.restype = ctypes.c_int
+    lib.sim_snapshot_paths.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_hits),
+                                       ctypes.POINTER(sim_geometry), P]
+    lib.sim_snapshot_run.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta),
+                                     ctypes.POINTER(sim_hits), ctypes.POINTER(sim_geometry), P, P, P]
     lib.sim_tuning_save.argtypes = [ctypes.c_char_p]
     lib.sim_tuning_load.argtypes = [ctypes.c_char_p]
     for f in ("sim_autotune", "sim_tuning_save", "sim_tuning_load", "sim_tuning_clear", "sim_tuning_count"):
@@ -205,6 +221,32 @@ def sim_decompose(ctx, rays: sim_rays, meta: sim_meta, rules, span_spectra=None,
     sp = None if span_spectra is None else (ctypes.c_void_p * n)(*[_addr(x) for x in span_spectra])
     return lib.sim_decompose(ctx, ctypes.byref(rays), ctypes.byref(meta) if meta is not None else None, n, rarr,
                              sp, _addr(span_labels), float(threshold))
+
+
+def make_geometry(arrays: Dict[str, object], ref_tx, ref_rx):
+    """(sim_geometry, sim_hits) over arrays keyed vertices [N_c][V][3] f64, triangles [T][3] i32,
+    tx_pos [n_tx][3] f64, rx_pos [n_rx][3] f64, hit_offset [n+1] i64, hit_triangle i32, hit_u,
+    hit_v f32 (numpy or torch; the caller keeps them alive)."""
+    vert, tri = arrays["vertices"], arrays["triangles"]
+    g = sim_geometry(int(vert.shape[1]), int(tri.shape[0]), _addr(vert), _addr(tri), _addr(arrays["tx_pos"]),
+                     _addr(arrays["rx_pos"]))
+    for c in range(3):
+        g.ref_tx[c] = float(ref_tx[c])
+        g.ref_rx[c] = float(ref_rx[c])
+    h = sim_hits(_addr(arrays["hit_offset"]), _addr(arrays["hit_triangle"]), _addr(arrays["hit_u"]),
+                 _addr(arrays["hit_v"]))
+    return g, h
+
+
+def sim_snapshot_paths(ctx, rays: sim_rays, hits: sim_hits, geom: sim_geometry, paths) -> int:
+    return lib.sim_snapshot_paths(ctx, ctypes.byref(rays), ctypes.byref(hits), ctypes.byref(geom), _addr(paths))
+
+
+def sim_snapshot_run(ctx, rays: sim_rays, meta: sim_meta, hits: sim_hits, geom: sim_geometry, spectrum=None,
+                     signal=None, labels=None) -> int:
+    return lib.sim_snapshot_run(ctx, ctypes.byref(rays), ctypes.byref(meta) if meta is not None else None,
+                                ctypes.byref(hits), ctypes.byref(geom), _addr(spectrum), _addr(signal),
+                                _addr(labels))
 
 
 def sim_autotune(ctx, n_rays: int) -> sim_tuning:
