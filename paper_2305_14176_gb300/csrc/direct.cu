@@ -2,9 +2,11 @@
 //
 //   s[k][m][n] = sum_i a_i exp(2 pi j (carrier_i + k nu_a,i + m nu_d,i + n nu_r,i))
 //
-// One FP32 sine and cosine per ray and output sample.  The phase is accumulated
-// exactly in Q0.64 integers (wrap = one cycle) and only its top 23 bits are turned into
-// an FP32 angle in [-pi, pi), so the hardware sin/cos sees a small argument.
+// A thread owns the samples n = t + j T of a row (T threads, j < NPT).  For each ray it takes
+// one FP32 sine and cosine of the exact Q0.64 phase of its first sample (only the top 23 bits
+// become an FP32 angle in [-pi, pi), so the hardware sin/cos sees a small argument) and steps
+// to the others by complex multiplication with e^{2 pi j T nu_r}: one sin/cos per NPT
+// contributions, the rest on the FMA pipe.
 //
 // A block owns one (k, m) row and all N_s samples; rays stream through shared memory
 // in chunks, and each chunk is summed into a per-thread partial before it is added
@@ -26,25 +28,113 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
   return (f - 1.5f) * 6.28318530717958647692f;
 }
 
-// Add one staged chunk of rays to the thread's samples n = t + j T (j < NPT): phase words
-// (base of the row, per-sample step) and amplitudes in shared memory.
+// e^{2 pi j q 2^-64} for a Q0.64 phase q, from the signed cycle count in FP32 (relative
+// precision 2^-24 of a value in [-1/2, 1/2)), for the phasor steps of the recurrence below
+__device__ __forceinline__ float2 phasor_of(uint64_t q) {
+  const float f = static_cast<float>(static_cast<int64_t>(q)) * 0x1p-64f;
+  float sn, cs;
+  sincospif(2.0f * f, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// Two FP32 lanes in one 64-bit register: element-wise f32x2 arithmetic, one instruction for a
+// pair of rays
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 pack2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float sum_lanes(f2 x) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+  return a + b;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// A staged chunk of rays: per ray its phase words (base of the row, per-sample step), its
+// amplitude and the T-sample step phasor e^{2 pi j T step} = (w_r, w_i), kept with -w_i.
+// An odd chunk is padded with one silent ray so rays go in pairs.
+struct Staged {
+  ulonglong2 ph[kChunk];
+  __align__(16) float amp[kChunk];
+  __align__(16) float wr[kChunk];
+  __align__(16) float wi[kChunk];
+  __align__(16) float nwi[kChunk];
+};
+
+__device__ __forceinline__ void stage_ray(Staged &st, int i, uint64_t base, uint64_t step, float amp, uint64_t T) {
+  st.ph[i] = make_ulonglong2(base, step);
+  st.amp[i] = amp;
+  const float2 w = phasor_of(T * step);
+  st.wr[i] = w.x;
+  st.wi[i] = w.y;
+  st.nwi[i] = -w.y;
+}
+
+__device__ __forceinline__ void stage_pad(Staged &st, int cnt) {
+  if (cnt & 1) {
+    st.ph[cnt] = make_ulonglong2(0, 0);
+    st.amp[cnt] = 0.f;
+    st.wr[cnt] = 1.f;
+    st.wi[cnt] = 0.f;
+    st.nwi[cnt] = 0.f;
+  }
+}
+
+// Add one staged chunk to the thread's samples n = t + j T (j < NPT), two rays at a time in
+// the lanes of f32x2 registers.  The first sample of each ray takes one sine and cosine of its
+// exact Q0.64 phase; the next NPT - 1 follow by complex multiplication with its step phasor
+// (FP32 error growing by about one rounding per step).  The two lanes are added at the end.
 template <int NPT>
-__device__ __forceinline__ void sum_chunk(const ulonglong2 *s_ph, const float *s_amp, int cnt, int t, uint64_t T,
-                                          float (&re)[NPT], float (&im)[NPT]) {
-#pragma unroll 2
-  for (int i = 0; i < cnt; ++i) {
-    const ulonglong2 q = s_ph[i];
-    const float a = s_amp[i];
-    uint64_t ph = q.x + static_cast<uint64_t>(t) * q.y;
-    const uint64_t step = T * q.y;
+__device__ __forceinline__ void sum_chunk(const Staged &st, int cnt, int t, float (&re)[NPT], float (&im)[NPT]) {
+  f2 accr[NPT], acci[NPT];
 #pragma unroll
-    for (int j = 0; j < NPT; ++j) {
-      float sn, cs;
-      __sincosf(q64_to_rad(ph), &sn, &cs);
-      re[j] = fmaf(a, cs, re[j]);
-      im[j] = fmaf(a, sn, im[j]);
-      ph += step;
+  for (int j = 0; j < NPT; ++j) { accr[j] = 0ull; acci[j] = 0ull; }
+  const uint64_t tt = static_cast<uint64_t>(t);
+#pragma unroll 2
+  for (int i = 0; i < cnt; i += 2) {
+    const ulonglong2 q0 = st.ph[i], q1 = st.ph[i + 1];
+    float s0, c0, s1, c1;
+    __sincosf(q64_to_rad(q0.x + tt * q0.y), &s0, &c0);
+    __sincosf(q64_to_rad(q1.x + tt * q1.y), &s1, &c1);
+    const f2 a = *reinterpret_cast<const f2 *>(st.amp + i);
+    f2 zr = mul2(a, pack2(c0, c1)), zi = mul2(a, pack2(s0, s1));
+    accr[0] = add2(accr[0], zr);
+    acci[0] = add2(acci[0], zi);
+    if constexpr (NPT > 1) {
+      const f2 wr = *reinterpret_cast<const f2 *>(st.wr + i);
+      const f2 wi = *reinterpret_cast<const f2 *>(st.wi + i);
+      const f2 nwi = *reinterpret_cast<const f2 *>(st.nwi + i);
+#pragma unroll
+      for (int j = 1; j < NPT; ++j) {
+        const f2 nr = fma2(zi, nwi, mul2(zr, wr));  // zr w_r - zi w_i
+        const f2 ni = fma2(zr, wi, mul2(zi, wr));   // zi w_r + zr w_i
+        zr = nr;
+        zi = ni;
+        accr[j] = add2(accr[j], zr);
+        acci[j] = add2(acci[j], zi);
+      }
     }
+  }
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) {
+    re[j] += sum_lanes(accr[j]);
+    im[j] += sum_lanes(acci[j]);
   }
 }
 
@@ -52,8 +142,7 @@ __device__ __forceinline__ void sum_chunk(const ulonglong2 *s_ph, const float *s
 template <int NPT>
 __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
                                                          int nrx, float2 *__restrict__ sig) {
-  __shared__ ulonglong2 s_ph[kChunk];  // (base phase of this row, range step)
-  __shared__ float s_amp[kChunk];
+  __shared__ Staged st;
   const int row = blockIdx.x;
   const uint64_t k = static_cast<uint64_t>(row / nc);
   const uint64_t m = static_cast<uint64_t>(row % nc);
@@ -72,15 +161,15 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
       // exact Eq. 2 adds n (m eps + tx eps_t): on row (tx, m) the per-sample increment grows by that
       const uint64_t nur = p.eps ? p.nu_r[r] + m * p.eps[r] + tx * p.eps_t[r] : p.nu_r[r];
       // channel k = tx N_rx + rx: phase tx nu_tx + rx nu_a (= k nu_a without TDM slots)
-      s_ph[i] = make_ulonglong2(p.carrier[r] + tx * p.nu_tx[r] + rx * p.nu_a[r] + m * p.nu_d[r], nur);
-      s_amp[i] = p.amp[r];
+      stage_ray(st, i, p.carrier[r] + tx * p.nu_tx[r] + rx * p.nu_a[r] + m * p.nu_d[r], nur, p.amp[r], T);
     }
+    if (t == 0) stage_pad(st, cnt);
     __syncthreads();
     // per-chunk partial sums, then added to the totals (two-level summation)
     float re[NPT], im[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { re[j] = 0.f; im[j] = 0.f; }
-    sum_chunk<NPT>(s_ph, s_amp, cnt, t, T, re, im);
+    sum_chunk<NPT>(st, cnt, t, re, im);
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
   }
@@ -102,8 +191,7 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
                                                        const float *__restrict__ amp, int64_t n_rays, int64_t stride,
                                                        int nc, int ns, int ntx, int nrx, int accumulate,
                                                        float2 *__restrict__ sig) {
-  __shared__ ulonglong2 s_ph[kChunk];
-  __shared__ float s_amp[kChunk];
+  __shared__ Staged st;
   const int row = blockIdx.x;
   const int k = row / nc, m = row % nc;
   const int tx = k / nrx, rx = k - tx * nrx;
@@ -119,14 +207,14 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const ulonglong2 a = wt[c0 + i], b = wr[c0 + i];
-      s_ph[i] = make_ulonglong2(a.x + b.x, a.y + b.y);
-      s_amp[i] = amp[c0 + i];
+      stage_ray(st, i, a.x + b.x, a.y + b.y, amp[c0 + i], T);
     }
+    if (t == 0) stage_pad(st, cnt);
     __syncthreads();
     float re[NPT], im[NPT];
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { re[j] = 0.f; im[j] = 0.f; }
-    sum_chunk<NPT>(s_ph, s_amp, cnt, t, T, re, im);
+    sum_chunk<NPT>(st, cnt, t, re, im);
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
   }
@@ -145,37 +233,43 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
   }
 }
 
+// Threads per row: 64 (two warps) with up to 32 samples each; N_s = 4096 takes 128 threads.
+// N_s is a power of two in 16 .. 4096, so the samples per thread are 1, 2, .., 32.
+int row_threads(int ns) { return ns <= 64 ? ns : (ns / 32 > 64 ? ns / 32 : 64); }
+
 }  // namespace
 
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s) {
   const int rows = g.nv * g.nc;
-  const int threads = g.ns < 128 ? g.ns : 128;
-  const int npt = g.ns / threads;  // N_s is a power of two >= 16
-  switch (npt) {
-    case 1: direct_sum_kernel<1><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
-    case 2: direct_sum_kernel<2><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
-    case 4: direct_sum_kernel<4><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
-    case 8: direct_sum_kernel<8><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
-    case 16: direct_sum_kernel<16><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
-    default: direct_sum_kernel<32><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig); break;
+  const int threads = row_threads(g.ns);
+#define RS_DIRECT(N) direct_sum_kernel<N><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig)
+  switch (g.ns / threads) {
+    case 1: RS_DIRECT(1); break;
+    case 2: RS_DIRECT(2); break;
+    case 4: RS_DIRECT(4); break;
+    case 8: RS_DIRECT(8); break;
+    case 16: RS_DIRECT(16); break;
+    case 32: RS_DIRECT(32); break;
+    default: return 0;
   }
+#undef RS_DIRECT
   return 1;
 }
 
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
                     int64_t stride, bool accumulate, float2 *sig, cudaStream_t s) {
   const int rows = g.nv * g.nc;
-  const int threads = g.ns < 128 ? g.ns : 128;
-  const int npt = g.ns / threads;
+  const int threads = row_threads(g.ns);
   const int acc = accumulate ? 1 : 0;
 #define RS_PAIR(N) pair_sum_kernel<N><<<rows, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, g.nc, g.ns, g.ntx, g.nrx, acc, sig)
-  switch (npt) {
+  switch (g.ns / threads) {
     case 1: RS_PAIR(1); break;
     case 2: RS_PAIR(2); break;
     case 4: RS_PAIR(4); break;
     case 8: RS_PAIR(8); break;
     case 16: RS_PAIR(16); break;
-    default: RS_PAIR(32); break;
+    case 32: RS_PAIR(32); break;
+    default: return 0;
   }
 #undef RS_PAIR
   return 1;

@@ -483,6 +483,15 @@ int upload_tables(sim_ctx *c) {
 
 int rs::derive_radar(const sim_radar_params *p, Derived *g) { return derive(p, g); }
 
+namespace rs {
+void record_stage_ms(sim_ctx *c, const float *ms, int kernels) {
+  Engine &e = engine();
+  std::lock_guard<std::mutex> lk(e.mu);
+  for (int i = 0; i < kNumEvents; ++i) c->last_ms[i] = ms[i];
+  c->last_kernels = kernels;
+}
+}  // namespace rs
+
 extern "C" {
 
 const char *sim_status_string(int s) {

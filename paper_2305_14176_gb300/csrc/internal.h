@@ -81,6 +81,8 @@ struct Tables {
 // ---- launchers (each returns the number of kernels it launched) ----
 int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s);
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s);
+// store a synchronous call's stage times (7 entries, the sim_last_stage_ms order) and kernel count
+void record_stage_ms(sim_ctx *c, const float *ms, int kernels);
 // direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase
 // words (base, per-sample step): w_tx[(m N_tx + t) stride + i], w_rx[(m N_rx + r) stride + i]
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,

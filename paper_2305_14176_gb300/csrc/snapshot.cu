@@ -16,6 +16,13 @@
 // of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
 // antennas take N_c (N_tx + N_rx) 16 bytes per ray, so rays go through in chunks that keep
 // them within 1 GiB.
+//
+// FP64 carries what needs it: the hit positions, the legs to the two reference antennas
+// s = |p - x_ref| and the phase words of the reference paths (f_c l / c is ~10^4 cycles).  An
+// antenna at x_ref + e differs from the reference leg by |u - e| - |u| = (|e|^2 - 2 u.e) /
+// (|u - e| + |u|), u = p - x_ref, a few centimetres for a compact array: that difference is
+// taken in FP32 (relative error ~2^-22, so ~5 nm for e = 2 cm, 8e-6 rad of carrier phase)
+// and added to the words as Q0.64.  The snapshot-0 terms of Eq. 7 are computed once per ray.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -35,8 +42,8 @@ constexpr size_t kWordBudget = size_t{1} << 30;
 struct GeomDev {
   const double *vert;  // [N_c][V][3]
   const int32_t *tri;  // [T][3]
-  const double *tx;    // [n_tx][3]
-  const double *rx;    // [n_rx][3]
+  const float4 *tx;    // [n_tx]: (e, |e|^2) with e = x_t - ref_tx
+  const float4 *rx;    // [n_rx]: (e, |e|^2) with e = x_r - ref_rx
   double ref_tx[3], ref_rx[3];
   const int64_t *off;  // [n + 1]
   const int32_t *htri;
@@ -75,9 +82,56 @@ __device__ __forceinline__ double dist3(const double *a, const double *b) {
   return sqrt(x * x + y * y + z * z);
 }
 
+// Hits of ray i at snapshot j: first and last position and the length between them; false
+// when the hit list or an index is out of range (nothing is read past it)
+__device__ bool ray_hits(const GeomDev &g, int64_t i, int64_t j, double pf[3], double pl[3], double &inner) {
+  const int64_t h0 = g.off[i], h1 = g.off[i + 1];
+  inner = 0.0;
+  if (!(h0 >= 0 && h1 > h0 && h1 <= g.n_hits)) return false;
+  if (!hit_at(g, j, h0, pf)) return false;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) pl[q] = pf[q];
+  for (int64_t h = h0 + 1; h < h1; ++h) {
+    double c[3];
+    if (!hit_at(g, j, h, c)) return false;
+    inner += dist3(pl, c);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) pl[q] = c[q];
+  }
+  return true;
+}
+
+// Per ray, snapshot 0 of Eq. 7: base0 = (d - inner(0) - |p_f(0) - ref_tx|, -|p_l(0) - ref_rx|)
+__global__ void __launch_bounds__(128) snapshot0_kernel(GeomDev g, const double *__restrict__ d, int64_t n,
+                                                        double2 *__restrict__ base0, uint32_t *status) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= n) return;
+  double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
+  if (!ray_hits(g, i, 0, pf, pl, inner)) {
+    atomicOr(status, kStatusBadGeometry);
+    base0[i] = make_double2(0.0, 0.0);
+    return;
+  }
+  base0[i] = make_double2(d[i] - inner - dist3(pf, g.ref_tx), -dist3(pl, g.ref_rx));
+}
+
+// |u - e| - |u| for an antenna offset e from the reference (see the file comment), FP32
+__device__ __forceinline__ float leg_offset(const double u[3], float s, float4 e) {
+  const float num = fmaf(-2.f, fmaf(static_cast<float>(u[0]), e.x,
+                                    fmaf(static_cast<float>(u[1]), e.y, static_cast<float>(u[2]) * e.z)),
+                         e.w);
+  const float den = sqrtf(fmaf(s, s, num)) + s;
+  return num / den;
+}
+
+// a small cycle count (|x| < 2^31) as a Q0.64 phase
+__device__ __forceinline__ uint64_t q64_small(float x) {
+  return static_cast<uint64_t>(__float2ll_rn(x * 4294967296.0f)) << 32;
+}
+
 // One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y).  paths != null:
 // l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the phase words of A_t and B_r.
-__global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double *__restrict__ d,
+__global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double2 *__restrict__ base0,
                                                        const float *__restrict__ p0, int64_t i0, int64_t cnt,
                                                        PhaseConst k, double *__restrict__ paths,
                                                        ulonglong2 *__restrict__ w_tx, ulonglong2 *__restrict__ w_rx,
@@ -86,49 +140,42 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double *
   const int64_t j = blockIdx.y;
   if (li >= cnt) return;
   const int64_t i = i0 + li;
-  const int64_t h0 = g.off[i], h1 = g.off[i + 1];
-  bool ok = h0 >= 0 && h1 > h0 && h1 <= g.n_hits;
-  double pf0[3] = {0, 0, 0}, pfj[3] = {0, 0, 0}, pl0[3] = {0, 0, 0}, plj[3] = {0, 0, 0};
-  double inner0 = 0.0, innerj = 0.0;
-  if (ok) ok = hit_at(g, 0, h0, pf0) && hit_at(g, j, h0, pfj);
-  if (ok) {
-#pragma unroll
-    for (int q = 0; q < 3; ++q) { pl0[q] = pf0[q]; plj[q] = pfj[q]; }
-    for (int64_t h = h0 + 1; h < h1; ++h) {
-      double c0[3], cj[3];
-      if (!hit_at(g, 0, h, c0) || !hit_at(g, j, h, cj)) {
-        ok = false;
-        break;
-      }
-      inner0 += dist3(pl0, c0);
-      innerj += dist3(plj, cj);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) { pl0[q] = c0[q]; plj[q] = cj[q]; }
-    }
-  }
+  double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
+  const bool ok = ray_hits(g, i, j, pf, pl, inner);
   if (!ok) atomicOr(status, kStatusBadGeometry);
-  // Eq. 7: the traced length without its snapshot-0 antenna legs, plus the new legs
-  const double base_a = d[i] + (innerj - inner0) - dist3(pf0, g.ref_tx);
-  const double base_b = -dist3(pl0, g.ref_rx);
+  const double ut[3] = {pf[0] - g.ref_tx[0], pf[1] - g.ref_tx[1], pf[2] - g.ref_tx[2]};
+  const double ur[3] = {pl[0] - g.ref_rx[0], pl[1] - g.ref_rx[1], pl[2] - g.ref_rx[2]};
+  const double st = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+  const double sr = sqrt(ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2]);
+  const double2 b0 = base0[i];
+  // Eq. 7 with the reference antennas: the traced length without its snapshot-0 antenna legs,
+  // the stretch between the hits re-measured, and the two reference legs at snapshot j
+  const double a_ref = b0.x + inner + st;
+  const double b_ref = b0.y + sr;
+  const float stf = static_cast<float>(st), srf = static_cast<float>(sr);
   if (paths) {
     const int nv = k.ntx * k.nrx;
     double *o = paths + (i * k.nc + j) * nv;
     for (int t = 0; t < k.ntx; ++t) {
-      const double a = base_a + dist3(pfj, g.tx + 3 * t);
-      for (int r = 0; r < k.nrx; ++r) o[t * k.nrx + r] = ok ? a + (base_b + dist3(plj, g.rx + 3 * r)) : 0.0;
+      const double a = a_ref + static_cast<double>(leg_offset(ut, stf, g.tx[t]));
+      for (int r = 0; r < k.nrx; ++r)
+        o[t * k.nrx + r] = ok ? a + (b_ref + static_cast<double>(leg_offset(ur, srf, g.rx[r]))) : 0.0;
     }
     return;
   }
   const uint64_t q0 = frac_q64(static_cast<double>(p0[i]) * kInv2Pi);
+  const uint64_t at_c = frac_q64(a_ref * k.fc_over_c) + q0, at_s = frac_q64(a_ref * k.step_per_m);
+  const uint64_t br_c = frac_q64(b_ref * k.fc_over_c), br_s = frac_q64(b_ref * k.step_per_m);
+  const float fc_f = static_cast<float>(k.fc_over_c), sp_f = static_cast<float>(k.step_per_m);
   for (int t = 0; t < k.ntx; ++t) {
-    const double a = base_a + dist3(pfj, g.tx + 3 * t);
+    const float e = leg_offset(ut, stf, g.tx[t]);
     w_tx[(j * k.ntx + t) * stride + li] =
-        ok ? make_ulonglong2(frac_q64(a * k.fc_over_c) + q0, frac_q64(a * k.step_per_m)) : make_ulonglong2(0, 0);
+        ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
   }
   for (int r = 0; r < k.nrx; ++r) {
-    const double b = base_b + dist3(plj, g.rx + 3 * r);
+    const float e = leg_offset(ur, srf, g.rx[r]);
     w_rx[(j * k.nrx + r) * stride + li] =
-        ok ? make_ulonglong2(frac_q64(b * k.fc_over_c), frac_q64(b * k.step_per_m)) : make_ulonglong2(0, 0);
+        ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
   }
 }
 
@@ -154,7 +201,7 @@ struct SnapRun {
   GeomDev gd{};
   size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
   size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
-  size_t o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
+  size_t o_base0 = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
   size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0;
   int64_t cap = 0;
   ~SnapRun() {
@@ -220,7 +267,8 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_el = take(4 * un); R.o_p0 = take(4 * un); R.o_obj = take(want_labels ? 4 * un : 0);
   const size_t o_off = take(8 * (un + 1)), o_ht = take(4 * uh), o_hu = take(4 * uh), o_hv = take(4 * uh);
   const size_t o_vert = take(vbytes), o_tri = take(12 * static_cast<size_t>(geom->n_triangles));
-  const size_t o_tx = take(8 * txp.size()), o_rx = take(8 * rxp.size());
+  const size_t o_tx = take(16 * static_cast<size_t>(g.ntx)), o_rx = take(16 * static_cast<size_t>(g.nrx));
+  R.o_base0 = take(16 * un);
   R.o_car = take(8 * up); R.o_nur = take(8 * up); R.o_nud = take(8 * up); R.o_nua = take(8 * up);
   R.o_amp = take(4 * up); R.o_cell = take(4 * up); R.o_en = take(8 * up); R.o_sd = take(8 * up);
   R.o_sr = take(8 * up); R.o_ntx = take(8 * up);
@@ -262,14 +310,29 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   cudaMemcpyAsync(b + o_off, hits->offset, 8 * (un + 1), cudaMemcpyDefault, s);
   cudaMemcpyAsync(b + o_vert, geom->vertices, vbytes, cudaMemcpyDefault, s);
   cudaMemcpyAsync(b + o_tri, geom->triangles, 12 * static_cast<size_t>(geom->n_triangles), cudaMemcpyDefault, s);
-  cudaMemcpyAsync(b + o_tx, txp.data(), 8 * txp.size(), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(b + o_rx, rxp.data(), 8 * rxp.size(), cudaMemcpyHostToDevice, s);
+  // antenna offsets from the reference antennas, FP32 with their squared length
+  std::vector<float> etx(4 * static_cast<size_t>(g.ntx)), erx(4 * static_cast<size_t>(g.nrx));
+  auto offsets = [](const std::vector<double> &x, const double *ref, std::vector<float> &e) {
+    for (size_t a = 0; a < e.size() / 4; ++a) {
+      double n2 = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const double d = x[3 * a + q] - ref[q];
+        e[4 * a + q] = static_cast<float>(d);
+        n2 += d * d;
+      }
+      e[4 * a + 3] = static_cast<float>(n2);
+    }
+  };
+  offsets(txp, geom->ref_tx, etx);
+  offsets(rxp, geom->ref_rx, erx);
+  cudaMemcpyAsync(b + o_tx, etx.data(), 4 * etx.size(), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(b + o_rx, erx.data(), 4 * erx.size(), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(b + R.o_status, 0, 4, s);
   GeomDev &gd = R.gd;
   gd.vert = reinterpret_cast<const double *>(b + o_vert);
   gd.tri = reinterpret_cast<const int32_t *>(b + o_tri);
-  gd.tx = reinterpret_cast<const double *>(b + o_tx);
-  gd.rx = reinterpret_cast<const double *>(b + o_rx);
+  gd.tx = reinterpret_cast<const float4 *>(b + o_tx);
+  gd.rx = reinterpret_cast<const float4 *>(b + o_rx);
   for (int q = 0; q < 3; ++q) {
     gd.ref_tx[q] = geom->ref_tx[q];
     gd.ref_rx[q] = geom->ref_rx[q];
@@ -281,9 +344,18 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   gd.n_vert = geom->n_vertices;
   gd.n_tri = geom->n_triangles;
   gd.n_hits = H;
-  // the hosts' copies of the antenna positions must outlive the copies above
+  // the host copies of the antenna offsets must outlive the copies above
   if (cudaStreamSynchronize(s) != cudaSuccess) return SIM_E_CUDA;
   return SIM_OK;
+}
+
+// the snapshot-0 terms of every ray (after snap_setup, on its stream); returns kernels launched
+int launch_snapshot0(SnapRun &R) {
+  if (R.n <= 0) return 0;
+  snapshot0_kernel<<<static_cast<unsigned>((R.n + 127) / 128), 128, 0, R.s>>>(
+      R.gd, reinterpret_cast<const double *>(R.b + R.o_d), R.n, reinterpret_cast<double2 *>(R.b + R.o_base0),
+      reinterpret_cast<uint32_t *>(R.b + R.o_status));
+  return 1;
 }
 
 PhaseConst phase_const(const Derived &g) {
@@ -315,10 +387,11 @@ extern "C" SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, co
   int rc = snap_setup(R, ctx, rays, nullptr, hits, geom, 0, false, false, dev);
   if (rc != SIM_OK) return rc;
   const Derived &g = *R.g;
+  launch_snapshot0(R);
   if (R.n > 0) {
     double *out = dev ? paths : reinterpret_cast<double *>(R.b + R.o_paths);
     const dim3 grid(static_cast<unsigned>((R.n + 127) / 128), static_cast<unsigned>(g.nc));
-    snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const double *>(R.b + R.o_d),
+    snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const double2 *>(R.b + R.o_base0),
                                            reinterpret_cast<const float *>(R.b + R.o_p0), 0, R.n, phase_const(g),
                                            out, nullptr, nullptr, 0, reinterpret_cast<uint32_t *>(R.b + R.o_status));
     if (!dev)
@@ -349,8 +422,16 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
               reinterpret_cast<float *>(b + R.o_amp), reinterpret_cast<int32_t *>(b + R.o_cell),
               reinterpret_cast<uint64_t *>(b + R.o_en), reinterpret_cast<float2 *>(b + R.o_sd),
               reinterpret_cast<float2 *>(b + R.o_sr), nullptr, reinterpret_cast<uint64_t *>(b + R.o_ntx), nullptr};
+  // events around every stage: prep, per chunk (phase words | direct sum), FFTs, labels
+  const int64_t n_chunks = R.chunk > 0 ? (R.n + R.chunk - 1) / R.chunk : 0;
+  std::vector<cudaEvent_t> ev(static_cast<size_t>(2 * n_chunks + 5), nullptr);
+  for (auto &e : ev) cudaEventCreate(&e);
+  int kernels = 0, ei = 0;
+  cudaEventRecord(ev[ei++], s);
   // per-ray validation, antenna-pattern amplitudes, label cells and energies
-  launch_prep(g, in, R.n, rp, status, s);
+  kernels += launch_prep(g, in, R.n, rp, status, s);
+  kernels += launch_snapshot0(R);
+  cudaEventRecord(ev[ei++], s);
   float2 *sig = reinterpret_cast<float2 *>(b + R.o_sig);
   if (R.n == 0) cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
   ulonglong2 *wt = reinterpret_cast<ulonglong2 *>(b + R.o_wt), *wr = reinterpret_cast<ulonglong2 *>(b + R.o_wr);
@@ -358,22 +439,47 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
   for (int64_t i0 = 0; i0 < R.n; i0 += R.chunk) {
     const int64_t cnt = R.n - i0 < R.chunk ? R.n - i0 : R.chunk;
     const dim3 grid(static_cast<unsigned>((cnt + 127) / 128), static_cast<unsigned>(g.nc));
-    snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, in.d, in.p0, i0, cnt, k, nullptr, wt, wr, R.chunk, status);
-    launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, s);
+    snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const double2 *>(b + R.o_base0), in.p0, i0, cnt, k,
+                                         nullptr, wt, wr, R.chunk, status);
+    cudaEventRecord(ev[ei++], s);
+    kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, s);
+    cudaEventRecord(ev[ei++], s);
   }
   if (signal) cudaMemcpyAsync(signal, sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
   if (spectrum) {
     float2 *spec = reinterpret_cast<float2 *>(b + R.o_spec);
-    launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + R.o_tmp), spec, s);
+    kernels += launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + R.o_tmp), spec, s);
     cudaMemcpyAsync(spectrum, spec, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
   }
+  cudaEventRecord(ev[ei++], s);
   if (labels) {
     LabelScratch sc{reinterpret_cast<uint64_t *>(b + R.o_pk), reinterpret_cast<uint64_t *>(b + R.o_pe),
                     reinterpret_cast<uint32_t *>(b + R.o_ck), reinterpret_cast<uint64_t *>(b + R.o_cm),
                     reinterpret_cast<uint32_t *>(b + R.o_co), R.cap};
     int32_t *dlab = reinterpret_cast<int32_t *>(b + R.o_lab);
-    launch_labels(g, rp, in.obj, R.n, sc, dlab, status, s);
+    kernels += launch_labels(g, rp, in.obj, R.n, sc, dlab, status, s);
     cudaMemcpyAsync(labels, dlab, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
   }
-  return snap_finish(R);
+  cudaEventRecord(ev[ei++], s);
+  rc = snap_finish(R);
+  if (rc == SIM_OK) {
+    auto span = [&](int a, int b2) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev[static_cast<size_t>(a)], ev[static_cast<size_t>(b2)]);
+      return ms;
+    };
+    float ms[7] = {0, span(0, 1), 0, 0, 0, 0, 0};
+    int prev = 1;
+    for (int64_t c = 0; c < n_chunks; ++c) {
+      ms[1] += span(prev, prev + 1);      // phase words of the chunk
+      ms[2] += span(prev + 1, prev + 2);  // its direct sum
+      prev += 2;
+    }
+    ms[4] = span(prev, prev + 1);
+    ms[5] = span(prev + 1, prev + 2);
+    ms[6] = span(0, prev + 2);
+    record_stage_ms(ctx, ms, kernels);
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  return rc;
 }

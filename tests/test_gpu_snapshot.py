@@ -54,7 +54,10 @@ def test_paths_match_oracle(device):
     rc, got = snapshot(radar, rays, hits, geom, device=device, paths=True)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     ref = oracle.paths(radar, rays, hits, geom)
-    assert np.abs(got - ref).max() <= 1e-9
+    # reference legs in FP64, antenna offsets (<= 1.6 cm here) from them in FP32: ~3e-7 of the
+    # offset, 5 nm
+    assert np.abs(got - ref).max() <= 2e-8
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-9   # the reference pair itself: FP64 only
 
 
 @pytest.mark.parametrize("shape", [(32, 16, 3, 4, 16), (64, 8, 1, 4, 16), (16, 4, 2, 3, 8)])
