@@ -226,9 +226,10 @@ def run_batch_workload(args, rs, torch):
     return 0
 
 
-# SFU bound of the direct sums: one sine and one cosine per contribution on 16 MUFU lanes per SM
-# per clock, 152 SMs at the 2070 MHz maximum SM clock
-DIRECT_PEAK_TCONTRIB = 152 * 16 * 2.07e9 / 2 / 1e12
+# FP32-pipe bound of the direct sums: each contribution past a thread's first sample of a ray is
+# one complex multiply (4 FP32 operations) and one complex add (2) on 128 FP32 lanes per SM per
+# clock, 152 SMs at the 2070 MHz maximum SM clock
+DIRECT_PEAK_TCONTRIB = 152 * 128 * 2.07e9 / 6 / 1e12
 
 
 def run_snapshot_workload(args, rs, torch):
@@ -297,7 +298,7 @@ def run_snapshot_workload(args, rs, torch):
             "gpu_launches": kernels,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": DIRECT_PEAK_TCONTRIB, "unit": "Tcontrib/s",
                          "frac": achieved / DIRECT_PEAK_TCONTRIB, "traffic": None, "kernel": "pair_sum_kernel",
-                         "peak_source": "SFU sin+cos per contribution at the maximum SM clock"},
+                         "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"},
             "cpu_baseline": None, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()
@@ -521,7 +522,7 @@ def main():
         achieved = contrib / main_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": DIRECT_PEAK_TCONTRIB, "unit": "Tcontrib/s",
                 "frac": achieved / DIRECT_PEAK_TCONTRIB, "traffic": None, "kernel": "direct_sum_kernel",
-                "peak_source": "SFU sin+cos per contribution at the maximum SM clock"}
+                "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -1,26 +1,30 @@
 // K_b1: the ray sum as a tensor-core GEMM (arXiv 2305.14176, Sec. II-A, Eq. 2).
 //
 // With the separable phase, the beat cube is a complex product over rays:
-//   S[row, n] = sum_i A[row, i] B[i, n],   row = (k, m) = k N_c + m
-//   A[row, i] = a_i exp(2 pi j (carrier_i + k nu_a,i + m nu_d,i))
+//   S[row, n] = sum_i A[row, i] B[i, n],   row = (k, m) = k N_c + m, k = t N_rx + r
+//   A[row, i] = a_i exp(2 pi j (carrier_i + t nu_tx,i + r nu_a,i + m nu_d,i))
 //   B[i, n]   = exp(2 pi j n nu_r,i)
-// made real as D[M, 2 N_s] = A'[M, 2R] B'[2R, 2 N_s] with
-//   A'[row, 2i] = Re A, A'[row, 2i+1] = Im A,
-//   B' (stored K-major, one row per output column):
-//     column 2n   : ( Re B, -Im B)   -> D[row, 2n]   = Re S
-//     column 2n+1 : ( Im B,  Re B)   -> D[row, 2n+1] = Im S
-// so the accumulator columns come out as interleaved complex64.
+// computed in planar form: per 16-ray K step, four real MMAs of N = NC complex columns,
+//   Re S += A_re B_re - A_im B_im   (the minus by the instruction descriptor's negate-B bit)
+//   Im S += A_re B_im + A_im B_re
+// into two TMEM accumulator blocks (Re, Im).  Split precision adds the cross terms
+// A_hi B_lo + A_lo B_hi of each product: twelve MMAs per K step.
 //
-// Operands are never stored in HBM: producer warps synthesise A' and B' tiles for a
-// stage of rays straight into shared memory (Q0.64 phases from the prep kernel, one FP32
-// sin/cos each, rounded to BF16 or FP16, optionally split into hi + lo), and one thread
-// issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory).  Split precision
-// accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi into the same accumulator.
+// Operands are never stored in HBM: three groups of producer warps synthesise the A and B
+// tiles of a stage of 32 rays straight into shared memory (Q0.64 phases from the prep
+// kernel, one FP32 sin/cos per phasor chain, then FP32 complex steps of 16 chirps or 16
+// samples with the prep kernel's FP64-accurate step phasors, rounded to BF16 or FP16 and
+// optionally split into hi + lo), in the no-swizzle K-major core-matrix layout.  One thread
+// issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory).  Four drain warps add
+// each finished accumulation chain (at most 16 stages, 512 rays, for split precision: the
+// tensor core's accumulate is not round-to-nearest, so long chains lose accuracy) to an FP32
+// running sum kept in tensor memory, and store the sum when the unit ends.
 //
-// Work is split over rays (split-K): each CTA sums one chunk of rays for one 128-row x
+// Work is split over rays (split-K): each unit sums one chunk of rays for one 128-row x
 // BN-column tile and writes an FP32 partial; a second kernel adds the partials in chunk
 // order.  The decomposition depends only on the scene's own shape, so a scene gives the
-// same bits alone or beside others.
+// same bits alone or beside others.  In the persistent form a CTA takes units from an
+// atomic work list (batches of scenes).
 //
 // Every mbarrier wait is bounded; a wait that runs out sets a status bit, the CTA stops
 // issuing work, drains what it issued, frees its tensor memory and returns.
