@@ -325,6 +325,15 @@ SIM_API int sim_tuning_count(void);
 SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
                               float *d, void *stream);
 
+/* Self-test of the two-SM tensor-core tile (not a simulation call): one CTA pair computes
+   D[256][N] = A[256][K] * B[N][K]^T with tcgen05.mma.cta_group::2, each CTA holding 128 rows
+   of A and N/2 rows of B in its shared memory.  A, B row-major 16-bit device matrices (f16 1:
+   FP16, 0: BF16), D row-major FP32 device memory; N a multiple of 16 in 32 .. 256, K even.
+   stream is a cudaStream_t (NULL = default); the call synchronizes it.
+   Errors: SIM_E_INVALID, SIM_E_NOMEM, SIM_E_CUDA, SIM_E_DEVICE (a wait ran out). */
+SIM_API int sim_selftest_umma_pair(int32_t f16, int32_t n, int64_t k, const void *a, const void *b, float *d,
+                                   void *stream);
+
 /* Ray sum without any device allocation.
    Some callers cannot call cudaMalloc: a host application whose framework allocator has
    already reserved the GPU's memory, a real-time loop that must not take the implicit

@@ -53,8 +53,8 @@ struct RaysPrep {
   float *amp;         // amplitude (0 for an invalid ray)
   int32_t *cell;      // flat label cell, -1 for an invalid ray
   uint64_t *energy;   // min(rint(a^2 2^32), 2^41)
-  float2 *step_d;     // e^{2 pi j 16 nu_d}: phasor step over sixteen chirps (FP64-accurate)
-  float2 *step_r;     // e^{2 pi j 16 nu_r}: phasor step over sixteen samples
+  float2 *step_d;     // e^{2 pi j 32 nu_d}: phasor step over 32 chirps (FP64-accurate)
+  float2 *step_r;     // e^{2 pi j 32 nu_r}: phasor step over 32 samples
   uint64_t *eps;      // exact Eq. 2 only (else null): range-migration cycles per sample x chirp
   uint64_t *nu_tx;    // cycles per transmitter: N_rx nu_a + nu_t (nu_t = TDM slot Doppler, 0 = none)
   uint64_t *eps_t;    // exact Eq. 2 only (else null): range-migration cycles per sample x TDM slot
@@ -100,10 +100,13 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
 
 // ---- batched tensor-core ray sum (one persistent launch over several scenes)
 struct UmmaBatch {
-  unsigned *counter;  // work-list cursor (device)
+  unsigned *counter;  // work-list cursors (device): [0] two-SM list, [1] one-SM list
   void *args;         // per-scene kernel arguments (device)
-  void *units;        // work list, longest first (device)
-  int n_units, n_scenes, bn_max;
+  void *units;        // two-SM work list (256-row tiles), longest first (device)
+  int n_units;
+  void *units1;       // one-SM work list (128-row tiles), longest first (device)
+  int n_units1;
+  int n_scenes, bn_max;
   bool f16, split, fast;
 };
 // device bytes of the batch's descriptors and counter

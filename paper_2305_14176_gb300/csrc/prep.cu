@@ -67,9 +67,9 @@ __device__ __forceinline__ uint64_t frac_q64(double x) {
   return __double2ull_rn(__dmul_rn(f, kTwo64));
 }
 
-// e^{2 pi j 16 q} for a Q0.64 phase increment q, from the exact Q0.64 product in FP64
-__device__ __forceinline__ float2 step16(uint64_t q) {
-  const double f = static_cast<double>(static_cast<int64_t>(q * 16ull)) * 0x1p-64;  // cycles in [-1/2, 1/2)
+// e^{2 pi j 32 q} for a Q0.64 phase increment q, from the exact Q0.64 product in FP64
+__device__ __forceinline__ float2 step32(uint64_t q) {
+  const double f = static_cast<double>(static_cast<int64_t>(q * 32ull)) * 0x1p-64;  // cycles in [-1/2, 1/2)
   double s, c;
   sincospi(2.0 * f, &s, &c);
   return make_float2(static_cast<float>(c), static_cast<float>(s));
@@ -129,8 +129,8 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   const uint64_t nu_d = frac_q64(__dmul_rn(x_d, k.inv_nc));
   out.nu_r[i] = nu_r;
   out.nu_d[i] = nu_d;
-  out.step_r[i] = step16(nu_r);
-  out.step_d[i] = step16(nu_d);
+  out.step_r[i] = step32(nu_r);
+  out.step_d[i] = step32(nu_d);
   const uint64_t nu_a = frac_q64(__dmul_rn(x_a, k.inv_na));
   out.nu_a[i] = nu_a;
   // TDM-MIMO: transmitter t fires chirp j at j T_d + t T_slot, so its phase gains t nu_t with

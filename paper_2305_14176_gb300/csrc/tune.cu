@@ -56,9 +56,9 @@ __global__ void synth_rays(RaysPrep p, int64_t n) {
   p.cell[i] = 0;
   p.energy[i] = 0;
   float s, c;
-  sincospif(2.0f * static_cast<float>(static_cast<int64_t>(p.nu_d[i] * 16ull)) * 0x1p-64f, &s, &c);
+  sincospif(2.0f * static_cast<float>(static_cast<int64_t>(p.nu_d[i] * 32ull)) * 0x1p-64f, &s, &c);
   p.step_d[i] = make_float2(c, s);
-  sincospif(2.0f * static_cast<float>(static_cast<int64_t>(p.nu_r[i] * 16ull)) * 0x1p-64f, &s, &c);
+  sincospif(2.0f * static_cast<float>(static_cast<int64_t>(p.nu_r[i] * 32ull)) * 0x1p-64f, &s, &c);
   p.step_r[i] = make_float2(c, s);
 }
 

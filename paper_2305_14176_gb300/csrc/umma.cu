@@ -57,10 +57,11 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a) {
 }
 // One potentially blocking test of a phase: the hardware suspends the thread until the
 // phase completes or about `hint_ns` passes, so a waiting warp does not spin on issue slots.
+// Cluster-scope acquire: the barriers of a CTA pair also receive the peer CTA's arrivals.
 __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity, uint32_t hint_ns = 1000000u) {
   uint32_t ok;
   asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(a), "r"(parity), "r"(hint_ns)
@@ -90,25 +91,76 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
+// PAIR: the two CTAs of a cluster work as one (tcgen05 .cta_group::2): the allocation is made
+// by one warp of each CTA, the even CTA issues the MMAs and commits to both CTAs' barriers.
+template <bool PAIR>
 __device__ __forceinline__ void tmem_alloc(uint32_t holder, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  if constexpr (PAIR) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  } else {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
 }
+template <bool PAIR>
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  if constexpr (PAIR)
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+  else
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+template <bool PAIR>
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if constexpr (PAIR)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
+// arrive on `mbar` (same offset) of this CTA, or of both CTAs of the pair, when the MMAs issued
+// so far complete
+template <bool PAIR>
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
+  if constexpr (PAIR)
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            mbar),
+        "h"(static_cast<uint16_t>(3))
+        : "memory");
+  else
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// shared address `a` of this CTA as seen in the cluster window of CTA `rank`
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cl_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+__device__ __forceinline__ void st_cluster_u32(uint32_t cl_addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(cl_addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 // 16 consecutive FP32 columns of this warp's 32 TMEM lanes
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -247,7 +299,7 @@ __device__ __forceinline__ bool mbar_wait_sleep(uint32_t a, uint32_t parity) {
 // (k0 = t0 N_rx + r0, m0).
 struct StageRays {
   uint64_t base[KS], car[KS], nua[KS], nud[KS], nur[KS], nutx[KS];
-  float2 wd[KS], wr[KS];
+  float2 wd[KS], wr[KS];  // e^{2 pi j 32 nu_d}, e^{2 pi j 32 nu_r}
   float amp[KS];
 };
 
@@ -326,21 +378,26 @@ __device__ __forceinline__ void put_octet(const float2 (&z)[OCT], uint8_t *re_hi
 // Synthesise one stage of operands in planar K order: within each 16-ray K step, the first
 // K chunk of the A tile holds Re A of eight rays and the next Im A, likewise for B.
 //   Shared layout of a stage: A_re | A_im (128 rows x 32 rays each, core matrices of 8 rows x
-//   8 rays, 2048 bytes per K chunk) | B_re | B_im (NC = bn/2 rows each) | the same four for lo.
-//   Threads 0..63 of the group build A (ray octet o = t/16, rows j, j+16, ... with j = t%16),
-//   threads 64..127 build B (complex columns j, j+16, ...).  Each holds eight independent
-//   phasor chains stepped by the FP64-accurate e^{2 pi j 16 nu} of the prep kernel.
-template <bool F16, bool SPLIT, bool FAST>
+//   8 rays, 2048 bytes per K chunk) | B_re | B_im (NC rows each) | the same four for lo.
+//   Every thread of the group takes ray octet o = t / 32 (one warp per octet) and lane
+//   j = t % 32: A rows j, j + 32, j + 64, j + 96 and B columns j, j + 32, ... below NC, so the
+//   work is even across the group and each warp's 16-byte stores cover 512 contiguous bytes.
+//   Each phasor chain starts from one hardware sin/cos of its exact Q0.64 phase and steps 32
+//   chirps / 32 samples per complex multiply with the FP64-accurate e^{2 pi j 32 nu} of the
+//   prep kernel.
+//   PAIR: this CTA holds B for its half of the tile's complex columns (NC = bn / 4 of them).
+template <bool F16, bool SPLIT, bool FAST, bool PAIR>
 __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &sr, uint8_t *stage, int gt, int row0,
-                                               int col0, float scale) {
-  const int NC = g.bn >> 1;
+                                               int col0, float scale, int rank) {
+  const int NC = PAIR ? g.bn >> 2 : g.bn >> 1;         // complex B columns held here
   const uint32_t a_half = BM * KS * 2;                 // bytes of A_re (or A_im)
   const uint32_t x_half = static_cast<uint32_t>(NC) * KS * 2;
   const uint32_t hi_bytes = 2 * a_half + 2 * x_half;
   uint8_t *a_re = stage, *a_im = stage + a_half, *x_re = stage + 2 * a_half, *x_im = x_re + x_half;
   const uint32_t lo = SPLIT ? hi_bytes : 0;
-  if (gt < 64) {
-    const int o = gt >> 4, j = gt & 15;
+  const int o = gt >> 5, j = gt & 31;
+  {
+    // ---- A: rows j + 32 l
     uint32_t off = o * (BM * 16) + (j >> 3) * 128 + (j & 7) * 16;
     float2 z[OCT], w[OCT];
     int grow = row0 + j;
@@ -374,14 +431,14 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
 #pragma unroll
     for (int q = 0; q < OCT; ++q) w[q] = sr.wd[o * OCT + q];
 #pragma unroll 1
-    for (int l = 0; l < BM / 16; ++l) {
+    for (int l = 0; l < BM / 32; ++l) {
       if (l > 0) {
         if constexpr (FAST) {
 #pragma unroll
-          for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // sixteen chirps on
+          for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // 32 chirps on
         } else {
-          grow += 16;
-          mq += 16;
+          grow += 32;
+          mq += 32;
           if (mq >= g.nc) {  // crossed into another channel: restart from the exact phases
             kq = grow / g.nc;
             mq = grow - kq * g.nc;
@@ -397,29 +454,29 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
         for (int q = 0; q < OCT; ++q) z[q] = make_float2(0.f, 0.f);
       }
       put_octet<F16, SPLIT>(z, a_re + off, a_im + off, a_re + lo + off, a_im + lo + off);
-      off += 256;
+      off += 512;
     }
-  } else {
-    const int t = gt - 64;
-    const int o = t >> 4, j = t & 15;
+  }
+  if (j < NC) {
+    // ---- B: columns j + 32 l below NC
     uint32_t off = o * static_cast<uint32_t>(NC * 16) + (j >> 3) * 128 + (j & 7) * 16;
     float2 z[OCT], w[OCT];
 #pragma unroll
     for (int q = 0; q < OCT; ++q) {
       const int i = o * OCT + q;
       float sn, cs;
-      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + j) * sr.nur[i]), &sn, &cs);
+      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + (PAIR ? rank * NC : 0) + j) * sr.nur[i]), &sn, &cs);
       z[q] = make_float2(cs, sn);
       w[q] = sr.wr[i];
     }
 #pragma unroll 1
-    for (int l = 0; l < NC / 16; ++l) {
-      if (l > 0) {
+    for (int c = j; c < NC; c += 32) {
+      if (c > j) {
 #pragma unroll
-        for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // sixteen samples on
+        for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // 32 samples on
       }
       put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
-      off += 256;
+      off += 512;
     }
   }
 }
@@ -478,28 +535,34 @@ struct Launch {
   int bn_layout;         // B rows the shared-memory stages are laid out for (max bn)
 };
 
-template <bool SPLIT, bool TEST>
+template <bool SPLIT, bool TEST, bool PAIR>
 __host__ __device__ constexpr int num_stages() {
-  return TEST ? 4 : (SPLIT ? 3 : 6);
+  return TEST ? 4 : (PAIR ? (SPLIT ? 4 : 8) : (SPLIT ? 3 : 6));
 }
 
-// bytes of one pipeline stage
-template <bool SPLIT, bool TEST>
+// bytes of one pipeline stage (PAIR: B for half the tile's columns)
+template <bool SPLIT, bool TEST, bool PAIR>
 __host__ __device__ constexpr uint32_t stage_size(int bn) {
   return TEST ? static_cast<uint32_t>(BM * KELEM * 2 + bn * KELEM * 2)
-              : static_cast<uint32_t>(BM * KELEM * 2 + bn * KS * 2) * (SPLIT ? 2u : 1u);
+              : static_cast<uint32_t>(BM * KELEM * 2 + (PAIR ? bn / 2 : bn) * KS * 2) * (SPLIT ? 2u : 1u);
 }
 
-template <bool F16, bool SPLIT, bool TEST, bool FAST>
+// PAIR: launched as clusters of two CTAs; each cluster takes one unit of 256 rows, the even
+// CTA (rank 0) holding rows 0..127 and issuing the M = 256 MMAs, the odd CTA rows 128..255.
+// Each CTA builds A for its rows and B for its half of the columns; every pipeline barrier the
+// issuer waits on lives in CTA 0 and counts both CTAs' arrivals.  One unit per cluster.
+template <bool F16, bool SPLIT, bool TEST, bool FAST, bool PAIR>
 __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ Args s_args;
   __shared__ Unit s_unit;
   __shared__ int s_abort;
+  __shared__ int s_next, s_peer_abort;  // PAIR work list: the pair's next unit, the odd CTA's abort
   __shared__ StageRays s_rays[NGROUP];
-  constexpr int NST = num_stages<SPLIT, TEST>();
+  constexpr int NST = num_stages<SPLIT, TEST, PAIR>();
   constexpr uint32_t TMEM_COLS = 512;  // accumulator (0..255) and running sum (256..511)
-  const uint32_t stage_bytes = stage_size<SPLIT, TEST>(L.bn_layout);
+  const uint32_t stage_bytes = stage_size<SPLIT, TEST, PAIR>(L.bn_layout);
+  const uint32_t rank = PAIR ? cluster_rank() : 0u;
   uint8_t *base = smem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
   // barriers: full[NST], empty[NST], acc_full, acc_empty, mma_done
@@ -509,31 +572,54 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   const uint32_t done = smem_u32(bars + 2 * NST + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+  // the issuer's barriers (in CTA 0) as every thread of the pair addresses them
+  const uint32_t full0_c = PAIR ? cluster_addr(full0, 0) : full0;
+  const uint32_t acce_c = PAIR ? cluster_addr(acce, 0) : acce;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      mbar_init(full0 + 8 * s, GSIZE);
+      mbar_init(full0 + 8 * s, PAIR ? 2 * GSIZE : GSIZE);
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accf, 1);
-    mbar_init(acce, NDRAIN);
+    mbar_init(acce, PAIR ? 2 * NDRAIN : NDRAIN);
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
+    s_next = 0;
+    s_peer_abort = 0;
   }
-  if (warp == MMA_WARP) tmem_alloc(smem_u32(tmem_holder), TMEM_COLS);
+  if (warp == MMA_WARP) tmem_alloc<PAIR>(smem_u32(tmem_holder), TMEM_COLS);
   tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
   // running counters shared by every role: pipeline stages, accumulation chains, units
   int gst = 0, gsub = 0, gunit = 0;
-  int u = static_cast<int>(blockIdx.x);
+  int u = static_cast<int>(PAIR ? blockIdx.x >> 1 : blockIdx.x);
+  // PAIR with a work list: CTA 0 takes the pair's next unit (or stops the pair when either CTA
+  // has aborted) and writes it into both CTAs' s_next; every thread of both CTAs calls this
+  auto pair_next = [&]() -> int {
+    if (rank != 0 && threadIdx.x == 0 && s_abort) st_cluster_u32(cluster_addr(smem_u32(&s_peer_abort), 0), 1u);
+    cluster_sync();
+    if (rank == 0 && threadIdx.x == 0) {
+      const int v = (s_abort || s_peer_abort) ? L.n_units : static_cast<int>(atomicAdd(L.counter, 1u));
+      s_next = v;
+      st_cluster_u32(cluster_addr(smem_u32(&s_next), 1), static_cast<uint32_t>(v));
+    }
+    cluster_sync();
+    return s_next;
+  };
   if (L.counter) {
-    if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
-    __syncthreads();
-    u = s_unit.scene;
-    __syncthreads();
+    if constexpr (PAIR) {
+      u = pair_next();
+    } else {
+      if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
+      __syncthreads();
+      u = s_unit.scene;
+      __syncthreads();
+    }
   }
   while (u < L.n_units) {
     if (threadIdx.x == 0) {
@@ -552,7 +638,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
     const Args &g = s_args;
     const int bn = g.bn;
     const int NC = bn >> 1;
-    const int row0 = s_unit.tile_m * BM;
+    const int row0 = (PAIR ? 2 * s_unit.tile_m + static_cast<int>(rank) : s_unit.tile_m) * BM;
     const int col0 = s_unit.tile_n * bn;  // real column; complex n0 = col0 / 2
     const int split = s_unit.split;
     const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
@@ -588,15 +674,19 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         if constexpr (TEST) {
           copy_stage(g, st_base, st_base + BM * KELEM * 2, ray0, row0, col0, gt);
         } else {
-          produce_planar<F16, SPLIT, FAST>(g, s_rays[grp], st_base, gt, row0, col0, scale);
+          produce_planar<F16, SPLIT, FAST, PAIR>(g, s_rays[grp], st_base, gt, row0, col0, scale,
+                                                 static_cast<int>(rank));
         }
         fence_proxy_async();
-        mbar_arrive(full0 + 8 * s);
+        if constexpr (PAIR) mbar_arrive_cluster(full0_c + 8 * s);
+        else mbar_arrive(full0 + 8 * s);
         if constexpr (!TEST) group_sync(grp);  // s_rays[grp] is rewritten next round
       }
     } else if (warp == MMA_WARP) {
-      // ---------------- MMA issuer
-      if (lane == 0) {
+      // ---------------- MMA issuer (PAIR: CTA 0 issues for both; CTA 1 only waits for the end)
+      if (lane == 0 && PAIR && rank != 0) {
+        if (!mbar_wait(done, gunit & 1)) failed = true;
+      } else if (lane == 0) {
         const uint32_t sbase = smem_u32(base);
         bool open = false;  // issued MMAs not yet committed to acc_full
         for (int st = 0; st < n_stages; ++st) {
@@ -614,22 +704,24 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
           }
           tc_fence_after();
           const uint32_t sb = sbase + s * stage_bytes;
-          if constexpr (TEST) {
+          if constexpr (TEST && !PAIR) {
             // interleaved layout: D = A B^T over 4 K steps of 16
             const uint32_t idesc = make_idesc(F16, BM, bn) | (g.test_negate_b ? (1u << 14) : 0u);
             const uint32_t lbo_a = BM * 16, lbo_b = static_cast<uint32_t>(bn) * 16;
             const uint32_t b0 = sb + BM * KELEM * 2;
 #pragma unroll
             for (int kk = 0; kk < KELEM / 16; ++kk)
-              mma_f16(tmem, make_sdesc(sb + kk * 2 * lbo_a, lbo_a, 128), make_sdesc(b0 + kk * 2 * lbo_b, lbo_b, 128),
-                      idesc, (!first || kk > 0) ? 1u : 0u);
+              mma_f16<false>(tmem, make_sdesc(sb + kk * 2 * lbo_a, lbo_a, 128),
+                             make_sdesc(b0 + kk * 2 * lbo_b, lbo_b, 128), idesc, (!first || kk > 0) ? 1u : 0u);
           } else {
             // planar layout: per 16-ray K step, Re S += A_re B_re - A_im B_im and
-            // Im S += A_re B_im + A_im B_re (the minus by the descriptor's negate-B bit)
-            const uint32_t idesc = make_idesc(F16, BM, NC);
+            // Im S += A_re B_im + A_im B_re (the minus by the descriptor's negate-B bit).
+            // PAIR: M = 256 over both CTAs, each CTA's B blocks hold NC / 2 of the NC columns.
+            const uint32_t idesc = make_idesc(F16, PAIR ? 2 * BM : BM, NC);
             const uint32_t ineg = idesc | (1u << 14);
-            const uint32_t lbo_a = BM * 16, lbo_x = static_cast<uint32_t>(NC) * 16;
-            const uint32_t a_half = BM * KS * 2, x_half = static_cast<uint32_t>(NC) * KS * 2;
+            const uint32_t ncx = static_cast<uint32_t>(PAIR ? NC / 2 : NC);
+            const uint32_t lbo_a = BM * 16, lbo_x = ncx * 16;
+            const uint32_t a_half = BM * KS * 2, x_half = ncx * KS * 2;
             const uint32_t ar = sb, ai = sb + a_half, xr = sb + 2 * a_half, xi = xr + x_half;
             const uint32_t lo = 2 * a_half + 2 * x_half;
             const uint32_t t_re = tmem, t_im = tmem + static_cast<uint32_t>(NC);
@@ -639,34 +731,34 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
               const uint32_t oa = kh * 2 * lbo_a, ox = kh * 2 * lbo_x;
               const uint64_t dar = make_sdesc(ar + oa, lbo_a, 128), dai = make_sdesc(ai + oa, lbo_a, 128);
               const uint64_t dxr = make_sdesc(xr + ox, lbo_x, 128), dxi = make_sdesc(xi + ox, lbo_x, 128);
-              mma_f16(t_re, dar, dxr, idesc, acc);
-              mma_f16(t_re, dai, dxi, ineg, 1u);
-              mma_f16(t_im, dar, dxi, idesc, acc);
-              mma_f16(t_im, dai, dxr, idesc, 1u);
+              mma_f16<PAIR>(t_re, dar, dxr, idesc, acc);
+              mma_f16<PAIR>(t_re, dai, dxi, ineg, 1u);
+              mma_f16<PAIR>(t_im, dar, dxi, idesc, acc);
+              mma_f16<PAIR>(t_im, dai, dxr, idesc, 1u);
               if constexpr (SPLIT) {
                 const uint64_t lar = make_sdesc(ar + lo + oa, lbo_a, 128), lai = make_sdesc(ai + lo + oa, lbo_a, 128);
                 const uint64_t lxr = make_sdesc(xr + lo + ox, lbo_x, 128), lxi = make_sdesc(xi + lo + ox, lbo_x, 128);
-                mma_f16(t_re, dar, lxr, idesc, 1u);
-                mma_f16(t_re, lar, dxr, idesc, 1u);
-                mma_f16(t_re, dai, lxi, ineg, 1u);
-                mma_f16(t_re, lai, dxi, ineg, 1u);
-                mma_f16(t_im, dar, lxi, idesc, 1u);
-                mma_f16(t_im, lar, dxi, idesc, 1u);
-                mma_f16(t_im, dai, lxr, idesc, 1u);
-                mma_f16(t_im, lai, dxr, idesc, 1u);
+                mma_f16<PAIR>(t_re, dar, lxr, idesc, 1u);
+                mma_f16<PAIR>(t_re, lar, dxr, idesc, 1u);
+                mma_f16<PAIR>(t_re, dai, lxi, ineg, 1u);
+                mma_f16<PAIR>(t_re, lai, dxi, ineg, 1u);
+                mma_f16<PAIR>(t_im, dar, lxi, idesc, 1u);
+                mma_f16<PAIR>(t_im, lar, dxi, idesc, 1u);
+                mma_f16<PAIR>(t_im, dai, lxr, idesc, 1u);
+                mma_f16<PAIR>(t_im, lai, dxr, idesc, 1u);
               }
             }
           }
           open = true;
-          mma_commit(empty0 + 8 * s);
+          mma_commit<PAIR>(empty0 + 8 * s);
           if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
-            mma_commit(accf);
+            mma_commit<PAIR>(accf);
             open = false;
           }
         }
-        if (open) mma_commit(accf);
-        // every issued MMA of this unit has completed once `done` fires
-        mma_commit(done);
+        if (open) mma_commit<PAIR>(accf);
+        // every issued MMA of this unit has completed once `done` fires (in both CTAs)
+        mma_commit<PAIR>(done);
         if (!mbar_wait(done, gunit & 1)) failed = true;
       }
     } else {
@@ -708,7 +800,8 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         }
         if (!last) tmem_wait_st();
         tc_fence_before();
-        mbar_arrive(acce);
+        if constexpr (PAIR) mbar_arrive_cluster(acce_c);
+        else mbar_arrive(acce);
       }
     }
     if (failed) {
@@ -721,17 +814,25 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
     tc_fence_before();
     __syncthreads();  // every role is done with this unit (and with s_args)
     tc_fence_after();
-    if (!L.counter || s_abort) break;
-    if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
-    __syncthreads();
-    u = s_unit.scene;
-    __syncthreads();
+    if (!L.counter) break;
+    if constexpr (PAIR) {
+      u = pair_next();  // both CTAs stop together
+    } else {
+      if (s_abort) break;
+      if (threadIdx.x == 0) s_unit.scene = static_cast<int>(atomicAdd(L.counter, 1u));
+      __syncthreads();
+      u = s_unit.scene;
+      __syncthreads();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  // PAIR: neither CTA leaves while the other may still arrive on its barriers or the issuer's
+  // MMAs may still read its shared memory
+  if constexpr (PAIR) cluster_sync();
+  else __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc(tmem, TMEM_COLS);
+    tmem_dealloc<PAIR>(tmem, TMEM_COLS);
   }
 }
 
@@ -833,50 +934,78 @@ Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
   return s;
 }
 
-size_t smem_bytes(bool split, int bn) {
-  const int nst = split ? num_stages<true, false>() : num_stages<false, false>();
-  const size_t stage = split ? stage_size<true, false>(bn) : stage_size<false, false>(bn);
+size_t smem_bytes(bool split, int bn, bool pair = false) {
+  const int nst = pair ? (split ? num_stages<true, false, true>() : num_stages<false, false, true>())
+                       : (split ? num_stages<true, false, false>() : num_stages<false, false, false>());
+  const size_t stage = pair ? (split ? stage_size<true, false, true>(bn) : stage_size<false, false, true>(bn))
+                            : (split ? stage_size<true, false, false>(bn) : stage_size<false, false, false>(bn));
   return nst * stage + 8 * (2 * nst + 3) + 16;
 }
 
 constexpr int kMaxDynSmem = 232448 - 8192;  // 227 KB per block, less the kernel's static shared memory
 
-template <bool F16, bool SPLIT, bool TEST, bool FAST>
+template <bool F16, bool SPLIT, bool TEST, bool FAST, bool PAIR>
 void set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256)));
+    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256, PAIR)));
     attr = true;
   }
 }
 
-// one scene, one unit per CTA
-template <bool F16, bool SPLIT, bool TEST, bool FAST>
+// one scene, one unit per CTA (PAIR: per cluster of two CTAs, units of 256 rows)
+template <bool F16, bool SPLIT, bool TEST, bool FAST, bool PAIR>
 void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
   // the self-test reserves the whole shared memory so that every descriptor it builds
   // points inside the allocation
-  const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn);
-  set_smem_attr<F16, SPLIT, TEST, FAST>();
+  const size_t sm = TEST ? kMaxDynSmem : smem_bytes(SPLIT, sh.bn, PAIR);
+  set_smem_attr<F16, SPLIT, TEST, FAST, PAIR>();
   Launch L{};
   L.inline_scene = a;
-  L.n_units = sh.mt * sh.nt * sh.splits;
-  L.mt = sh.mt;
+  L.mt = PAIR ? (sh.mt + 1) / 2 : sh.mt;
   L.nt = sh.nt;
+  L.n_units = L.mt * sh.nt * sh.splits;
   L.bn_layout = sh.bn;
-  umma_sum_kernel<F16, SPLIT, TEST, FAST><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
+  if constexpr (PAIR) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2u * static_cast<unsigned>(L.n_units));
+    cfg.blockDim = dim3(NTHREADS_ALL);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, L);
+  } else {
+    umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
+  }
 }
+
+// Two-SM tiles (M = 256 over a CTA pair, each CTA building B for half the columns) when the
+// tile has at least 32 complex columns; the split-K chunks are those of the one-SM tiling.
+bool use_pair(const Shape &sh) { return sh.bn >= 64; }
 
 // FAST: every tile's 128 rows lie in one channel (N_c a multiple of 128); the general kernel
 // gives the same bits on such scenes, only with more work per row
-void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, const Args &a, cudaStream_t s) {
+template <bool PAIR>
+void launch_gemm_dispatch_p(bool f16, bool split, bool fast, const Shape &sh, const Args &a, cudaStream_t s) {
   if (f16) {
-    if (split) fast ? launch_gemm<true, true, false, true>(sh, a, s) : launch_gemm<true, true, false, false>(sh, a, s);
-    else fast ? launch_gemm<true, false, false, true>(sh, a, s) : launch_gemm<true, false, false, false>(sh, a, s);
+    if (split) fast ? launch_gemm<true, true, false, true, PAIR>(sh, a, s) : launch_gemm<true, true, false, false, PAIR>(sh, a, s);
+    else fast ? launch_gemm<true, false, false, true, PAIR>(sh, a, s) : launch_gemm<true, false, false, false, PAIR>(sh, a, s);
   } else {
-    if (split) fast ? launch_gemm<false, true, false, true>(sh, a, s) : launch_gemm<false, true, false, false>(sh, a, s);
-    else fast ? launch_gemm<false, false, false, true>(sh, a, s) : launch_gemm<false, false, false, false>(sh, a, s);
+    if (split) fast ? launch_gemm<false, true, false, true, PAIR>(sh, a, s) : launch_gemm<false, true, false, false, PAIR>(sh, a, s);
+    else fast ? launch_gemm<false, false, false, true, PAIR>(sh, a, s) : launch_gemm<false, false, false, false, PAIR>(sh, a, s);
   }
+}
+
+void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, const Args &a, cudaStream_t s) {
+  if (use_pair(sh)) launch_gemm_dispatch_p<true>(f16, split, fast, sh, a, s);
+  else launch_gemm_dispatch_p<false>(f16, split, fast, sh, a, s);
 }
 
 }  // namespace
@@ -990,8 +1119,10 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
                        void *const *workspaces, uint32_t *const *statuses, void *scratch, cudaStream_t s,
                        UmmaBatch *out) {
   std::vector<Args> args(static_cast<size_t>(n_scenes));
-  std::vector<Unit> units;
-  std::vector<int64_t> cost;
+  // two work lists: scenes whose standalone launch uses two-SM tiles get pair units (256 rows),
+  // the others one-SM units, so that every scene's units are those of its standalone launch
+  std::vector<Unit> units, units1;
+  std::vector<int64_t> cost, cost1;
   bool f16 = false, split = false;
   int bn_max = 32;
   for (int i = 0; i < n_scenes; ++i) {
@@ -1020,26 +1151,35 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
     a.amax_bits = static_cast<const uint32_t *>(workspaces[i]);
     a.status = statuses[i];
     if (sh.bn > bn_max) bn_max = sh.bn;
+    const bool pair = use_pair(sh);
+    const int mt = pair ? (sh.mt + 1) / 2 : sh.mt;
     for (int sp = 0; sp < sh.splits; ++sp) {
       const int64_t rays = std::min<int64_t>(sh.chunk, ns[i] - sp * sh.chunk);
       for (int tn = 0; tn < sh.nt; ++tn)
-        for (int tm = 0; tm < sh.mt; ++tm) {
-          units.push_back(Unit{i, tm, tn, sp});
-          cost.push_back(std::max<int64_t>(rays, 0) * sh.bn);
+        for (int tm = 0; tm < mt; ++tm) {
+          (pair ? units : units1).push_back(Unit{i, tm, tn, sp});
+          (pair ? cost : cost1).push_back(std::max<int64_t>(rays, 0) * sh.bn);
         }
     }
   }
   // longest first (stable: ties keep scene, split, tile order)
-  std::vector<size_t> order(units.size());
-  for (size_t k = 0; k < order.size(); ++k) order[k] = k;
-  std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
-  std::vector<Unit> sorted(units.size());
-  for (size_t k = 0; k < order.size(); ++k) sorted[k] = units[order[k]];
+  auto longest_first = [](const std::vector<Unit> &u, const std::vector<int64_t> &c) {
+    std::vector<size_t> order(u.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return c[x] > c[y]; });
+    std::vector<Unit> sorted(u.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = u[order[k]];
+    return sorted;
+  };
+  std::vector<Unit> sorted = longest_first(units, cost), sorted1 = longest_first(units1, cost1);
+  sorted.insert(sorted.end(), sorted1.begin(), sorted1.end());
   uint8_t *scr = static_cast<uint8_t *>(scratch);
-  out->counter = reinterpret_cast<unsigned *>(scr);
+  out->counter = reinterpret_cast<unsigned *>(scr);  // [0] pair list, [1] one-SM list
   out->args = scr + 256;
   out->units = scr + 256 + sizeof(Args) * static_cast<size_t>(n_scenes);
-  out->n_units = static_cast<int>(sorted.size());
+  out->n_units = static_cast<int>(units.size());
+  out->units1 = static_cast<uint8_t *>(out->units) + sizeof(Unit) * units.size();
+  out->n_units1 = static_cast<int>(units1.size());
   out->n_scenes = n_scenes;
   out->f16 = f16;
   out->split = split;
@@ -1052,37 +1192,80 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
   bool all_fast = true;
   for (int i = 0; i < n_scenes; ++i) all_fast = all_fast && (gs[i]->nc % BM) == 0;
   out->fast = all_fast;
-  set_smem_attr<true, true, false, true>();
-  set_smem_attr<true, false, false, true>();
-  set_smem_attr<false, true, false, true>();
-  set_smem_attr<false, false, false, true>();
-  set_smem_attr<true, true, false, false>();
-  set_smem_attr<true, false, false, false>();
-  set_smem_attr<false, true, false, false>();
-  set_smem_attr<false, false, false, false>();
+  set_smem_attr<true, true, false, true, false>();
+  set_smem_attr<true, false, false, true, false>();
+  set_smem_attr<false, true, false, true, false>();
+  set_smem_attr<false, false, false, true, false>();
+  set_smem_attr<true, true, false, false, false>();
+  set_smem_attr<true, false, false, false, false>();
+  set_smem_attr<false, true, false, false, false>();
+  set_smem_attr<false, false, false, false, false>();
+  set_smem_attr<true, true, false, true, true>();
+  set_smem_attr<true, false, false, true, true>();
+  set_smem_attr<false, true, false, true, true>();
+  set_smem_attr<false, false, false, true, true>();
+  set_smem_attr<true, true, false, false, true>();
+  set_smem_attr<true, false, false, false, true>();
+  set_smem_attr<false, true, false, false, true>();
+  set_smem_attr<false, false, false, false, true>();
   return SIM_OK;
 }
 
+// persistent launch over one work list: one CTA per SM (PAIR: one cluster of two per SM pair)
+template <bool F16, bool SPLIT, bool FAST, bool PAIR>
+void launch_persistent(const Launch &L, size_t sm, cudaStream_t s) {
+  if constexpr (PAIR) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(2u * static_cast<unsigned>(std::min(L.n_units, num_sms() / 2)));
+    cfg.blockDim = dim3(NTHREADS_ALL);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, false, FAST, true>, L);
+  } else {
+    umma_sum_kernel<F16, SPLIT, false, FAST, false><<<std::min(L.n_units, num_sms()), NTHREADS_ALL, sm, s>>>(L);
+  }
+}
+
+template <bool PAIR>
+void launch_persistent_dispatch(const UmmaBatch &b, const Launch &L, cudaStream_t s) {
+  const size_t sm = smem_bytes(b.split, b.bn_max, PAIR);
+  if (b.f16) {
+    if (b.split) b.fast ? launch_persistent<true, true, true, PAIR>(L, sm, s) : launch_persistent<true, true, false, PAIR>(L, sm, s);
+    else b.fast ? launch_persistent<true, false, true, PAIR>(L, sm, s) : launch_persistent<true, false, false, PAIR>(L, sm, s);
+  } else {
+    if (b.split) b.fast ? launch_persistent<false, true, true, PAIR>(L, sm, s) : launch_persistent<false, true, false, PAIR>(L, sm, s);
+    else b.fast ? launch_persistent<false, false, true, PAIR>(L, sm, s) : launch_persistent<false, false, false, PAIR>(L, sm, s);
+  }
+}
+
 int launch_umma_batch(const UmmaBatch &b, cudaStream_t s) {
+  cudaMemsetAsync(b.counter, 0, 8, s);
+  int kernels = 0;
   Launch L{};
   L.scenes = static_cast<const Args *>(b.args);
-  L.units = static_cast<const Unit *>(b.units);
-  L.n_units = b.n_units;
-  L.counter = b.counter;
   L.bn_layout = b.bn_max;
-  const size_t sm = smem_bytes(b.split, b.bn_max);
-  const int grid = std::min(b.n_units, num_sms());
-  cudaMemsetAsync(b.counter, 0, 4, s);
-#define RS_BATCH_LAUNCH(F, SP, FA) umma_sum_kernel<F, SP, false, FA><<<grid, NTHREADS_ALL, sm, s>>>(L)
-  if (b.f16) {
-    if (b.split) b.fast ? RS_BATCH_LAUNCH(true, true, true) : RS_BATCH_LAUNCH(true, true, false);
-    else b.fast ? RS_BATCH_LAUNCH(true, false, true) : RS_BATCH_LAUNCH(true, false, false);
-  } else {
-    if (b.split) b.fast ? RS_BATCH_LAUNCH(false, true, true) : RS_BATCH_LAUNCH(false, true, false);
-    else b.fast ? RS_BATCH_LAUNCH(false, false, true) : RS_BATCH_LAUNCH(false, false, false);
+  if (b.n_units > 0) {
+    L.units = static_cast<const Unit *>(b.units);
+    L.n_units = b.n_units;
+    L.counter = b.counter;
+    launch_persistent_dispatch<true>(b, L, s);
+    ++kernels;
   }
-#undef RS_BATCH_LAUNCH
-  return 1;
+  if (b.n_units1 > 0) {
+    L.units = static_cast<const Unit *>(b.units1);
+    L.n_units = b.n_units1;
+    L.counter = b.counter + 1;
+    launch_persistent_dispatch<false>(b, L, s);
+    ++kernels;
+  }
+  return kernels;
 }
 
 // amax (FP16 scaling) and split reduction of one scene of a batch, around the batched GEMM
@@ -1187,8 +1370,8 @@ extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int6
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(status, 0, 4, s);
   args.status = status;
-  if (f16) launch_gemm<true, false, true, true>(sh, args, s);
-  else launch_gemm<false, false, true, true>(sh, args, s);
+  if (f16) launch_gemm<true, false, true, true, false>(sh, args, s);
+  else launch_gemm<false, false, true, true, false>(sh, args, s);
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);

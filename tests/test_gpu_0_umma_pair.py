@@ -1,0 +1,23 @@
+"""The two-SM tensor-core tile (tcgen05.mma.cta_group::2 across a CTA pair, operands split
+over both CTAs' shared memory, barriers across the pair) on plain matrices, against an FP64
+matmul of the same 16-bit operands."""
+import pytest
+import torch
+
+from paper_2305_14176_gb300 import radarsim as rs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("f16,n,k", [(0, 256, 64), (0, 32, 64), (1, 128, 64), (0, 256, 4096), (1, 64, 1002)])
+def test_pair_tile_matches_fp64_matmul(f16, n, k):
+    g = torch.Generator().manual_seed(n * 3 + k)
+    dt = torch.float16 if f16 else torch.bfloat16
+    A = torch.randn(256, k, generator=g).to(dt)
+    B = torch.randn(n, k, generator=g).to(dt)
+    ref = A.double() @ B.double().T
+    D = torch.full((256, n), float("nan"), dtype=torch.float32, device="cuda")
+    rc = rs.sim_selftest_umma_pair(f16, n, k, A.cuda(), B.cuda(), D, torch.cuda.current_stream().cuda_stream)
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    err = (D.cpu().double() - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
