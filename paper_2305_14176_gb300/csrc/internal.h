@@ -106,7 +106,7 @@ struct UmmaBatch {
   int n_units;
   void *units1;       // one-SM work list (128-row tiles), longest first (device)
   int n_units1;
-  int n_scenes, bn_max;
+  int n_scenes, bn_max, bn_max1;  // widest tile (real columns) of each list
   bool f16, split, fast;
 };
 // device bytes of the batch's descriptors and counter

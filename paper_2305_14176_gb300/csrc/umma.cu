@@ -537,7 +537,7 @@ struct Launch {
 
 template <bool SPLIT, bool TEST, bool PAIR>
 __host__ __device__ constexpr int num_stages() {
-  return TEST ? 4 : (PAIR ? (SPLIT ? 4 : 8) : (SPLIT ? 3 : 6));
+  return TEST ? 4 : (PAIR ? (SPLIT ? 4 : 6) : (SPLIT ? 3 : 6));
 }
 
 // bytes of one pipeline stage (PAIR: B for half the tile's columns)
@@ -563,6 +563,10 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   constexpr uint32_t TMEM_COLS = 512;  // accumulator (0..255) and running sum (256..511)
   const uint32_t stage_bytes = stage_size<SPLIT, TEST, PAIR>(L.bn_layout);
   const uint32_t rank = PAIR ? cluster_rank() : 0u;
+  // How producers signal a finished stage: single pass, whose stages are short, gains from one
+  // arrival per group after the group barrier; split precision (MMA-bound) from every thread
+  // arriving as soon as its own stores are done (same-box timing of both schemes).
+  constexpr bool ONE_ARRIVE = !SPLIT && !TEST;
   uint8_t *base = smem;
   uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
   // barriers: full[NST], empty[NST], acc_full, acc_empty, mma_done
@@ -577,7 +581,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   const uint32_t acce_c = PAIR ? cluster_addr(acce, 0) : acce;
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
-      mbar_init(full0 + 8 * s, PAIR ? 2 * GSIZE : GSIZE);
+      mbar_init(full0 + 8 * s, (ONE_ARRIVE ? 1 : GSIZE) * (PAIR ? 2 : 1));
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(accf, 1);
@@ -677,10 +681,20 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
           produce_planar<F16, SPLIT, FAST, PAIR>(g, s_rays[grp], st_base, gt, row0, col0, scale,
                                                  static_cast<int>(rank));
         }
-        fence_proxy_async();
-        if constexpr (PAIR) mbar_arrive_cluster(full0_c + 8 * s);
-        else mbar_arrive(full0 + 8 * s);
-        if constexpr (!TEST) group_sync(grp);  // s_rays[grp] is rewritten next round
+        fence_proxy_async();  // this thread's stores, visible to the tensor core
+        if constexpr (ONE_ARRIVE) {
+          // the whole group's stores are done (and s_rays[grp] is free for the next round):
+          // one thread signals the stage
+          group_sync(grp);
+          if (gt == 0) {
+            if constexpr (PAIR) mbar_arrive_cluster(full0_c + 8 * s);
+            else mbar_arrive(full0 + 8 * s);
+          }
+        } else {
+          if constexpr (PAIR) mbar_arrive_cluster(full0_c + 8 * s);
+          else mbar_arrive(full0 + 8 * s);
+          if constexpr (!TEST) group_sync(grp);  // s_rays[grp] is rewritten next round
+        }
       }
     } else if (warp == MMA_WARP) {
       // ---------------- MMA issuer (PAIR: CTA 0 issues for both; CTA 1 only waits for the end)
@@ -902,7 +916,11 @@ Shape plan_shape(const Derived &g, int64_t n) {
 Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
   Shape s;
   const int M = g.nv * g.nc;
-  s.bn = 2 * g.ns < 256 ? 2 * g.ns : 256;
+  // single pass keeps no running sum in tensor memory, so its tiles can take 256 complex columns
+  // (Re and Im blocks fill all 512 TMEM columns); split precision tiles take 128
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  const int bn_cap = split ? 256 : 512;
+  s.bn = 2 * g.ns < bn_cap ? 2 * g.ns : bn_cap;
   s.mt = (M + BM - 1) / BM;
   s.nt = 2 * g.ns / s.bn;
   const int sms = num_sms();
@@ -949,7 +967,7 @@ void set_smem_attr() {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, 256, PAIR)));
+                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, SPLIT || !PAIR ? 256 : 512, PAIR)));
     attr = true;
   }
 }
@@ -1124,7 +1142,7 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
   std::vector<Unit> units, units1;
   std::vector<int64_t> cost, cost1;
   bool f16 = false, split = false;
-  int bn_max = 32;
+  int bn_max = 32, bn_max1 = 32;  // widest tile of the two-SM and of the one-SM work list
   for (int i = 0; i < n_scenes; ++i) {
     const Derived &g = *gs[i];
     const Shape sh = plan_shape(g, ns[i]);
@@ -1150,8 +1168,9 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
     a.partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspaces[i]) + 256);
     a.amax_bits = static_cast<const uint32_t *>(workspaces[i]);
     a.status = statuses[i];
-    if (sh.bn > bn_max) bn_max = sh.bn;
     const bool pair = use_pair(sh);
+    int &bmax = pair ? bn_max : bn_max1;
+    if (sh.bn > bmax) bmax = sh.bn;
     const int mt = pair ? (sh.mt + 1) / 2 : sh.mt;
     for (int sp = 0; sp < sh.splits; ++sp) {
       const int64_t rays = std::min<int64_t>(sh.chunk, ns[i] - sp * sh.chunk);
@@ -1184,6 +1203,7 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
   out->f16 = f16;
   out->split = split;
   out->bn_max = bn_max;
+  out->bn_max1 = bn_max1;
   if (cudaMemcpyAsync(out->args, args.data(), sizeof(Args) * args.size(), cudaMemcpyHostToDevice, s) != cudaSuccess ||
       cudaMemcpyAsync(out->units, sorted.data(), sizeof(Unit) * sorted.size(), cudaMemcpyHostToDevice, s) !=
           cudaSuccess ||
@@ -1235,7 +1255,7 @@ void launch_persistent(const Launch &L, size_t sm, cudaStream_t s) {
 
 template <bool PAIR>
 void launch_persistent_dispatch(const UmmaBatch &b, const Launch &L, cudaStream_t s) {
-  const size_t sm = smem_bytes(b.split, b.bn_max, PAIR);
+  const size_t sm = smem_bytes(b.split, L.bn_layout, PAIR);
   if (b.f16) {
     if (b.split) b.fast ? launch_persistent<true, true, true, PAIR>(L, sm, s) : launch_persistent<true, true, false, PAIR>(L, sm, s);
     else b.fast ? launch_persistent<true, false, true, PAIR>(L, sm, s) : launch_persistent<true, false, false, PAIR>(L, sm, s);
@@ -1250,8 +1270,8 @@ int launch_umma_batch(const UmmaBatch &b, cudaStream_t s) {
   int kernels = 0;
   Launch L{};
   L.scenes = static_cast<const Args *>(b.args);
-  L.bn_layout = b.bn_max;
   if (b.n_units > 0) {
+    L.bn_layout = b.bn_max;
     L.units = static_cast<const Unit *>(b.units);
     L.n_units = b.n_units;
     L.counter = b.counter;
@@ -1259,6 +1279,7 @@ int launch_umma_batch(const UmmaBatch &b, cudaStream_t s) {
     ++kernels;
   }
   if (b.n_units1 > 0) {
+    L.bn_layout = b.bn_max1;
     L.units = static_cast<const Unit *>(b.units1);
     L.n_units = b.n_units1;
     L.counter = b.counter + 1;
