@@ -37,9 +37,9 @@ import numpy as np  # noqa: E402
 
 import scenegen  # noqa: E402
 
-# DRAM bytes (read + write) of one ray-sum launch on this workload, from the ncu capture
-# summarised in profiles/umma_sum_kernel_automotive_fp16split.md; None where not captured.
-TRAFFIC_BYTES = {"fp16_split": 197.39e6}
+# DRAM bytes (read + write) of one ray-sum launch on this workload, from the ncu captures
+# summarised in profiles/umma_sum_kernel_automotive_{fp16split,bf16}.md; None where not captured.
+TRAFFIC_BYTES = {"fp16_split": 197.39e6, "bf16": 195.43e6}
 
 METRIC = "ray-sample contributions/s"
 UNIT = "contributions/s"
