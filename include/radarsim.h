@@ -263,7 +263,9 @@ SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int
 /* Per-stage device time in milliseconds of the most recently fetched ticket of
    this context, from CUDA events on the stream the scene ran on: [0] ingest
    copies, [1] per-ray prep, [2] ray-sum main kernel, [3] ray-sum split reduction,
-   [4] FFTs, [5] labels, [6] whole device pipeline; n is the array length (<= 8).
+   [4] FFTs, [5] labels (they run on a second stream beside the ray sum once the prep is done;
+   this is the time they add after the FFTs), [6] whole device pipeline; n is the array
+   length (<= 8).
    Entries for stages that did not run are 0.  sim_snapshot_run also records its
    stages here: [1] holds the prep and the path / phase-word kernels, [2] the direct
    sums, [6] prep to labels (its input copies happen before, synchronously). */

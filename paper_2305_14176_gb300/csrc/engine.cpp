@@ -38,6 +38,10 @@ struct Job;
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev[kNumEvents] = {};
+  // the labels need only the prep: they run on a second stream beside the ray sum and FFTs,
+  // between lab[0] and lab[1], and the slot's stream waits for lab[1] before its last event
+  cudaStream_t side = nullptr;
+  cudaEvent_t lab[2] = {};
   bool busy = false;
   Job *job = nullptr;  // the scene running on this slot
 };
@@ -216,6 +220,16 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
   int kernels = 0;
   kernels += launch_prep(g, in, j->n, rp, status, s);
   cudaEventRecord(sl.ev[2], s);
+  const bool labels = (g.outputs & SIM_OUT_LABELS) != 0;
+  if (labels) {
+    cudaStreamWaitEvent(sl.side, sl.ev[2], 0);
+    cudaEventRecord(sl.lab[0], sl.side);
+    LabelScratch sc{reinterpret_cast<uint64_t *>(b + p.pk), reinterpret_cast<uint64_t *>(b + p.pe),
+                    reinterpret_cast<uint32_t *>(b + p.ck), reinterpret_cast<uint64_t *>(b + p.cm),
+                    reinterpret_cast<uint32_t *>(b + p.co), p.cap};
+    kernels += launch_labels(g, rp, in.obj, j->n, sc, reinterpret_cast<int32_t *>(b + p.labels), status, sl.side);
+    cudaEventRecord(sl.lab[1], sl.side);
+  }
   if (g.precision == SIM_PREC_FP32_DIRECT) {
     kernels += launch_direct_sum(g, rp, j->n, sig, s);
     cudaEventRecord(sl.ev[3], s);
@@ -227,12 +241,7 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
     kernels += launch_fft(g, j->ctx->t, sig, reinterpret_cast<float2 *>(b + p.tmp),
                           reinterpret_cast<float2 *>(b + p.spec), s);
   cudaEventRecord(sl.ev[5], s);
-  if (g.outputs & SIM_OUT_LABELS) {
-    LabelScratch sc{reinterpret_cast<uint64_t *>(b + p.pk), reinterpret_cast<uint64_t *>(b + p.pe),
-                    reinterpret_cast<uint32_t *>(b + p.ck), reinterpret_cast<uint64_t *>(b + p.cm),
-                    reinterpret_cast<uint32_t *>(b + p.co), p.cap};
-    kernels += launch_labels(g, rp, in.obj, j->n, sc, reinterpret_cast<int32_t *>(b + p.labels), status, s);
-  }
+  if (labels) cudaStreamWaitEvent(s, sl.lab[1], 0);  // join: the scene ends when its labels do
   cudaEventRecord(sl.ev[6], s);
   j->kernels = kernels;
   if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
@@ -356,6 +365,9 @@ int start_engine_locked(Engine &e) {
   for (auto &s : e.slots) {
     if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess) return SIM_E_CUDA;
     for (auto &ev : s.ev)
+      if (cudaEventCreate(&ev) != cudaSuccess) return SIM_E_CUDA;
+    if (cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking) != cudaSuccess) return SIM_E_CUDA;
+    for (auto &ev : s.lab)
       if (cudaEventCreate(&ev) != cudaSuccess) return SIM_E_CUDA;
   }
   e.egress.resize(4);

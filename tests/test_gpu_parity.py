@@ -46,7 +46,10 @@ def test_tiny_scene_full_cube(tiny, precision, device_inputs):
 @pytest.mark.parametrize("shape,n", [((16, 2, 1, 3, 4), 1), ((32, 4, 1, 3, 4), 255),
                                      ((64, 8, 2, 3, 8), 257), ((128, 128, 3, 4, 16), 700),
                                      ((256, 32, 1, 1, 1), 33), ((2048, 2, 1, 1, 1), 301),
-                                     ((4096, 4, 1, 2, 2), 97)])
+                                     ((4096, 4, 1, 2, 2), 97),
+                                     # three 128-row tiles in one channel each: the second
+                                     # two-SM tile's odd CTA lies wholly past the last row
+                                     ((64, 128, 1, 3, 4), 400)])
 def test_ragged_shapes(precision, shape, n):
     ns, nc, ntx, nrx, na = shape
     radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na)
