@@ -191,7 +191,19 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
   uint8_t *b = j->block;
   const size_t un = static_cast<size_t>(j->n);
   cudaEventRecord(sl.ev[0], s);
-  if (j->n > 0) {
+  const bool dev_src = j->n > 0 && is_device_ptr(src.range_rt_m) && is_device_ptr(src.amplitude) &&
+                       is_device_ptr(src.radial_velocity_mps) && is_device_ptr(src.azimuth_rad) &&
+                       is_device_ptr(src.elevation_rad) && is_device_ptr(src.phase0_rad) &&
+                       (!j->has_obj || is_device_ptr(src_obj));
+  int ingest_kernels = 0;
+  if (dev_src) {
+    IngestArgs x{src.range_rt_m, src.amplitude, src.radial_velocity_mps, src.azimuth_rad, src.elevation_rad,
+                 src.phase0_rad, j->has_obj ? src_obj : nullptr, reinterpret_cast<double *>(b + p.d),
+                 reinterpret_cast<float *>(b + p.a), reinterpret_cast<float *>(b + p.v),
+                 reinterpret_cast<float *>(b + p.az), reinterpret_cast<float *>(b + p.el),
+                 reinterpret_cast<float *>(b + p.p0), reinterpret_cast<int32_t *>(b + p.obj)};
+    ingest_kernels = launch_ingest(x, j->n, s);
+  } else if (j->n > 0) {
     cudaMemcpyAsync(b + p.d, src.range_rt_m, 8 * un, cudaMemcpyDefault, s);
     cudaMemcpyAsync(b + p.a, src.amplitude, 4 * un, cudaMemcpyDefault, s);
     cudaMemcpyAsync(b + p.v, src.radial_velocity_mps, 4 * un, cudaMemcpyDefault, s);
@@ -217,7 +229,7 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
               g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + p.eps_t) : nullptr};
   uint32_t *status = reinterpret_cast<uint32_t *>(b + p.status);
   float2 *sig = reinterpret_cast<float2 *>(b + p.sig);
-  int kernels = 0;
+  int kernels = ingest_kernels;
   kernels += launch_prep(g, in, j->n, rp, status, s);
   cudaEventRecord(sl.ev[2], s);
   const bool labels = (g.outputs & SIM_OUT_LABELS) != 0;

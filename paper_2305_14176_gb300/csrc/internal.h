@@ -80,6 +80,16 @@ struct Tables {
 
 // ---- launchers (each returns the number of kernels it launched) ----
 int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s);
+// copy device-resident input arrays (obj may be null) into a scene's block in one launch
+struct IngestArgs {
+  const double *d;
+  const float *a, *v, *az, *el, *p0;
+  const int32_t *obj;
+  double *dst_d;
+  float *dst_a, *dst_v, *dst_az, *dst_el, *dst_p0;
+  int32_t *dst_obj;
+};
+int launch_ingest(const IngestArgs &x, int64_t n, cudaStream_t s);
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s);
 // store a synchronous call's stage times (7 entries, the sim_last_stage_ms order) and kernel count
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels);

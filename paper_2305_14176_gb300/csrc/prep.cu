@@ -159,6 +159,27 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
 
 }  // namespace
 
+// device-resident caller arrays into the scene's block: one launch for all seven arrays
+__global__ void __launch_bounds__(256) ingest_kernel(IngestArgs x, int64_t n) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    x.dst_d[i] = x.d[i];
+    x.dst_a[i] = x.a[i];
+    x.dst_v[i] = x.v[i];
+    x.dst_az[i] = x.az[i];
+    x.dst_el[i] = x.el[i];
+    x.dst_p0[i] = x.p0[i];
+    if (x.obj) x.dst_obj[i] = x.obj[i];
+  }
+}
+
+int launch_ingest(const IngestArgs &x, int64_t n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int64_t blocks = (n + 255) / 256;
+  ingest_kernel<<<static_cast<unsigned>(blocks < 1216 ? blocks : 1216), 256, 0, s>>>(x, n);
+  return 1;
+}
+
 int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *status, cudaStream_t s) {
   if (n <= 0) return 0;
   PrepConst k;
