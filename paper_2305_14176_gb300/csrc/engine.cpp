@@ -422,7 +422,9 @@ int derive(const sim_radar_params *p, Derived *g) {
   if (p->outputs <= 0 || p->outputs > 7) return SIM_E_INVALID;
   if (p->max_rays < 1 || p->max_rays > (int64_t{1} << 21)) return SIM_E_INVALID;
   if (p->model != SIM_MODEL_SEPARABLE && p->model != SIM_MODEL_EXACT) return SIM_E_INVALID;
-  if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT) return SIM_E_INVALID;
+  // the exact model on tensor cores has no TDM slot term in its per-chirp sample operand
+  if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT && p->tdm_slot_s != 0.0)
+    return SIM_E_INVALID;
   if (p->pattern_exp < 0 || p->pattern_exp > 16) return SIM_E_INVALID;
   if (!(isfinite(p->tdm_slot_s) && p->tdm_slot_s >= 0.0 && p->tdm_slot_s <= 1.0)) return SIM_E_INVALID;
   const int64_t n_cell = static_cast<int64_t>(na) * p->n_chirps * p->n_samples;

@@ -101,6 +101,11 @@ int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp
 int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
                   int32_t *labels, uint32_t *status, cudaStream_t s);
 
+// exact Eq. 2 on tensor cores (samples x channels tiles per chirp), used by launch_umma_sum
+// for SIM_MODEL_EXACT contexts
+int64_t exact_workspace_bytes(const Derived &g, int64_t n);
+int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                     cudaStream_t s, cudaEvent_t after_main);
 // tensor-core ray sum: workspace bytes it needs and its launcher
 int64_t umma_workspace_bytes(const Derived &g, int64_t n);
 // `after_main` (may be null) is recorded on `s` right after the GEMM kernel, before the

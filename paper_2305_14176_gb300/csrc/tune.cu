@@ -106,6 +106,8 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   if (!ctx || n_rays < 1 || n_rays > ctx->g.max_rays) return SIM_E_INVALID;
   const Derived &g = ctx->g;
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
+  // the table holds separable-model choices; the exact model's tiles are planned on their own
+  if (tensor && g.model == SIM_MODEL_EXACT) return SIM_E_INVALID;
   int cand[16];
   const int nc = tensor ? umma_split_candidates(g, n_rays, cand, 16) : 0;
   int max_splits = 1;

@@ -784,12 +784,14 @@ void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, cons
 }  // namespace
 
 int64_t umma_workspace_bytes(const Derived &g, int64_t n) {
+  if (g.model == SIM_MODEL_EXACT) return exact_workspace_bytes(g, n);
   const Shape sh = plan_shape(g, n);
   return 256 + static_cast<int64_t>(sh.splits) * g.nv * g.nc * 2 * g.ns * 4;
 }
 
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                     cudaStream_t s, cudaEvent_t after_main) {
+  if (g.model == SIM_MODEL_EXACT) return launch_exact_sum(g, p, n, sig, workspace, status, s, after_main);
   const Shape sh = plan_shape(g, n);
   uint32_t *amax = static_cast<uint32_t *>(workspace);
   float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
@@ -909,7 +911,7 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
     } else if (fi != f16 || si != split || g.precision == SIM_PREC_FP32_DIRECT) {
       return SIM_E_INVALID;
     }
-    if (g.precision == SIM_PREC_FP32_DIRECT) return SIM_E_INVALID;
+    if (g.precision == SIM_PREC_FP32_DIRECT || g.model == SIM_MODEL_EXACT) return SIM_E_INVALID;
     Args &a = args[static_cast<size_t>(i)];
     a = Args{};
     a.p = ps[i];
@@ -1069,6 +1071,10 @@ int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, 
 
 int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, int64_t ws_bytes,
                        uint32_t *status, cudaStream_t s) {
+  if (g.model == SIM_MODEL_EXACT) {
+    if (exact_workspace_bytes(g, n) > ws_bytes) return -1;
+    return launch_exact_sum(g, p, n, sig, workspace, status, s, nullptr);
+  }
   Shape sh = plan_shape(g, n);
   const int64_t per_split = static_cast<int64_t>(g.nv) * g.nc * 2 * g.ns * 4;
   const int64_t fit = (ws_bytes - 256) / per_split;

@@ -44,7 +44,7 @@ def _params(**kw):
     dict(n_tx=64, n_rx=32), dict(n_angle=2), dict(n_angle=24), dict(window=(0, 9, 0)),
     dict(precision=7), dict(outputs=0), dict(outputs=8), dict(max_rays=0), dict(max_rays=(1 << 21) + 1),
     dict(element_spacing_m=-0.001), dict(n_samples=4096, n_chirps=4096, n_angle=1024),
-    dict(model=2), dict(model=1, precision=2), dict(pattern_exp=17), dict(pattern_exp=-1),
+    dict(model=2), dict(model=1, precision=2, tdm_slot_s=1e-5), dict(pattern_exp=17), dict(pattern_exp=-1),
     dict(tdm_slot_s=-1e-6), dict(tdm_slot_s=float("nan")), dict(tdm_slot_s=2.0),
 ])
 def test_create_rejects_bad_params_without_a_gpu(bad):

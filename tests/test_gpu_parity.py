@@ -290,3 +290,48 @@ def test_tdm_exact_model():
     assert rc == rs.SIM_OK
     assert rel_max(sig, ref) <= 1e-5 and rel_rms(sig, ref) <= 1e-5
     assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16,
+                                       rs.SIM_PREC_FP16])
+def test_exact_model_tensor_core(precision):
+    """The exact model on tensor cores: per chirp, samples x channels tiles."""
+    radar, rays = scenegen.tiny_scene(seed=16, n_rays=900)
+    radar = radar.replace(model=1)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+    # channels past a 16-column tile, samples below one 128-sample tile, and a ragged ray count
+    small = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=8, n_tx=3, n_rx=7, n_angle=32, model=1)
+    rays2 = scenegen.uniform_rays(seed=61, n=333, v_max=30.0)
+    ref2 = oracle.signal(small, rays2)
+    ctx = rs.Context(small, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig2, _, _ = run(small, rays2, precision, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK
+    assert rel_max(sig2, ref2) <= tol and rel_rms(sig2, ref2) <= trms
+
+
+def test_exact_model_tensor_core_automotive_sampled():
+    radar, rays = scenegen.automotive_scene(seed=45, n_rays=50_000)
+    radar = radar.replace(model=1)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, _, lab = run(radar, rays, rs.SIM_PREC_FP16_SPLIT, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK
+    idx = scenegen.randint(45, 3, 1024, 0, sig.size - 1).astype(np.int64)
+    ref = oracle.signal_at(radar, rays, idx)
+    assert rel_max(sig.reshape(-1)[idx], ref) <= 1e-5 and rel_rms(sig.reshape(-1)[idx], ref) <= 1e-5
+    assert np.array_equal(lab, oracle.labels(radar, rays))
