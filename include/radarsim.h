@@ -87,7 +87,9 @@ extern "C" {
 /* signal model */
 #define SIM_MODEL_SEPARABLE 0     /* Eq. 2 without the range-migration product (a GEMM) */
 #define SIM_MODEL_EXACT 1         /* Eq. 2 with mu t (tau_i(j) - tau_i(0)): phase + n m eps_i,
-                                     eps_i = B 2 v_i T_d / (c N_s); FP32_DIRECT precision only */
+                                     eps_i = B 2 v_i T_d / (c N_s); any precision (the tensor-core
+                                     precisions compute it per chirp, samples x channels, and
+                                     need tdm_slot_s = 0) */
 
 /* outputs bitmask */
 #define SIM_OUT_SIGNAL 1
