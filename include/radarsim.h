@@ -329,6 +329,13 @@ SIM_API int sim_tuning_count(void);
 SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int64_t k, const void *a, const void *b,
                               float *d, void *stream);
 
+/* Self-test of the bounded waits (not a simulation call): one GPU thread waits on an
+   mbarrier that nothing arrives on, with the wait every pipeline kernel uses and a limit of
+   limit_ms (1 .. 1000) instead of their 4 s.  Expected result: SIM_E_DEVICE (the wait ran out
+   and the kernel reported it in its status word) with *waited_ms about limit_ms; the context
+   stays usable.  stream is a cudaStream_t (NULL = default); the call synchronizes it. */
+SIM_API int sim_selftest_wait(int32_t limit_ms, int32_t *waited_ms, void *stream);
+
 /* Self-test of the two-SM tensor-core tile (not a simulation call): one CTA pair computes
    D[256][N] = A[256][K] * B[N][K]^T with tcgen05.mma.cta_group::2, each CTA holding 128 rows
    of A and N/2 rows of B in its shared memory.  A, B row-major 16-bit device matrices (f16 1:

@@ -39,14 +39,17 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: false if the barrier phase has not completed after kWaitLimitNs
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// bounded wait: false if the barrier phase has not completed after limit_ns
+__device__ __forceinline__ bool mbar_wait_for(uint32_t a, uint32_t parity, uint64_t limit_ns) {
   if (mbar_try(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
     if (mbar_try(a, parity)) return true;
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  return mbar_wait_for(a, parity, kWaitLimitNs);
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

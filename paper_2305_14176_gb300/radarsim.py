@@ -102,6 +102,7 @@ def _load() -> ctypes.CDLL:
     lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
     lib.sim_selftest_umma.argtypes = [I32, I32, I32, I64, P, P, P, P]
     lib.sim_selftest_umma_pair.argtypes = [I32, I32, I64, P, P, P, P]
+    lib.sim_selftest_wait.argtypes = [I32, ctypes.POINTER(ctypes.c_int32), P]
     lib.sim_raysum_noalloc.argtypes = [ctypes.POINTER(sim_radar_params), ctypes.POINTER(sim_rays), P, P]
     lib.sim_run_batch.argtypes = [I32, P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), P, P, P,
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]
@@ -187,6 +188,13 @@ def sim_selftest_umma_pair(f16: int, n: int, k: int, a, b, d, stream=None) -> in
     """D[256][N] = A B^T through the two-SM tensor-core tile (see include/radarsim.h)."""
     return lib.sim_selftest_umma_pair(int(f16), int(n), int(k), _addr(a), _addr(b), _addr(d),
                                       _addr(stream) if stream is not None else None)
+
+
+def sim_selftest_wait(limit_ms: int, stream=None):
+    """(status, waited_ms) of a bounded wait that nothing ends (see include/radarsim.h)."""
+    w = ctypes.c_int32(0)
+    rc = lib.sim_selftest_wait(int(limit_ms), ctypes.byref(w), _addr(stream) if stream is not None else None)
+    return int(rc), int(w.value)
 
 
 def sim_raysum_noalloc(params: sim_radar_params, rays: sim_rays, signal, stream=None) -> int:

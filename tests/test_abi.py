@@ -61,3 +61,5 @@ def test_null_arguments():
     assert rs.lib.sim_destroy(None) == rs.SIM_E_INVALID
     assert rs.sim_engine_configure(-5, 4, 8) == rs.SIM_E_INVALID
     assert rs.sim_engine_configure(0, 0, 8) == rs.SIM_E_INVALID
+    assert rs.lib.sim_selftest_wait(0, None, None) == rs.SIM_E_INVALID
+    assert rs.lib.sim_selftest_wait(2000, None, None) == rs.SIM_E_INVALID

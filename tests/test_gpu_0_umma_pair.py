@@ -21,3 +21,18 @@ def test_pair_tile_matches_fp64_matmul(f16, n, k):
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     err = (D.cpu().double() - ref).abs().max().item() / ref.abs().max().item()
     assert err < 1e-5, err
+
+
+def test_bounded_wait_runs_out_and_reports():
+    """A pipeline wait that nothing ends expires after its limit, the kernel reports it in its
+    status word (SIM_E_DEVICE) and the context stays usable."""
+    rc, waited = rs.sim_selftest_wait(50)
+    assert rc == rs.SIM_E_DEVICE
+    assert 45 <= waited <= 1000
+    # the next call on the same context works
+    A = torch.randn(256, 64).to(torch.bfloat16)
+    B = torch.randn(32, 64).to(torch.bfloat16)
+    D = torch.zeros((256, 32), dtype=torch.float32, device="cuda")
+    assert rs.sim_selftest_umma_pair(0, 32, 64, A.cuda(), B.cuda(), D) == rs.SIM_OK
+    ref = A.double() @ B.double().T
+    assert (D.cpu().double() - ref).abs().max().item() <= 1e-5 * ref.abs().max().item()
