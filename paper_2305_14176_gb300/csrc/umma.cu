@@ -608,25 +608,31 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
 // Sum the split partials in split order and interleave each tile's (Re block, Im block):
 //   sig[row][n] = sum_s (P_s[row][t bn + nl], P_s[row][t bn + bn/2 + nl]) / scale,
 //   t = n / (bn/2), nl = n % (bn/2).
+// A thread takes four consecutive samples (16-byte loads; bn / 2 and N_s are multiples of 16).
 template <bool F16>
 __global__ void reduce_partials(const float *__restrict__ part, int splits, int64_t m_rows, int ns, int bn,
                                 float2 *__restrict__ sig, const uint32_t *amax_bits) {
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
-  const int64_t n_c = m_rows * ns;
+  const int64_t n_q = m_rows * ns / 4;
   const int64_t plane = m_rows * 2 * ns;
-  const int half = bn / 2;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_c;
+  const int half = bn / 2, ns4 = ns / 4;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_q;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t row = i / ns;
-    const int n = static_cast<int>(i - row * ns);
+    const int64_t row = i / ns4;
+    const int n = static_cast<int>(i - row * ns4) * 4;
     const int t = n / half, nl = n - t * half;
     const float *p = part + row * 2 * ns + t * bn + nl;
-    float re = p[0], im = p[half];
+    float4 re = *reinterpret_cast<const float4 *>(p), im = *reinterpret_cast<const float4 *>(p + half);
+#pragma unroll 6
     for (int s = 1; s < splits; ++s) {
-      re += p[s * plane];
-      im += p[s * plane + half];
+      const float4 a = *reinterpret_cast<const float4 *>(p + s * plane);
+      const float4 b = *reinterpret_cast<const float4 *>(p + s * plane + half);
+      re.x += a.x; re.y += a.y; re.z += a.z; re.w += a.w;
+      im.x += b.x; im.y += b.y; im.z += b.z; im.w += b.w;
     }
-    sig[i] = make_float2(re * inv, im * inv);
+    float4 *o = reinterpret_cast<float4 *>(sig + row * ns + n);
+    o[0] = make_float4(re.x * inv, im.x * inv, re.y * inv, im.y * inv);
+    o[1] = make_float4(re.z * inv, im.z * inv, re.w * inv, im.w * inv);
   }
 }
 
