@@ -106,6 +106,17 @@ int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, L
 int64_t exact_workspace_bytes(const Derived &g, int64_t n);
 int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                      cudaStream_t s, cudaEvent_t after_main);
+// its two halves; `gate` (device word, may be null) holding 4 or 8 makes both return at once
+int launch_exact_main(const Derived &g, RaysPrep p, int64_t n, void *workspace, uint32_t *status, cudaStream_t s,
+                      const uint32_t *gate);
+int launch_exact_reduce(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s,
+                        const uint32_t *gate);
+// exact Eq. 2 on tensor cores through the per-tile expansion of the range-migration phase
+// (umma_taylor.cu), falling back on the device to the per-chirp kernel when the expansion's
+// bound is not met; the workspace covers both
+int64_t exact_tensor_workspace_bytes(const Derived &g, int64_t n);
+int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                        cudaStream_t s, cudaEvent_t after_main);
 // tensor-core ray sum: workspace bytes it needs and its launcher
 int64_t umma_workspace_bytes(const Derived &g, int64_t n);
 // `after_main` (may be null) is recorded on `s` right after the GEMM kernel, before the

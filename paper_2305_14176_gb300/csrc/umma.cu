@@ -790,14 +790,14 @@ void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, cons
 }  // namespace
 
 int64_t umma_workspace_bytes(const Derived &g, int64_t n) {
-  if (g.model == SIM_MODEL_EXACT) return exact_workspace_bytes(g, n);
+  if (g.model == SIM_MODEL_EXACT) return exact_tensor_workspace_bytes(g, n);
   const Shape sh = plan_shape(g, n);
   return 256 + static_cast<int64_t>(sh.splits) * g.nv * g.nc * 2 * g.ns * 4;
 }
 
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                     cudaStream_t s, cudaEvent_t after_main) {
-  if (g.model == SIM_MODEL_EXACT) return launch_exact_sum(g, p, n, sig, workspace, status, s, after_main);
+  if (g.model == SIM_MODEL_EXACT) return launch_exact_tensor(g, p, n, sig, workspace, status, s, after_main);
   const Shape sh = plan_shape(g, n);
   uint32_t *amax = static_cast<uint32_t *>(workspace);
   float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);

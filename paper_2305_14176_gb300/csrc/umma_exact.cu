@@ -49,7 +49,15 @@ struct XArgs {
   float *partials;          // [split][N_v][N_c][N_s] complex64
   const uint32_t *amax_bits;
   uint32_t *status;
+  const uint32_t *gate;     // may be null; when it holds 4 or 8 the expanded kernel owns the scene
 };
+
+// the expanded tensor-core kernel (umma_taylor.cu) has taken the scene
+__device__ __forceinline__ bool gated_off(const uint32_t *gate) {
+  if (!gate) return false;
+  const uint32_t v = *gate;
+  return v == 4u || v == 8u;
+}
 
 struct XStage {               // per-ray words of one stage
   uint64_t car[XK], nur[XK], nua[XK], nutx[XK];
@@ -161,6 +169,7 @@ __global__ void __launch_bounds__(XTHREADS, 1) exact_sum_kernel(XArgs g) {
   __shared__ XStage s_rays[XGROUPS];
   __shared__ uint64_t bars[2 * XMAX_ST + 3];
   __shared__ uint32_t tmem_holder;
+  if (gated_off(g.gate)) return;  // uniform over the grid, before any barrier or allocation
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nst = g.nst;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + XMAX_ST);
@@ -350,7 +359,8 @@ __global__ void __launch_bounds__(XTHREADS, 1) exact_sum_kernel(XArgs g) {
 // sig[i] = sum_s P_s[i] / scale, splits in order
 template <bool F16>
 __global__ void exact_reduce(const float2 *__restrict__ part, int splits, int64_t n_sig, float2 *__restrict__ sig,
-                             const uint32_t *amax_bits) {
+                             const uint32_t *amax_bits, const uint32_t *gate) {
+  if (gated_off(gate)) return;
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_sig;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -427,19 +437,11 @@ int64_t exact_workspace_bytes(const Derived &g, int64_t n) {
   return 256 + static_cast<int64_t>(s.splits) * g.n_sig * 8;
 }
 
-int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
-                     cudaStream_t s, cudaEvent_t after_main) {
+int launch_exact_main(const Derived &g, RaysPrep p, int64_t n, void *workspace, uint32_t *status, cudaStream_t s,
+                      const uint32_t *gate) {
   const XShape sh = plan_exact(g, n);
   const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
   const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
-  uint32_t *amax = static_cast<uint32_t *>(workspace);
-  float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
-  int kernels = 0;
-  cudaMemsetAsync(amax, 0, 4, s);
-  if (f16 && n > 0) {
-    exact_amax<<<2 * sms_count(), 256, 0, s>>>(p.amp, n, amax);
-    ++kernels;
-  }
   XArgs a{};
   a.p = p;
   a.n_rays = n;
@@ -453,9 +455,10 @@ int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void 
   a.ktiles = sh.ktiles;
   a.nst = sh.nst;
   a.stage_bytes = sh.stage_bytes;
-  a.partials = partials;
-  a.amax_bits = amax;
+  a.partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
+  a.amax_bits = static_cast<uint32_t *>(workspace);
   a.status = status;
+  a.gate = gate;
   const size_t smem = static_cast<size_t>(sh.nst) * sh.stage_bytes;
   const unsigned grid = static_cast<unsigned>(static_cast<int64_t>(g.nc) * sh.mtiles * sh.ktiles * sh.splits);
 #define RS_EXACT(F, SP)                                                                                      \
@@ -471,12 +474,34 @@ int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void 
     else RS_EXACT(false, false);
   }
 #undef RS_EXACT
-  ++kernels;
-  if (after_main) cudaEventRecord(after_main, s);
+  return 1;
+}
+
+int launch_exact_reduce(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s,
+                        const uint32_t *gate) {
+  const XShape sh = plan_exact(g, n);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const uint32_t *amax = static_cast<uint32_t *>(workspace);
+  const float2 *partials = reinterpret_cast<const float2 *>(static_cast<uint8_t *>(workspace) + 256);
   const int rb = 4 * sms_count();
-  if (f16) exact_reduce<true><<<rb, 256, 0, s>>>(reinterpret_cast<const float2 *>(partials), sh.splits, g.n_sig, sig, amax);
-  else exact_reduce<false><<<rb, 256, 0, s>>>(reinterpret_cast<const float2 *>(partials), sh.splits, g.n_sig, sig, amax);
-  ++kernels;
+  if (f16) exact_reduce<true><<<rb, 256, 0, s>>>(partials, sh.splits, g.n_sig, sig, amax, gate);
+  else exact_reduce<false><<<rb, 256, 0, s>>>(partials, sh.splits, g.n_sig, sig, amax, gate);
+  return 1;
+}
+
+int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                     cudaStream_t s, cudaEvent_t after_main) {
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  uint32_t *amax = static_cast<uint32_t *>(workspace);
+  int kernels = 0;
+  cudaMemsetAsync(amax, 0, 4, s);
+  if (f16 && n > 0) {
+    exact_amax<<<2 * sms_count(), 256, 0, s>>>(p.amp, n, amax);
+    ++kernels;
+  }
+  kernels += launch_exact_main(g, p, n, workspace, status, s, nullptr);
+  if (after_main) cudaEventRecord(after_main, s);
+  kernels += launch_exact_reduce(g, n, sig, workspace, s, nullptr);
   return kernels;
 }
 

@@ -1,0 +1,638 @@
+// K_b1x: the exact signal model on tensor cores by a per-tile expansion of the range-migration
+// phase (arXiv 2305.14176, Sec. II-A, Eq. 2 with mu t (tau_i(j) - tau_i(0)) kept).
+//
+// The exact phase of ray i at channel k = (t, r), chirp m and sample n is
+//   phi_i + t nu_tx,i + r nu_a,i + m nu_d,i + n nu_r,i + n m eps_i.
+// Inside one output tile write m = m_c + m' and n = n_c + n' about the tile's centre:
+//   n m eps = n_c m' eps + n m_c eps + n' m' eps.
+// The first two terms are exact per-tile shifts of the chirp and sample frequencies; only
+// e^{2 pi j n' m' eps} still couples rows and columns, and over a tile |m'| <= m_h, |n'| <= n_h
+// are small, so it is replaced by its Taylor polynomial of P terms,
+//   e^{j x} = sum_{p<P} (j x)^p / p! + R,   |R| <= |x|^P / P!,   x = 2 pi eps m' n'.
+// Each term is separable, (j 2 pi eps m' n_h)^p / p! on the row side times (n' / n_h)^p on the
+// column side, so the tile is one complex product over K = P x rays:
+//   S[row, n] = sum_{i, p} A_p[row, i] B_p[i, n]
+//   A_p[row, i] = a_i e^{2 pi j (phi + t nu_tx + r nu_a + m nu_d + n_c m' eps)} (j x_row,i)^p / p!
+//   B_p[i, n]   = e^{2 pi j n (nu_r + m_c eps)} (n' / n_h)^p,      x_row,i = 2 pi eps_i m' n_h
+// Rows are chirp-major (row = m N_v + k), so a 256-row tile spans only about 256 / N_v chirps,
+// and each synthesised value serves a whole 256 x NC tile instead of N_v channels.
+//
+// P is 4 or 8, the smaller one whose bound (2 pi max|eps| m_h n_h)^P / P! is at most 1e-6 for
+// the hi + lo precisions (1e-5 single pass, whose operand rounding is ~3e-4); a device kernel
+// takes it from the scene's largest |eps|, so no host round trip is needed.  When even P = 8
+// would not meet the bound (velocities far beyond road traffic), P = 0 is written and the
+// per-chirp kernel of umma_exact.cu, launched behind this one, computes the scene instead: each
+// of the two kernels (and its reduction) returns at once when the other one owns the scene.
+//
+// Pipeline, tensor-core issue and drain are those of the separable kernel's two-SM form: CTA
+// pairs (cta_group::2, M = 256), planar K (Re S += A_re B_re - A_im B_im, Im S += A_re B_im +
+// A_im B_re, split precision adds the hi / lo cross terms), FP32 running sum in tensor memory
+// every 512 K slots at split precision, FP32 partials per ray chunk added by a second kernel.
+// A stage holds 32 K slots: 32 / P rays times P terms, slot = p (32 / P) + q.  Every mbarrier
+// wait is bounded; a wait that runs out sets a status bit and the CTA drains and returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "tcgen05.cuh"
+
+namespace rs {
+namespace {
+
+constexpr int TBM = 128;               // rows per CTA (TMEM lanes); a CTA pair covers 256
+constexpr int TKS = 32;                // K slots per stage
+constexpr int TNPROD = 384;            // producer threads: three groups of 128
+constexpr int TGROUPS = 3;
+constexpr int TGSIZE = TNPROD / TGROUPS;
+constexpr int TMMA_WARP = TNPROD / 32;
+constexpr int TNDRAIN = 128;
+constexpr int TTHREADS = TNPROD + 32 + TNDRAIN;
+constexpr int TSUBST_SPLIT = 16;       // stages per accumulation chain at split precision
+constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
+constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
+constexpr int kMaxDynSmemT = 232448 - 8192;
+// workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64)
+constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kHeader = 256;
+
+struct TArgs {
+  RaysPrep p;
+  int64_t n_rays, chunk;  // rays, rays per split (multiple of 8)
+  int nc, ns, nv, nrx, m_rows;
+  int bn;                 // real columns per tile, 2 NC
+  int mt2, nt;            // 256-row tiles, column tiles
+  float *partials;        // [split][M chirp-major rows][2 N_s], each tile as (Re block | Im block)
+  const uint32_t *amax_bits;
+  const uint32_t *terms;  // P chosen on the device; 0: the per-chirp kernel owns the scene
+  uint32_t *status;
+};
+
+// per-ray words of one stage (at most 8 rays)
+struct TStage {
+  uint64_t car[TMAX_RAYS], nua[TMAX_RAYS], nud[TMAX_RAYS], nutx[TMAX_RAYS], nur[TMAX_RAYS], eps[TMAX_RAYS];
+  float amp[TMAX_RAYS];
+};
+
+struct TWords {
+  uint64_t car, nua, nud, nutx, nur, eps;
+  float amp;
+};
+
+// thread gt < rays of the stage fetches its ray's words (rays past the chunk read as 0)
+__device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays, int64_t k_hi, int gt) {
+  TWords w{0, 0, 0, 0, 0, 0, 0.f};
+  const int64_t ray = ray0 + gt;
+  if (gt < rays && ray < k_hi) {
+    w.car = g.p.carrier[ray];
+    w.nua = g.p.nu_a[ray];
+    w.nud = g.p.nu_d[ray];
+    w.nutx = g.p.nu_tx[ray];
+    w.nur = g.p.nu_r[ray];
+    w.eps = g.p.eps[ray];
+    w.amp = g.p.amp[ray];
+  }
+  return w;
+}
+
+__device__ __forceinline__ void tstore(TStage &s, int gt, const TWords &w) {
+  if (gt < TMAX_RAYS) {
+    s.car[gt] = w.car;
+    s.nua[gt] = w.nua;
+    s.nud[gt] = w.nud;
+    s.nutx[gt] = w.nutx;
+    s.nur[gt] = w.nur;
+    s.eps[gt] = w.eps;
+    s.amp[gt] = w.amp;
+  }
+}
+
+__device__ __forceinline__ void tgroup_sync(int g) {
+  asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(TGSIZE) : "memory");
+}
+
+// What one producer thread needs of its A row and B columns for a whole unit.
+struct RowCtx {
+  uint64_t tx, rx, m, ncm;  // channel (t, r), chirp, n_c m' (two's complement)
+  float xm;                 // 2 pi m' n_h 2^-64: x_row,i = xm * (signed eps_i word)
+  bool valid;
+};
+struct ColCtx {
+  uint64_t n, nmc;          // sample index, n m_c
+  float up[8];              // (n' / n_h)^p
+  int c;                    // column in this CTA's B block
+  uint32_t octets;          // bit o: this thread writes K chunk o of the column
+  bool active;
+};
+
+// One stage of operands: A row gt (all 32 slots) and this thread's B column octets, in the
+// no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
+template <bool F16, bool SPLIT, int P>
+__device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
+                                               const ColCtx &cc, float scale) {
+  constexpr int RS = TKS / P;   // rays per stage
+  constexpr int TPO = P / 4;    // terms per octet
+  const uint32_t a_half = TBM * TKS * 2;
+  const uint32_t x_half = static_cast<uint32_t>(ncb) * TKS * 2;
+  const uint32_t lo = SPLIT ? 2 * a_half + 2 * x_half : 0;
+  uint8_t *a_re = stage, *a_im = stage + a_half, *x_re = stage + 2 * a_half, *x_im = x_re + x_half;
+  {
+    float2 t[RS];
+    float x[RS];
+#pragma unroll
+    for (int q = 0; q < RS; ++q) {
+      float sn, cs;
+      __sincosf(q64_to_rad(sr.car[q] + rc.tx * sr.nutx[q] + rc.rx * sr.nua[q] + rc.m * sr.nud[q] + rc.ncm * sr.eps[q]),
+                &sn, &cs);
+      const float am = rc.valid ? sr.amp[q] * scale : 0.f;
+      t[q] = make_float2(am * cs, am * sn);
+      x[q] = rc.xm * static_cast<float>(static_cast<int64_t>(sr.eps[q]));
+    }
+    uint32_t off = (gt >> 3) * 128 + (gt & 7) * 16;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      float2 z[OCT];
+#pragma unroll
+      for (int tt = 0; tt < TPO; ++tt) {
+        const int p = o * TPO + tt;
+#pragma unroll
+        for (int q = 0; q < RS; ++q) z[tt * RS + q] = t[q];
+        if (p + 1 < P) {
+          const float inv = 1.f / static_cast<float>(p + 1);  // compile-time after unrolling
+#pragma unroll
+          for (int q = 0; q < RS; ++q) {
+            const float f = x[q] * inv;  // t <- t (j x) / (p + 1)
+            t[q] = make_float2(-t[q].y * f, t[q].x * f);
+          }
+        }
+      }
+      put_octet<F16, SPLIT>(z, a_re + off, a_im + off, a_re + lo + off, a_im + lo + off);
+      off += TBM * 16;
+    }
+  }
+  if (cc.active) {
+    float2 b[RS];
+#pragma unroll
+    for (int q = 0; q < RS; ++q) {
+      float sn, cs;
+      __sincosf(q64_to_rad(cc.n * sr.nur[q] + cc.nmc * sr.eps[q]), &sn, &cs);
+      b[q] = make_float2(cs, sn);
+    }
+    const uint32_t off0 = (cc.c >> 3) * 128 + (cc.c & 7) * 16;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+      if (!((cc.octets >> o) & 1)) continue;
+      float2 z[OCT];
+#pragma unroll
+      for (int tt = 0; tt < TPO; ++tt) {
+        const float u = cc.up[o * TPO + tt];
+#pragma unroll
+        for (int q = 0; q < RS; ++q) z[tt * RS + q] = make_float2(b[q].x * u, b[q].y * u);
+      }
+      const uint32_t off = o * static_cast<uint32_t>(ncb) * 16 + off0;
+      put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
+    }
+  }
+}
+
+template <bool SPLIT>
+__host__ __device__ constexpr int t_stages() {
+  return SPLIT ? 4 : 6;
+}
+// bytes of one stage: A (Re, Im) 128 x 32 slots and this CTA's B (Re, Im) bn/4 x 32, x2 for lo
+template <bool SPLIT>
+__host__ __device__ constexpr uint32_t t_stage_bytes(int bn) {
+  return static_cast<uint32_t>(TBM * TKS * 2 * 2 + (bn / 4) * TKS * 2 * 2) * (SPLIT ? 2u : 1u);
+}
+
+// Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
+// CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
+template <bool F16, bool SPLIT>
+__global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ TStage s_rays[TGROUPS];
+  const uint32_t P = *g.terms;
+  if (P != 4u && P != 8u) return;  // the per-chirp kernel owns this scene (both CTAs return)
+  constexpr int NST = t_stages<SPLIT>();
+  constexpr uint32_t TMEM_COLS = 512;
+  constexpr bool ONE_ARRIVE = !SPLIT;
+  const uint32_t stage_bytes = t_stage_bytes<SPLIT>(g.bn);
+  const uint32_t rank = cluster_rank();
+  uint8_t *base = smem;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(base + NST * stage_bytes);
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 2 * NST + 3);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NST);
+  const uint32_t accf = smem_u32(bars + 2 * NST), acce = smem_u32(bars + 2 * NST + 1);
+  const uint32_t done = smem_u32(bars + 2 * NST + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0_c = cluster_addr(full0, 0);
+  const uint32_t acce_c = cluster_addr(acce, 0);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(full0 + 8 * s, (ONE_ARRIVE ? 1 : TGSIZE) * 2);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(acce, 2 * TNDRAIN);
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == TMMA_WARP) tmem_alloc<true>(smem_u32(tmem_holder), TMEM_COLS);
+  tc_fence_before();
+  cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  const int u = static_cast<int>(blockIdx.x >> 1);
+  const int per = g.mt2 * g.nt;
+  const int split = u / per;
+  const int tile_n = (u - split * per) / g.mt2;
+  const int tile_m = u - split * per - tile_n * g.mt2;
+  const int bn = g.bn, NC = bn >> 1, ncb = bn >> 2;
+  const int r0 = tile_m * 2 * TBM;                    // first row of the pair's tile
+  const int row0 = r0 + static_cast<int>(rank) * TBM;  // this CTA's rows
+  const int col0 = tile_n * bn;                        // real column; complex n0 = col0 / 2
+  const int n0 = tile_n * NC;
+  const int m_c = (r0 + TBM) / g.nv;                   // tile centre: chirp and sample
+  const int n_c = n0 + NC / 2, n_h = NC / 2;
+  const int RS = TKS / static_cast<int>(P);
+  const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
+  const int64_t k_hi = k_lo + g.chunk < g.n_rays ? k_lo + g.chunk : g.n_rays;
+  const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + RS - 1) / RS) : 0;
+  const int SUBST = SPLIT ? TSUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
+  const int n_sub = (n_stages + SUBST - 1) / SUBST;
+  bool failed = false;
+
+  if (warp < TMMA_WARP) {
+    // ---------------- producers: group grp builds stages grp, grp + 3, ...
+    const int grp = warp / (TGSIZE / 32), gt = threadIdx.x % TGSIZE;
+    const float scale = amp_scale<F16>(g.amax_bits);
+    RowCtx rc;
+    {
+      const int r = row0 + gt;
+      rc.valid = r < g.m_rows;
+      const int m = r / g.nv, k = r - m * g.nv;
+      const int t = k / g.nrx;
+      rc.tx = static_cast<uint64_t>(t);
+      rc.rx = static_cast<uint64_t>(k - t * g.nrx);
+      rc.m = static_cast<uint64_t>(m);
+      const int mp = m - m_c;
+      rc.ncm = static_cast<uint64_t>(static_cast<int64_t>(n_c) * mp);
+      rc.xm = static_cast<float>(mp) * static_cast<float>(n_h) * 3.40612158008655459e-19f;  // 2 pi 2^-64
+    }
+    ColCtx cc;
+    {
+      // ncb <= 128 columns: tpc threads share a column, thread h of them takes octets h, h + tpc, ...
+      const int tpc = TGSIZE / ncb, h = gt / ncb;
+      cc.c = gt % ncb;
+      cc.octets = 0;
+      for (int o = h; o < 4; o += tpc) cc.octets |= 1u << o;
+      cc.active = cc.octets != 0;
+      const int n = n0 + static_cast<int>(rank) * ncb + cc.c;
+      cc.n = static_cast<uint64_t>(n);
+      cc.nmc = static_cast<uint64_t>(n) * static_cast<uint64_t>(m_c);
+      const float uu = static_cast<float>(n - n_c) / static_cast<float>(n_h);  // n_h is a power of two
+      float v = 1.f;
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        cc.up[p] = v;
+        v *= uu;
+      }
+    }
+    TWords nxt{0, 0, 0, 0, 0, 0, 0.f};
+    if (grp < n_stages) nxt = tfetch(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt);
+    for (int st = grp; st < n_stages; st += TGROUPS) {
+      const int s = st % NST;
+      const int64_t ray0 = k_lo + static_cast<int64_t>(st) * RS;
+      tstore(s_rays[grp], gt, nxt);
+      if (st + TGROUPS < n_stages) nxt = tfetch(g, ray0 + TGROUPS * RS, RS, k_hi, gt);
+      tgroup_sync(grp);
+      if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
+        failed = true;
+        break;
+      }
+      uint8_t *st_base = base + s * stage_bytes;
+      if (P == 4u) produce_taylor<F16, SPLIT, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale);
+      else produce_taylor<F16, SPLIT, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale);
+      fence_proxy_async();  // this thread's stores, visible to the tensor core
+      if constexpr (ONE_ARRIVE) {
+        tgroup_sync(grp);  // the group's stores are done and s_rays[grp] is free again
+        if (gt == 0) mbar_arrive_cluster(full0_c + 8 * s);
+      } else {
+        mbar_arrive_cluster(full0_c + 8 * s);
+        tgroup_sync(grp);  // s_rays[grp] is rewritten next round
+      }
+    }
+  } else if (warp == TMMA_WARP) {
+    // ---------------- MMA issuer (CTA 0 issues for both; CTA 1 only waits for the end)
+    if (lane == 0 && rank != 0) {
+      if (!mbar_wait(done, 0)) failed = true;
+    } else if (lane == 0) {
+      const uint32_t sbase = smem_u32(base);
+      bool open = false;
+      const uint32_t idesc = make_idesc(F16, 2 * TBM, NC);
+      const uint32_t ineg = idesc | (1u << 14);  // negate B: Re S -= A_im B_im
+      const uint32_t lbo_a = TBM * 16, lbo_x = static_cast<uint32_t>(ncb) * 16;
+      const uint32_t a_half = TBM * TKS * 2, x_half = static_cast<uint32_t>(ncb) * TKS * 2;
+      const uint32_t lo = 2 * a_half + 2 * x_half;
+      const uint32_t t_re = tmem, t_im = tmem + static_cast<uint32_t>(NC);
+      for (int st = 0; st < n_stages; ++st) {
+        const int s = st % NST;
+        const int gc = st / SUBST;
+        const bool first = (st % SUBST) == 0;
+        if (first && gc > 0 && !mbar_wait(acce, (gc - 1) & 1)) {
+          failed = true;
+          break;
+        }
+        if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t sb = sbase + s * stage_bytes;
+        const uint32_t ar = sb, ai = sb + a_half, xr = sb + 2 * a_half, xi = xr + x_half;
+#pragma unroll
+        for (int kh = 0; kh < TKS / 16; ++kh) {
+          const uint32_t acc = (!first || kh > 0) ? 1u : 0u;
+          const uint32_t oa = kh * 2 * lbo_a, ox = kh * 2 * lbo_x;
+          const uint64_t dar = make_sdesc(ar + oa, lbo_a, 128), dai = make_sdesc(ai + oa, lbo_a, 128);
+          const uint64_t dxr = make_sdesc(xr + ox, lbo_x, 128), dxi = make_sdesc(xi + ox, lbo_x, 128);
+          mma_f16<true>(t_re, dar, dxr, idesc, acc);
+          mma_f16<true>(t_re, dai, dxi, ineg, 1u);
+          mma_f16<true>(t_im, dar, dxi, idesc, acc);
+          mma_f16<true>(t_im, dai, dxr, idesc, 1u);
+          if constexpr (SPLIT) {
+            const uint64_t lar = make_sdesc(ar + lo + oa, lbo_a, 128), lai = make_sdesc(ai + lo + oa, lbo_a, 128);
+            const uint64_t lxr = make_sdesc(xr + lo + ox, lbo_x, 128), lxi = make_sdesc(xi + lo + ox, lbo_x, 128);
+            mma_f16<true>(t_re, dar, lxr, idesc, 1u);
+            mma_f16<true>(t_re, lar, dxr, idesc, 1u);
+            mma_f16<true>(t_re, dai, lxi, ineg, 1u);
+            mma_f16<true>(t_re, lai, dxi, ineg, 1u);
+            mma_f16<true>(t_im, dar, lxi, idesc, 1u);
+            mma_f16<true>(t_im, lar, dxi, idesc, 1u);
+            mma_f16<true>(t_im, dai, lxr, idesc, 1u);
+            mma_f16<true>(t_im, lai, dxr, idesc, 1u);
+          }
+        }
+        open = true;
+        mma_commit<true>(empty0 + 8 * s);
+        if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
+          mma_commit<true>(accf);
+          open = false;
+        }
+      }
+      if (open) mma_commit<true>(accf);
+      mma_commit<true>(done);  // fires in both CTAs once every issued MMA has completed
+      if (!mbar_wait(done, 0)) failed = true;
+    }
+  } else {
+    // ---------------- drain: TMEM lane quarter warp % 4; each finished chain is added in FP32
+    // to the running sum in tensor memory, the last one goes to this split's partial.
+    const int q = warp & 3;
+    const int grow = row0 + q * 32 + lane;
+    float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    if (n_stages == 0 && grow < g.m_rows) {
+      for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int sub = 0; sub < n_sub; ++sub) {
+      if (!mbar_wait_sleep(accf, sub & 1)) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      const bool last = sub == n_sub - 1;
+      for (int c = 0; c < bn; c += 16) {
+        uint32_t h[16];
+        tmem_ld16(trow + static_cast<uint32_t>(c), h);
+        if (sub > 0) {
+          uint32_t r[16];
+          tmem_ld16(trow + TSUM_COL + static_cast<uint32_t>(c), r);
+#pragma unroll
+          for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+        }
+        if (!last) {
+          tmem_st16(trow + TSUM_COL + static_cast<uint32_t>(c), h);
+        } else if (grow < g.m_rows) {
+#pragma unroll
+          for (int x = 0; x < 16; x += 4)
+            *reinterpret_cast<float4 *>(dst + c + x) = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]),
+                                                                   __uint_as_float(h[x + 2]), __uint_as_float(h[x + 3]));
+        }
+      }
+      if (!last) tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive_cluster(acce_c);
+    }
+  }
+  if (failed) atomicOr(g.status, kStatusWaitLimit);
+  tc_fence_before();
+  // neither CTA leaves while the other may still arrive on its barriers or the issuer's MMAs may
+  // still read its shared memory
+  cluster_sync();
+  if (warp == TMMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc<true>(tmem, TMEM_COLS);
+  }
+}
+
+// Partials of the chirp-major rows -> the signal in channel-major order:
+//   sig[k][m][n] = sum_s (P_s[m N_v + k][t bn + nl], P_s[m N_v + k][t bn + bn/2 + nl]) / scale,
+// t = n / (bn/2), nl = n % (bn/2); four samples per thread, splits added in order.
+template <bool F16>
+__global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv, int nc, int ns, int bn,
+                              float2 *__restrict__ sig, const uint32_t *amax_bits, const uint32_t *terms) {
+  const uint32_t P = *terms;
+  if (P != 4u && P != 8u) return;
+  const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
+  const int64_t m_rows = static_cast<int64_t>(nv) * nc;
+  const int64_t n_q = m_rows * ns / 4;
+  const int64_t plane = m_rows * 2 * ns;
+  const int half = bn / 2, ns4 = ns / 4;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_q;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = i / ns4;  // k N_c + m
+    const int n = static_cast<int>(i - row * ns4) * 4;
+    const int k = static_cast<int>(row / nc), m = static_cast<int>(row - static_cast<int64_t>(k) * nc);
+    const int64_t prow = static_cast<int64_t>(m) * nv + k;
+    const int t = n / half, nl = n - t * half;
+    const float *p = part + prow * 2 * ns + t * bn + nl;
+    float4 re = *reinterpret_cast<const float4 *>(p), im = *reinterpret_cast<const float4 *>(p + half);
+#pragma unroll 6
+    for (int s = 1; s < splits; ++s) {
+      const float4 a = *reinterpret_cast<const float4 *>(p + s * plane);
+      const float4 b = *reinterpret_cast<const float4 *>(p + s * plane + half);
+      re.x += a.x; re.y += a.y; re.z += a.z; re.w += a.w;
+      im.x += b.x; im.y += b.y; im.z += b.z; im.w += b.w;
+    }
+    float4 *o = reinterpret_cast<float4 *>(sig + row * ns + n);
+    o[0] = make_float4(re.x * inv, im.x * inv, re.y * inv, im.y * inv);
+    o[1] = make_float4(re.z * inv, im.z * inv, re.w * inv, im.w * inv);
+  }
+}
+
+// amplitude maximum (FP16 scaling) and largest |eps| of the scene
+__global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__restrict__ eps, int64_t n, bool want_amax,
+                            uint32_t *amax_bits, unsigned long long *eps_max) {
+  uint32_t ma = 0;
+  unsigned long long me = 0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    if (want_amax) ma = max(ma, __float_as_uint(amp[i]));  // amplitudes are >= 0
+    const uint64_t e = eps[i];
+    const unsigned long long mag = static_cast<int64_t>(e) < 0 ? ~e + 1ull : e;  // |signed word|
+    me = max(me, mag);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (want_amax) atomicMax(amax_bits, ma);
+    atomicMax(eps_max, me);
+  }
+}
+
+// P from the truncation bound theta^P / P! <= tol, theta = 2 pi max|eps| m_h n_h
+__global__ void choose_terms(const unsigned long long *eps_max, uint32_t *terms, double xscale, double tol) {
+  const double th = static_cast<double>(*eps_max) * xscale;
+  const double t2 = th * th, t4 = t2 * t2;
+  uint32_t P = 0;
+  if (t4 / 24.0 <= tol) P = 4;
+  else if (t4 * t4 / 40320.0 <= tol) P = 8;
+  *terms = P;
+}
+
+int sms_t() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  }
+  return sms;
+}
+
+struct TShape {
+  int bn, mt2, nt, splits, mh;
+  int64_t chunk;
+};
+
+// Pair tiles of 256 chirp-major rows x bn real columns (512 single pass, 256 split); rays split
+// into chunks so that the CTA pairs fill whole waves (at least four) as evenly as possible.
+TShape plan_taylor(const Derived &g, int64_t n) {
+  TShape s{};
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  const int cap = split ? 256 : 512;
+  s.bn = 2 * g.ns < cap ? 2 * g.ns : cap;
+  const int M = g.nv * g.nc;
+  s.mt2 = (M + 2 * TBM - 1) / (2 * TBM);
+  s.nt = 2 * g.ns / s.bn;
+  s.mh = TBM / g.nv + 1;  // |m - m_c| over a 256-row tile
+  const int64_t wave = sms_t() / 2;  // CTA pairs per wave
+  const int64_t tiles = static_cast<int64_t>(s.mt2) * s.nt;
+  const int64_t lo = std::max<int64_t>(1, (4 * wave + tiles - 1) / tiles);
+  int64_t best = lo, best_waste = -1, best_slots = 1;
+  for (int64_t sp = lo; sp <= 3 * lo; ++sp) {
+    const int64_t ctas = tiles * sp, slots = (ctas + wave - 1) / wave * wave, waste = slots - ctas;
+    if (best_waste < 0 || waste * best_slots < best_waste * slots) {
+      best = sp;
+      best_waste = waste;
+      best_slots = slots;
+    }
+  }
+  const int64_t max_splits = std::max<int64_t>(1, (n + TMAX_RAYS - 1) / TMAX_RAYS);
+  int64_t splits = std::max<int64_t>(1, std::min<int64_t>(best, max_splits));
+  int64_t chunk = (n + splits - 1) / splits;
+  chunk = std::max<int64_t>(TMAX_RAYS, (chunk + TMAX_RAYS - 1) / TMAX_RAYS * TMAX_RAYS);
+  s.chunk = chunk;
+  s.splits = static_cast<int>(std::max<int64_t>(1, (n + chunk - 1) / chunk));
+  return s;
+}
+
+// the expansion needs two-SM tiles of at least 32 complex columns
+bool taylor_eligible(const Derived &g) { return g.ns >= 32; }
+
+template <bool F16, bool SPLIT>
+void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
+  const size_t smem =
+      t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(sh.bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmemT);
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(2u * static_cast<unsigned>(sh.mt2 * sh.nt * sh.splits));
+  cfg.blockDim = dim3(TTHREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT>, a);
+}
+
+}  // namespace
+
+int64_t exact_tensor_workspace_bytes(const Derived &g, int64_t n) {
+  const int64_t chirp = exact_workspace_bytes(g, n);
+  if (!taylor_eligible(g)) return chirp;
+  const TShape t = plan_taylor(g, n);
+  const int64_t tb = static_cast<int64_t>(kHeader) + static_cast<int64_t>(t.splits) * g.nv * g.nc * 2 * g.ns * 4;
+  return std::max(chirp, tb);
+}
+
+int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
+                        cudaStream_t s, cudaEvent_t after_main) {
+  if (!taylor_eligible(g) || n <= 0) return launch_exact_sum(g, p, n, sig, workspace, status, s, after_main);
+  const TShape sh = plan_taylor(g, n);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  uint32_t *amax = reinterpret_cast<uint32_t *>(ws);
+  uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
+  unsigned long long *eps_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
+  int kernels = 0;
+  cudaMemsetAsync(ws, 0, 16, s);
+  exact_stats<<<2 * sms_t(), 256, 0, s>>>(p.amp, p.eps, n, f16, amax, eps_max);
+  // theta = 2 pi max|eps| m_h n_h with eps in cycles (the word times 2^-64)
+  const double xscale = 6.283185307179586 * sh.mh * (sh.bn / 4) * 5.421010862427522e-20;
+  choose_terms<<<1, 1, 0, s>>>(eps_max, terms, xscale, split ? 1e-6 : 1e-5);
+  kernels += 2;
+  TArgs a{};
+  a.p = p;
+  a.n_rays = n;
+  a.chunk = sh.chunk;
+  a.nc = g.nc;
+  a.ns = g.ns;
+  a.nv = g.nv;
+  a.nrx = g.nrx;
+  a.m_rows = g.nv * g.nc;
+  a.bn = sh.bn;
+  a.mt2 = sh.mt2;
+  a.nt = sh.nt;
+  a.partials = reinterpret_cast<float *>(ws + kHeader);
+  a.amax_bits = amax;
+  a.terms = terms;
+  a.status = status;
+  if (f16) split ? launch_taylor<true, true>(sh, a, s) : launch_taylor<true, false>(sh, a, s);
+  else split ? launch_taylor<false, true>(sh, a, s) : launch_taylor<false, false>(sh, a, s);
+  ++kernels;
+  // the per-chirp kernel, which returns at once unless P = 0
+  kernels += launch_exact_main(g, p, n, workspace, status, s, terms);
+  if (after_main) cudaEventRecord(after_main, s);
+  const int rb = 4 * sms_t();
+  if (f16)
+    taylor_reduce<true><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms);
+  else
+    taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms);
+  ++kernels;
+  kernels += launch_exact_reduce(g, n, sig, workspace, s, terms);
+  return kernels;
+}
+
+}  // namespace rs

@@ -322,6 +322,34 @@ def test_exact_model_tensor_core(precision):
     assert rel_max(sig2, ref2) <= tol and rel_rms(sig2, ref2) <= trms
 
 
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16,
+                                       rs.SIM_PREC_FP16])
+@pytest.mark.parametrize("case", ["narrow_tile", "beyond_expansion", "short_chirp"])
+def test_exact_model_tensor_core_regimes(precision, case):
+    """The exact model's per-tile expansion of the range-migration phase in its edge regimes:
+    the narrowest two-SM tile (32 samples, 16 columns of B per CTA, 43 chirps per tile: eight
+    terms); a velocity whose migration phase no eight-term expansion bounds (the device hands
+    the scene to the per-chirp kernel); and 16 samples (per-chirp kernel chosen on the host)."""
+    ns, nc, ntx, nrx, na, v_max = {"narrow_tile": (32, 16, 1, 3, 4, 15.0),
+                                   "beyond_expansion": (64, 32, 1, 4, 16, 2000.0),
+                                   "short_chirp": (16, 32, 2, 2, 4, 15.0)}[case]
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na, model=1)
+    rays = scenegen.uniform_rays(seed=ns * nc + ntx, n=517, n_objects=4, v_max=v_max)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+    # the migration term matters here: the separable model misses the cube by far more
+    assert rel_max(oracle.signal(radar.replace(model=0), rays), ref) > 10 * tol
+
+
 def test_exact_model_tensor_core_automotive_sampled():
     radar, rays = scenegen.automotive_scene(seed=45, n_rays=50_000)
     radar = radar.replace(model=1)
