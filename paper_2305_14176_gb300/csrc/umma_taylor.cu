@@ -24,6 +24,12 @@
 // per-chirp kernel of umma_exact.cu, launched behind this one, computes the scene instead: each
 // of the two kernels (and its reduction) returns at once when the other one owns the scene.
 //
+// At the hi + lo precisions the terms of order p >= P / 2 (the second 16-slot K step of every
+// stage) are at most theta^(P/2) / (P/2)! of the ray's amplitude, so single-pass operand
+// rounding (<= 2u relative, u = 2^-11 FP16, 2^-8 BF16) adds at most that times 2u; when the
+// device finds this below 2e-6 those terms skip their lo operands and the hi x lo MMAs (8 MMA
+// units per stage instead of 12 at P = 4).
+//
 // Pipeline, tensor-core issue and drain are those of the separable kernel's two-SM form: CTA
 // pairs (cta_group::2, M = 256), planar K (Re S += A_re B_re - A_im B_im, Im S += A_re B_im +
 // A_im B_re, split precision adds the hi / lo cross terms), FP32 running sum in tensor memory
@@ -52,8 +58,9 @@ constexpr int TSUBST_SPLIT = 16;       // stages per accumulation chain at split
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
 constexpr int kMaxDynSmemT = 232448 - 8192;
-// workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64)
-constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kHeader = 256;
+// workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64), whether the
+// high-order K step keeps its lo operands (u32)
+constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kHeader = 256;
 
 struct TArgs {
   RaysPrep p;
@@ -64,6 +71,7 @@ struct TArgs {
   float *partials;        // [split][M chirp-major rows][2 N_s], each tile as (Re block | Im block)
   const uint32_t *amax_bits;
   const uint32_t *terms;  // P chosen on the device; 0: the per-chirp kernel owns the scene
+  const uint32_t *lo_high;  // split precision: 0 when the terms p >= P/2 go single pass
   uint32_t *status;
 };
 
@@ -128,7 +136,7 @@ struct ColCtx {
 // no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
 template <bool F16, bool SPLIT, int P>
 __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
-                                               const ColCtx &cc, float scale) {
+                                               const ColCtx &cc, float scale, bool lo_high) {
   constexpr int RS = TKS / P;   // rays per stage
   constexpr int TPO = P / 4;    // terms per octet
   const uint32_t a_half = TBM * TKS * 2;
@@ -165,7 +173,8 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
           }
         }
       }
-      put_octet<F16, SPLIT>(z, a_re + off, a_im + off, a_re + lo + off, a_im + lo + off);
+      if (o < 2 || lo_high) put_octet<F16, SPLIT>(z, a_re + off, a_im + off, a_re + lo + off, a_im + lo + off);
+      else put_octet<F16, false>(z, a_re + off, a_im + off, a_re + off, a_im + off);
       off += TBM * 16;
     }
   }
@@ -189,7 +198,8 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
         for (int q = 0; q < RS; ++q) z[tt * RS + q] = make_float2(b[q].x * u, b[q].y * u);
       }
       const uint32_t off = o * static_cast<uint32_t>(ncb) * 16 + off0;
-      put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
+      if (o < 2 || lo_high) put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
+      else put_octet<F16, false>(z, x_re + off, x_im + off, x_re + off, x_im + off);
     }
   }
 }
@@ -212,6 +222,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
   __shared__ TStage s_rays[TGROUPS];
   const uint32_t P = *g.terms;
   if (P != 4u && P != 8u) return;  // the per-chirp kernel owns this scene (both CTAs return)
+  const bool lo_high = !SPLIT || *g.lo_high != 0u;
   constexpr int NST = t_stages<SPLIT>();
   constexpr uint32_t TMEM_COLS = 512;
   constexpr bool ONE_ARRIVE = !SPLIT;
@@ -311,8 +322,8 @@ __global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
         break;
       }
       uint8_t *st_base = base + s * stage_bytes;
-      if (P == 4u) produce_taylor<F16, SPLIT, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale);
-      else produce_taylor<F16, SPLIT, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale);
+      if (P == 4u) produce_taylor<F16, SPLIT, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
+      else produce_taylor<F16, SPLIT, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
       fence_proxy_async();  // this thread's stores, visible to the tensor core
       if constexpr (ONE_ARRIVE) {
         tgroup_sync(grp);  // the group's stores are done and s_rays[grp] is free again
@@ -360,7 +371,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
           mma_f16<true>(t_re, dai, dxi, ineg, 1u);
           mma_f16<true>(t_im, dar, dxi, idesc, acc);
           mma_f16<true>(t_im, dai, dxr, idesc, 1u);
-          if constexpr (SPLIT) {
+          if (SPLIT && (kh == 0 || lo_high)) {
             const uint64_t lar = make_sdesc(ar + lo + oa, lbo_a, 128), lai = make_sdesc(ai + lo + oa, lbo_a, 128);
             const uint64_t lxr = make_sdesc(xr + lo + ox, lbo_x, 128), lxi = make_sdesc(xi + lo + ox, lbo_x, 128);
             mma_f16<true>(t_re, dar, lxr, idesc, 1u);
@@ -492,14 +503,19 @@ __global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__res
   }
 }
 
-// P from the truncation bound theta^P / P! <= tol, theta = 2 pi max|eps| m_h n_h
-__global__ void choose_terms(const unsigned long long *eps_max, uint32_t *terms, double xscale, double tol) {
+// P from the truncation bound theta^P / P! <= tol, theta = 2 pi max|eps| m_h n_h; at split
+// precision (two_u = twice the unit roundoff) the terms p >= P/2 drop their lo operands when
+// theta^(P/2) / (P/2)! * two_u <= tol_lo
+__global__ void choose_terms(const unsigned long long *eps_max, uint32_t *terms, uint32_t *lo_high, double xscale,
+                             double tol, double two_u, double tol_lo) {
   const double th = static_cast<double>(*eps_max) * xscale;
   const double t2 = th * th, t4 = t2 * t2;
   uint32_t P = 0;
   if (t4 / 24.0 <= tol) P = 4;
   else if (t4 * t4 / 40320.0 <= tol) P = 8;
   *terms = P;
+  const double high = P == 4 ? t2 / 2.0 : t4 / 24.0;  // largest term of the second K step
+  *lo_high = (two_u > 0.0 && high * two_u > tol_lo) ? 1u : 0u;
 }
 
 int sms_t() {
@@ -596,12 +612,15 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   uint32_t *amax = reinterpret_cast<uint32_t *>(ws);
   uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
   unsigned long long *eps_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
+  uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
   int kernels = 0;
-  cudaMemsetAsync(ws, 0, 16, s);
+  cudaMemsetAsync(ws, 0, 24, s);
   exact_stats<<<2 * sms_t(), 256, 0, s>>>(p.amp, p.eps, n, f16, amax, eps_max);
   // theta = 2 pi max|eps| m_h n_h with eps in cycles (the word times 2^-64)
   const double xscale = 6.283185307179586 * sh.mh * (sh.bn / 4) * 5.421010862427522e-20;
-  choose_terms<<<1, 1, 0, s>>>(eps_max, terms, xscale, split ? 1e-6 : 1e-5);
+  // unit roundoff 2^-11 (FP16), 2^-8 (BF16); single pass has no lo operands to drop
+  const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
+  choose_terms<<<1, 1, 0, s>>>(eps_max, terms, lo_high, xscale, split ? 1e-6 : 1e-5, two_u, 2e-6);
   kernels += 2;
   TArgs a{};
   a.p = p;
@@ -618,6 +637,7 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.partials = reinterpret_cast<float *>(ws + kHeader);
   a.amax_bits = amax;
   a.terms = terms;
+  a.lo_high = lo_high;
   a.status = status;
   if (f16) split ? launch_taylor<true, true>(sh, a, s) : launch_taylor<true, false>(sh, a, s);
   else split ? launch_taylor<false, true>(sh, a, s) : launch_taylor<false, false>(sh, a, s);

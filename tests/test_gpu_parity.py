@@ -350,12 +350,16 @@ def test_exact_model_tensor_core_regimes(precision, case):
     assert rel_max(oracle.signal(radar.replace(model=0), rays), ref) > 10 * tol
 
 
-def test_exact_model_tensor_core_automotive_sampled():
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT])
+def test_exact_model_tensor_core_automotive_sampled(precision):
+    """Full automotive radar size (four expansion terms): at FP16 hi + lo the third and fourth
+    terms go single pass (their bound times the FP16 rounding is below 2e-6), at BF16 hi + lo
+    they keep their lo operands."""
     radar, rays = scenegen.automotive_scene(seed=45, n_rays=50_000)
     radar = radar.replace(model=1)
-    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT, model=rs.SIM_MODEL_EXACT)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
     try:
-        rc, sig, _, lab = run(radar, rays, rs.SIM_PREC_FP16_SPLIT, ctx=ctx)
+        rc, sig, _, lab = run(radar, rays, precision, ctx=ctx)
     finally:
         ctx.close()
     assert rc == rs.SIM_OK
