@@ -48,12 +48,20 @@ namespace {
 
 constexpr int TBM = 128;               // rows per CTA (TMEM lanes); a CTA pair covers 256
 constexpr int TKS = 32;                // K slots per stage
-constexpr int TNPROD = 384;            // producer threads: three groups of 128
-constexpr int TGROUPS = 3;
-constexpr int TGSIZE = TNPROD / TGROUPS;
-constexpr int TMMA_WARP = TNPROD / 32;
+constexpr int TGSIZE = 128;            // producer threads per group (one A row each)
+constexpr int TMAX_GROUPS = 4;
 constexpr int TNDRAIN = 128;
-constexpr int TTHREADS = TNPROD + 32 + TNDRAIN;
+// producer groups: four for single pass; three at split precision, whose 96 registers per
+// thread a fourth group would cut to 80 with spills (measured: 4 groups 6.69 -> 6.40 ms single
+// pass, 15.07 -> 15.49 ms FP16 hi + lo per automotive frame)
+template <bool SPLIT>
+__host__ __device__ constexpr int t_groups() {
+  return SPLIT ? 3 : 4;
+}
+template <bool SPLIT>
+__host__ __device__ constexpr int t_threads() {
+  return t_groups<SPLIT>() * TGSIZE + 32 + TNDRAIN;
+}
 constexpr int TSUBST_SPLIT = 16;       // stages per accumulation chain at split precision
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
@@ -126,7 +134,7 @@ struct RowCtx {
 };
 struct ColCtx {
   uint64_t n, nmc;          // sample index, n m_c
-  float up[8];              // (n' / n_h)^p
+  float u;                  // n' / n_h
   int c;                    // column in this CTA's B block
   uint32_t octets;          // bit o: this thread writes K chunk o of the column
   bool active;
@@ -193,7 +201,9 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
       float2 z[OCT];
 #pragma unroll
       for (int tt = 0; tt < TPO; ++tt) {
-        const float u = cc.up[o * TPO + tt];
+        float u = 1.f;  // (n' / n_h)^p, p = o TPO + tt (a compile-time count of products)
+#pragma unroll
+        for (int e = 0; e < o * TPO + tt; ++e) u *= cc.u;
 #pragma unroll
         for (int q = 0; q < RS; ++q) z[tt * RS + q] = make_float2(b[q].x * u, b[q].y * u);
       }
@@ -217,9 +227,11 @@ __host__ __device__ constexpr uint32_t t_stage_bytes(int bn) {
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
 template <bool F16, bool SPLIT>
-__global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
+__global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ TStage s_rays[TGROUPS];
+  constexpr int TGROUPS = t_groups<SPLIT>();
+  constexpr int TMMA_WARP = TGROUPS * TGSIZE / 32;
+  __shared__ TStage s_rays[TMAX_GROUPS];
   const uint32_t P = *g.terms;
   if (P != 4u && P != 8u) return;  // the per-chirp kernel owns this scene (both CTAs return)
   const bool lo_high = !SPLIT || *g.lo_high != 0u;
@@ -274,7 +286,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
   bool failed = false;
 
   if (warp < TMMA_WARP) {
-    // ---------------- producers: group grp builds stages grp, grp + 3, ...
+    // ---------------- producers: group grp builds stages grp, grp + TGROUPS, ...
     const int grp = warp / (TGSIZE / 32), gt = threadIdx.x % TGSIZE;
     const float scale = amp_scale<F16>(g.amax_bits);
     RowCtx rc;
@@ -301,13 +313,7 @@ __global__ void __launch_bounds__(TTHREADS, 1) taylor_sum_kernel(TArgs g) {
       const int n = n0 + static_cast<int>(rank) * ncb + cc.c;
       cc.n = static_cast<uint64_t>(n);
       cc.nmc = static_cast<uint64_t>(n) * static_cast<uint64_t>(m_c);
-      const float uu = static_cast<float>(n - n_c) / static_cast<float>(n_h);  // n_h is a power of two
-      float v = 1.f;
-#pragma unroll
-      for (int p = 0; p < 8; ++p) {
-        cc.up[p] = v;
-        v *= uu;
-      }
+      cc.u = static_cast<float>(n - n_c) / static_cast<float>(n_h);  // n_h is a power of two
     }
     TWords nxt{0, 0, 0, 0, 0, 0, 0.f};
     if (grp < n_stages) nxt = tfetch(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt);
@@ -579,7 +585,7 @@ void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(2u * static_cast<unsigned>(sh.mt2 * sh.nt * sh.splits));
-  cfg.blockDim = dim3(TTHREADS);
+  cfg.blockDim = dim3(t_threads<SPLIT>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
