@@ -9,10 +9,14 @@
 // there, among the spans whose image passes a relative threshold: the paper's simple binary
 // segmentation of each part, with overlaps resolved by energy.
 //
-// The per-ray prep runs once; each span reuses it with the amplitudes of the other rays
-// zeroed, through the context's ray-sum arithmetic (direct or tensor core).
+// The per-ray prep runs once.  Each span's rays are then packed in ray order (block counts of
+// every span, a scan, one read-back of the span sizes, a stable gather) and summed alone
+// through the context's ray-sum arithmetic (direct or tensor core): a span costs its own ray
+// count, so the spans of a partition cost one scene's ray sums together, and a span's part is
+// bit for bit the scene of its rays alone.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -25,11 +29,8 @@ struct RuleDev {
   int32_t object_id, material_id, min_hits, max_hits, exclude;
 };
 
-__global__ void span_mask_kernel(const float *__restrict__ amp, const int32_t *__restrict__ obj,
-                                 const int32_t *__restrict__ mat, const int32_t *__restrict__ hits, int64_t n,
-                                 RuleDev r, float *__restrict__ out) {
-  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ bool in_span(const RuleDev &r, const int32_t *obj, const int32_t *mat,
+                                        const int32_t *hits, int64_t i) {
   bool in = true;
   if (r.object_id >= 0) in = in && obj && obj[i] == r.object_id;
   if (r.material_id >= 0) in = in && mat && mat[i] == r.material_id;
@@ -37,8 +38,98 @@ __global__ void span_mask_kernel(const float *__restrict__ amp, const int32_t *_
     const int32_t h = hits ? hits[i] : 1;
     in = in && h >= r.min_hits && (r.max_hits < 0 || h <= r.max_hits);
   }
-  if (r.exclude) in = !in;
-  out[i] = in ? amp[i] : 0.f;
+  return r.exclude ? !in : in;
+}
+
+constexpr int kSpanBlock = 1024;  // rays per compaction block (one thread each)
+
+// cnt[h nb + b]: rays of block b in span h (grid nb x n_spans)
+__global__ void __launch_bounds__(kSpanBlock) span_count_kernel(const int32_t *__restrict__ obj,
+                                                                const int32_t *__restrict__ mat,
+                                                                const int32_t *__restrict__ hits, int64_t n,
+                                                                const RuleDev *__restrict__ rules, int nb,
+                                                                uint32_t *__restrict__ cnt) {
+  __shared__ uint32_t wsum[kSpanBlock / 32];
+  const int h = blockIdx.y;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kSpanBlock) + threadIdx.x;
+  const bool f = i < n && in_span(rules[h], obj, mat, hits, i);
+  const uint32_t bal = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(bal);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t v = wsum[threadIdx.x];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) cnt[static_cast<int64_t>(h) * nb + blockIdx.x] = v;
+  }
+}
+
+// per span h (one block each): off[h nb + b] = rays of span h in blocks before b; total[h]
+__global__ void __launch_bounds__(kSpanBlock) span_scan_kernel(const uint32_t *__restrict__ cnt, int nb,
+                                                               uint32_t *__restrict__ off,
+                                                               uint32_t *__restrict__ total) {
+  __shared__ uint32_t sh[kSpanBlock];
+  const int64_t base = static_cast<int64_t>(blockIdx.x) * nb;
+  const int per = (nb + kSpanBlock - 1) / kSpanBlock;
+  const int t = threadIdx.x, s0 = t * per;
+  uint32_t local = 0;
+  for (int k = 0; k < per; ++k)
+    if (s0 + k < nb) local += cnt[base + s0 + k];
+  sh[t] = local;
+  __syncthreads();
+  for (int d = 1; d < kSpanBlock; d <<= 1) {  // inclusive scan
+    const uint32_t v = t >= d ? sh[t - d] : 0u;
+    __syncthreads();
+    sh[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = sh[t] - local;
+  for (int k = 0; k < per; ++k)
+    if (s0 + k < nb) {
+      off[base + s0 + k] = run;
+      run += cnt[base + s0 + k];
+    }
+  if (t == kSpanBlock - 1) total[blockIdx.x] = sh[t];
+}
+
+// The prep words of span h's rays, packed in ray order: ray i of the span goes to
+// off_h[block] + (its rank among the span's rays of the block).
+__global__ void __launch_bounds__(kSpanBlock) span_gather_kernel(RaysPrep src, RaysPrep dst,
+                                                                 const int32_t *__restrict__ obj,
+                                                                 const int32_t *__restrict__ mat,
+                                                                 const int32_t *__restrict__ hits, int64_t n,
+                                                                 const RuleDev *__restrict__ rule,
+                                                                 const uint32_t *__restrict__ off_h) {
+  __shared__ uint32_t wpre[kSpanBlock / 32];
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kSpanBlock) + threadIdx.x;
+  const bool f = i < n && in_span(*rule, obj, mat, hits, i);
+  const uint32_t bal = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) wpre[w] = __popc(bal);
+  __syncthreads();
+  if (w == 0) {  // exclusive scan of the 32 warp counts
+    const uint32_t v = wpre[lane];
+    uint32_t x = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+      if (lane >= d) x += y;
+    }
+    wpre[lane] = x - v;
+  }
+  __syncthreads();
+  if (!f) return;
+  const int64_t j = off_h[blockIdx.x] + wpre[w] + __popc(bal & ((1u << lane) - 1u));
+  dst.carrier[j] = src.carrier[i];
+  dst.nu_r[j] = src.nu_r[i];
+  dst.nu_d[j] = src.nu_d[i];
+  dst.nu_a[j] = src.nu_a[i];
+  dst.amp[j] = src.amp[i];
+  dst.step_d[j] = src.step_d[i];
+  dst.step_r[j] = src.step_r[i];
+  dst.nu_tx[j] = src.nu_tx[i];
+  if (src.eps) {
+    dst.eps[j] = src.eps[i];
+    dst.eps_t[j] = src.eps_t[i];
+  }
 }
 
 // largest |X|^2 over all spans and cells (non-negative floats: bit order is value order)
@@ -98,9 +189,13 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                 !rays->elevation_rad || !rays->phase0_rad))
     return SIM_E_INVALID;
 
-  // device workspace: inputs, meta, prep, masked amplitudes, signal, FFT scratch, spectra
+  // device workspace: inputs, meta, prep, the packed prep of one span, compaction counts,
+  // signal, FFT scratch, spectra (the tensor-core scratch follows once the span sizes are known)
   const size_t un = static_cast<size_t>(n), up = (un + 31) / 32 * 32;
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
+  const bool exact = g.model == SIM_MODEL_EXACT;
+  const int nb = n > 0 ? static_cast<int>((n + kSpanBlock - 1) / kSpanBlock) : 0;
+  const size_t ub = static_cast<size_t>(nb) * static_cast<size_t>(n_spans);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -112,12 +207,16 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                o_hit = take(4 * un);
   const size_t o_car = take(8 * up), o_nur = take(8 * up), o_nud = take(8 * up), o_nua = take(8 * up),
                o_amp = take(4 * up), o_cell = take(4 * up), o_en = take(8 * up), o_sd = take(8 * up),
-               o_sr = take(8 * up), o_eps = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0), o_mamp = take(4 * up),
-               o_ntx = take(8 * up), o_epst = take(g.model == SIM_MODEL_EXACT ? 8 * up : 0);
+               o_sr = take(8 * up), o_eps = take(exact ? 8 * up : 0), o_ntx = take(8 * up),
+               o_epst = take(exact ? 8 * up : 0);
+  const size_t c_car = take(8 * up), c_nur = take(8 * up), c_nud = take(8 * up), c_nua = take(8 * up),
+               c_amp = take(4 * up), c_sd = take(8 * up), c_sr = take(8 * up), c_eps = take(exact ? 8 * up : 0),
+               c_ntx = take(8 * up), c_epst = take(exact ? 8 * up : 0);
+  const size_t o_rules = take(sizeof(RuleDev) * static_cast<size_t>(n_spans)), o_cnt = take(4 * ub),
+               o_off = take(4 * ub), o_tot = take(4 * static_cast<size_t>(n_spans));
   const size_t o_status = take(256), o_max = take(256);
   const size_t o_sig = take(8 * static_cast<size_t>(g.n_sig)), o_tmp = take(8 * static_cast<size_t>(g.n_sig));
   const size_t o_spec = take(8 * static_cast<size_t>(g.n_cell) * static_cast<size_t>(n_spans));
-  const size_t o_ws = take(tensor ? static_cast<size_t>(umma_workspace_bytes(g, n)) : 0);
   const size_t o_lab = take(4 * static_cast<size_t>(g.n_cell));
   uint8_t *b = nullptr;
   if (cudaMalloc(&b, off) != cudaSuccess) {
@@ -129,6 +228,15 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     cudaFree(b);
     return SIM_E_CUDA;
   }
+  void *ws = nullptr;  // tensor-core scratch
+  auto finish = [&](int rc) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (ws) cudaFree(ws);
+    cudaFree(b);
+    cudaGetLastError();
+    return rc;
+  };
   const int32_t *dobj = nullptr, *dmat = nullptr, *dhit = nullptr;
   if (n > 0) {
     cudaMemcpyAsync(b + o_d, rays->range_rt_m, 8 * un, cudaMemcpyDefault, s);
@@ -150,6 +258,12 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
       dhit = reinterpret_cast<const int32_t *>(b + o_hit);
     }
   }
+  std::vector<RuleDev> hrules(static_cast<size_t>(n_spans));
+  for (int h = 0; h < n_spans; ++h)
+    hrules[h] = RuleDev{rules[h].object_id, rules[h].material_id, rules[h].min_hits, rules[h].max_hits,
+                        rules[h].exclude};
+  const RuleDev *drules = reinterpret_cast<const RuleDev *>(b + o_rules);
+  cudaMemcpyAsync(b + o_rules, hrules.data(), sizeof(RuleDev) * hrules.size(), cudaMemcpyHostToDevice, s);
   uint32_t *status = reinterpret_cast<uint32_t *>(b + o_status);
   uint32_t *pmax = reinterpret_cast<uint32_t *>(b + o_max);
   cudaMemsetAsync(status, 0, 4, s);
@@ -161,27 +275,67 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
               reinterpret_cast<uint64_t *>(b + o_nud), reinterpret_cast<uint64_t *>(b + o_nua),
               reinterpret_cast<float *>(b + o_amp), reinterpret_cast<int32_t *>(b + o_cell),
               reinterpret_cast<uint64_t *>(b + o_en), reinterpret_cast<float2 *>(b + o_sd),
-              reinterpret_cast<float2 *>(b + o_sr),
-              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + o_eps) : nullptr,
-              reinterpret_cast<uint64_t *>(b + o_ntx),
-              g.model == SIM_MODEL_EXACT ? reinterpret_cast<uint64_t *>(b + o_epst) : nullptr};
-  launch_prep(g, in, n, rp, status, s);
-  RaysPrep span = rp;
-  span.amp = reinterpret_cast<float *>(b + o_mamp);
+              reinterpret_cast<float2 *>(b + o_sr), exact ? reinterpret_cast<uint64_t *>(b + o_eps) : nullptr,
+              reinterpret_cast<uint64_t *>(b + o_ntx), exact ? reinterpret_cast<uint64_t *>(b + o_epst) : nullptr};
+  // the packed span: its own copies of every word a ray sum reads (cell and energy unused)
+  RaysPrep cp{reinterpret_cast<uint64_t *>(b + c_car), reinterpret_cast<uint64_t *>(b + c_nur),
+              reinterpret_cast<uint64_t *>(b + c_nud), reinterpret_cast<uint64_t *>(b + c_nua),
+              reinterpret_cast<float *>(b + c_amp), rp.cell, rp.energy, reinterpret_cast<float2 *>(b + c_sd),
+              reinterpret_cast<float2 *>(b + c_sr), exact ? reinterpret_cast<uint64_t *>(b + c_eps) : nullptr,
+              reinterpret_cast<uint64_t *>(b + c_ntx), exact ? reinterpret_cast<uint64_t *>(b + c_epst) : nullptr};
+  // events: start, after the span sizes, per span (after its sum, after its FFT), after labels
+  std::vector<cudaEvent_t> ev(static_cast<size_t>(3 + 2 * n_spans), nullptr);
+  for (auto &e : ev) cudaEventCreate(&e);
+  struct EventsGuard {
+    std::vector<cudaEvent_t> &v;
+    ~EventsGuard() {
+      for (auto &e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } ev_guard{ev};
+  int kernels = 0;
+  cudaEventRecord(ev[0], s);
+  kernels += launch_prep(g, in, n, rp, status, s);
+  // span sizes: block counts of every span, their scan, one read-back of the sizes
+  uint32_t *cnt = reinterpret_cast<uint32_t *>(b + o_cnt), *boff = reinterpret_cast<uint32_t *>(b + o_off);
+  uint32_t *tot = reinterpret_cast<uint32_t *>(b + o_tot);
+  std::vector<uint32_t> sizes(static_cast<size_t>(n_spans), 0u);
+  if (n > 0) {
+    span_count_kernel<<<dim3(static_cast<unsigned>(nb), static_cast<unsigned>(n_spans)), kSpanBlock, 0, s>>>(
+        dobj, dmat, dhit, n, drules, nb, cnt);
+    span_scan_kernel<<<static_cast<unsigned>(n_spans), kSpanBlock, 0, s>>>(cnt, nb, boff, tot);
+    kernels += 2;
+  }
+  cudaEventRecord(ev[1], s);
+  if (n > 0) cudaMemcpyAsync(sizes.data(), tot, 4 * sizes.size(), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return finish(SIM_E_CUDA);
+  if (tensor) {
+    int64_t need = 0;
+    for (uint32_t nh : sizes)
+      if (nh > 0) need = std::max<int64_t>(need, umma_workspace_bytes(g, static_cast<int64_t>(nh)));
+    if (need > 0 && cudaMalloc(&ws, static_cast<size_t>(need)) != cudaSuccess) {
+      ws = nullptr;
+      return finish(SIM_E_NOMEM);
+    }
+  }
   float2 *sig = reinterpret_cast<float2 *>(b + o_sig);
   float2 *spectra = reinterpret_cast<float2 *>(b + o_spec);
   for (int h = 0; h < n_spans; ++h) {
-    const sim_span_rule &r = rules[h];
-    const RuleDev rd{r.object_id, r.material_id, r.min_hits, r.max_hits, r.exclude};
-    if (n > 0)
-      span_mask_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(rp.amp, dobj, dmat, dhit, n, rd,
-                                                                               span.amp);
-    if (tensor) launch_umma_sum(g, span, n, sig, b + o_ws, status, s, nullptr);
-    else launch_direct_sum(g, span, n, sig, s);
+    const int64_t nh = sizes[h];
+    if (nh > 0) {
+      span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, s>>>(rp, cp, dobj, dmat, dhit, n, drules + h,
+                                                                          boff + static_cast<int64_t>(h) * nb);
+      kernels += 1 + (tensor ? launch_umma_sum(g, cp, nh, sig, ws, status, s, nullptr)
+                             : launch_direct_sum(g, cp, nh, sig, s));
+    } else {
+      cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
+    }
+    cudaEventRecord(ev[2 + 2 * h], s);
     float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
-    launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + o_tmp), x, s);
+    kernels += launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + o_tmp), x, s);
     if (span_spectra && span_spectra[h])
       cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+    cudaEventRecord(ev[3 + 2 * h], s);
   }
   if (span_labels) {
     const int64_t all = g.n_cell * n_spans;
@@ -195,15 +349,32 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     else dlab = reinterpret_cast<int32_t *>(b + o_lab);
     const float t2 = threshold * threshold;
     span_label_kernel<<<1024, 256, 0, s>>>(spectra, n_spans, g.n_cell, t2, pmax, dlab);
+    kernels += 2;
     if (!dev_out)
       cudaMemcpyAsync(span_labels, dlab, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDeviceToHost, s);
   }
+  cudaEventRecord(ev[2 + 2 * n_spans], s);
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);
-  cudaStreamDestroy(s);
-  cudaFree(b);
-  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
-  if (st & kStatusBadRay) return SIM_E_INVALID;
-  return st ? SIM_E_DEVICE : SIM_OK;
+  const bool launch_ok = cudaGetLastError() == cudaSuccess;
+  if (e != cudaSuccess || !launch_ok) return finish(SIM_E_CUDA);
+  if (st & kStatusBadRay) return finish(SIM_E_INVALID);
+  if (st) return finish(SIM_E_DEVICE);
+  // stage times as sim_last_stage_ms reports them: prep (with the span sizes), ray sums (with
+  // the packing), FFTs, labels, and the whole call on the device's clock (with the read-back
+  // of the span sizes)
+  auto el = [&](int a, int c) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[static_cast<size_t>(a)], ev[static_cast<size_t>(c)]);
+    return ms;
+  };
+  float ms[7] = {0, el(0, 1), 0, 0, 0, 0, el(0, 2 + 2 * n_spans)};
+  for (int h = 0; h < n_spans; ++h) {
+    ms[2] += el(h == 0 ? 1 : 1 + 2 * h, 2 + 2 * h);
+    ms[4] += el(2 + 2 * h, 3 + 2 * h);
+  }
+  ms[5] = el(1 + 2 * n_spans, 2 + 2 * n_spans);
+  record_stage_ms(ctx, ms, kernels);
+  return finish(SIM_OK);
 }

@@ -78,6 +78,32 @@ def test_partition_parts_add_up_to_the_scene():
         ctx.close()
 
 
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16])
+def test_span_part_is_the_scene_of_its_rays(precision):
+    """A span's rays are packed in ray order and summed alone, so its spectrum is bit for bit
+    the spectrum of a scene holding only those rays; an empty span gives zeros."""
+    radar, rays, mat, hits = _scene(24, 1400)
+    ctx = rs.Context(radar, precision=precision)
+    try:
+        arr = {k: np.ascontiguousarray(v) for k, v in dict(rays.arrays(), material_id=mat, n_hits=hits).items()}
+        r, m = rs.make_rays(arr, rays.n)
+        rules = [dict(object_id=2, material_id=-1, min_hits=0, max_hits=-1, exclude=0),
+                 dict(object_id=-1, material_id=1, min_hits=2, max_hits=-1, exclude=0),
+                 dict(object_id=9, material_id=-1, min_hits=0, max_hits=-1, exclude=0)]   # no such object
+        spans = [np.full(ctx.cube_shape + (2,), np.nan, np.float32) for _ in rules]
+        assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(**q) for q in rules], spans, None, 0.0) == rs.SIM_OK
+        for q, x in zip(rules[:2], spans[:2]):
+            mask = oracle.span_mask(q, rays.object_id, mat, hits)
+            sub = {k: np.ascontiguousarray(v[mask]) for k, v in arr.items()}
+            alone = np.zeros(ctx.cube_shape + (2,), np.float32)
+            t = ctx.submit(sub, int(mask.sum()))
+            assert ctx.fetch(t, alone) == rs.SIM_OK
+            assert np.array_equal(x, alone)
+        assert not spans[2].any()
+    finally:
+        ctx.close()
+
+
 def test_rules_needing_missing_meta_are_rejected():
     radar, rays, mat, hits = _scene(23, 100)
     ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
