@@ -359,7 +359,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   const cudaError_t e = cudaStreamSynchronize(s);
   const bool launch_ok = cudaGetLastError() == cudaSuccess;
   if (e != cudaSuccess || !launch_ok) return finish(SIM_E_CUDA);
-  if (st & kStatusBadRay) return finish(SIM_E_INVALID);
+  if (st & (kStatusBadRay | kStatusModelRange)) return finish(SIM_E_INVALID);
   if (st) return finish(SIM_E_DEVICE);
   // stage times as sim_last_stage_ms reports them: prep (with the span sizes), ray sums (with
   // the packing), FFTs, labels, and the whole call on the device's clock (with the read-back

@@ -422,8 +422,10 @@ int derive(const sim_radar_params *p, Derived *g) {
   if (p->outputs <= 0 || p->outputs > 7) return SIM_E_INVALID;
   if (p->max_rays < 1 || p->max_rays > (int64_t{1} << 21)) return SIM_E_INVALID;
   if (p->model != SIM_MODEL_SEPARABLE && p->model != SIM_MODEL_EXACT) return SIM_E_INVALID;
-  // the exact model on tensor cores has no TDM slot term in its per-chirp sample operand
-  if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT && p->tdm_slot_s != 0.0)
+  // the exact model with TDM slots on tensor cores needs the per-tile expansion, which needs
+  // two-SM tiles of at least 32 samples (the per-chirp product has no slot term)
+  if (p->model == SIM_MODEL_EXACT && p->precision != SIM_PREC_FP32_DIRECT && p->tdm_slot_s != 0.0 &&
+      p->n_samples < 32)
     return SIM_E_INVALID;
   if (p->pattern_exp < 0 || p->pattern_exp > 16) return SIM_E_INVALID;
   if (!(isfinite(p->tdm_slot_s) && p->tdm_slot_s >= 0.0 && p->tdm_slot_s <= 1.0)) return SIM_E_INVALID;
@@ -743,7 +745,7 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
   delete j;
   if (launch_error != SIM_OK) return launch_error;
   if (sync_rc != cudaSuccess) return SIM_E_CUDA;
-  if (status & kStatusBadRay) return SIM_E_INVALID;
+  if (status & (kStatusBadRay | kStatusModelRange)) return SIM_E_INVALID;
   if (status) return SIM_E_DEVICE;
   return SIM_OK;
 }

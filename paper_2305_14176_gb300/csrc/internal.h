@@ -19,6 +19,8 @@ enum : uint32_t {
   kStatusWaitLimit = 4u,     // a tensor-core pipeline wait ran past its limit
   kStatusBadLaunch = 8u,     // a kernel saw a launch shape it was not built for
   kStatusBadGeometry = 16u,  // a hit list, triangle or vertex index was out of range
+  kStatusModelRange = 32u,   // exact model with TDM slots on tensor cores: the range migration is
+                             // beyond the per-tile expansion's bound (reported as invalid rays)
 };
 
 // Radar constants derived on the host in FP64 from sim_radar_params.

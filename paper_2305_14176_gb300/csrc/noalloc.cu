@@ -108,7 +108,8 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   if (g.precision == SIM_PREC_FP32_DIRECT) {
     launch_direct_sum(g, rp, n, sig, s);
   } else if (launch_umma_sum_in(g, rp, n, sig, ws, ws_bytes, status, s) < 0) {
-    return SIM_E_INVALID;  // one split of this cube does not fit the scratch array
+    return SIM_E_INVALID;  // one split of this cube does not fit the scratch array, or the exact
+                           // model with TDM slots (no per-chirp form) was asked for
   }
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);

@@ -1078,7 +1078,8 @@ int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, 
 int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, int64_t ws_bytes,
                        uint32_t *status, cudaStream_t s) {
   if (g.model == SIM_MODEL_EXACT) {
-    if (exact_workspace_bytes(g, n) > ws_bytes) return -1;
+    // the per-chirp product has no TDM slot term; its workspace must fit
+    if (g.tslot != 0.0 || exact_workspace_bytes(g, n) > ws_bytes) return -1;
     return launch_exact_sum(g, p, n, sig, workspace, status, s, nullptr);
   }
   Shape sh = plan_shape(g, n);

@@ -16,13 +16,19 @@
 //   B_p[i, n]   = e^{2 pi j n (nu_r + m_c eps)} (n' / n_h)^p,      x_row,i = 2 pi eps_i m' n_h
 // Rows are chirp-major (row = m N_v + k), so a 256-row tile spans only about 256 / N_v chirps,
 // and each synthesised value serves a whole 256 x NC tile instead of N_v channels.
+// With TDM slot offsets the phase also holds n t eps_t (transmitter t); with t = t_c + t' it
+// joins the coupling the same way: the shifts take n_c t' eps_t (rows) and n t_c eps_t
+// (columns), and x = 2 pi n' (m' eps + t' eps_t).
 //
-// P is 4 or 8, the smaller one whose bound (2 pi max|eps| m_h n_h)^P / P! is at most 1e-6 for
+// P is 4 or 8, the smaller one whose bound theta^P / P!, theta = 2 pi n_h (max|eps| m_h +
+// max|eps_t| t_h), is at most 1e-6 for
 // the hi + lo precisions (1e-5 single pass, whose operand rounding is ~3e-4); a device kernel
 // takes it from the scene's largest |eps|, so no host round trip is needed.  When even P = 8
 // would not meet the bound (velocities far beyond road traffic), P = 0 is written and the
 // per-chirp kernel of umma_exact.cu, launched behind this one, computes the scene instead: each
 // of the two kernels (and its reduction) returns at once when the other one owns the scene.
+// The per-chirp form has no slot term, so with TDM slots P = 0 is an error instead (a status
+// bit reported as invalid rays).
 //
 // At the hi + lo precisions the terms of order p >= P / 2 (the second 16-slot K step of every
 // stage) are at most theta^(P/2) / (P/2)! of the ray's amplitude, so single-pass operand
@@ -67,13 +73,14 @@ constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
 constexpr int kMaxDynSmemT = 232448 - 8192;
 // workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64), whether the
-// high-order K step keeps its lo operands (u32)
-constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kHeader = 256;
+// high-order K step keeps its lo operands (u32), largest |eps_t| (u64)
+constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 24, kHeader = 256;
 
 struct TArgs {
   RaysPrep p;
   int64_t n_rays, chunk;  // rays, rays per split (multiple of 8)
   int nc, ns, nv, nrx, m_rows;
+  int t_c;                // centre transmitter of the slot term
   int bn;                 // real columns per tile, 2 NC
   int mt2, nt;            // 256-row tiles, column tiles
   float *partials;        // [split][M chirp-major rows][2 N_s], each tile as (Re block | Im block)
@@ -86,17 +93,19 @@ struct TArgs {
 // per-ray words of one stage (at most 8 rays)
 struct TStage {
   uint64_t car[TMAX_RAYS], nua[TMAX_RAYS], nud[TMAX_RAYS], nutx[TMAX_RAYS], nur[TMAX_RAYS], eps[TMAX_RAYS];
+  uint64_t epst[TMAX_RAYS];
   float amp[TMAX_RAYS];
 };
 
 struct TWords {
-  uint64_t car, nua, nud, nutx, nur, eps;
+  uint64_t car, nua, nud, nutx, nur, eps, epst;
   float amp;
 };
 
 // thread gt < rays of the stage fetches its ray's words (rays past the chunk read as 0)
+template <bool TDM>
 __device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays, int64_t k_hi, int gt) {
-  TWords w{0, 0, 0, 0, 0, 0, 0.f};
+  TWords w{0, 0, 0, 0, 0, 0, 0, 0.f};
   const int64_t ray = ray0 + gt;
   if (gt < rays && ray < k_hi) {
     w.car = g.p.carrier[ray];
@@ -105,11 +114,13 @@ __device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays,
     w.nutx = g.p.nu_tx[ray];
     w.nur = g.p.nu_r[ray];
     w.eps = g.p.eps[ray];
+    if constexpr (TDM) w.epst = g.p.eps_t[ray];
     w.amp = g.p.amp[ray];
   }
   return w;
 }
 
+template <bool TDM>
 __device__ __forceinline__ void tstore(TStage &s, int gt, const TWords &w) {
   if (gt < TMAX_RAYS) {
     s.car[gt] = w.car;
@@ -118,6 +129,7 @@ __device__ __forceinline__ void tstore(TStage &s, int gt, const TWords &w) {
     s.nutx[gt] = w.nutx;
     s.nur[gt] = w.nur;
     s.eps[gt] = w.eps;
+    if constexpr (TDM) s.epst[gt] = w.epst;
     s.amp[gt] = w.amp;
   }
 }
@@ -128,12 +140,13 @@ __device__ __forceinline__ void tgroup_sync(int g) {
 
 // What one producer thread needs of its A row and B columns for a whole unit.
 struct RowCtx {
-  uint64_t tx, rx, m, ncm;  // channel (t, r), chirp, n_c m' (two's complement)
-  float xm;                 // 2 pi m' n_h 2^-64: x_row,i = xm * (signed eps_i word)
+  uint32_t tx, rx, m;       // channel (t, r), chirp
+  int32_t ncm, nct;         // n_c m', n_c t' (|n_c m'| < 2^23)
+  float xm, xt;             // 2 pi m' n_h 2^-64, 2 pi t' n_h 2^-64: x = xm eps_i + xt eps_t,i (words)
   bool valid;
 };
 struct ColCtx {
-  uint64_t n, nmc;          // sample index, n m_c
+  uint32_t n, nmc, ntc;     // sample index, n m_c, n t_c (< 2^26)
   float u;                  // n' / n_h
   int c;                    // column in this CTA's B block
   uint32_t octets;          // bit o: this thread writes K chunk o of the column
@@ -142,7 +155,7 @@ struct ColCtx {
 
 // One stage of operands: A row gt (all 32 slots) and this thread's B column octets, in the
 // no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
-template <bool F16, bool SPLIT, int P>
+template <bool F16, bool SPLIT, bool TDM, int P>
 __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
                                                const ColCtx &cc, float scale, bool lo_high) {
   constexpr int RS = TKS / P;   // rays per stage
@@ -157,11 +170,14 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
-      __sincosf(q64_to_rad(sr.car[q] + rc.tx * sr.nutx[q] + rc.rx * sr.nua[q] + rc.m * sr.nud[q] + rc.ncm * sr.eps[q]),
-                &sn, &cs);
+      uint64_t ph = sr.car[q] + static_cast<uint64_t>(rc.tx) * sr.nutx[q] + static_cast<uint64_t>(rc.rx) * sr.nua[q] +
+                    static_cast<uint64_t>(rc.m) * sr.nud[q] + static_cast<uint64_t>(static_cast<int64_t>(rc.ncm)) * sr.eps[q];
+      if constexpr (TDM) ph += static_cast<uint64_t>(static_cast<int64_t>(rc.nct)) * sr.epst[q];
+      __sincosf(q64_to_rad(ph), &sn, &cs);
       const float am = rc.valid ? sr.amp[q] * scale : 0.f;
       t[q] = make_float2(am * cs, am * sn);
       x[q] = rc.xm * static_cast<float>(static_cast<int64_t>(sr.eps[q]));
+      if constexpr (TDM) x[q] += rc.xt * static_cast<float>(static_cast<int64_t>(sr.epst[q]));
     }
     uint32_t off = (gt >> 3) * 128 + (gt & 7) * 16;
 #pragma unroll
@@ -191,7 +207,9 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
-      __sincosf(q64_to_rad(cc.n * sr.nur[q] + cc.nmc * sr.eps[q]), &sn, &cs);
+      uint64_t ph = static_cast<uint64_t>(cc.n) * sr.nur[q] + static_cast<uint64_t>(cc.nmc) * sr.eps[q];
+      if constexpr (TDM) ph += static_cast<uint64_t>(cc.ntc) * sr.epst[q];
+      __sincosf(q64_to_rad(ph), &sn, &cs);
       b[q] = make_float2(cs, sn);
     }
     const uint32_t off0 = (cc.c >> 3) * 128 + (cc.c & 7) * 16;
@@ -226,7 +244,7 @@ __host__ __device__ constexpr uint32_t t_stage_bytes(int bn) {
 
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
-template <bool F16, bool SPLIT>
+template <bool F16, bool SPLIT, bool TDM>
 __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int TGROUPS = t_groups<SPLIT>();
@@ -295,12 +313,15 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
       rc.valid = r < g.m_rows;
       const int m = r / g.nv, k = r - m * g.nv;
       const int t = k / g.nrx;
-      rc.tx = static_cast<uint64_t>(t);
-      rc.rx = static_cast<uint64_t>(k - t * g.nrx);
-      rc.m = static_cast<uint64_t>(m);
+      rc.tx = static_cast<uint32_t>(t);
+      rc.rx = static_cast<uint32_t>(k - t * g.nrx);
+      rc.m = static_cast<uint32_t>(m);
       const int mp = m - m_c;
-      rc.ncm = static_cast<uint64_t>(static_cast<int64_t>(n_c) * mp);
+      rc.ncm = n_c * mp;
       rc.xm = static_cast<float>(mp) * static_cast<float>(n_h) * 3.40612158008655459e-19f;  // 2 pi 2^-64
+      const int tp = t - g.t_c;
+      rc.nct = n_c * tp;
+      rc.xt = static_cast<float>(tp) * static_cast<float>(n_h) * 3.40612158008655459e-19f;
     }
     ColCtx cc;
     {
@@ -311,25 +332,26 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
       for (int o = h; o < 4; o += tpc) cc.octets |= 1u << o;
       cc.active = cc.octets != 0;
       const int n = n0 + static_cast<int>(rank) * ncb + cc.c;
-      cc.n = static_cast<uint64_t>(n);
-      cc.nmc = static_cast<uint64_t>(n) * static_cast<uint64_t>(m_c);
+      cc.n = static_cast<uint32_t>(n);
+      cc.nmc = static_cast<uint32_t>(n) * static_cast<uint32_t>(m_c);
+      cc.ntc = static_cast<uint32_t>(n) * static_cast<uint32_t>(g.t_c);
       cc.u = static_cast<float>(n - n_c) / static_cast<float>(n_h);  // n_h is a power of two
     }
-    TWords nxt{0, 0, 0, 0, 0, 0, 0.f};
-    if (grp < n_stages) nxt = tfetch(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt);
+    TWords nxt{0, 0, 0, 0, 0, 0, 0, 0.f};
+    if (grp < n_stages) nxt = tfetch<TDM>(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt);
     for (int st = grp; st < n_stages; st += TGROUPS) {
       const int s = st % NST;
       const int64_t ray0 = k_lo + static_cast<int64_t>(st) * RS;
-      tstore(s_rays[grp], gt, nxt);
-      if (st + TGROUPS < n_stages) nxt = tfetch(g, ray0 + TGROUPS * RS, RS, k_hi, gt);
+      tstore<TDM>(s_rays[grp], gt, nxt);
+      if (st + TGROUPS < n_stages) nxt = tfetch<TDM>(g, ray0 + TGROUPS * RS, RS, k_hi, gt);
       tgroup_sync(grp);
       if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
         failed = true;
         break;
       }
       uint8_t *st_base = base + s * stage_bytes;
-      if (P == 4u) produce_taylor<F16, SPLIT, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
-      else produce_taylor<F16, SPLIT, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
+      if (P == 4u) produce_taylor<F16, SPLIT, TDM, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
+      else produce_taylor<F16, SPLIT, TDM, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
       fence_proxy_async();  // this thread's stores, visible to the tensor core
       if constexpr (ONE_ARRIVE) {
         tgroup_sync(grp);  // the group's stores are done and s_rays[grp] is free again
@@ -487,34 +509,42 @@ __global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv
   }
 }
 
-// amplitude maximum (FP16 scaling) and largest |eps| of the scene
-__global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__restrict__ eps, int64_t n, bool want_amax,
-                            uint32_t *amax_bits, unsigned long long *eps_max) {
+__device__ __forceinline__ unsigned long long signed_mag(uint64_t e) {
+  return static_cast<int64_t>(e) < 0 ? ~e + 1ull : e;  // |signed Q0.64 word|
+}
+
+// amplitude maximum (FP16 scaling) and largest |eps| and |eps_t| of the scene
+__global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__restrict__ eps,
+                            const uint64_t *__restrict__ eps_t, int64_t n, bool want_amax, uint32_t *amax_bits,
+                            unsigned long long *eps_max, unsigned long long *eps_t_max) {
   uint32_t ma = 0;
-  unsigned long long me = 0;
+  unsigned long long me = 0, mt = 0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     if (want_amax) ma = max(ma, __float_as_uint(amp[i]));  // amplitudes are >= 0
-    const uint64_t e = eps[i];
-    const unsigned long long mag = static_cast<int64_t>(e) < 0 ? ~e + 1ull : e;  // |signed word|
-    me = max(me, mag);
+    me = max(me, signed_mag(eps[i]));
+    mt = max(mt, signed_mag(eps_t[i]));
   }
   for (int o = 16; o > 0; o >>= 1) {
     ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
     me = max(me, __shfl_xor_sync(0xffffffffu, me, o));
+    mt = max(mt, __shfl_xor_sync(0xffffffffu, mt, o));
   }
   if ((threadIdx.x & 31) == 0) {
     if (want_amax) atomicMax(amax_bits, ma);
     atomicMax(eps_max, me);
+    atomicMax(eps_t_max, mt);
   }
 }
 
-// P from the truncation bound theta^P / P! <= tol, theta = 2 pi max|eps| m_h n_h; at split
-// precision (two_u = twice the unit roundoff) the terms p >= P/2 drop their lo operands when
-// theta^(P/2) / (P/2)! * two_u <= tol_lo
-__global__ void choose_terms(const unsigned long long *eps_max, uint32_t *terms, uint32_t *lo_high, double xscale,
-                             double tol, double two_u, double tol_lo) {
-  const double th = static_cast<double>(*eps_max) * xscale;
+// P from the truncation bound theta^P / P! <= tol, theta = 2 pi n_h (max|eps| m_h + max|eps_t| t_h)
+// (xs_m, xs_t: the factors of the two word maxima); at split precision (two_u = twice the unit
+// roundoff) the terms p >= P/2 drop their lo operands when theta^(P/2) / (P/2)! * two_u <= tol_lo.
+// With TDM slots there is no per-chirp fallback: P = 0 raises the model-range status bit.
+__global__ void choose_terms(const unsigned long long *eps_max, const unsigned long long *eps_t_max, uint32_t *terms,
+                             uint32_t *lo_high, double xs_m, double xs_t, double tol, double two_u, double tol_lo,
+                             bool tdm, uint32_t *status) {
+  const double th = static_cast<double>(*eps_max) * xs_m + static_cast<double>(*eps_t_max) * xs_t;
   const double t2 = th * th, t4 = t2 * t2;
   uint32_t P = 0;
   if (t4 / 24.0 <= tol) P = 4;
@@ -522,6 +552,7 @@ __global__ void choose_terms(const unsigned long long *eps_max, uint32_t *terms,
   *terms = P;
   const double high = P == 4 ? t2 / 2.0 : t4 / 24.0;  // largest term of the second K step
   *lo_high = (two_u > 0.0 && high * two_u > tol_lo) ? 1u : 0u;
+  if (P == 0 && tdm) atomicOr(status, kStatusModelRange);
 }
 
 int sms_t() {
@@ -574,13 +605,14 @@ TShape plan_taylor(const Derived &g, int64_t n) {
 // the expansion needs two-SM tiles of at least 32 complex columns
 bool taylor_eligible(const Derived &g) { return g.ns >= 32; }
 
-template <bool F16, bool SPLIT>
+template <bool F16, bool SPLIT, bool TDM>
 void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   const size_t smem =
       t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(sh.bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmemT);
+    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, TDM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kMaxDynSmemT);
     attr = true;
   }
   cudaLaunchConfig_t cfg{};
@@ -595,7 +627,7 @@ void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT>, a);
+  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, TDM>, a);
 }
 
 }  // namespace
@@ -619,14 +651,18 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
   unsigned long long *eps_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
   uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
+  unsigned long long *eps_t_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsTMax);
+  const bool tdm = g.tslot != 0.0;
+  const int t_c = g.ntx / 2, t_h = std::max(t_c, g.ntx - 1 - t_c);  // |t - t_c| <= t_h
   int kernels = 0;
-  cudaMemsetAsync(ws, 0, 24, s);
-  exact_stats<<<2 * sms_t(), 256, 0, s>>>(p.amp, p.eps, n, f16, amax, eps_max);
-  // theta = 2 pi max|eps| m_h n_h with eps in cycles (the word times 2^-64)
-  const double xscale = 6.283185307179586 * sh.mh * (sh.bn / 4) * 5.421010862427522e-20;
+  cudaMemsetAsync(ws, 0, 32, s);
+  exact_stats<<<2 * sms_t(), 256, 0, s>>>(p.amp, p.eps, p.eps_t, n, f16, amax, eps_max, eps_t_max);
+  // theta = 2 pi n_h (max|eps| m_h + max|eps_t| t_h) with eps in cycles (the word times 2^-64)
+  const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
   // unit roundoff 2^-11 (FP16), 2^-8 (BF16); single pass has no lo operands to drop
   const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
-  choose_terms<<<1, 1, 0, s>>>(eps_max, terms, lo_high, xscale, split ? 1e-6 : 1e-5, two_u, 2e-6);
+  choose_terms<<<1, 1, 0, s>>>(eps_max, eps_t_max, terms, lo_high, xs * sh.mh, xs * t_h, split ? 1e-6 : 1e-5, two_u,
+                               2e-6, tdm, status);
   kernels += 2;
   TArgs a{};
   a.p = p;
@@ -637,6 +673,7 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.nv = g.nv;
   a.nrx = g.nrx;
   a.m_rows = g.nv * g.nc;
+  a.t_c = t_c;
   a.bn = sh.bn;
   a.mt2 = sh.mt2;
   a.nt = sh.nt;
@@ -645,11 +682,16 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.terms = terms;
   a.lo_high = lo_high;
   a.status = status;
-  if (f16) split ? launch_taylor<true, true>(sh, a, s) : launch_taylor<true, false>(sh, a, s);
-  else split ? launch_taylor<false, true>(sh, a, s) : launch_taylor<false, false>(sh, a, s);
+  if (tdm) {
+    if (f16) split ? launch_taylor<true, true, true>(sh, a, s) : launch_taylor<true, false, true>(sh, a, s);
+    else split ? launch_taylor<false, true, true>(sh, a, s) : launch_taylor<false, false, true>(sh, a, s);
+  } else {
+    if (f16) split ? launch_taylor<true, true, false>(sh, a, s) : launch_taylor<true, false, false>(sh, a, s);
+    else split ? launch_taylor<false, true, false>(sh, a, s) : launch_taylor<false, false, false>(sh, a, s);
+  }
   ++kernels;
-  // the per-chirp kernel, which returns at once unless P = 0
-  kernels += launch_exact_main(g, p, n, workspace, status, s, terms);
+  // the per-chirp kernel, which returns at once unless P = 0 (it has no slot term: not with TDM)
+  if (!tdm) kernels += launch_exact_main(g, p, n, workspace, status, s, terms);
   if (after_main) cudaEventRecord(after_main, s);
   const int rb = 4 * sms_t();
   if (f16)
@@ -657,7 +699,7 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   else
     taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms);
   ++kernels;
-  kernels += launch_exact_reduce(g, n, sig, workspace, s, terms);
+  if (!tdm) kernels += launch_exact_reduce(g, n, sig, workspace, s, terms);
   return kernels;
 }
 

@@ -44,7 +44,8 @@ def _params(**kw):
     dict(n_tx=64, n_rx=32), dict(n_angle=2), dict(n_angle=24), dict(window=(0, 9, 0)),
     dict(precision=7), dict(outputs=0), dict(outputs=8), dict(max_rays=0), dict(max_rays=(1 << 21) + 1),
     dict(element_spacing_m=-0.001), dict(n_samples=4096, n_chirps=4096, n_angle=1024),
-    dict(model=2), dict(model=1, precision=2, tdm_slot_s=1e-5), dict(pattern_exp=17), dict(pattern_exp=-1),
+    dict(model=2), dict(model=1, precision=2, tdm_slot_s=1e-5, n_samples=16), dict(pattern_exp=17),
+    dict(pattern_exp=-1),
     dict(tdm_slot_s=-1e-6), dict(tdm_slot_s=float("nan")), dict(tdm_slot_s=2.0),
 ])
 def test_create_rejects_bad_params_without_a_gpu(bad):
@@ -52,6 +53,16 @@ def test_create_rejects_bad_params_without_a_gpu(bad):
     rc = rs.lib.sim_create(ctypes.byref(_params(**bad)), ctypes.byref(ctx))
     assert rc == rs.SIM_E_INVALID
     assert ctx.value is None
+
+
+def test_exact_model_with_tdm_slots_on_tensor_cores_is_accepted_from_32_samples():
+    """The exact model with TDM slot offsets runs on tensor cores through the per-tile
+    expansion, which needs tiles of at least 32 samples."""
+    for prec in (rs.SIM_PREC_BF16, rs.SIM_PREC_FP16_SPLIT):
+        ctx = ctypes.c_void_p()
+        rc = rs.lib.sim_create(ctypes.byref(_params(model=1, precision=prec, tdm_slot_s=1e-5)), ctypes.byref(ctx))
+        assert rc == rs.SIM_OK and ctx.value is not None
+        assert rs.lib.sim_destroy(ctx) == rs.SIM_OK
 
 
 def test_null_arguments():

@@ -277,19 +277,51 @@ def test_tdm_slot_offsets(precision, shape):
     assert rel_max(oracle.signal(radar.replace(tdm_slot_s=0.0), rays), ref) > 100 * tol
 
 
-def test_tdm_exact_model():
-    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=32, n_tx=3, n_rx=4, n_angle=16,
-                  tdm_slot_s=13.3e-6, model=1)
-    rays = scenegen.uniform_rays(seed=71, n=600, n_objects=4, v_max=30.0)
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape", [(64, 32, 3, 4, 16, 30.0), (128, 64, 4, 2, 8, 30.0), (64, 32, 3, 4, 16, 5.0)])
+def test_tdm_exact_model(precision, shape):
+    """Exact Eq. 2 with TDM slot offsets on every path: on tensor cores the slot term n t eps_t
+    joins the per-tile expansion (transmitters about their centre); eight terms at 30 m/s, four
+    at 5 m/s."""
+    ns, nc, ntx, nrx, na, v_max = shape
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na,
+                  tdm_slot_s=9.1e-6, model=1)
+    rays = scenegen.uniform_rays(seed=71 + ns, n=600, n_objects=4, v_max=v_max)
     ref = oracle.signal(radar, rays)
-    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT, model=rs.SIM_MODEL_EXACT)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
     try:
-        rc, sig, spec, lab = run(radar, rays, rs.SIM_PREC_FP32_DIRECT, ctx=ctx)
+        rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
     finally:
         ctx.close()
-    assert rc == rs.SIM_OK
-    assert rel_max(sig, ref) <= 1e-5 and rel_rms(sig, ref) <= 1e-5
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
     assert np.array_equal(lab, oracle.labels(radar, rays))
+    # both couplings matter: without the slot term, or without the migration, the cube is off
+    assert rel_max(oracle.signal(radar.replace(tdm_slot_s=0.0), rays), ref) > 1e-4
+    assert rel_max(oracle.signal(radar.replace(model=0), rays), ref) > 1e-4
+
+
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16])
+def test_tdm_exact_model_beyond_the_expansion_is_reported(precision):
+    """With TDM slots the exact model has no per-chirp tensor form, so a migration beyond the
+    eight-term bound is an error (invalid rays) rather than a silent approximation; the same
+    context then computes an ordinary scene."""
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=32, n_tx=3, n_rx=4, n_angle=16,
+                  tdm_slot_s=9.1e-6, model=1)
+    fast = scenegen.uniform_rays(seed=72, n=300, n_objects=4, v_max=2000.0)
+    slow = scenegen.uniform_rays(seed=73, n=300, n_objects=4, v_max=15.0)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, _, _, _ = run(radar, fast, precision, ctx=ctx)
+        assert rc == rs.SIM_E_INVALID
+        rc, sig, _, _ = run(radar, slow, precision, ctx=ctx)
+        assert rc == rs.SIM_OK
+        ref = oracle.signal(radar, slow)
+        assert rel_max(sig, ref) <= TOL[precision]
+    finally:
+        ctx.close()
 
 
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16,
