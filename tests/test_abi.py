@@ -55,16 +55,6 @@ def test_create_rejects_bad_params_without_a_gpu(bad):
     assert ctx.value is None
 
 
-def test_exact_model_with_tdm_slots_on_tensor_cores_is_accepted_from_32_samples():
-    """The exact model with TDM slot offsets runs on tensor cores through the per-tile
-    expansion, which needs tiles of at least 32 samples."""
-    for prec in (rs.SIM_PREC_BF16, rs.SIM_PREC_FP16_SPLIT):
-        ctx = ctypes.c_void_p()
-        rc = rs.lib.sim_create(ctypes.byref(_params(model=1, precision=prec, tdm_slot_s=1e-5)), ctypes.byref(ctx))
-        assert rc == rs.SIM_OK and ctx.value is not None
-        assert rs.lib.sim_destroy(ctx) == rs.SIM_OK
-
-
 def test_null_arguments():
     assert rs.lib.sim_create(None, None) == rs.SIM_E_INVALID
     assert rs.lib.sim_submit(None, None, None, None) == rs.SIM_E_INVALID
