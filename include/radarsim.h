@@ -87,9 +87,12 @@ extern "C" {
 /* signal model */
 #define SIM_MODEL_SEPARABLE 0     /* Eq. 2 without the range-migration product (a GEMM) */
 #define SIM_MODEL_EXACT 1         /* Eq. 2 with mu t (tau_i(j) - tau_i(0)): phase + n m eps_i,
-                                     eps_i = B 2 v_i T_d / (c N_s); any precision (the tensor-core
-                                     precisions compute it per chirp, samples x channels, and
-                                     need tdm_slot_s = 0) */
+                                     eps_i = B 2 v_i T_d / (c N_s); any precision.  The tensor-core
+                                     precisions expand the coupling about each output tile's centre
+                                     (4 or 8 Taylor terms, truncation <= 1e-6 of a contribution at
+                                     hi + lo, 1e-5 single pass); a scene beyond that bound runs per
+                                     chirp instead.  With tdm_slot_s > 0 they need n_samples >= 32,
+                                     and a scene beyond the bound is reported as SIM_E_INVALID. */
 
 /* outputs bitmask */
 #define SIM_OUT_SIGNAL 1
@@ -164,8 +167,9 @@ SIM_API int sim_submit(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta,
    slots free up): fetching it while no other fetch is under way and the queue head cannot
    be admitted returns SIM_E_BUSY at once (ticket kept) instead of waiting forever.
    Errors: SIM_E_UNKNOWN_TICKET, SIM_E_TIMEOUT / SIM_E_NOT_READY / SIM_E_BUSY (ticket kept),
-   SIM_E_INVALID (the scene held an invalid ray; ticket consumed), SIM_E_DEVICE,
-   SIM_E_CUDA. */
+   SIM_E_INVALID (the scene held an invalid ray, or - exact model with TDM slots on tensor
+   cores - a range migration beyond the expansion's bound; ticket consumed, outputs undefined),
+   SIM_E_DEVICE, SIM_E_CUDA. */
 SIM_API int sim_fetch(sim_ctx *ctx, uint64_t ticket, void *spectrum_c64, void *signal_c64,
               int32_t *labels, int32_t timeout_ms);
 

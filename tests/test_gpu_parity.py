@@ -303,6 +303,7 @@ def test_tdm_exact_model(precision, shape):
     assert rel_max(oracle.signal(radar.replace(model=0), rays), ref) > 1e-4
 
 
+@pytest.mark.filterwarnings("ignore:invalid value encountered in cast")  # a failed fetch's outputs are undefined
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16])
 def test_tdm_exact_model_beyond_the_expansion_is_reported(precision):
     """With TDM slots the exact model has no per-chirp tensor form, so a migration beyond the
