@@ -6,8 +6,9 @@
 // Forward, unnormalised, natural bin order.
 //
 // Each pass stages a tile of lines in shared memory (window fused into the load, in
-// bit-reversed order), runs an in-place radix-2 decimation-in-time FFT on all lines of
-// the tile, and writes the tile back.  Tiles are chosen so global accesses are
+// bit-reversed order; 16-byte global loads and stores, two complex samples each), runs an
+// in-place decimation-in-time FFT on all lines of the tile (radix-4 stages, one radix-2
+// stage for an odd log2 N), and writes the tile back.  Tiles are chosen so global accesses are
 // contiguous runs: whole rows for the range pass, 16-column strips for Doppler and
 // 32-column strips of the (m, n) plane for angle.  Twiddles e^{-2 pi i j/N} come from an
 // FP64 host table rounded to FP32.
@@ -24,38 +25,64 @@ __device__ __forceinline__ int bitrev(int t, int log2n) {
   return static_cast<int>(__brev(static_cast<unsigned>(t)) >> (32 - log2n));
 }
 
-// In-place radix-2 DIT butterflies over `lines` sequences of length N held at
-// x[pt * ps + line * ls], already in bit-reversed order.  LINE_FAST decides whether
-// consecutive threads walk lines (column tiles) or points (row tiles).
+// In-place radix-2 DIT FFT over `lines` sequences of length N held at x[pt * ps + line * ls],
+// already in bit-reversed order.  Stages go two at a time as radix-4 (2^2) butterflies: the
+// four points (base + t half), t = 0..3, of stages s and s + 1 stay in registers, with the
+// radix-2 twiddles of both stages (the same table entries and operations as one stage at a
+// time, so the same bits); an odd log2 N starts with one radix-2 stage.  LINE_FAST decides
+// whether consecutive threads walk lines (column tiles) or points (row tiles).
 template <bool LINE_FAST>
 __device__ void smem_fft(float2 *x, int N, int log2N, int lines, int ps, int ls,
                          const float2 *__restrict__ tw) {
-  const int half_n = N >> 1;
-  const int nb = half_n * lines;
-  for (int s = 1; s <= log2N; ++s) {
-    const int half = 1 << (s - 1);
-    const int tws = N >> s;
+  int s = 1;
+  if (log2N & 1) {  // stage 1: pairs (2i, 2i + 1), twiddle tw[0] = 1
+    const int nb = (N >> 1) * lines;
     __syncthreads();
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
       int line, bb;
       if (LINE_FAST) { line = b % lines; bb = b / lines; }
-      else { line = b / half_n; bb = b - line * half_n; }
-      const int j = bb & (half - 1);
-      const int i0 = ((bb >> (s - 1)) << s) + j;
-      const int i1 = i0 + half;
-      const float2 w = tw[j * tws];
-      float2 *p0 = x + i0 * ps + line * ls;
-      float2 *p1 = x + i1 * ps + line * ls;
+      else { line = b / (N >> 1); bb = b - line * (N >> 1); }
+      float2 *p0 = x + (2 * bb) * ps + line * ls;
+      float2 *p1 = p0 + ps;
       const float2 a = *p0;
-      const float2 t = cmul(w, *p1);
+      const float2 t = cmul(tw[0], *p1);
       *p0 = make_float2(a.x + t.x, a.y + t.y);
       *p1 = make_float2(a.x - t.x, a.y - t.y);
+    }
+    s = 2;
+  }
+  const int quarter = N >> 2;
+  const int ng = quarter * lines;
+  for (; s < log2N; s += 2) {
+    const int half = 1 << (s - 1);
+    const int tws = N >> s, tws1 = N >> (s + 1);
+    __syncthreads();
+    for (int b = threadIdx.x; b < ng; b += blockDim.x) {
+      int line, gq;
+      if (LINE_FAST) { line = b % lines; gq = b / lines; }
+      else { line = b / quarter; gq = b - line * quarter; }
+      const int j = gq & (half - 1);
+      const int i0 = ((gq >> (s - 1)) << (s + 1)) + j;
+      float2 *p0 = x + i0 * ps + line * ls;
+      float2 *p1 = p0 + half * ps, *p2 = p0 + 2 * half * ps, *p3 = p0 + 3 * half * ps;
+      const float2 w = tw[j * tws];                // stage s, both pairs
+      const float2 u = tw[j * tws1];               // stage s + 1, pair (0, 2)
+      const float2 v = tw[(j + half) * tws1];      // stage s + 1, pair (1, 3)
+      const float2 a0 = *p0, a2 = *p2;
+      const float2 t1 = cmul(w, *p1), t3 = cmul(w, *p3);
+      const float2 b0 = make_float2(a0.x + t1.x, a0.y + t1.y), b1 = make_float2(a0.x - t1.x, a0.y - t1.y);
+      const float2 b2 = make_float2(a2.x + t3.x, a2.y + t3.y), b3 = make_float2(a2.x - t3.x, a2.y - t3.y);
+      const float2 t2 = cmul(u, b2), t4 = cmul(v, b3);
+      *p0 = make_float2(b0.x + t2.x, b0.y + t2.y);
+      *p2 = make_float2(b0.x - t2.x, b0.y - t2.y);
+      *p1 = make_float2(b1.x + t4.x, b1.y + t4.y);
+      *p3 = make_float2(b1.x - t4.x, b1.y - t4.y);
     }
   }
   __syncthreads();
 }
 
-// range: lines are rows of N_s contiguous samples
+// range: lines are rows of N_s contiguous samples; 16-byte loads and stores (two samples)
 __global__ void __launch_bounds__(256) fft_range_kernel(const float2 *__restrict__ in, float2 *out,
                                                         const float *__restrict__ win,
                                                         const float2 *__restrict__ tw, int N, int log2N,
@@ -63,62 +90,80 @@ __global__ void __launch_bounds__(256) fft_range_kernel(const float2 *__restrict
   extern __shared__ float2 sm[];
   const int64_t line0 = static_cast<int64_t>(blockIdx.x) * lines_per_cta;
   const int lines = static_cast<int>(total_lines - line0 < lines_per_cta ? total_lines - line0 : lines_per_cta);
-  const float2 *src = in + line0 * N;
-  for (int e = threadIdx.x; e < lines * N; e += blockDim.x) {
-    const int l = e >> log2N, t = e & (N - 1);
-    const float2 v = src[e];
-    const float w = win[t];
-    sm[l * N + bitrev(t, log2N)] = make_float2(v.x * w, v.y * w);
+  const float4 *src = reinterpret_cast<const float4 *>(in + line0 * N);
+  for (int e = threadIdx.x; e < lines * N / 2; e += blockDim.x) {
+    const int i = 2 * e, l = i >> log2N, t = i & (N - 1);
+    const float4 v = src[e];
+    const float w0 = win[t], w1 = win[t + 1];
+    sm[l * N + bitrev(t, log2N)] = make_float2(v.x * w0, v.y * w0);
+    sm[l * N + bitrev(t + 1, log2N)] = make_float2(v.z * w1, v.w * w1);
   }
   smem_fft<false>(sm, N, log2N, lines, 1, N, tw);
-  float2 *dst = out + line0 * N;
-  for (int e = threadIdx.x; e < lines * N; e += blockDim.x) dst[e] = sm[e];
+  float4 *dst = reinterpret_cast<float4 *>(out + line0 * N);
+  for (int e = threadIdx.x; e < lines * N / 2; e += blockDim.x) {
+    const float2 a = sm[2 * e], b = sm[2 * e + 1];
+    dst[e] = make_float4(a.x, a.y, b.x, b.y);
+  }
 }
 
-// Doppler: a strip of TW consecutive samples n of one channel, all N_c chirps (in place)
+// Doppler: a strip of TW (even) consecutive samples n of one channel, all N_c chirps (in place);
+// 16-byte accesses cover two neighbouring samples
 __global__ void __launch_bounds__(256) fft_doppler_kernel(float2 *data, const float *__restrict__ win,
                                                           const float2 *__restrict__ tw, int Nc, int log2Nc,
                                                           int Ns, int TW) {
   extern __shared__ float2 sm[];
   float2 *base = data + static_cast<int64_t>(blockIdx.y) * Nc * Ns + static_cast<int64_t>(blockIdx.x) * TW;
-  for (int e = threadIdx.x; e < Nc * TW; e += blockDim.x) {
-    const int m = e / TW, c = e - m * TW;
-    const float2 v = base[static_cast<int64_t>(m) * Ns + c];
+  for (int e = threadIdx.x; e < Nc * TW / 2; e += blockDim.x) {
+    const int i = 2 * e, m = i / TW, c = i - m * TW;
+    const float4 v = *reinterpret_cast<const float4 *>(base + static_cast<int64_t>(m) * Ns + c);
     const float w = win[m];
-    sm[bitrev(m, log2Nc) * TW + c] = make_float2(v.x * w, v.y * w);
+    float2 *d = sm + bitrev(m, log2Nc) * TW + c;
+    d[0] = make_float2(v.x * w, v.y * w);
+    d[1] = make_float2(v.z * w, v.w * w);
   }
   smem_fft<true>(sm, Nc, log2Nc, TW, TW, 1, tw);
-  for (int e = threadIdx.x; e < Nc * TW; e += blockDim.x) {
-    const int m = e / TW, c = e - m * TW;
-    base[static_cast<int64_t>(m) * Ns + c] = sm[e];
+  for (int e = threadIdx.x; e < Nc * TW / 2; e += blockDim.x) {
+    const int i = 2 * e, m = i / TW, c = i - m * TW;
+    const float2 a = sm[i], b = sm[i + 1];
+    *reinterpret_cast<float4 *>(base + static_cast<int64_t>(m) * Ns + c) = make_float4(a.x, a.y, b.x, b.y);
   }
 }
 
-// angle: a strip of TW consecutive (m, n) positions, channels k < N_v, zero padded to N_a
+// angle: a strip of TW (even) consecutive (m, n) positions, channels k < N_v, zero padded to N_a
 __global__ void __launch_bounds__(256) fft_angle_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
                                                         const float *__restrict__ win,
                                                         const float2 *__restrict__ tw, int Nv, int Na,
                                                         int log2Na, int64_t plane, int TW) {
   extern __shared__ float2 sm[];
   const int64_t f0 = static_cast<int64_t>(blockIdx.x) * TW;
-  for (int e = threadIdx.x; e < Na * TW; e += blockDim.x) {
-    const int k = e / TW, c = e - k * TW;
-    float2 v = make_float2(0.f, 0.f);
+  for (int e = threadIdx.x; e < Na * TW / 2; e += blockDim.x) {
+    const int i = 2 * e, k = i / TW, c = i - k * TW;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (k < Nv) {
-      const float2 x = in[static_cast<int64_t>(k) * plane + f0 + c];
+      const float4 x = *reinterpret_cast<const float4 *>(in + static_cast<int64_t>(k) * plane + f0 + c);
       const float w = win[k];
-      v = make_float2(x.x * w, x.y * w);
+      v = make_float4(x.x * w, x.y * w, x.z * w, x.w * w);
     }
-    sm[bitrev(k, log2Na) * TW + c] = v;
+    float2 *d = sm + bitrev(k, log2Na) * TW + c;
+    d[0] = make_float2(v.x, v.y);
+    d[1] = make_float2(v.z, v.w);
   }
   smem_fft<true>(sm, Na, log2Na, TW, TW, 1, tw);
-  for (int e = threadIdx.x; e < Na * TW; e += blockDim.x) {
-    const int a = e / TW, c = e - a * TW;
-    out[static_cast<int64_t>(a) * plane + f0 + c] = sm[e];
+  for (int e = threadIdx.x; e < Na * TW / 2; e += blockDim.x) {
+    const int i = 2 * e, a = i / TW, c = i - a * TW;
+    const float2 p = sm[i], q = sm[i + 1];
+    *reinterpret_cast<float4 *>(out + static_cast<int64_t>(a) * plane + f0 + c) = make_float4(p.x, p.y, q.x, q.y);
   }
 }
 
 bool g_attr_done = false;
+
+// the largest power of two <= x, at least 2
+int pow2_floor_min2(int x) {
+  int p = 2;
+  while (p * 2 <= x) p *= 2;
+  return p;
+}
 
 }  // namespace
 
@@ -145,11 +190,13 @@ int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2
   const int64_t rb = (rows + lpc - 1) / lpc;
   fft_range_kernel<<<static_cast<unsigned>(rb), 256, sizeof(float2) * lpc * g.ns, s>>>(
       sig, tmp, t.win_r, t.tw_r, g.ns, g.log2_ns, lpc, rows);
-  // Doppler: strips of TW samples, N_c * TW * 8 bytes <= 64 KB
+  // Doppler: strips of TW samples, N_c * TW * 8 bytes <= 64 KB; TW a power of two >= 2 (the
+  // 16-byte accesses cover two samples)
   int twd = 8192 / g.nc;
   const int twd_pref = tu.fft_doppler_strip > 0 ? tu.fft_doppler_strip : 16;
   if (twd > twd_pref) twd = twd_pref;
   if (twd > g.ns) twd = g.ns;
+  twd = pow2_floor_min2(twd);
   dim3 gd(g.ns / twd, g.nv);
   fft_doppler_kernel<<<gd, 256, sizeof(float2) * g.nc * twd, s>>>(tmp, t.win_d, t.tw_d, g.nc, g.log2_nc, g.ns, twd);
   // angle: strips of TW positions of the (m, n) plane
@@ -157,6 +204,7 @@ int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2
   int twa = 8192 / g.na;
   const int twa_pref = tu.fft_angle_strip > 0 ? tu.fft_angle_strip : 32;
   if (twa > twa_pref) twa = twa_pref;
+  twa = pow2_floor_min2(twa);
   const int64_t ab = plane / twa;
   fft_angle_kernel<<<static_cast<unsigned>(ab), 256, sizeof(float2) * g.na * twa, s>>>(
       tmp, spec, t.win_a, t.tw_a, g.nv, g.na, g.log2_na, plane, twa);

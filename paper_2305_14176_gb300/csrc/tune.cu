@@ -253,6 +253,9 @@ extern "C" SIM_API int sim_tuning_load(const char *path) {
                "\"fft_angle_strip\": %d}",
                &nv, &nc, &ns, &na, &prec, &bucket, &sp, &rp, &dp, &ap) == 10) {
       if (sp < 0 || rp < 0 || dp < 0 || ap < 0 || sp > 65535 || rp > 4096 || dp > 4096 || ap > 4096) continue;
+      // FFT tile widths are powers of two (0 = built-in choice)
+      auto p2 = [](int x) { return x == 0 || (x & (x - 1)) == 0; };
+      if (!p2(rp) || !p2(dp) || !p2(ap)) continue;
       g_table[Key(nv, nc, ns, na, prec, bucket)] = Tuning{sp, rp, dp, ap};
       ++loaded;
     }

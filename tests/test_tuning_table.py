@@ -12,7 +12,11 @@ def test_tuning_table_round_trip(tmp_path):
             dict(n_virtual=4, n_chirps=64, n_samples=128, n_angle=16, precision=2, ray_bucket=11, splits=7,
                  fft_range_points=0, fft_doppler_strip=8, fft_angle_strip=0),
             dict(n_virtual=4, n_chirps=64, n_samples=128, n_angle=16, precision=2, ray_bucket=12, splits=-3,
-                 fft_range_points=0, fft_doppler_strip=8, fft_angle_strip=0)]  # invalid: skipped
+                 fft_range_points=0, fft_doppler_strip=8, fft_angle_strip=0),   # invalid: skipped
+            dict(n_virtual=4, n_chirps=64, n_samples=128, n_angle=16, precision=2, ray_bucket=13, splits=3,
+                 fft_range_points=0, fft_doppler_strip=3, fft_angle_strip=0),   # odd strip: skipped
+            dict(n_virtual=4, n_chirps=64, n_samples=128, n_angle=16, precision=2, ray_bucket=14, splits=3,
+                 fft_range_points=1000, fft_doppler_strip=8, fft_angle_strip=0)]  # not a power of two: skipped
     with open(src, "w") as f:
         f.write("[\n" + ",\n".join("  " + json.dumps(r) for r in rows) + "\n]\n")
     assert rs.sim_tuning_load(str(src)) == rs.SIM_OK
