@@ -12,8 +12,8 @@
 //
 // Operands are never stored in HBM: three groups of producer warps synthesise the A and B
 // tiles of a stage of 32 rays straight into shared memory (Q0.64 phases from the prep
-// kernel, one FP32 sin/cos per phasor chain, then FP32 complex steps of 16 chirps or 16
-// samples with the prep kernel's FP64-accurate step phasors, rounded to BF16 or FP16 and
+// kernel, one FP32 sin/cos per phasor chain, then FP32 complex steps of 32 chirps or 32
+// samples with the prep kernel's step phasors (exact Q0.64 phase, ~1.5 ulp), rounded to BF16 or FP16 and
 // optionally split into hi + lo), in the no-swizzle K-major core-matrix layout.  One thread
 // issues tcgen05.mma (kind::f16, FP32 accumulation in tensor memory).  Four drain warps add
 // each finished accumulation chain (at most 16 stages, 512 rays, for split precision: the
@@ -138,8 +138,8 @@ __device__ __forceinline__ void group_sync(int g) {
 //   j = t % 32: A rows j, j + 32, j + 64, j + 96 and B columns j, j + 32, ... below NC, so the
 //   work is even across the group and each warp's 16-byte stores cover 512 contiguous bytes.
 //   Each phasor chain starts from one hardware sin/cos of its exact Q0.64 phase and steps 32
-//   chirps / 32 samples per complex multiply with the FP64-accurate e^{2 pi j 32 nu} of the
-//   prep kernel.
+//   chirps / 32 samples per complex multiply with the prep kernel's e^{2 pi j 32 nu} (from the
+//   exact Q0.64 product, within ~1.5 ulp).
 //   PAIR: this CTA holds B for its half of the tile's complex columns (NC = bn / 4 of them).
 template <bool F16, bool SPLIT, bool FAST, bool PAIR>
 __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &sr, uint8_t *stage, int gt, int row0,
