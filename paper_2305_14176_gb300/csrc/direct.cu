@@ -233,9 +233,14 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
   }
 }
 
-// Threads per row: 64 (two warps) with up to 32 samples each; N_s = 4096 takes 128 threads.
-// N_s is a power of two in 16 .. 4096, so the samples per thread are 1, 2, .., 32.
-int row_threads(int ns) { return ns <= 64 ? ns : (ns / 32 > 64 ? ns / 32 : 64); }
+// Threads per row, N_s a power of two in 16 .. 4096 (samples per thread 1, 2, .., 32).
+// Separable sum: one warp with up to 32 samples each, N_s > 1024 taking N_s / 32 threads (the
+// per-ray start of a phasor chain, one sin/cos and a 64-bit phase product, is shared by more
+// samples: 80.5 -> 76.1 ms per automotive frame against two warps).  Snapshot sum: two warps,
+// whose staging (two phase words and a sin/cos per ray) needs the wider block (one warp:
+// 76.9 -> 78.9 ms).
+int row_threads(int ns) { return ns <= 32 ? ns : (ns / 32 > 32 ? ns / 32 : 32); }
+int pair_row_threads(int ns) { return ns <= 64 ? ns : (ns / 32 > 64 ? ns / 32 : 64); }
 
 }  // namespace
 
@@ -259,7 +264,7 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cuda
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
                     int64_t stride, bool accumulate, float2 *sig, cudaStream_t s) {
   const int rows = g.nv * g.nc;
-  const int threads = row_threads(g.ns);
+  const int threads = pair_row_threads(g.ns);
   const int acc = accumulate ? 1 : 0;
 #define RS_PAIR(N) pair_sum_kernel<N><<<rows, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, g.nc, g.ns, g.ntx, g.nrx, acc, sig)
   switch (g.ns / threads) {
