@@ -143,10 +143,23 @@ def cpu_oracle_rate(radar, rays, seconds: float = 10.0, seed: int = 17):
     n_pts = int(max(64, min(n_out, 64 * seconds / dt)))
     idx = scenegen.randint(seed, 2, n_pts, 0, n_out - 1).astype(np.int64)
     t0 = time.perf_counter()
-    oracle.signal_at(radar, rays, idx)
+    ref = oracle.signal_at(radar, rays, idx)
     dt = time.perf_counter() - t0
     rate = n_pts * rays.n / dt
-    return rate, n_pts, dt, oracle.threads()
+    return rate, n_pts, dt, oracle.threads(), idx, ref
+
+
+def result_error(radar, rays, sig_h, lab_h, idx, ref):
+    """The frame's error against the FP64 oracle: normwise max and RMS relative error of the
+    signal on the oracle's sampled output points, and whether every label matches."""
+    import oracle
+    flat = sig_h.reshape(-1, 2)[idx]
+    got = flat[:, 0].astype(np.float64) + 1j * flat[:, 1].astype(np.float64)
+    d = np.abs(got - ref)
+    return {"vs": "FP64 oracle", "points": int(len(idx)),
+            "max_rel": float(d.max() / max(np.abs(ref).max(), 1e-300)),
+            "rms_rel": float(np.sqrt(np.sum(d * d) / max(np.sum(np.abs(ref) ** 2), 1e-300))),
+            "labels_exact": bool(np.array_equal(lab_h, oracle.labels(radar, rays)))}
 
 
 def run_reference(args, world, rank):
@@ -599,6 +612,10 @@ def main():
             kernels += rs.sim_last_kernel_count(ctx.ctx)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
+    # the last timed frame's outputs, for its error against the oracle (outside the timed region)
+    want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    sig_h = sig.cpu().numpy() if want_cpu else None
+    lab_h = lab.cpu().numpy() if want_cpu else None
     if world > 1:
         dist.barrier()
     dev_s = sum(totals) / 1e3
@@ -682,12 +699,13 @@ def main():
                 "frac": achieved / DIRECT_PEAK_TCONTRIB, "traffic": None, "kernel": "direct_sum_kernel",
                 "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, pts, secs, cores = cpu_oracle_rate(radar, rays, args.cpu_seconds)
+    cpu, error = None, None
+    if want_cpu:
+        rate, pts, secs, cores, idx, ref = cpu_oracle_rate(radar, rays, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{pts} of {radar.n_virtual * radar.n_chirps * radar.n_samples} output points x "
                          f"{n} rays, FP64 direct sum, {secs:.1f} s"}
+        error = result_error(radar, rays, sig_h, lab_h, idx, ref)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -706,6 +724,7 @@ def main():
         "gpu_launches": kernels,
         "roofline": roof,
         "cpu_baseline": cpu,
+        "error": error,
         "clocks": clk.summary(),
         "wall_s_timed": wall,
     }
