@@ -228,13 +228,11 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     cudaFree(b);
     return SIM_E_CUDA;
   }
-  void *ws = nullptr;     // tensor-core scratch (span after span)
-  uint8_t *bb = nullptr;  // batched spans: packed prep, workspaces, signals, batch descriptors
+  void *ws = nullptr;  // tensor-core scratch
   auto finish = [&](int rc) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (ws) cudaFree(ws);
-    if (bb) cudaFree(bb);
     cudaFree(b);
     cudaGetLastError();
     return rc;
@@ -311,119 +309,33 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   cudaEventRecord(ev[1], s);
   if (n > 0) cudaMemcpyAsync(sizes.data(), tot, 4 * sizes.size(), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return finish(SIM_E_CUDA);
-  float2 *sig = reinterpret_cast<float2 *>(b + o_sig);
-  float2 *spectra = reinterpret_cast<float2 *>(b + o_spec);
-  // Separable model on tensor cores: every non-empty span gets its own packed prep words,
-  // ray-sum workspace and signal, and all spans' work units run in one persistent launch (the
-  // batch path: each span's units are those of its own launch, so the bits are the same).
-  // Otherwise, or if that memory cannot be had, span after span.
-  std::vector<int> live;
-  for (int h = 0; h < n_spans; ++h)
-    if (sizes[h] > 0) live.push_back(h);
-  if (tensor && g.model == SIM_MODEL_SEPARABLE && live.size() > 1) {
-    std::vector<size_t> o_prep(live.size()), o_ws(live.size()), o_sg(live.size());
-    size_t boff2 = 0;
-    auto take2 = [&](size_t bytes) {
-      const size_t o = boff2;
-      boff2 += round256(bytes > 0 ? bytes : 1);
-      return o;
-    };
-    int64_t units = 0;
-    for (size_t q = 0; q < live.size(); ++q) {
-      const int64_t nh = sizes[live[q]];
-      const size_t upq = (static_cast<size_t>(nh) + 31) / 32 * 32;
-      o_prep[q] = take2(60 * upq);  // carrier, nu_r, nu_d, nu_a, nu_tx (8 B), step_d, step_r (8 B), amp (4 B)
-      o_ws[q] = take2(static_cast<size_t>(umma_workspace_bytes(g, nh)));
-      o_sg[q] = take2(8 * static_cast<size_t>(g.n_sig));
-      units += umma_units_of(g, nh);
-    }
-    const size_t o_scr = take2(static_cast<size_t>(umma_batch_scratch_bytes(static_cast<int>(live.size()), units)));
-    if (cudaMalloc(&bb, boff2) != cudaSuccess) {
-      cudaGetLastError();
-      bb = nullptr;  // span after span instead
-    } else {
-      std::vector<RaysPrep> ps(live.size());
-      std::vector<const Derived *> gs(live.size(), &g);
-      std::vector<int64_t> ns(live.size());
-      std::vector<void *> wss(live.size());
-      std::vector<uint32_t *> sts(live.size(), status);
-      for (size_t q = 0; q < live.size(); ++q) {
-        const int h = live[q];
-        const size_t upq = (static_cast<size_t>(sizes[h]) + 31) / 32 * 32;
-        uint8_t *pb = bb + o_prep[q];
-        RaysPrep &pq = ps[q];
-        pq = cp;
-        pq.carrier = reinterpret_cast<uint64_t *>(pb);
-        pq.nu_r = reinterpret_cast<uint64_t *>(pb + 8 * upq);
-        pq.nu_d = reinterpret_cast<uint64_t *>(pb + 16 * upq);
-        pq.nu_a = reinterpret_cast<uint64_t *>(pb + 24 * upq);
-        pq.nu_tx = reinterpret_cast<uint64_t *>(pb + 32 * upq);
-        pq.step_d = reinterpret_cast<float2 *>(pb + 40 * upq);
-        pq.step_r = reinterpret_cast<float2 *>(pb + 48 * upq);
-        pq.amp = reinterpret_cast<float *>(pb + 56 * upq);
-        pq.eps = nullptr;
-        pq.eps_t = nullptr;
-        ns[q] = sizes[h];
-        wss[q] = bb + o_ws[q];
-        span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, s>>>(rp, pq, dobj, dmat, dhit, n, drules + h,
-                                                                            boff + static_cast<int64_t>(h) * nb);
-        ++kernels;
-      }
-      UmmaBatch ub{};
-      if (prepare_umma_batch(static_cast<int>(live.size()), gs.data(), ps.data(), ns.data(), wss.data(), sts.data(),
-                             bb + o_scr, s, &ub) != SIM_OK)
-        return finish(SIM_E_CUDA);
-      for (size_t q = 0; q < live.size(); ++q) kernels += launch_umma_pre(g, ps[q], ns[q], wss[q], s);
-      kernels += launch_umma_batch(ub, s);
-      for (size_t q = 0; q < live.size(); ++q)
-        kernels += launch_umma_post(g, ns[q], reinterpret_cast<float2 *>(bb + o_sg[q]), wss[q], s);
-      cudaEventRecord(ev[2], s);
-      size_t q = 0;
-      for (int h = 0; h < n_spans; ++h) {
-        if (h > 0) cudaEventRecord(ev[2 + 2 * h], s);  // the sums all ran above
-        const float2 *sh = nullptr;
-        if (q < live.size() && live[q] == h) {
-          sh = reinterpret_cast<const float2 *>(bb + o_sg[q]);
-          ++q;
-        } else {
-          cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
-          sh = sig;
-        }
-        float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
-        kernels += launch_fft(g, ctx->t, sh, reinterpret_cast<float2 *>(b + o_tmp), x, s);
-        if (span_spectra && span_spectra[h])
-          cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-        cudaEventRecord(ev[3 + 2 * h], s);
-      }
+  if (tensor) {
+    int64_t need = 0;
+    for (uint32_t nh : sizes)
+      if (nh > 0) need = std::max<int64_t>(need, umma_workspace_bytes(g, static_cast<int64_t>(nh)));
+    if (need > 0 && cudaMalloc(&ws, static_cast<size_t>(need)) != cudaSuccess) {
+      ws = nullptr;
+      return finish(SIM_E_NOMEM);
     }
   }
-  if (!bb) {
-    if (tensor) {
-      int64_t need = 0;
-      for (uint32_t nh : sizes)
-        if (nh > 0) need = std::max<int64_t>(need, umma_workspace_bytes(g, static_cast<int64_t>(nh)));
-      if (need > 0 && cudaMalloc(&ws, static_cast<size_t>(need)) != cudaSuccess) {
-        ws = nullptr;
-        return finish(SIM_E_NOMEM);
-      }
+  float2 *sig = reinterpret_cast<float2 *>(b + o_sig);
+  float2 *spectra = reinterpret_cast<float2 *>(b + o_spec);
+  for (int h = 0; h < n_spans; ++h) {
+    const int64_t nh = sizes[h];
+    if (nh > 0) {
+      span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, s>>>(rp, cp, dobj, dmat, dhit, n, drules + h,
+                                                                          boff + static_cast<int64_t>(h) * nb);
+      kernels += 1 + (tensor ? launch_umma_sum(g, cp, nh, sig, ws, status, s, nullptr)
+                             : launch_direct_sum(g, cp, nh, sig, s));
+    } else {
+      cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
     }
-    for (int h = 0; h < n_spans; ++h) {
-      const int64_t nh = sizes[h];
-      if (nh > 0) {
-        span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, s>>>(rp, cp, dobj, dmat, dhit, n, drules + h,
-                                                                            boff + static_cast<int64_t>(h) * nb);
-        kernels += 1 + (tensor ? launch_umma_sum(g, cp, nh, sig, ws, status, s, nullptr)
-                               : launch_direct_sum(g, cp, nh, sig, s));
-      } else {
-        cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
-      }
-      cudaEventRecord(ev[2 + 2 * h], s);
-      float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
-      kernels += launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + o_tmp), x, s);
-      if (span_spectra && span_spectra[h])
-        cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-      cudaEventRecord(ev[3 + 2 * h], s);
-    }
+    cudaEventRecord(ev[2 + 2 * h], s);
+    float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
+    kernels += launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + o_tmp), x, s);
+    if (span_spectra && span_spectra[h])
+      cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+    cudaEventRecord(ev[3 + 2 * h], s);
   }
   if (span_labels) {
     const int64_t all = g.n_cell * n_spans;
