@@ -79,11 +79,14 @@ def test_partition_parts_add_up_to_the_scene():
 
 
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16])
-def test_span_part_is_the_scene_of_its_rays(precision):
+@pytest.mark.parametrize("model", [rs.SIM_MODEL_SEPARABLE, rs.SIM_MODEL_EXACT])
+def test_span_part_is_the_scene_of_its_rays(precision, model):
     """A span's rays are packed in ray order and summed alone, so its spectrum is bit for bit
-    the spectrum of a scene holding only those rays; an empty span gives zeros."""
+    the spectrum of a scene holding only those rays; an empty span gives zeros.  The exact
+    model's packed spans carry the range-migration words too."""
     radar, rays, mat, hits = _scene(24, 1400)
-    ctx = rs.Context(radar, precision=precision)
+    radar = radar.replace(model=model)
+    ctx = rs.Context(radar, precision=precision, model=model)
     try:
         arr = {k: np.ascontiguousarray(v) for k, v in dict(rays.arrays(), material_id=mat, n_hits=hits).items()}
         r, m = rs.make_rays(arr, rays.n)

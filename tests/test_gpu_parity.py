@@ -383,6 +383,26 @@ def test_exact_model_tensor_core_regimes(precision, case):
     assert rel_max(oracle.signal(radar.replace(model=0), rays), ref) > 10 * tol
 
 
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16])
+@pytest.mark.parametrize("shape", [(4096, 4, 1, 2, 2), (64, 2, 1, 1, 1), (256, 512, 2, 2, 4)])
+def test_exact_model_tensor_core_size_extremes(precision, shape):
+    """The expansion at the edges of the radar sizes: 4096 samples (16 column tiles of 256),
+    two chirps with one channel (the tile's rows are mostly past M), and 512 chirps of four
+    channels (64 chirps per 256-row tile, eight terms)."""
+    ns, nc, ntx, nrx, na = shape
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na, model=1)
+    rays = scenegen.uniform_rays(seed=ns + nc, n=150, n_objects=3, v_max=15.0)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, _, lab = run(radar, rays, precision, ctx=ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    assert rel_max(sig, ref) <= TOL[precision] and rel_rms(sig, ref) <= TOL_RMS[precision]
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT])
 def test_exact_model_tensor_core_automotive_sampled(precision):
     """Full automotive radar size (four expansion terms): at FP16 hi + lo the third and fourth
