@@ -98,6 +98,8 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   // the tensor-core path needs room for at least one FP32 partial of the whole cube
   const int64_t one_split = 256 + 8 * g.n_sig;
   if (g.precision != SIM_PREC_FP32_DIRECT && one_split > ws_bytes) return SIM_E_INVALID;
+  // the per-chirp exact form used here has no TDM slot term
+  if (g.model == SIM_MODEL_EXACT && g.precision != SIM_PREC_FP32_DIRECT && g.tslot != 0.0) return SIM_E_INVALID;
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float2 *sig = static_cast<float2 *>(signal_c64);
