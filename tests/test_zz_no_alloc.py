@@ -59,3 +59,7 @@ def test_noalloc_rejects_oversize_and_host_pointers():
     big = torch.empty(16, dtype=torch.float32, device="cuda")  # never written: rejected first
     assert rs.sim_raysum_noalloc(rs.make_params(img, precision=rs.SIM_PREC_BF16_SPLIT,
                                                 outputs=rs.SIM_OUT_SIGNAL), r, big, stream) == rs.SIM_E_INVALID
+    # the exact model with TDM slots has no allocation-free tensor-core form
+    tdm = rs.make_params(radar.replace(tdm_slot_s=9.1e-6), precision=rs.SIM_PREC_BF16_SPLIT,
+                         outputs=rs.SIM_OUT_SIGNAL, model=rs.SIM_MODEL_EXACT)
+    assert rs.sim_raysum_noalloc(tdm, r, big, stream) == rs.SIM_E_INVALID
