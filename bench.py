@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -529,7 +530,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-points", type=int, default=2048)
-    ap.add_argument("--clocks-csv", default=os.path.join(ROOT, "gpurun_out", "bench_clocks.csv"))
+    ap.add_argument("--clocks-csv",
+                    default=os.path.join(os.environ.get("RADARSIM_ARTIFACT_DIR") or tempfile.gettempdir(),
+                                         "bench_clocks.csv"),
+                    help="nvidia-smi clock samples of the timed region (kept for inspection)")
     ap.add_argument("--workload", default="automotive",
                     choices=["automotive", "batch", "serve", "snapshot", "decompose"])
     ap.add_argument("--model", default="separable", choices=["separable", "exact"],

@@ -1,6 +1,7 @@
 """Precision study: the automotive frame scaled to 1,000,000 rays, every ray-sum variant
 against the FP64 oracle at 512 sampled signal points (all rays each) and labels whole.
-The table is written to gpurun_out/precision_study.json when that folder exists."""
+The table is also written to $RADARSIM_ARTIFACT_DIR/precision_study.json when that variable
+names a folder."""
 import json
 import os
 
@@ -29,8 +30,8 @@ def test_precision_study_one_million_rays():
         got = sig.reshape(-1)[idx]
         table[name] = {"max_rel": rel_max(got, ref), "rms_rel": rel_rms(got, ref),
                        "labels_exact": bool(np.array_equal(lab, ref_lab))}
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("RADARSIM_ARTIFACT_DIR", "")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "precision_study.json"), "w") as f:
             json.dump({"rays": rays.n, "points": int(idx.size), "variants": table}, f, indent=1)
     for name, prec in rs.PRECISION_NAMES.items():
