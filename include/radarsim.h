@@ -252,8 +252,9 @@ typedef struct {
    segmentation of each span image; ties to the lower h), -1 if none passes.  0 <= threshold
    <= 1.  Rays and meta: host or device, as for sim_submit.  Synchronous; allocates its own
    working memory outside the engine's budget.  Each span's rays are packed in ray order and
-   summed alone, so a span costs its own ray count and its part is bit for bit the scene of its
-   rays alone; the parts of spans that partition the rays add up to the whole scene (Eq. 5).
+   summed alone (up to four spans at once, on their own streams), so a span costs its own ray
+   count and its part is bit for bit the scene of its rays alone; the parts of spans that
+   partition the rays add up to the whole scene (Eq. 5).
    Errors: SIM_E_INVALID (bad rule, missing meta a rule needs, bad ray), SIM_E_NOMEM,
    SIM_E_CUDA, SIM_E_DEVICE. */
 SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, int32_t n_spans,
@@ -276,9 +277,9 @@ SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int
    Entries for stages that did not run are 0.  sim_snapshot_run also records its
    stages here: [1] holds the prep and the path / phase-word kernels, [2] the direct
    sums, [6] prep to labels (its input copies happen before, synchronously).  So does a
-   successful sim_decompose: [1] prep and the span sizes, [2] every span's packing and ray
-   sum, [4] every span's FFTs, [5] the span labels, [6] prep to labels (including the wait for
-   the span sizes and the allocation of the ray-sum scratch). */
+   successful sim_decompose: [1] prep and the span sizes, [2] the spans' packing, ray sums
+   and FFTs (they overlap on up to four streams), [5] the span labels, [6] prep to labels
+   (including the wait for the span sizes and the allocation of the spans' scratch). */
 SIM_API int sim_last_stage_ms(sim_ctx *ctx, float *ms, int32_t n);
 
 /* Number of kernels the most recently fetched ticket of this context launched (or the last

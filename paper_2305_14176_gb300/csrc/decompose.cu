@@ -13,7 +13,8 @@
 // every span, a scan, one read-back of the span sizes, a stable gather) and summed alone
 // through the context's ray-sum arithmetic (direct or tensor core): a span costs its own ray
 // count, so the spans of a partition cost one scene's ray sums together, and a span's part is
-// bit for bit the scene of its rays alone.
+// bit for bit the scene of its rays alone.  Spans run on up to four streams at once, each with
+// its own packed prep, workspace, signal and FFT scratch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,6 +43,7 @@ __device__ __forceinline__ bool in_span(const RuleDev &r, const int32_t *obj, co
 }
 
 constexpr int kSpanBlock = 1024;  // rays per compaction block (one thread each)
+constexpr int kLanes = 4;         // spans summed concurrently (streams)
 
 // cnt[h nb + b]: rays of block b in span h (grid nb x n_spans)
 __global__ void __launch_bounds__(kSpanBlock) span_count_kernel(const int32_t *__restrict__ obj,
@@ -189,8 +191,8 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                 !rays->elevation_rad || !rays->phase0_rad))
     return SIM_E_INVALID;
 
-  // device workspace: inputs, meta, prep, the packed prep of one span, compaction counts,
-  // signal, FFT scratch, spectra (the tensor-core scratch follows once the span sizes are known)
+  // device workspace: inputs, meta, prep, compaction counts, spectra, labels (the lanes' blocks
+  // follow once the span sizes are known)
   const size_t un = static_cast<size_t>(n), up = (un + 31) / 32 * 32;
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
   const bool exact = g.model == SIM_MODEL_EXACT;
@@ -209,13 +211,9 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                o_amp = take(4 * up), o_cell = take(4 * up), o_en = take(8 * up), o_sd = take(8 * up),
                o_sr = take(8 * up), o_eps = take(exact ? 8 * up : 0), o_ntx = take(8 * up),
                o_epst = take(exact ? 8 * up : 0);
-  const size_t c_car = take(8 * up), c_nur = take(8 * up), c_nud = take(8 * up), c_nua = take(8 * up),
-               c_amp = take(4 * up), c_sd = take(8 * up), c_sr = take(8 * up), c_eps = take(exact ? 8 * up : 0),
-               c_ntx = take(8 * up), c_epst = take(exact ? 8 * up : 0);
   const size_t o_rules = take(sizeof(RuleDev) * static_cast<size_t>(n_spans)), o_cnt = take(4 * ub),
                o_off = take(4 * ub), o_tot = take(4 * static_cast<size_t>(n_spans));
   const size_t o_status = take(256), o_max = take(256);
-  const size_t o_sig = take(8 * static_cast<size_t>(g.n_sig)), o_tmp = take(8 * static_cast<size_t>(g.n_sig));
   const size_t o_spec = take(8 * static_cast<size_t>(g.n_cell) * static_cast<size_t>(n_spans));
   const size_t o_lab = take(4 * static_cast<size_t>(g.n_cell));
   uint8_t *b = nullptr;
@@ -228,8 +226,18 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     cudaFree(b);
     return SIM_E_CUDA;
   }
-  void *ws = nullptr;  // tensor-core scratch
+  void *ws = nullptr;  // the lanes' blocks: packed prep, ray-sum workspace, signal, FFT scratch
+  cudaStream_t lane_s[kLanes] = {};
+  cudaEvent_t lane_done[kLanes] = {};
+  for (int l = 1; l < kLanes; ++l) cudaEventCreateWithFlags(&lane_done[l], cudaEventDisableTiming);
   auto finish = [&](int rc) {
+    for (int l = 1; l < kLanes; ++l) {
+      if (lane_s[l]) {
+        cudaStreamSynchronize(lane_s[l]);
+        cudaStreamDestroy(lane_s[l]);
+      }
+      if (lane_done[l]) cudaEventDestroy(lane_done[l]);
+    }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
     if (ws) cudaFree(ws);
@@ -277,14 +285,8 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
               reinterpret_cast<uint64_t *>(b + o_en), reinterpret_cast<float2 *>(b + o_sd),
               reinterpret_cast<float2 *>(b + o_sr), exact ? reinterpret_cast<uint64_t *>(b + o_eps) : nullptr,
               reinterpret_cast<uint64_t *>(b + o_ntx), exact ? reinterpret_cast<uint64_t *>(b + o_epst) : nullptr};
-  // the packed span: its own copies of every word a ray sum reads (cell and energy unused)
-  RaysPrep cp{reinterpret_cast<uint64_t *>(b + c_car), reinterpret_cast<uint64_t *>(b + c_nur),
-              reinterpret_cast<uint64_t *>(b + c_nud), reinterpret_cast<uint64_t *>(b + c_nua),
-              reinterpret_cast<float *>(b + c_amp), rp.cell, rp.energy, reinterpret_cast<float2 *>(b + c_sd),
-              reinterpret_cast<float2 *>(b + c_sr), exact ? reinterpret_cast<uint64_t *>(b + c_eps) : nullptr,
-              reinterpret_cast<uint64_t *>(b + c_ntx), exact ? reinterpret_cast<uint64_t *>(b + c_epst) : nullptr};
-  // events: start, after the span sizes, per span (after its sum, after its FFT), after labels
-  std::vector<cudaEvent_t> ev(static_cast<size_t>(3 + 2 * n_spans), nullptr);
+  // events: start, after the span sizes, after every span's sum and FFT, after the labels
+  std::vector<cudaEvent_t> ev(4, nullptr);
   for (auto &e : ev) cudaEventCreate(&e);
   struct EventsGuard {
     std::vector<cudaEvent_t> &v;
@@ -309,34 +311,76 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   cudaEventRecord(ev[1], s);
   if (n > 0) cudaMemcpyAsync(sizes.data(), tot, 4 * sizes.size(), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return finish(SIM_E_CUDA);
-  if (tensor) {
-    int64_t need = 0;
+  // Spans run on up to kLanes streams at once.  Each lane has its own packed prep, ray-sum
+  // workspace, signal and FFT scratch, so small spans' launches fill each other's gaps on the
+  // device while every span's arithmetic stays what it would be alone.
+  int live = 0;
+  for (uint32_t nh : sizes) live += nh > 0 ? 1 : 0;
+  int lanes = std::max(1, std::min(kLanes, live));
+  int64_t need = 0;
+  if (tensor)
     for (uint32_t nh : sizes)
       if (nh > 0) need = std::max<int64_t>(need, umma_workspace_bytes(g, static_cast<int64_t>(nh)));
-    if (need > 0 && cudaMalloc(&ws, static_cast<size_t>(need)) != cudaSuccess) {
-      ws = nullptr;
-      return finish(SIM_E_NOMEM);
-    }
+  const size_t l_prep = round256((exact ? 76 : 60) * up), l_ws = round256(static_cast<size_t>(need)),
+               l_sig = round256(8 * static_cast<size_t>(g.n_sig));
+  const size_t lane_bytes = l_prep + l_ws + 2 * l_sig;  // prep, workspace, signal, FFT scratch
+  while (cudaMalloc(&ws, lane_bytes * static_cast<size_t>(lanes)) != cudaSuccess) {
+    cudaGetLastError();
+    ws = nullptr;
+    if (lanes == 1) return finish(SIM_E_NOMEM);
+    lanes = 1;
   }
-  float2 *sig = reinterpret_cast<float2 *>(b + o_sig);
+  for (int l = 1; l < lanes; ++l) {
+    if (cudaStreamCreateWithFlags(&lane_s[l], cudaStreamNonBlocking) != cudaSuccess) return finish(SIM_E_CUDA);
+    cudaStreamWaitEvent(lane_s[l], ev[1], 0);  // after prep and the span sizes
+  }
+  lane_s[0] = s;
+  auto lane_prep = [&](int l) {
+    uint8_t *pb = static_cast<uint8_t *>(ws) + static_cast<size_t>(l) * lane_bytes;
+    RaysPrep q = rp;  // a packed span: its own copies of every word a ray sum reads (cell and
+                      // energy stay the scene's, unused)
+    q.carrier = reinterpret_cast<uint64_t *>(pb);
+    q.nu_r = reinterpret_cast<uint64_t *>(pb + 8 * up);
+    q.nu_d = reinterpret_cast<uint64_t *>(pb + 16 * up);
+    q.nu_a = reinterpret_cast<uint64_t *>(pb + 24 * up);
+    q.nu_tx = reinterpret_cast<uint64_t *>(pb + 32 * up);
+    q.step_d = reinterpret_cast<float2 *>(pb + 40 * up);
+    q.step_r = reinterpret_cast<float2 *>(pb + 48 * up);
+    q.amp = reinterpret_cast<float *>(pb + 56 * up);
+    q.eps = exact ? reinterpret_cast<uint64_t *>(pb + 60 * up) : nullptr;
+    q.eps_t = exact ? reinterpret_cast<uint64_t *>(pb + 68 * up) : nullptr;
+    return q;
+  };
   float2 *spectra = reinterpret_cast<float2 *>(b + o_spec);
+  int next = 0;
   for (int h = 0; h < n_spans; ++h) {
     const int64_t nh = sizes[h];
-    if (nh > 0) {
-      span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, s>>>(rp, cp, dobj, dmat, dhit, n, drules + h,
-                                                                          boff + static_cast<int64_t>(h) * nb);
-      kernels += 1 + (tensor ? launch_umma_sum(g, cp, nh, sig, ws, status, s, nullptr)
-                             : launch_direct_sum(g, cp, nh, sig, s));
-    } else {
-      cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
-    }
-    cudaEventRecord(ev[2 + 2 * h], s);
     float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
-    kernels += launch_fft(g, ctx->t, sig, reinterpret_cast<float2 *>(b + o_tmp), x, s);
-    if (span_spectra && span_spectra[h])
-      cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-    cudaEventRecord(ev[3 + 2 * h], s);
+    if (nh > 0) {
+      const int l = next++ % lanes;
+      cudaStream_t sl = lane_s[l];
+      uint8_t *lb = static_cast<uint8_t *>(ws) + static_cast<size_t>(l) * lane_bytes;
+      const RaysPrep q = lane_prep(l);
+      float2 *lsig = reinterpret_cast<float2 *>(lb + l_prep + l_ws);
+      float2 *ltmp = reinterpret_cast<float2 *>(lb + l_prep + l_ws + l_sig);
+      span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, sl>>>(rp, q, dobj, dmat, dhit, n, drules + h,
+                                                                           boff + static_cast<int64_t>(h) * nb);
+      kernels += 1 + (tensor ? launch_umma_sum(g, q, nh, lsig, lb + l_prep, status, sl, nullptr)
+                             : launch_direct_sum(g, q, nh, lsig, sl));
+      kernels += launch_fft(g, ctx->t, lsig, ltmp, x, sl);
+      if (span_spectra && span_spectra[h])
+        cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, sl);
+    } else {
+      cudaMemsetAsync(x, 0, 8 * static_cast<size_t>(g.n_cell), s);  // the FFT of zeros
+      if (span_spectra && span_spectra[h])
+        cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
+    }
   }
+  for (int l = 1; l < lanes; ++l) {  // join the lanes before the labels read every spectrum
+    cudaEventRecord(lane_done[l], lane_s[l]);
+    cudaStreamWaitEvent(s, lane_done[l], 0);
+  }
+  cudaEventRecord(ev[2], s);
   if (span_labels) {
     const int64_t all = g.n_cell * n_spans;
     power_max_kernel<<<1024, 256, 0, s>>>(spectra, all, pmax);
@@ -353,7 +397,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     if (!dev_out)
       cudaMemcpyAsync(span_labels, dlab, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDeviceToHost, s);
   }
-  cudaEventRecord(ev[2 + 2 * n_spans], s);
+  cudaEventRecord(ev[3], s);
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);
@@ -361,20 +405,15 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   if (e != cudaSuccess || !launch_ok) return finish(SIM_E_CUDA);
   if (st & (kStatusBadRay | kStatusModelRange)) return finish(SIM_E_INVALID);
   if (st) return finish(SIM_E_DEVICE);
-  // stage times as sim_last_stage_ms reports them: prep (with the span sizes), ray sums (with
-  // the packing), FFTs, labels, and the whole call on the device's clock (with the read-back
-  // of the span sizes)
+  // stage times as sim_last_stage_ms reports them: prep (with the span sizes), the spans'
+  // packing, ray sums and FFTs together (they overlap on the lanes), labels, and the whole
+  // call on the device's clock (with the read-back of the span sizes)
   auto el = [&](int a, int c) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[static_cast<size_t>(a)], ev[static_cast<size_t>(c)]);
     return ms;
   };
-  float ms[7] = {0, el(0, 1), 0, 0, 0, 0, el(0, 2 + 2 * n_spans)};
-  for (int h = 0; h < n_spans; ++h) {
-    ms[2] += el(h == 0 ? 1 : 1 + 2 * h, 2 + 2 * h);
-    ms[4] += el(2 + 2 * h, 3 + 2 * h);
-  }
-  ms[5] = el(1 + 2 * n_spans, 2 + 2 * n_spans);
+  float ms[7] = {0, el(0, 1), el(1, 2), 0, 0, el(2, 3), el(0, 3)};
   record_stage_ms(ctx, ms, kernels);
   return finish(SIM_OK);
 }
