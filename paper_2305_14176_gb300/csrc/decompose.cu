@@ -317,10 +317,11 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   int live = 0;
   for (uint32_t nh : sizes) live += nh > 0 ? 1 : 0;
   int lanes = std::max(1, std::min(kLanes, live));
-  int64_t need = 0;
-  if (tensor)
-    for (uint32_t nh : sizes)
-      if (nh > 0) need = std::max<int64_t>(need, umma_workspace_bytes(g, static_cast<int64_t>(nh)));
+  int64_t need = 0;  // ray-sum workspace of the largest span
+  for (uint32_t nh : sizes)
+    if (nh > 0)
+      need = std::max<int64_t>(need, tensor ? umma_workspace_bytes(g, static_cast<int64_t>(nh))
+                                            : direct_workspace_bytes(g, static_cast<int64_t>(nh)));
   const size_t l_prep = round256((exact ? 76 : 60) * up), l_ws = round256(static_cast<size_t>(need)),
                l_sig = round256(8 * static_cast<size_t>(g.n_sig));
   const size_t lane_bytes = l_prep + l_ws + 2 * l_sig;  // prep, workspace, signal, FFT scratch
@@ -366,7 +367,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
       span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, sl>>>(rp, q, dobj, dmat, dhit, n, drules + h,
                                                                            boff + static_cast<int64_t>(h) * nb);
       kernels += 1 + (tensor ? launch_umma_sum(g, q, nh, lsig, lb + l_prep, status, sl, nullptr)
-                             : launch_direct_sum(g, q, nh, lsig, sl));
+                             : launch_direct_sum(g, q, nh, lsig, lb + l_prep, sl));
       kernels += launch_fft(g, ctx->t, lsig, ltmp, x, sl);
       if (span_spectra && span_spectra[h])
         cudaMemcpyAsync(span_spectra[h], x, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, sl);

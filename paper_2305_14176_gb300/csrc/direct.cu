@@ -138,10 +138,13 @@ __device__ __forceinline__ void sum_chunk(const Staged &st, int cnt, int t, floa
   }
 }
 
-// One block per (k, m) row: thread t owns samples n = t + j * T (j < NPT).
+// One block per ((k, m) row, ray part): thread t owns samples n = t + j * T (j < NPT) and sums
+// the rays of part blockIdx.y, [ray_lo + y part_len, ...) below ray_hi; part 0 writes sig,
+// part y > 0 writes parts[(y - 1) n_sig + ...] (added in order afterwards).
 template <int NPT>
-__global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int nc, int ns,
-                                                         int nrx, float2 *__restrict__ sig) {
+__global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_rays, int64_t part_len, int nc,
+                                                         int ns, int nrx, float2 *__restrict__ sig,
+                                                         float2 *__restrict__ parts, int64_t n_sig) {
   __shared__ Staged st;
   const int row = blockIdx.x;
   const uint64_t k = static_cast<uint64_t>(row / nc);
@@ -153,8 +156,10 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
 #pragma unroll
   for (int j = 0; j < NPT; ++j) { tot_re[j] = 0.f; tot_im[j] = 0.f; }
 
-  for (int64_t c0 = 0; c0 < n_rays; c0 += kChunk) {
-    const int cnt = static_cast<int>(n_rays - c0 < kChunk ? n_rays - c0 : kChunk);
+  const int64_t lo = static_cast<int64_t>(blockIdx.y) * part_len;
+  const int64_t hi = lo + part_len < n_rays ? lo + part_len : n_rays;
+  for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+    const int cnt = static_cast<int>(hi - c0 < kChunk ? hi - c0 : kChunk);
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const int64_t r = c0 + i;
@@ -173,11 +178,26 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
   }
-  float2 *o = sig + static_cast<int64_t>(row) * ns;
+  float2 *o = (blockIdx.y == 0 ? sig : parts + (static_cast<int64_t>(blockIdx.y) - 1) * n_sig) +
+              static_cast<int64_t>(row) * ns;
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     const int n = t + j * blockDim.x;
     if (n < ns) o[n] = make_float2(tot_re[j], tot_im[j]);
+  }
+}
+
+// sig += parts[0] + parts[1] + ... in part order
+__global__ void add_parts_kernel(float2 *__restrict__ sig, const float2 *__restrict__ parts, int extra,
+                                 int64_t n_sig) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_sig;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float2 v = sig[i];
+    for (int q = 0; q < extra; ++q) {
+      const float2 w = parts[q * n_sig + i];
+      v = make_float2(v.x + w.x, v.y + w.y);
+    }
+    sig[i] = v;
   }
 }
 
@@ -244,10 +264,62 @@ int pair_row_threads(int ns) { return ns <= 64 ? ns : (ns / 32 > 64 ? ns / 32 : 
 
 }  // namespace
 
-int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s) {
+// Ray parts of the separable direct sum: one block per (row, part), so a frame whose rows are
+// too few for the resident blocks (3072 automotive rows at 16 blocks per SM: 1.26 waves) fills
+// the SMs; the smallest part count giving at least three waves, at most 4, at least 512 rays
+// per part.  The part signals are added in fixed order afterwards.
+namespace {
+template <int NPT>
+int resident_blocks(int threads) {
+  static int per_sm = 0;
+  if (per_sm == 0 &&
+      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_sum_kernel<NPT>, threads, 0) != cudaSuccess ||
+       per_sm <= 0)) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  return per_sm * sms;
+}
+
+int resident_for(const Derived &g) {
+  const int threads = row_threads(g.ns);
+  switch (g.ns / threads) {
+    case 1: return resident_blocks<1>(threads);
+    case 2: return resident_blocks<2>(threads);
+    case 4: return resident_blocks<4>(threads);
+    case 8: return resident_blocks<8>(threads);
+    case 16: return resident_blocks<16>(threads);
+    default: return resident_blocks<32>(threads);
+  }
+}
+}  // namespace
+
+int direct_parts(const Derived &g, int64_t n) {
+  const int64_t rows = static_cast<int64_t>(g.nv) * g.nc;
+  const int64_t resident = resident_for(g);
+  int parts = 1;
+  while (parts < 4 && rows * parts < 3 * resident && n / (parts + 1) >= 512) ++parts;
+  return parts;
+}
+
+int64_t direct_workspace_bytes(const Derived &g, int64_t n) {
+  return static_cast<int64_t>(direct_parts(g, n) - 1) * 8 * g.n_sig;
+}
+
+int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, cudaStream_t s) {
   const int rows = g.nv * g.nc;
   const int threads = row_threads(g.ns);
-#define RS_DIRECT(N) direct_sum_kernel<N><<<rows, threads, 0, s>>>(p, n, g.nc, g.ns, g.nrx, sig)
+  const int P = workspace ? direct_parts(g, n) : 1;
+  int64_t part_len = (n + P - 1) / P;
+  part_len = (part_len + 1) / 2 * 2;  // whole ray pairs per part
+  if (part_len < 2) part_len = 2;
+  float2 *parts = static_cast<float2 *>(workspace);
+  const dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(P));
+#define RS_DIRECT(N) \
+  direct_sum_kernel<N><<<grid, threads, 0, s>>>(p, n, part_len, g.nc, g.ns, g.nrx, sig, parts, g.n_sig)
   switch (g.ns / threads) {
     case 1: RS_DIRECT(1); break;
     case 2: RS_DIRECT(2); break;
@@ -258,6 +330,10 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cuda
     default: return 0;
   }
 #undef RS_DIRECT
+  if (P > 1) {
+    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig);
+    return 2;
+  }
   return 1;
 }
 

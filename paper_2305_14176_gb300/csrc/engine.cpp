@@ -152,7 +152,8 @@ Plan make_plan(const Derived &g, int64_t n, bool has_obj) {
   p.ck = take(4 * cap);
   p.cm = take(8 * cap);
   p.co = take(4 * cap);
-  p.ws = take(g.precision == SIM_PREC_FP32_DIRECT ? 0 : static_cast<size_t>(umma_workspace_bytes(g, n)));
+  p.ws = take(static_cast<size_t>(g.precision == SIM_PREC_FP32_DIRECT ? direct_workspace_bytes(g, n)
+                                                                      : umma_workspace_bytes(g, n)));
   p.total = off;
   return p;
 }
@@ -243,7 +244,7 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
     cudaEventRecord(sl.lab[1], sl.side);
   }
   if (g.precision == SIM_PREC_FP32_DIRECT) {
-    kernels += launch_direct_sum(g, rp, j->n, sig, s);
+    kernels += launch_direct_sum(g, rp, j->n, sig, b + p.ws, s);
     cudaEventRecord(sl.ev[3], s);
   } else {
     kernels += launch_umma_sum(g, rp, j->n, sig, b + p.ws, status, s, sl.ev[3]);

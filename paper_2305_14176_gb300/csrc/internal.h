@@ -92,7 +92,10 @@ struct IngestArgs {
   int32_t *dst_obj;
 };
 int launch_ingest(const IngestArgs &x, int64_t n, cudaStream_t s);
-int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, cudaStream_t s);
+// separable direct sum; `workspace` (may be null: one ray part) of direct_workspace_bytes(g, n)
+// lets the rays go in parts that fill the SMs
+int64_t direct_workspace_bytes(const Derived &g, int64_t n);
+int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, cudaStream_t s);
 // store a synchronous call's stage times (7 entries, the sim_last_stage_ms order) and kernel count
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels);
 // direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase

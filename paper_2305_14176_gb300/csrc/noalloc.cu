@@ -108,7 +108,7 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
             rays->elevation_rad, rays->phase0_rad, nullptr};
   launch_prep(g, in, n, rp, status, s);
   if (g.precision == SIM_PREC_FP32_DIRECT) {
-    launch_direct_sum(g, rp, n, sig, s);
+    launch_direct_sum(g, rp, n, sig, direct_workspace_bytes(g, n) <= ws_bytes ? ws : nullptr, s);
   } else if (launch_umma_sum_in(g, rp, n, sig, ws, ws_bytes, status, s) < 0) {
     return SIM_E_INVALID;  // one split of this cube does not fit the scratch array, or the exact
                            // model with TDM slots (no per-chirp form) was asked for
