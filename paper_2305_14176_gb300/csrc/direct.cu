@@ -204,13 +204,16 @@ __global__ void add_parts_kernel(float2 *__restrict__ sig, const float2 *__restr
 // The same sum with phase words per (ray, chirp, transmitter) and (ray, chirp, receiver):
 // row (k = tx N_rx + rx, m) takes base = wt.x + wr.x and step = wt.y + wr.y, wt =
 // w_tx[(m N_tx + tx) stride + i], wr = w_rx[(m N_rx + rx) stride + i] (Q0.64, wrap-exact
-// sums).  With `accumulate` the row is added to what sig holds (rays in several chunks).
+// sums).  With `accumulate` the row is added to what sig holds (rays in several chunks).  Ray
+// part blockIdx.y > 0 (rays [y part_len, ...)) writes its row to parts[(y - 1) n_sig + ...]
+// instead, added in order afterwards.
 template <int NPT>
 __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restrict__ w_tx,
                                                        const ulonglong2 *__restrict__ w_rx,
                                                        const float *__restrict__ amp, int64_t n_rays, int64_t stride,
-                                                       int nc, int ns, int ntx, int nrx, int accumulate,
-                                                       float2 *__restrict__ sig) {
+                                                       int64_t part_len, int nc, int ns, int ntx, int nrx,
+                                                       int accumulate, float2 *__restrict__ sig,
+                                                       float2 *__restrict__ parts, int64_t n_sig) {
   __shared__ Staged st;
   const int row = blockIdx.x;
   const int k = row / nc, m = row % nc;
@@ -222,8 +225,10 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
   float tot_re[NPT], tot_im[NPT];
 #pragma unroll
   for (int j = 0; j < NPT; ++j) { tot_re[j] = 0.f; tot_im[j] = 0.f; }
-  for (int64_t c0 = 0; c0 < n_rays; c0 += kChunk) {
-    const int cnt = static_cast<int>(n_rays - c0 < kChunk ? n_rays - c0 : kChunk);
+  const int64_t lo = static_cast<int64_t>(blockIdx.y) * part_len;
+  const int64_t hi = lo + part_len < n_rays ? lo + part_len : n_rays;
+  for (int64_t c0 = lo; c0 < hi; c0 += kChunk) {
+    const int cnt = static_cast<int>(hi - c0 < kChunk ? hi - c0 : kChunk);
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
       const ulonglong2 a = wt[c0 + i], b = wr[c0 + i];
@@ -238,12 +243,13 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
 #pragma unroll
     for (int j = 0; j < NPT; ++j) { tot_re[j] += re[j]; tot_im[j] += im[j]; }
   }
-  float2 *o = sig + static_cast<int64_t>(row) * ns;
+  const bool to_sig = blockIdx.y == 0;
+  float2 *o = (to_sig ? sig : parts + (static_cast<int64_t>(blockIdx.y) - 1) * n_sig) + static_cast<int64_t>(row) * ns;
 #pragma unroll
   for (int j = 0; j < NPT; ++j) {
     const int n = t + j * blockDim.x;
     if (n < ns) {
-      if (accumulate) {
+      if (accumulate && to_sig) {
         const float2 v = o[n];
         o[n] = make_float2(v.x + tot_re[j], v.y + tot_im[j]);
       } else {
@@ -337,12 +343,46 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void
   return 1;
 }
 
+int pair_parts(const Derived &g, int64_t n) {
+  const int64_t rows = static_cast<int64_t>(g.nv) * g.nc;
+  const int threads = pair_row_threads(g.ns);
+  int per_sm = 0;
+  switch (g.ns / threads) {  // resident blocks of the instance this shape launches
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<1>, threads, 0); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<2>, threads, 0); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<4>, threads, 0); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<8>, threads, 0); break;
+    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<16>, threads, 0); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<32>, threads, 0); break;
+  }
+  cudaGetLastError();
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
+  const int64_t resident = static_cast<int64_t>(per_sm > 0 ? per_sm : 1) * sms;
+  int parts = 1;
+  while (parts < 4 && rows * parts < 3 * resident && n / (parts + 1) >= 512) ++parts;
+  return parts;
+}
+
+int64_t pair_workspace_bytes(const Derived &g, int64_t n) {
+  return static_cast<int64_t>(pair_parts(g, n) - 1) * 8 * g.n_sig;
+}
+
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
-                    int64_t stride, bool accumulate, float2 *sig, cudaStream_t s) {
+                    int64_t stride, bool accumulate, float2 *sig, void *workspace, cudaStream_t s) {
   const int rows = g.nv * g.nc;
   const int threads = pair_row_threads(g.ns);
   const int acc = accumulate ? 1 : 0;
-#define RS_PAIR(N) pair_sum_kernel<N><<<rows, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, g.nc, g.ns, g.ntx, g.nrx, acc, sig)
+  const int P = workspace ? pair_parts(g, n) : 1;
+  int64_t part_len = (n + P - 1) / P;
+  part_len = (part_len + 1) / 2 * 2;
+  if (part_len < 2) part_len = 2;
+  float2 *parts = static_cast<float2 *>(workspace);
+  const dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(P));
+#define RS_PAIR(N)                                                                                                 \
+  pair_sum_kernel<N><<<grid, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, part_len, g.nc, g.ns, g.ntx, g.nrx, acc, \
+                                              sig, parts, g.n_sig)
   switch (g.ns / threads) {
     case 1: RS_PAIR(1); break;
     case 2: RS_PAIR(2); break;
@@ -353,6 +393,10 @@ int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *
     default: return 0;
   }
 #undef RS_PAIR
+  if (P > 1) {
+    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig);
+    return 2;
+  }
   return 1;
 }
 

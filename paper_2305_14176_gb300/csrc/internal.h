@@ -100,8 +100,11 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels);
 // direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase
 // words (base, per-sample step): w_tx[(m N_tx + t) stride + i], w_rx[(m N_rx + r) stride + i]
+// `workspace` (may be null: one ray part) of pair_workspace_bytes(g, n) lets the rays go in
+// parts that fill the SMs
+int64_t pair_workspace_bytes(const Derived &g, int64_t n);
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
-                    int64_t stride, bool accumulate, float2 *sig, cudaStream_t s);
+                    int64_t stride, bool accumulate, float2 *sig, void *workspace, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);
 int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
                   int32_t *labels, uint32_t *status, cudaStream_t s);

@@ -202,7 +202,7 @@ struct SnapRun {
   size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
   size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
   size_t o_base0 = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
-  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0;
+  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0;
   int64_t cap = 0;
   ~SnapRun() {
     if (s) cudaStreamDestroy(s);
@@ -276,6 +276,7 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_wt = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.ntx : 0);
   R.o_wr = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.nrx : 0);
   R.o_sig = take(mode == 1 ? 8 * static_cast<size_t>(g.n_sig) : 0);
+  R.o_pw = take(mode == 1 && chunk > 0 ? static_cast<size_t>(pair_workspace_bytes(g, chunk)) : 0);  // ray parts
   R.o_tmp = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_spec = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
   R.o_lab = take(want_labels ? 4 * static_cast<size_t>(g.n_cell) : 0);
@@ -442,7 +443,7 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
     snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const double2 *>(b + R.o_base0), in.p0, i0, cnt, k,
                                          nullptr, wt, wr, R.chunk, status);
     cudaEventRecord(ev[ei++], s);
-    kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, s);
+    kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, b + R.o_pw, s);
     cudaEventRecord(ev[ei++], s);
   }
   if (signal) cudaMemcpyAsync(signal, sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
