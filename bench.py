@@ -186,7 +186,11 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "rays": rays.n, "l2": "n/a (host)"},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rays": rays.n, "n_virtual": radar.n_virtual, "n_chirps": radar.n_chirps,
+                   "n_samples": radar.n_samples, "n_angle": radar.n_angle, "precision": "fp64 (oracle)",
+                   "outputs": "signal at sampled output points", "l2": "n/a (host)",
+                   "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{per_step} output points x {rays.n} rays per step (FP64 direct sum)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
