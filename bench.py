@@ -281,10 +281,11 @@ def single_pass_variant(rs, torch, radar, dev_in, n, contrib, flush, peaks, step
 def run_snapshot_workload(args, rs, torch):
     """Virtual snapshots (Eq. 6) and Eq. 7 antenna paths: a seeded moving-box scene at the
     automotive radar size (12 channels x 256 chirps x 512 samples), per-(ray, chirp, channel)
-    path lengths into Eq. 2 on the direct-sum path, then FFTs and labels."""
+    path lengths into Eq. 2 (FP32 direct sum, or at the tensor-core precisions the per-tile
+    expansion over each row's phase words), then FFTs and labels."""
     radar = scenegen.radar_automotive()
     rays, hits, geom = scenegen.moving_scene(5000, radar, args.rays, n_objects=20)
-    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
+    ctx = rs.Context(radar, precision=rs.PRECISION_NAMES[args.precision])
     a = dict(rays.arrays())
     a.update(vertices=geom.vertices, triangles=geom.triangles, tx_pos=geom.tx_pos, rx_pos=geom.rx_pos,
              hit_offset=hits.offset, hit_triangle=hits.triangle, hit_u=hits.u, hit_v=hits.v)
@@ -327,13 +328,26 @@ def run_snapshot_workload(args, rs, torch):
             e2e.append(time.perf_counter() - t0)
     dev_s = stages["total"] / 1e3
     sum_s = stages["ray_sum"] / 1e3
-    achieved = contrib * args.steps / sum_s / 1e12
+    if args.precision == "fp32":
+        achieved = contrib * args.steps / sum_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": DIRECT_PEAK_TCONTRIB, "unit": "Tcontrib/s",
+                "frac": achieved / DIRECT_PEAK_TCONTRIB, "traffic": None, "kernel": "pair_sum_kernel",
+                "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"}
+    else:
+        peaks, peak_src = _peaks()
+        achieved = 8.0 * contrib * args.steps / sum_s / 1e12
+        peak = float(peaks["bf16_tflops"])
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "taylor_sum_kernel (snapshot phase words, with its stats and reduction)",
+                "peak_source": f"{peak_src} bf16 dense burst"}
     line = {"metric": METRIC, "value": contrib * args.steps / dev_s, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32"}.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": "virtual snapshots: moving boxes, Eq. 6 hit update + Eq. 7 antenna paths, "
                                    "12 virtual ch x 256 chirps x 512 samples",
                        "rays": rays.n, "hits": int(hits.offset[-1]), "triangles": int(geom.triangles.shape[0]),
+                       "precision": args.precision,
                        "l2": "flushed (256 MB write) before each step"},
             "stage_ms_mean": {k: v / args.steps for k, v in stages.items()},
             "e2e": {"value": contrib * len(e2e) / sum(e2e), "unit": UNIT,
@@ -341,11 +355,7 @@ def run_snapshot_workload(args, rs, torch):
                     "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out)),
                     "ms_per_step": 1e3 * sum(e2e) / len(e2e),
                     "note": "synchronous call: includes its device allocation and input copies"},
-            "gpu_launches": kernels,
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": DIRECT_PEAK_TCONTRIB, "unit": "Tcontrib/s",
-                         "frac": achieved / DIRECT_PEAK_TCONTRIB, "traffic": None, "kernel": "pair_sum_kernel",
-                         "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"},
-            "cpu_baseline": None, "clocks": clk.summary()}
+            "gpu_launches": kernels, "roofline": roof, "cpu_baseline": None, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0

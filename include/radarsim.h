@@ -209,8 +209,8 @@ typedef struct {
 } sim_hits;
 
 /* Path lengths l(j, t, r) of every ray into paths, double[n][N_c][N_v] (k = t N_rx + r), host or
-   device.  The context gives N_c, n_tx, n_rx; it must use SIM_PREC_FP32_DIRECT and no TDM slot
-   time.  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
+   device.  The context gives N_c, n_tx, n_rx (any precision: paths are FP64) and must have no
+   TDM slot time.  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
    memory.  SIM_E_INVALID for bad arguments, a hit list or index out of range (checked before
    any access) or a ray failing sim_submit's checks. */
 SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hits *hits, const sim_geometry *geom,
@@ -222,8 +222,12 @@ SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hit
    a_i' the amplitude after the antenna pattern; then the spectrum and the labels as for
    sim_fetch (labels from the rays' analytic cells of d, v, az, el).  Any of spectrum,
    signal, labels may be NULL (not all); spectrum and labels need the context's outputs
-   bit.  Same context limits, memory and errors as sim_snapshot_paths; the direct sum runs
-   in chunks of rays whose phase words fit 1 GiB. */
+   bit.  Same context limits, memory and errors as sim_snapshot_paths.  Rays go in chunks
+   whose phase words fit 1 GiB.  SIM_PREC_FP32_DIRECT sums each chunk directly; the
+   tensor-core precisions expand each tile's coupling of samples and rows about its centre,
+   the exact-model expansion with every row's own phase words (4 or 8 terms, truncation
+   <= 1e-6 of a contribution at hi + lo, 1e-5 single pass, chosen on the device per chunk).
+   A chunk beyond that bound, or N_s < 32, is summed directly in FP32. */
 SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, const sim_hits *hits,
                              const sim_geometry *geom, void *spectrum, void *signal, int32_t *labels);
 

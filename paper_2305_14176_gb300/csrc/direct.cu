@@ -187,9 +187,17 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
   }
 }
 
+// gate (may be null) holding 4 or 8: a tensor-core expansion computed the chunk instead
+__device__ __forceinline__ bool gated_off(const uint32_t *gate) {
+  if (!gate) return false;
+  const uint32_t v = *gate;
+  return v == 4u || v == 8u;
+}
+
 // sig += parts[0] + parts[1] + ... in part order
 __global__ void add_parts_kernel(float2 *__restrict__ sig, const float2 *__restrict__ parts, int extra,
-                                 int64_t n_sig) {
+                                 int64_t n_sig, const uint32_t *gate) {
+  if (gated_off(gate)) return;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_sig;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float2 v = sig[i];
@@ -213,7 +221,9 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
                                                        const float *__restrict__ amp, int64_t n_rays, int64_t stride,
                                                        int64_t part_len, int nc, int ns, int ntx, int nrx,
                                                        int accumulate, float2 *__restrict__ sig,
-                                                       float2 *__restrict__ parts, int64_t n_sig) {
+                                                       float2 *__restrict__ parts, int64_t n_sig,
+                                                       const uint32_t *gate) {
+  if (gated_off(gate)) return;  // the tensor-core expansion owns this chunk
   __shared__ Staged st;
   const int row = blockIdx.x;
   const int k = row / nc, m = row % nc;
@@ -337,7 +347,7 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void
   }
 #undef RS_DIRECT
   if (P > 1) {
-    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig);
+    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig, nullptr);
     return 2;
   }
   return 1;
@@ -370,7 +380,8 @@ int64_t pair_workspace_bytes(const Derived &g, int64_t n) {
 }
 
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
-                    int64_t stride, bool accumulate, float2 *sig, void *workspace, cudaStream_t s) {
+                    int64_t stride, bool accumulate, float2 *sig, void *workspace, const uint32_t *gate,
+                    cudaStream_t s) {
   const int rows = g.nv * g.nc;
   const int threads = pair_row_threads(g.ns);
   const int acc = accumulate ? 1 : 0;
@@ -382,7 +393,7 @@ int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *
   const dim3 grid(static_cast<unsigned>(rows), static_cast<unsigned>(P));
 #define RS_PAIR(N)                                                                                                 \
   pair_sum_kernel<N><<<grid, threads, 0, s>>>(w_tx, w_rx, amp, n, stride, part_len, g.nc, g.ns, g.ntx, g.nrx, acc, \
-                                              sig, parts, g.n_sig)
+                                              sig, parts, g.n_sig, gate)
   switch (g.ns / threads) {
     case 1: RS_PAIR(1); break;
     case 2: RS_PAIR(2); break;
@@ -394,7 +405,7 @@ int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *
   }
 #undef RS_PAIR
   if (P > 1) {
-    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig);
+    add_parts_kernel<<<4 * 152, 256, 0, s>>>(sig, parts, P - 1, g.n_sig, gate);
     return 2;
   }
   return 1;

@@ -103,8 +103,17 @@ void record_stage_ms(sim_ctx *c, const float *ms, int kernels);
 // `workspace` (may be null: one ray part) of pair_workspace_bytes(g, n) lets the rays go in
 // parts that fill the SMs
 int64_t pair_workspace_bytes(const Derived &g, int64_t n);
+// `gate` (device word, may be null) holding 4 or 8 makes both of its kernels return at once
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
-                    int64_t stride, bool accumulate, float2 *sig, void *workspace, cudaStream_t s);
+                    int64_t stride, bool accumulate, float2 *sig, void *workspace, const uint32_t *gate,
+                    cudaStream_t s);
+// virtual snapshots on tensor cores, one chunk of phase words (umma_taylor.cu): the per-tile
+// expansion, or the pair sum when the expansion's bound fails; workspace of
+// snap_tensor_workspace_bytes(g, chunk), pair_ws of pair_workspace_bytes(g, chunk)
+int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk);
+int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, int64_t stride,
+                       const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
+                       uint32_t *status, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);
 int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
                   int32_t *labels, uint32_t *status, cudaStream_t s);

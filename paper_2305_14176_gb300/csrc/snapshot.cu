@@ -10,7 +10,9 @@
 //                  + |p_l(j) - x_r| - |p_l(0) - x_ref,rx|          = A_t(j) + B_r(j).
 //
 // Each path enters Eq. 2 with tau = l / c in both the beat and the carrier term, so the sum is
-// not separable over chirps and channels and runs on the direct-sum path.  One thread per
+// not separable over chirps and channels: it runs on the direct-sum path (FP32) or, at the
+// tensor-core precisions, through the per-tile expansion of umma_taylor.cu with each row's own
+// phase words (the direct sum remains that path's fallback, gated on the device).  One thread per
 // (ray, chirp) computes A_t and B_r in FP64 and stores them as Q0.64 phase words (carrier
 // f_c l / c plus the start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m)
 // of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
@@ -202,7 +204,7 @@ struct SnapRun {
   size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
   size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
   size_t o_base0 = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
-  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0;
+  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0;
   int64_t cap = 0;
   ~SnapRun() {
     if (s) cudaStreamDestroy(s);
@@ -217,7 +219,7 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   if (!ctx || !rays || !hits || !geom) return SIM_E_INVALID;
   const Derived &g = ctx->g;
   R.g = &g;
-  if (g.precision != SIM_PREC_FP32_DIRECT || g.tslot != 0.0) return SIM_E_INVALID;
+  if (g.tslot != 0.0) return SIM_E_INVALID;  // snapshots exist at j T_d only
   const int64_t n = rays->n;
   if (n < 0 || n > g.max_rays) return SIM_E_INVALID;
   if (geom->n_vertices < 1 || geom->n_vertices > (int64_t{1} << 31) || geom->n_triangles < 1 ||
@@ -277,6 +279,10 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_wr = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.nrx : 0);
   R.o_sig = take(mode == 1 ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_pw = take(mode == 1 && chunk > 0 ? static_cast<size_t>(pair_workspace_bytes(g, chunk)) : 0);  // ray parts
+  // tensor-core precisions: the expansion's header and split-K partials
+  R.o_tw = take(mode == 1 && chunk > 0 && g.precision != SIM_PREC_FP32_DIRECT
+                    ? static_cast<size_t>(snap_tensor_workspace_bytes(g, chunk))
+                    : 0);
   R.o_tmp = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_spec = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
   R.o_lab = take(want_labels ? 4 * static_cast<size_t>(g.n_cell) : 0);
@@ -443,7 +449,11 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
     snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const double2 *>(b + R.o_base0), in.p0, i0, cnt, k,
                                          nullptr, wt, wr, R.chunk, status);
     cudaEventRecord(ev[ei++], s);
-    kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, b + R.o_pw, s);
+    if (g.precision == SIM_PREC_FP32_DIRECT)
+      kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, b + R.o_pw, nullptr, s);
+    else
+      kernels += 1 + launch_snap_tensor(g, wt, wr, R.chunk, rp.amp + i0, cnt, i0 > 0, sig, b + R.o_tw, b + R.o_pw,
+                                        status, s);
     cudaEventRecord(ev[ei++], s);
   }
   if (signal) cudaMemcpyAsync(signal, sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);

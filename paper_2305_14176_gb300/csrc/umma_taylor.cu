@@ -76,8 +76,19 @@ constexpr int kMaxDynSmemT = 232448 - 8192;
 // high-order K step keeps its lo operands (u32), largest |eps_t| (u64)
 constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 24, kHeader = 256;
 
+// what the rows and columns are synthesised from
+constexpr int kExact = 0;     // exact Eq. 2: per-ray words of the prep kernel
+constexpr int kExactTdm = 1;  // the same with TDM slot offsets
+constexpr int kSnap = 2;      // virtual snapshots: per-(ray, chirp, antenna) phase words
+
 struct TArgs {
   RaysPrep p;
+  // kSnap: phase words (base, per-sample step) w_tx[(m N_tx + t) stride + i],
+  // w_rx[(m N_rx + r) stride + i] of the chunk's rays, their amplitudes, the reference antennas
+  const ulonglong2 *w_tx, *w_rx;
+  int64_t stride;
+  const float *samp;
+  int ntx, r_c;
   int64_t n_rays, chunk;  // rays, rays per split (multiple of 8)
   int nc, ns, nv, nrx, m_rows;
   int t_c;                // centre transmitter of the slot term
@@ -102,11 +113,21 @@ struct TWords {
   float amp;
 };
 
-// thread gt < rays of the stage fetches its ray's words (rays past the chunk read as 0)
-template <bool TDM>
-__device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays, int64_t k_hi, int gt) {
+// thread gt < rays of the stage fetches its ray's words (rays past the chunk read as 0).
+// kSnap: the ray's reference per-sample step (the tile's centre chirp m_c, antennas t_c, r_c),
+// kept in `nur`, and its amplitude.
+template <int MODE>
+__device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays, int64_t k_hi, int gt, int m_c) {
   TWords w{0, 0, 0, 0, 0, 0, 0, 0.f};
   const int64_t ray = ray0 + gt;
+  if constexpr (MODE == kSnap) {
+    if (gt < rays && ray < k_hi) {
+      w.nur = g.w_tx[(static_cast<int64_t>(m_c) * g.ntx + g.t_c) * g.stride + ray].y +
+              g.w_rx[(static_cast<int64_t>(m_c) * g.nrx + g.r_c) * g.stride + ray].y;
+      w.amp = g.samp[ray];
+    }
+    return w;
+  }
   if (gt < rays && ray < k_hi) {
     w.car = g.p.carrier[ray];
     w.nua = g.p.nu_a[ray];
@@ -114,14 +135,21 @@ __device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays,
     w.nutx = g.p.nu_tx[ray];
     w.nur = g.p.nu_r[ray];
     w.eps = g.p.eps[ray];
-    if constexpr (TDM) w.epst = g.p.eps_t[ray];
+    if constexpr (MODE == kExactTdm) w.epst = g.p.eps_t[ray];
     w.amp = g.p.amp[ray];
   }
   return w;
 }
 
-template <bool TDM>
+template <int MODE>
 __device__ __forceinline__ void tstore(TStage &s, int gt, const TWords &w) {
+  if constexpr (MODE == kSnap) {
+    if (gt < TMAX_RAYS) {
+      s.nur[gt] = w.nur;
+      s.amp[gt] = w.amp;
+    }
+    return;
+  }
   if (gt < TMAX_RAYS) {
     s.car[gt] = w.car;
     s.nua[gt] = w.nua;
@@ -129,7 +157,7 @@ __device__ __forceinline__ void tstore(TStage &s, int gt, const TWords &w) {
     s.nutx[gt] = w.nutx;
     s.nur[gt] = w.nur;
     s.eps[gt] = w.eps;
-    if constexpr (TDM) s.epst[gt] = w.epst;
+    if constexpr (MODE == kExactTdm) s.epst[gt] = w.epst;
     s.amp[gt] = w.amp;
   }
 }
@@ -144,6 +172,10 @@ struct RowCtx {
   int32_t ncm, nct;         // n_c m', n_c t' (|n_c m'| < 2^23)
   float xm, xt;             // 2 pi m' n_h 2^-64, 2 pi t' n_h 2^-64: x = xm eps_i + xt eps_t,i (words)
   bool valid;
+  // kSnap: the row's phase-word rows, n_c, and 2 pi n_h 2^-64 (x = xs delta_i, words)
+  const ulonglong2 *wt, *wr;
+  uint32_t n_c;
+  float xs;
 };
 struct ColCtx {
   uint32_t n, nmc, ntc;     // sample index, n m_c, n t_c (< 2^26)
@@ -155,9 +187,12 @@ struct ColCtx {
 
 // One stage of operands: A row gt (all 32 slots) and this thread's B column octets, in the
 // no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
-template <bool F16, bool SPLIT, bool TDM, int P>
+// kSnap: rays li0 + q, q < valid, of the chunk are present; the rest read as silent.
+template <bool F16, bool SPLIT, int MODE, int P>
 __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
-                                               const ColCtx &cc, float scale, bool lo_high) {
+                                               const ColCtx &cc, float scale, bool lo_high, int64_t li0,
+                                               int valid) {
+  constexpr bool TDM = MODE == kExactTdm;
   constexpr int RS = TKS / P;   // rays per stage
   constexpr int TPO = P / 4;    // terms per octet
   const uint32_t a_half = TBM * TKS * 2;
@@ -170,14 +205,31 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
-      uint64_t ph = sr.car[q] + static_cast<uint64_t>(rc.tx) * sr.nutx[q] + static_cast<uint64_t>(rc.rx) * sr.nua[q] +
-                    static_cast<uint64_t>(rc.m) * sr.nud[q] + static_cast<uint64_t>(static_cast<int64_t>(rc.ncm)) * sr.eps[q];
-      if constexpr (TDM) ph += static_cast<uint64_t>(static_cast<int64_t>(rc.nct)) * sr.epst[q];
-      __sincosf(q64_to_rad(ph), &sn, &cs);
-      const float am = rc.valid ? sr.amp[q] * scale : 0.f;
-      t[q] = make_float2(am * cs, am * sn);
-      x[q] = rc.xm * static_cast<float>(static_cast<int64_t>(sr.eps[q]));
-      if constexpr (TDM) x[q] += rc.xt * static_cast<float>(static_cast<int64_t>(sr.epst[q]));
+      if constexpr (MODE == kSnap) {
+        // base C and per-sample step S of this row's path, delta = S - S_ref (a small signed
+        // word): phase C + n_c delta, expansion variable x = 2 pi n_h delta
+        const bool live = rc.valid && q < valid;
+        uint64_t c = 0, d = 0;
+        if (live) {
+          const ulonglong2 a = rc.wt[li0 + q], b = rc.wr[li0 + q];
+          c = a.x + b.x;
+          d = a.y + b.y - sr.nur[q];
+        }
+        __sincosf(q64_to_rad(c + static_cast<uint64_t>(rc.n_c) * d), &sn, &cs);
+        const float am = live ? sr.amp[q] * scale : 0.f;
+        t[q] = make_float2(am * cs, am * sn);
+        x[q] = rc.xs * static_cast<float>(static_cast<int64_t>(d));
+      } else {
+        uint64_t ph = sr.car[q] + static_cast<uint64_t>(rc.tx) * sr.nutx[q] + static_cast<uint64_t>(rc.rx) * sr.nua[q] +
+                      static_cast<uint64_t>(rc.m) * sr.nud[q] +
+                      static_cast<uint64_t>(static_cast<int64_t>(rc.ncm)) * sr.eps[q];
+        if constexpr (TDM) ph += static_cast<uint64_t>(static_cast<int64_t>(rc.nct)) * sr.epst[q];
+        __sincosf(q64_to_rad(ph), &sn, &cs);
+        const float am = rc.valid ? sr.amp[q] * scale : 0.f;
+        t[q] = make_float2(am * cs, am * sn);
+        x[q] = rc.xm * static_cast<float>(static_cast<int64_t>(sr.eps[q]));
+        if constexpr (TDM) x[q] += rc.xt * static_cast<float>(static_cast<int64_t>(sr.epst[q]));
+      }
     }
     uint32_t off = (gt >> 3) * 128 + (gt & 7) * 16;
 #pragma unroll
@@ -207,8 +259,13 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
-      uint64_t ph = static_cast<uint64_t>(cc.n) * sr.nur[q] + static_cast<uint64_t>(cc.nmc) * sr.eps[q];
-      if constexpr (TDM) ph += static_cast<uint64_t>(cc.ntc) * sr.epst[q];
+      uint64_t ph;
+      if constexpr (MODE == kSnap) {
+        ph = static_cast<uint64_t>(cc.n) * sr.nur[q];  // the ray's reference step
+      } else {
+        ph = static_cast<uint64_t>(cc.n) * sr.nur[q] + static_cast<uint64_t>(cc.nmc) * sr.eps[q];
+        if constexpr (TDM) ph += static_cast<uint64_t>(cc.ntc) * sr.epst[q];
+      }
       __sincosf(q64_to_rad(ph), &sn, &cs);
       b[q] = make_float2(cs, sn);
     }
@@ -244,7 +301,7 @@ __host__ __device__ constexpr uint32_t t_stage_bytes(int bn) {
 
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
-template <bool F16, bool SPLIT, bool TDM>
+template <bool F16, bool SPLIT, int MODE>
 __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int TGROUPS = t_groups<SPLIT>();
@@ -293,7 +350,8 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
   const int row0 = r0 + static_cast<int>(rank) * TBM;  // this CTA's rows
   const int col0 = tile_n * bn;                        // real column; complex n0 = col0 / 2
   const int n0 = tile_n * NC;
-  const int m_c = (r0 + TBM) / g.nv;                   // tile centre: chirp and sample
+  // tile centre: chirp and sample (kSnap: a chirp that exists, its reference words are read)
+  const int m_c = MODE == kSnap ? min((r0 + TBM) / g.nv, g.nc - 1) : (r0 + TBM) / g.nv;
   const int n_c = n0 + NC / 2, n_h = NC / 2;
   const int RS = TKS / static_cast<int>(P);
   const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
@@ -322,6 +380,13 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
       const int tp = t - g.t_c;
       rc.nct = n_c * tp;
       rc.xt = static_cast<float>(tp) * static_cast<float>(n_h) * 3.40612158008655459e-19f;
+      rc.n_c = static_cast<uint32_t>(n_c);
+      rc.xs = static_cast<float>(n_h) * 3.40612158008655459e-19f;
+      rc.wt = rc.wr = nullptr;
+      if (MODE == kSnap && rc.valid) {
+        rc.wt = g.w_tx + (static_cast<int64_t>(m) * g.ntx + t) * g.stride;
+        rc.wr = g.w_rx + (static_cast<int64_t>(m) * g.nrx + (k - t * g.nrx)) * g.stride;
+      }
     }
     ColCtx cc;
     {
@@ -338,20 +403,23 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
       cc.u = static_cast<float>(n - n_c) / static_cast<float>(n_h);  // n_h is a power of two
     }
     TWords nxt{0, 0, 0, 0, 0, 0, 0, 0.f};
-    if (grp < n_stages) nxt = tfetch<TDM>(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt);
+    if (grp < n_stages) nxt = tfetch<MODE>(g, k_lo + static_cast<int64_t>(grp) * RS, RS, k_hi, gt, m_c);
     for (int st = grp; st < n_stages; st += TGROUPS) {
       const int s = st % NST;
       const int64_t ray0 = k_lo + static_cast<int64_t>(st) * RS;
-      tstore<TDM>(s_rays[grp], gt, nxt);
-      if (st + TGROUPS < n_stages) nxt = tfetch<TDM>(g, ray0 + TGROUPS * RS, RS, k_hi, gt);
+      tstore<MODE>(s_rays[grp], gt, nxt);
+      if (st + TGROUPS < n_stages) nxt = tfetch<MODE>(g, ray0 + TGROUPS * RS, RS, k_hi, gt, m_c);
+      const int valid = static_cast<int>(k_hi - ray0 < RS ? k_hi - ray0 : RS);
       tgroup_sync(grp);
       if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
         failed = true;
         break;
       }
       uint8_t *st_base = base + s * stage_bytes;
-      if (P == 4u) produce_taylor<F16, SPLIT, TDM, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
-      else produce_taylor<F16, SPLIT, TDM, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high);
+      if (P == 4u)
+        produce_taylor<F16, SPLIT, MODE, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+      else
+        produce_taylor<F16, SPLIT, MODE, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       fence_proxy_async();  // this thread's stores, visible to the tensor core
       if constexpr (ONE_ARRIVE) {
         tgroup_sync(grp);  // the group's stores are done and s_rays[grp] is free again
@@ -477,9 +545,11 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
 // Partials of the chirp-major rows -> the signal in channel-major order:
 //   sig[k][m][n] = sum_s (P_s[m N_v + k][t bn + nl], P_s[m N_v + k][t bn + bn/2 + nl]) / scale,
 // t = n / (bn/2), nl = n % (bn/2); four samples per thread, splits added in order.
+// With `accumulate` the result is added to what sig holds (snapshot rays in several chunks).
 template <bool F16>
 __global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv, int nc, int ns, int bn,
-                              float2 *__restrict__ sig, const uint32_t *amax_bits, const uint32_t *terms) {
+                              float2 *__restrict__ sig, const uint32_t *amax_bits, const uint32_t *terms,
+                              int accumulate) {
   const uint32_t P = *terms;
   if (P != 4u && P != 8u) return;
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
@@ -504,8 +574,15 @@ __global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv
       im.x += b.x; im.y += b.y; im.z += b.z; im.w += b.w;
     }
     float4 *o = reinterpret_cast<float4 *>(sig + row * ns + n);
-    o[0] = make_float4(re.x * inv, im.x * inv, re.y * inv, im.y * inv);
-    o[1] = make_float4(re.z * inv, im.z * inv, re.w * inv, im.w * inv);
+    float4 v0 = make_float4(re.x * inv, im.x * inv, re.y * inv, im.y * inv);
+    float4 v1 = make_float4(re.z * inv, im.z * inv, re.w * inv, im.w * inv);
+    if (accumulate) {
+      const float4 a0 = o[0], a1 = o[1];
+      v0 = make_float4(a0.x + v0.x, a0.y + v0.y, a0.z + v0.z, a0.w + v0.w);
+      v1 = make_float4(a1.x + v1.x, a1.y + v1.y, a1.z + v1.z, a1.w + v1.w);
+    }
+    o[0] = v0;
+    o[1] = v1;
   }
 }
 
@@ -553,6 +630,47 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
   const double high = P == 4 ? t2 / 2.0 : t4 / 24.0;  // largest term of the second K step
   *lo_high = (two_u > 0.0 && high * two_u > tol_lo) ? 1u : 0u;
   if (P == 0 && tdm) atomicOr(status, kStatusModelRange);
+}
+
+// Virtual snapshots: the largest |S - S_ref| over the chunk's rays and every row, S the
+// per-sample step of row (m, k = t N_rx + r) and S_ref the ray's reference step of that row's
+// 256-row tile (chirp m_c, antennas t_c, r_c), as signed Q0.64 words; and the amplitude maximum
+// (FP16 scaling).  One thread per (ray, chirp), consecutive threads on consecutive rays.
+__global__ void snap_stats(const ulonglong2 *__restrict__ w_tx, const ulonglong2 *__restrict__ w_rx, int64_t stride,
+                           const float *__restrict__ amp, int64_t cnt, int nc, int nv, int ntx, int nrx, int t_c,
+                           int r_c, bool want_amax, uint32_t *amax_bits, unsigned long long *d_max) {
+  uint32_t ma = 0;
+  unsigned long long md = 0;
+  const int64_t total = cnt * nc;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int m = static_cast<int>(e / cnt);
+    const int64_t li = e - static_cast<int64_t>(m) * cnt;
+    if (want_amax && m == 0) ma = max(ma, __float_as_uint(amp[li]));
+    int last_tile = -1;
+    uint64_t sref = 0;
+    for (int k = 0; k < nv; ++k) {
+      const int tile = (m * nv + k) >> 8;
+      if (tile != last_tile) {
+        last_tile = tile;
+        const int mc = min((tile * 256 + 128) / nv, nc - 1);
+        sref = w_tx[(static_cast<int64_t>(mc) * ntx + t_c) * stride + li].y +
+               w_rx[(static_cast<int64_t>(mc) * nrx + r_c) * stride + li].y;
+      }
+      const int t = k / nrx, r = k - t * nrx;
+      const uint64_t step = w_tx[(static_cast<int64_t>(m) * ntx + t) * stride + li].y +
+                            w_rx[(static_cast<int64_t>(m) * nrx + r) * stride + li].y;
+      md = max(md, signed_mag(step - sref));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (want_amax) atomicMax(amax_bits, ma);
+    atomicMax(d_max, md);
+  }
 }
 
 int sms_t() {
@@ -605,13 +723,13 @@ TShape plan_taylor(const Derived &g, int64_t n) {
 // the expansion needs two-SM tiles of at least 32 complex columns
 bool taylor_eligible(const Derived &g) { return g.ns >= 32; }
 
-template <bool F16, bool SPLIT, bool TDM>
+template <bool F16, bool SPLIT, int MODE>
 void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   const size_t smem =
       t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(sh.bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, TDM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kMaxDynSmemT);
     attr = true;
   }
@@ -627,7 +745,13 @@ void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, TDM>, a);
+  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE>, a);
+}
+
+template <int MODE>
+void launch_taylor_mode(bool f16, bool split, const TShape &sh, const TArgs &a, cudaStream_t s) {
+  if (f16) split ? launch_taylor<true, true, MODE>(sh, a, s) : launch_taylor<true, false, MODE>(sh, a, s);
+  else split ? launch_taylor<false, true, MODE>(sh, a, s) : launch_taylor<false, false, MODE>(sh, a, s);
 }
 
 }  // namespace
@@ -682,24 +806,93 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.terms = terms;
   a.lo_high = lo_high;
   a.status = status;
-  if (tdm) {
-    if (f16) split ? launch_taylor<true, true, true>(sh, a, s) : launch_taylor<true, false, true>(sh, a, s);
-    else split ? launch_taylor<false, true, true>(sh, a, s) : launch_taylor<false, false, true>(sh, a, s);
-  } else {
-    if (f16) split ? launch_taylor<true, true, false>(sh, a, s) : launch_taylor<true, false, false>(sh, a, s);
-    else split ? launch_taylor<false, true, false>(sh, a, s) : launch_taylor<false, false, false>(sh, a, s);
-  }
+  if (tdm) launch_taylor_mode<kExactTdm>(f16, split, sh, a, s);
+  else launch_taylor_mode<kExact>(f16, split, sh, a, s);
   ++kernels;
   // the per-chirp kernel, which returns at once unless P = 0 (it has no slot term: not with TDM)
   if (!tdm) kernels += launch_exact_main(g, p, n, workspace, status, s, terms);
   if (after_main) cudaEventRecord(after_main, s);
   const int rb = 4 * sms_t();
   if (f16)
-    taylor_reduce<true><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms);
+    taylor_reduce<true><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms, 0);
   else
-    taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms);
+    taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms, 0);
   ++kernels;
   if (!tdm) kernels += launch_exact_reduce(g, n, sig, workspace, s, terms);
+  return kernels;
+}
+
+int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk) {
+  if (!taylor_eligible(g) || chunk <= 0) return 0;
+  const TShape t = plan_taylor(g, chunk);
+  return static_cast<int64_t>(kHeader) + static_cast<int64_t>(t.splits) * g.nv * g.nc * 2 * g.ns * 4;
+}
+
+// Virtual snapshots on tensor cores, one chunk of rays: the same per-tile expansion with each
+// row's exact phase words, S_ref the ray's step at the tile's centre chirp and antennas,
+//   A_p[row, i] = a_i e^{2 pi j (C_row,i + n_c delta)} (j 2 pi n_h delta)^p / p!,
+//   B_p[i, n]   = e^{2 pi j n S_ref,i} (n' / n_h)^p,      delta = S_row,i - S_ref,i,
+// P from the chunk's largest |delta|; beyond the bound the direct pair sum runs instead (both
+// are launched, each returns at once when the other owns the chunk).  Adds to sig when
+// `accumulate`.
+int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, int64_t stride,
+                       const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
+                       uint32_t *status, cudaStream_t s) {
+  if (!taylor_eligible(g) || cnt <= 0)
+    return launch_pair_sum(g, w_tx, w_rx, amp, cnt, stride, accumulate, sig, pair_ws, nullptr, s);
+  const TShape sh = plan_taylor(g, cnt);
+  const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  uint8_t *ws = static_cast<uint8_t *>(workspace);
+  uint32_t *amax = reinterpret_cast<uint32_t *>(ws);
+  uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
+  unsigned long long *d_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
+  uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
+  unsigned long long *none = reinterpret_cast<unsigned long long *>(ws + kOffEpsTMax);  // stays 0
+  const int t_c = g.ntx / 2, r_c = g.nrx / 2;
+  int kernels = 0;
+  cudaMemsetAsync(ws, 0, 32, s);
+  snap_stats<<<4 * sms_t(), 256, 0, s>>>(w_tx, w_rx, stride, amp, cnt, g.nc, g.nv, g.ntx, g.nrx, t_c, r_c, f16, amax,
+                                         d_max);
+  // theta = 2 pi n_h max|delta|, delta in cycles per sample (the word times 2^-64)
+  const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
+  const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
+  choose_terms<<<1, 1, 0, s>>>(d_max, none, terms, lo_high, xs, 0.0, split ? 1e-6 : 1e-5, two_u, 2e-6, false, status);
+  kernels += 2;
+  TArgs a{};
+  a.w_tx = w_tx;
+  a.w_rx = w_rx;
+  a.stride = stride;
+  a.samp = amp;
+  a.ntx = g.ntx;
+  a.r_c = r_c;
+  a.n_rays = cnt;
+  a.chunk = sh.chunk;
+  a.nc = g.nc;
+  a.ns = g.ns;
+  a.nv = g.nv;
+  a.nrx = g.nrx;
+  a.m_rows = g.nv * g.nc;
+  a.t_c = t_c;
+  a.bn = sh.bn;
+  a.mt2 = sh.mt2;
+  a.nt = sh.nt;
+  a.partials = reinterpret_cast<float *>(ws + kHeader);
+  a.amax_bits = amax;
+  a.terms = terms;
+  a.lo_high = lo_high;
+  a.status = status;
+  launch_taylor_mode<kSnap>(f16, split, sh, a, s);
+  const int rb = 4 * sms_t();
+  if (f16)
+    taylor_reduce<true><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms,
+                                           accumulate ? 1 : 0);
+  else
+    taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms,
+                                            accumulate ? 1 : 0);
+  kernels += 2;
+  // the direct pair sum, which returns at once unless P = 0
+  kernels += launch_pair_sum(g, w_tx, w_rx, amp, cnt, stride, accumulate, sig, pair_ws, terms, s);
   return kernels;
 }
 

@@ -8,7 +8,7 @@ import torch
 import oracle
 import scenegen
 from paper_2305_14176_gb300 import radarsim as rs
-from gpu_helpers import rel_max, rel_rms, to_c
+from gpu_helpers import TOL, TOL_RMS, rel_max, rel_rms, to_c
 
 pytestmark = pytest.mark.gpu
 
@@ -60,27 +60,37 @@ def test_paths_match_oracle(device):
     assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-9   # the reference pair itself: FP64 only
 
 
-@pytest.mark.parametrize("shape", [(32, 16, 3, 4, 16), (64, 8, 1, 4, 16), (16, 4, 2, 3, 8)])
-def test_signal_spectrum_labels_match_oracle(shape):
+PRECISIONS = [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16,
+              rs.SIM_PREC_BF16]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+@pytest.mark.parametrize("shape", [(32, 16, 3, 4, 16), (64, 8, 1, 4, 16), (16, 4, 2, 3, 8), (128, 64, 2, 2, 4)])
+def test_signal_spectrum_labels_match_oracle(shape, precision):
+    """Every precision: FP32 sums directly; the tensor-core precisions expand each tile about
+    its centre with each row's own phase words (N_s = 16 is summed directly at any precision)."""
     ns, nc, ntx, nrx, na = shape
     radar = scenegen.Radar(77e9, 1e9, 51.2e-6, 60e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na)
     rays, hits, geom = scenegen.moving_scene(ns + nc, radar, 333, n_objects=5, bounce_frac=0.3)
-    rc, sig, spec, lab = snapshot(radar, rays, hits, geom)
+    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     ref = oracle.signal_geom(radar, rays, hits, geom)
-    assert rel_max(sig, ref) <= 1e-5 and rel_rms(sig, ref) <= 1e-5
-    assert rel_max(spec, oracle.spectrum(radar, ref)) <= 1e-5
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
     assert np.array_equal(lab, oracle.labels(radar, rays))
     # host inputs give the same bits
-    rc, sig_h, _, _ = snapshot(radar, rays, hits, geom, device=False)
+    rc, sig_h, _, _ = snapshot(radar, rays, hits, geom, device=False, precision=precision)
     assert rc == rs.SIM_OK and np.array_equal(sig_h, sig)
 
 
-def test_automotive_size_in_two_chunks_sampled():
-    """256 chirps x 512 samples x 12 channels; 45,000 rays need two chunks of phase words."""
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT])
+def test_automotive_size_in_two_chunks_sampled(precision):
+    """256 chirps x 512 samples x 12 channels; 45,000 rays need two chunks of phase words (the
+    second chunk adds to the first, on tensor cores too)."""
     radar = scenegen.radar_automotive()
     rays, hits, geom = scenegen.moving_scene(1234, radar, 45_000, n_objects=20)
-    rc, sig, spec, lab = snapshot(radar, rays, hits, geom)
+    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     idx = scenegen.randint(1234, 9, 384, 0, sig.size - 1).astype(np.int64)
     ref = oracle.signal_geom_at(radar, rays, hits, geom, idx)
@@ -103,7 +113,7 @@ def test_invalid_geometry_is_an_error():
     off = hits.offset.copy()
     off[10] = off[11]                                  # ray 10 left without hits
     assert snapshot(radar, rays, scenegen.Hits(off, hits.triangle, hits.u, hits.v), geom)[0] == rs.SIM_E_INVALID
-    # the tensor-core precisions have no non-separable path
-    assert snapshot(radar, rays, hits, geom, precision=rs.SIM_PREC_BF16_SPLIT)[0] == rs.SIM_E_INVALID
+    # the tensor-core precisions run snapshots too
+    assert snapshot(radar, rays, hits, geom, precision=rs.SIM_PREC_BF16_SPLIT)[0] == rs.SIM_OK
     # and a good call still works afterwards
     assert snapshot(radar, rays, hits, geom)[0] == rs.SIM_OK
