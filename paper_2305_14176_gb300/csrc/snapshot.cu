@@ -37,7 +37,6 @@ using namespace rs;
 
 namespace {
 
-constexpr double kTwo64 = 18446744073709551616.0;
 constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;
 constexpr size_t kWordBudget = size_t{1} << 30;
 
@@ -56,12 +55,62 @@ struct GeomDev {
 struct PhaseConst {
   double fc_over_c;   // f_c / c: carrier cycles per metre of path
   double step_per_m;  // B / (c N_s): beat cycles per sample per metre of path
+  float fc_f, sp_f;   // the two in FP32, for the antenna offsets
   int nc, ntx, nrx;
 };
 
+// The FP64 pipe of this GPU runs at 1/64 of the FP32 rate, so the kernels below keep on it
+// only the arithmetic that needs 53 bits (hit positions, squared legs, the Newton step of each
+// leg, the path-to-cycles products) and do conversions and the Q0.64 reduction in integer and
+// FP32 instructions.
+
+// x mod 1 as a Q0.64 phase, from the bits of x: x = +-m 2^(e - 1075) with m the 53-bit
+// significand, so x 2^64 mod 2^64 = +-m 2^(e - 1011) mod 2^64 (rounded to nearest when the
+// shift is to the right; zero, subnormal and non-finite x give 0)
 __device__ __forceinline__ uint64_t frac_q64(double x) {
-  const double f = x - floor(x);
-  return __double2ull_rn(f * kTwo64);
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff) return 0;
+  const uint64_t m = (b & 0xfffffffffffffull) | (uint64_t{1} << 52);
+  const int sh = e - 1011;
+  uint64_t q = 0;
+  if (sh >= 0) {
+    if (sh < 64) q = m << sh;
+  } else if (sh > -64) {
+    q = (m + (uint64_t{1} << (-sh - 1))) >> -sh;
+  }
+  return (b >> 63) ? uint64_t{0} - q : q;
+}
+
+// x to FP32 by its bits, the fraction truncated to 23 bits (relative error below 2^-23); zero
+// and magnitudes outside the normal FP32 range go through the conversion instruction
+__device__ __forceinline__ float f32_of(double x) {
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e < 1 || e > 254) return static_cast<float>(x);
+  return __uint_as_float(static_cast<uint32_t>(b >> 32 & 0x80000000u) | (static_cast<uint32_t>(e) << 23) |
+                         static_cast<uint32_t>(b >> 29 & 0x7fffffu));
+}
+
+// x to FP64 by its bits (exact); zero, subnormal and non-finite x through the instruction
+__device__ __forceinline__ double f64_of(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xff;
+  if (e == 0 || e == 0xff) return static_cast<double>(x);
+  return __longlong_as_double(static_cast<long long>((static_cast<uint64_t>(u & 0x80000000u) << 32) |
+                                                     (static_cast<uint64_t>(e + 896) << 52) |
+                                                     (static_cast<uint64_t>(u & 0x7fffffu) << 29)));
+}
+
+// sqrt(x) for x >= 0 by one Newton (Heron) step from the FP32 root: s0 = sqrtf(x) is within
+// ~2^-23 of the root, s0 + (x - s0^2) / (2 s0) within ~2^-46 (the residual x - s0^2 in one FP64
+// fma, its scaling in FP32, which costs another ~2^-23 of a 2^-23 correction)
+__device__ __forceinline__ double sqrt_newton(double x) {
+  const float s0 = sqrtf(f32_of(x));
+  if (!(s0 > 0.f) || !(s0 < 1e18f)) return sqrt(x);
+  const double s0d = f64_of(s0);
+  const float r = f32_of(fma(-s0d, s0d, x));
+  return s0d + f64_of(r * (0.5f / s0));
 }
 
 // hit h at snapshot j (Eq. 6); false when its triangle or one of the vertex indices is out of range
@@ -72,7 +121,7 @@ __device__ bool hit_at(const GeomDev &g, int64_t j, int64_t h, double p[3]) {
                 c = g.tri[3 * static_cast<int64_t>(tr) + 2];
   if (a < 0 || a >= g.n_vert || b < 0 || b >= g.n_vert || c < 0 || c >= g.n_vert) return false;
   const double *V = g.vert + j * g.n_vert * 3;
-  const double u = static_cast<double>(g.hu[h]), v = static_cast<double>(g.hv[h]);
+  const double u = f64_of(g.hu[h]), v = f64_of(g.hv[h]);
   const double w = 1.0 - u - v;
 #pragma unroll
   for (int q = 0; q < 3; ++q) p[q] = w * V[3 * a + q] + u * V[3 * b + q] + v * V[3 * c + q];
@@ -84,8 +133,14 @@ __device__ __forceinline__ double dist3(const double *a, const double *b) {
   return sqrt(x * x + y * y + z * z);
 }
 
+__device__ __forceinline__ double dist3_newton(const double *a, const double *b) {
+  const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
+  return sqrt_newton(x * x + y * y + z * z);
+}
+
 // Hits of ray i at snapshot j: first and last position and the length between them; false
 // when the hit list or an index is out of range (nothing is read past it)
+template <bool NEWTON>
 __device__ bool ray_hits(const GeomDev &g, int64_t i, int64_t j, double pf[3], double pl[3], double &inner) {
   const int64_t h0 = g.off[i], h1 = g.off[i + 1];
   inner = 0.0;
@@ -96,7 +151,7 @@ __device__ bool ray_hits(const GeomDev &g, int64_t i, int64_t j, double pf[3], d
   for (int64_t h = h0 + 1; h < h1; ++h) {
     double c[3];
     if (!hit_at(g, j, h, c)) return false;
-    inner += dist3(pl, c);
+    inner += NEWTON ? dist3_newton(pl, c) : dist3(pl, c);
 #pragma unroll
     for (int q = 0; q < 3; ++q) pl[q] = c[q];
   }
@@ -109,7 +164,7 @@ __global__ void __launch_bounds__(128) snapshot0_kernel(GeomDev g, const double 
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
   double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
-  if (!ray_hits(g, i, 0, pf, pl, inner)) {
+  if (!ray_hits<false>(g, i, 0, pf, pl, inner)) {
     atomicOr(status, kStatusBadGeometry);
     base0[i] = make_double2(0.0, 0.0);
     return;
@@ -119,16 +174,16 @@ __global__ void __launch_bounds__(128) snapshot0_kernel(GeomDev g, const double 
 
 // |u - e| - |u| for an antenna offset e from the reference (see the file comment), FP32
 __device__ __forceinline__ float leg_offset(const double u[3], float s, float4 e) {
-  const float num = fmaf(-2.f, fmaf(static_cast<float>(u[0]), e.x,
-                                    fmaf(static_cast<float>(u[1]), e.y, static_cast<float>(u[2]) * e.z)),
-                         e.w);
+  const float num = fmaf(-2.f, fmaf(f32_of(u[0]), e.x, fmaf(f32_of(u[1]), e.y, f32_of(u[2]) * e.z)), e.w);
   const float den = sqrtf(fmaf(s, s, num)) + s;
   return num / den;
 }
 
-// a small cycle count (|x| < 2^31) as a Q0.64 phase
+// a small cycle count as a Q0.64 phase: only x - rint(x), exact and within +-1/2, counts, so
+// a 32-bit conversion of it times 2^32 gives the word's upper half
 __device__ __forceinline__ uint64_t q64_small(float x) {
-  return static_cast<uint64_t>(__float2ll_rn(x * 4294967296.0f)) << 32;
+  const float f = x - rintf(x);
+  return static_cast<uint64_t>(static_cast<uint32_t>(__float2int_rn(f * 4294967296.0f))) << 32;
 }
 
 // One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y).  paths != null:
@@ -143,32 +198,31 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double2 
   if (li >= cnt) return;
   const int64_t i = i0 + li;
   double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
-  const bool ok = ray_hits(g, i, j, pf, pl, inner);
+  const bool ok = ray_hits<true>(g, i, j, pf, pl, inner);
   if (!ok) atomicOr(status, kStatusBadGeometry);
   const double ut[3] = {pf[0] - g.ref_tx[0], pf[1] - g.ref_tx[1], pf[2] - g.ref_tx[2]};
   const double ur[3] = {pl[0] - g.ref_rx[0], pl[1] - g.ref_rx[1], pl[2] - g.ref_rx[2]};
-  const double st = sqrt(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-  const double sr = sqrt(ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2]);
+  const double st = sqrt_newton(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
+  const double sr = sqrt_newton(ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2]);
   const double2 b0 = base0[i];
   // Eq. 7 with the reference antennas: the traced length without its snapshot-0 antenna legs,
   // the stretch between the hits re-measured, and the two reference legs at snapshot j
   const double a_ref = b0.x + inner + st;
   const double b_ref = b0.y + sr;
-  const float stf = static_cast<float>(st), srf = static_cast<float>(sr);
+  const float stf = f32_of(st), srf = f32_of(sr);
   if (paths) {
     const int nv = k.ntx * k.nrx;
     double *o = paths + (i * k.nc + j) * nv;
     for (int t = 0; t < k.ntx; ++t) {
-      const double a = a_ref + static_cast<double>(leg_offset(ut, stf, g.tx[t]));
-      for (int r = 0; r < k.nrx; ++r)
-        o[t * k.nrx + r] = ok ? a + (b_ref + static_cast<double>(leg_offset(ur, srf, g.rx[r]))) : 0.0;
+      const double a = a_ref + f64_of(leg_offset(ut, stf, g.tx[t]));
+      for (int r = 0; r < k.nrx; ++r) o[t * k.nrx + r] = ok ? a + (b_ref + f64_of(leg_offset(ur, srf, g.rx[r]))) : 0.0;
     }
     return;
   }
-  const uint64_t q0 = frac_q64(static_cast<double>(p0[i]) * kInv2Pi);
+  const uint64_t q0 = frac_q64(f64_of(p0[i]) * kInv2Pi);
   const uint64_t at_c = frac_q64(a_ref * k.fc_over_c) + q0, at_s = frac_q64(a_ref * k.step_per_m);
   const uint64_t br_c = frac_q64(b_ref * k.fc_over_c), br_s = frac_q64(b_ref * k.step_per_m);
-  const float fc_f = static_cast<float>(k.fc_over_c), sp_f = static_cast<float>(k.step_per_m);
+  const float fc_f = k.fc_f, sp_f = k.sp_f;
   for (int t = 0; t < k.ntx; ++t) {
     const float e = leg_offset(ut, stf, g.tx[t]);
     w_tx[(j * k.ntx + t) * stride + li] =
@@ -369,6 +423,8 @@ PhaseConst phase_const(const Derived &g) {
   PhaseConst k;
   k.fc_over_c = g.fc / kC;
   k.step_per_m = g.bw / (kC * static_cast<double>(g.ns));
+  k.fc_f = static_cast<float>(k.fc_over_c);
+  k.sp_f = static_cast<float>(k.step_per_m);
   k.nc = g.nc;
   k.ntx = g.ntx;
   k.nrx = g.nrx;
