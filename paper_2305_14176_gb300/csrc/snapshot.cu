@@ -13,18 +13,21 @@
 // not separable over chirps and channels: it runs on the direct-sum path (FP32) or, at the
 // tensor-core precisions, through the per-tile expansion of umma_taylor.cu with each row's own
 // phase words (the direct sum remains that path's fallback, gated on the device).  One thread per
-// (ray, chirp) computes A_t and B_r in FP64 and stores them as Q0.64 phase words (carrier
+// (ray, chirp) computes A_t and B_r and stores them as Q0.64 phase words (carrier
 // f_c l / c plus the start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m)
 // of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
 // antennas take N_c (N_tx + N_rx) 16 bytes per ray, so rays go through in chunks that keep
 // them within 1 GiB.
 //
-// FP64 carries what needs it: the hit positions, the legs to the two reference antennas
-// s = |p - x_ref| and the phase words of the reference paths (f_c l / c is ~10^4 cycles).  An
+// The reference paths need ~48 bits (f_c l / c is ~10^4 cycles, wanted to ~10^-9): the hit
+// positions, the legs to the two reference antennas s = |p - x_ref| and the reference phase
+// words are carried per chirp as float-float numbers (hi + lo FP32), since this GPU's FP64 rate
+// is 1/64 of its FP32 rate; FP64 is used once per call (the vertices, split into float-float
+// relative to the reference transmitter) and once per ray (the snapshot-0 terms of Eq. 7).  An
 // antenna at x_ref + e differs from the reference leg by |u - e| - |u| = (|e|^2 - 2 u.e) /
 // (|u - e| + |u|), u = p - x_ref, a few centimetres for a compact array: that difference is
 // taken in FP32 (relative error ~2^-22, so ~5 nm for e = 2 cm, 8e-6 rad of carrier phase)
-// and added to the words as Q0.64.  The snapshot-0 terms of Eq. 7 are computed once per ray.
+// and added to the words as Q0.64.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -40,12 +43,19 @@ namespace {
 constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;
 constexpr size_t kWordBudget = size_t{1} << 30;
 
+// Float-float numbers x = hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits
+struct ff {
+  float hi, lo;
+};
+
 struct GeomDev {
   const double *vert;  // [N_c][V][3]
+  const float2 *vff;   // [N_c][V][3]: the vertices minus ref_tx as float-float (hi, lo)
   const int32_t *tri;  // [T][3]
   const float4 *tx;    // [n_tx]: (e, |e|^2) with e = x_t - ref_tx
   const float4 *rx;    // [n_rx]: (e, |e|^2) with e = x_r - ref_rx
   double ref_tx[3], ref_rx[3];
+  ff t2r[3];           // ref_tx - ref_rx
   const int64_t *off;  // [n + 1]
   const int32_t *htri;
   const float *hu, *hv;
@@ -53,16 +63,10 @@ struct GeomDev {
 };
 
 struct PhaseConst {
-  double fc_over_c;   // f_c / c: carrier cycles per metre of path
-  double step_per_m;  // B / (c N_s): beat cycles per sample per metre of path
-  float fc_f, sp_f;   // the two in FP32, for the antenna offsets
+  ff fc;  // f_c / c: carrier cycles per metre of path
+  ff sp;  // B / (c N_s): beat cycles per sample per metre of path
   int nc, ntx, nrx;
 };
-
-// The FP64 pipe of this GPU runs at 1/64 of the FP32 rate, so the kernels below keep on it
-// only the arithmetic that needs 53 bits (hit positions, squared legs, the Newton step of each
-// leg, the path-to-cycles products) and do conversions and the Q0.64 reduction in integer and
-// FP32 instructions.
 
 // x mod 1 as a Q0.64 phase, from the bits of x: x = +-m 2^(e - 1075) with m the 53-bit
 // significand, so x 2^64 mod 2^64 = +-m 2^(e - 1011) mod 2^64 (rounded to nearest when the
@@ -82,16 +86,6 @@ __device__ __forceinline__ uint64_t frac_q64(double x) {
   return (b >> 63) ? uint64_t{0} - q : q;
 }
 
-// x to FP32 by its bits, the fraction truncated to 23 bits (relative error below 2^-23); zero
-// and magnitudes outside the normal FP32 range go through the conversion instruction
-__device__ __forceinline__ float f32_of(double x) {
-  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
-  const int e = static_cast<int>((b >> 52) & 0x7ff) - 1023 + 127;
-  if (e < 1 || e > 254) return static_cast<float>(x);
-  return __uint_as_float(static_cast<uint32_t>(b >> 32 & 0x80000000u) | (static_cast<uint32_t>(e) << 23) |
-                         static_cast<uint32_t>(b >> 29 & 0x7fffffu));
-}
-
 // x to FP64 by its bits (exact); zero, subnormal and non-finite x through the instruction
 __device__ __forceinline__ double f64_of(float x) {
   const uint32_t u = __float_as_uint(x);
@@ -102,29 +96,115 @@ __device__ __forceinline__ double f64_of(float x) {
                                                      (static_cast<uint64_t>(u & 0x7fffffu) << 29)));
 }
 
-// sqrt(x) for x >= 0 by one Newton (Heron) step from the FP32 root: s0 = sqrtf(x) is within
-// ~2^-23 of the root, s0 + (x - s0^2) / (2 s0) within ~2^-46 (the residual x - s0^2 in one FP64
-// fma, its scaling in FP32, which costs another ~2^-23 of a 2^-23 correction)
-__device__ __forceinline__ double sqrt_newton(double x) {
-  const float s0 = sqrtf(f32_of(x));
-  if (!(s0 > 0.f) || !(s0 < 1e18f)) return sqrt(x);
-  const double s0d = f64_of(s0);
-  const float r = f32_of(fma(-s0d, s0d, x));
-  return s0d + f64_of(r * (0.5f / s0));
+// ---- float-float arithmetic.  This GPU's FP64 pipe runs at 1/64 of its FP32 rate, so the
+// per-chirp path lengths are carried as unevaluated sums of two floats, using the error-free
+// transformations of Knuth (two-sum), Dekker (fast two-sum) and the fma product error.  Every
+// operand here is a length of at most ~10^3 m (or one times a cycles-per-metre constant), and
+// the sums below err by ~2^-47 of their operands, so a path stays within ~10^-12 m of its FP64
+// value.  Products that must be rounded use __fmul_rn, which is never fused into an fma.
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ ff ff_fast(float a, float b) {  // a + b, |a| >= |b| or a = 0
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_fast(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ ff ff_add_f(ff a, float b) {
+  const ff s = ff_two_sum(a.hi, b);
+  return ff_fast(s.hi, s.lo + a.lo);
+}
+
+__device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, {-b.hi, -b.lo}); }
+
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  return ff_fast(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, fmaf(a.hi, b.hi, -p))));
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  return ff_fast(p, fmaf(a.lo, b, fmaf(a.hi, b, -p)));
+}
+
+__device__ __forceinline__ ff ff_sqr(ff a) {
+  const float p = __fmul_rn(a.hi, a.hi);
+  return ff_fast(p, fmaf(2.f * a.hi, a.lo, fmaf(a.hi, a.hi, -p)));
+}
+
+// sqrt(x), x >= 0: the FP32 root s0 and one Newton (Heron) step s0 + (x - s0^2) / (2 s0), the
+// residual formed exactly to first order (x.hi - s0^2 is exact by Sterbenz's lemma)
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+  if (!(x.hi > 0.f)) return {0.f, 0.f};
+  const float s0 = sqrtf(x.hi);
+  const float p = __fmul_rn(s0, s0);
+  const float r = ((x.hi - p) - fmaf(s0, s0, -p)) + x.lo;
+  return ff_fast(s0, __fdividef(r, s0 + s0));
+}
+
+__device__ __forceinline__ ff ff_norm(const ff u[3]) {
+  return ff_sqrt(ff_add(ff_add(ff_sqr(u[0]), ff_sqr(u[1])), ff_sqr(u[2])));
+}
+
+// a cycle count x (any float) mod 1 as a Q0.64 phase: f = x - rint(x) is exact and within
+// +-1/2; f 2^64 is taken as h 2^33 + l 2^2 with h = rint(f 2^31) and l = rint((f 2^31 - h) 2^31),
+// both exact 31-bit conversions
+__device__ __forceinline__ uint64_t q64_of(float x) {
+  const float y = (x - rintf(x)) * 2147483648.0f;
+  const float h = rintf(y);
+  return (static_cast<uint64_t>(static_cast<int64_t>(__float2int_rn(h))) << 33) +
+         (static_cast<uint64_t>(static_cast<int64_t>(__float2int_rn((y - h) * 2147483648.0f))) << 2);
+}
+
+// (a K) mod 1 as a Q0.64 phase for a length a and a cycles-per-metre constant K, both
+// float-float: the rounded product p, and its error plus the cross terms t (~2^-9 for a 10^4-cycle
+// path), each reduced on its own and added as integers
+__device__ __forceinline__ uint64_t q64_prod(ff a, ff K) {
+  const float p = __fmul_rn(a.hi, K.hi);
+  const float t = fmaf(a.hi, K.lo, fmaf(a.lo, K.hi, fmaf(a.hi, K.hi, -p)));
+  return q64_of(p) + q64_of(t);
 }
 
 // hit h at snapshot j (Eq. 6); false when its triangle or one of the vertex indices is out of range
-__device__ bool hit_at(const GeomDev &g, int64_t j, int64_t h, double p[3]) {
+__device__ __forceinline__ bool hit_tri(const GeomDev &g, int64_t h, int32_t &a, int32_t &b, int32_t &c) {
   const int32_t tr = g.htri[h];
   if (tr < 0 || tr >= g.n_tri) return false;
-  const int32_t a = g.tri[3 * static_cast<int64_t>(tr)], b = g.tri[3 * static_cast<int64_t>(tr) + 1],
-                c = g.tri[3 * static_cast<int64_t>(tr) + 2];
-  if (a < 0 || a >= g.n_vert || b < 0 || b >= g.n_vert || c < 0 || c >= g.n_vert) return false;
+  a = g.tri[3 * static_cast<int64_t>(tr)];
+  b = g.tri[3 * static_cast<int64_t>(tr) + 1];
+  c = g.tri[3 * static_cast<int64_t>(tr) + 2];
+  return a >= 0 && a < g.n_vert && b >= 0 && b < g.n_vert && c >= 0 && c < g.n_vert;
+}
+
+__device__ bool hit_at(const GeomDev &g, int64_t j, int64_t h, double p[3]) {
+  int32_t a, b, c;
+  if (!hit_tri(g, h, a, b, c)) return false;
   const double *V = g.vert + j * g.n_vert * 3;
-  const double u = f64_of(g.hu[h]), v = f64_of(g.hv[h]);
+  const double u = static_cast<double>(g.hu[h]), v = static_cast<double>(g.hv[h]);
   const double w = 1.0 - u - v;
 #pragma unroll
   for (int q = 0; q < 3; ++q) p[q] = w * V[3 * a + q] + u * V[3 * b + q] + v * V[3 * c + q];
+  return true;
+}
+
+// the same in float-float, relative to ref_tx
+__device__ bool hit_at_ff(const GeomDev &g, int64_t j, int64_t h, ff p[3]) {
+  int32_t a, b, c;
+  if (!hit_tri(g, h, a, b, c)) return false;
+  const float2 *V = g.vff + j * g.n_vert * 3;
+  const float u = g.hu[h], v = g.hv[h];
+  const ff w = ff_add_f(ff_two_sum(1.f, -u), -v);
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float2 va = V[3 * a + q], vb = V[3 * b + q], vc = V[3 * c + q];
+    p[q] = ff_add(ff_add(ff_mul(w, {va.x, va.y}), ff_mul_f({vb.x, vb.y}, u)), ff_mul_f({vc.x, vc.y}, v));
+  }
   return true;
 }
 
@@ -133,48 +213,77 @@ __device__ __forceinline__ double dist3(const double *a, const double *b) {
   return sqrt(x * x + y * y + z * z);
 }
 
-__device__ __forceinline__ double dist3_newton(const double *a, const double *b) {
-  const double x = a[0] - b[0], y = a[1] - b[1], z = a[2] - b[2];
-  return sqrt_newton(x * x + y * y + z * z);
+// Hits of ray i at snapshot j: first and last position and the length between them; false
+// when the hit list or an index is out of range (nothing is read past it).  P is double (FP64,
+// absolute positions) or ff (float-float, relative to ref_tx).
+__device__ __forceinline__ bool hit_pos(const GeomDev &g, int64_t j, int64_t h, double p[3]) {
+  return hit_at(g, j, h, p);
+}
+__device__ __forceinline__ bool hit_pos(const GeomDev &g, int64_t j, int64_t h, ff p[3]) {
+  return hit_at_ff(g, j, h, p);
+}
+__device__ __forceinline__ void leg_add(double &s, const double *a, const double *b) { s += dist3(a, b); }
+__device__ __forceinline__ void leg_add(ff &s, const ff *a, const ff *b) {
+  const ff d[3] = {ff_sub(a[0], b[0]), ff_sub(a[1], b[1]), ff_sub(a[2], b[2])};
+  s = ff_add(s, ff_norm(d));
 }
 
-// Hits of ray i at snapshot j: first and last position and the length between them; false
-// when the hit list or an index is out of range (nothing is read past it)
-template <bool NEWTON>
-__device__ bool ray_hits(const GeomDev &g, int64_t i, int64_t j, double pf[3], double pl[3], double &inner) {
+template <typename P>
+__device__ bool ray_hits(const GeomDev &g, int64_t i, int64_t j, P pf[3], P pl[3], P &inner) {
   const int64_t h0 = g.off[i], h1 = g.off[i + 1];
-  inner = 0.0;
   if (!(h0 >= 0 && h1 > h0 && h1 <= g.n_hits)) return false;
-  if (!hit_at(g, j, h0, pf)) return false;
+  if (!hit_pos(g, j, h0, pf)) return false;
 #pragma unroll
   for (int q = 0; q < 3; ++q) pl[q] = pf[q];
   for (int64_t h = h0 + 1; h < h1; ++h) {
-    double c[3];
-    if (!hit_at(g, j, h, c)) return false;
-    inner += NEWTON ? dist3_newton(pl, c) : dist3(pl, c);
+    P c[3];
+    if (!hit_pos(g, j, h, c)) return false;
+    leg_add(inner, pl, c);
 #pragma unroll
     for (int q = 0; q < 3; ++q) pl[q] = c[q];
   }
   return true;
 }
 
-// Per ray, snapshot 0 of Eq. 7: base0 = (d - inner(0) - |p_f(0) - ref_tx|, -|p_l(0) - ref_rx|)
-__global__ void __launch_bounds__(128) snapshot0_kernel(GeomDev g, const double *__restrict__ d, int64_t n,
-                                                        double2 *__restrict__ base0, uint32_t *status) {
+__device__ __forceinline__ float4 ff_pair(double a, double b) {
+  const float ah = static_cast<float>(a), bh = static_cast<float>(b);
+  return make_float4(ah, static_cast<float>(a - static_cast<double>(ah)), bh,
+                     static_cast<float>(b - static_cast<double>(bh)));
+}
+
+// Per ray, in FP64: snapshot 0 of Eq. 7, base0 = (d - inner(0) - |p_f(0) - ref_tx|,
+// -|p_l(0) - ref_rx|) as two float-float numbers, and the start phase phi0 / 2 pi as Q0.64
+__global__ void __launch_bounds__(128) snapshot0_kernel(GeomDev g, const double *__restrict__ d,
+                                                        const float *__restrict__ p0, int64_t n,
+                                                        float4 *__restrict__ base0, uint64_t *__restrict__ q0,
+                                                        uint32_t *status) {
   const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (i >= n) return;
+  q0[i] = frac_q64(static_cast<double>(p0[i]) * kInv2Pi);
   double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
-  if (!ray_hits<false>(g, i, 0, pf, pl, inner)) {
+  if (!ray_hits(g, i, 0, pf, pl, inner)) {
     atomicOr(status, kStatusBadGeometry);
-    base0[i] = make_double2(0.0, 0.0);
+    base0[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     return;
   }
-  base0[i] = make_double2(d[i] - inner - dist3(pf, g.ref_tx), -dist3(pl, g.ref_rx));
+  base0[i] = ff_pair(d[i] - inner - dist3(pf, g.ref_tx), -dist3(pl, g.ref_rx));
+}
+
+// The vertices of every snapshot minus ref_tx, split into float-float (FP64, once per call)
+__global__ void split_vertices_kernel(const double *__restrict__ v, int64_t n_val, double r0, double r1, double r2,
+                                      float2 *__restrict__ out) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n_val;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int q = static_cast<int>(e % 3);
+    const double x = v[e] - (q == 0 ? r0 : (q == 1 ? r1 : r2));
+    const float hi = static_cast<float>(x);
+    out[e] = make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+  }
 }
 
 // |u - e| - |u| for an antenna offset e from the reference (see the file comment), FP32
-__device__ __forceinline__ float leg_offset(const double u[3], float s, float4 e) {
-  const float num = fmaf(-2.f, fmaf(f32_of(u[0]), e.x, fmaf(f32_of(u[1]), e.y, f32_of(u[2]) * e.z)), e.w);
+__device__ __forceinline__ float leg_offset(const ff u[3], float s, float4 e) {
+  const float num = fmaf(-2.f, fmaf(u[0].hi, e.x, fmaf(u[1].hi, e.y, u[2].hi * e.z)), e.w);
   const float den = sqrtf(fmaf(s, s, num)) + s;
   return num / den;
 }
@@ -186,10 +295,11 @@ __device__ __forceinline__ uint64_t q64_small(float x) {
   return static_cast<uint64_t>(static_cast<uint32_t>(__float2int_rn(f * 4294967296.0f))) << 32;
 }
 
-// One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y).  paths != null:
-// l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the phase words of A_t and B_r.
-__global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double2 *__restrict__ base0,
-                                                       const float *__restrict__ p0, int64_t i0, int64_t cnt,
+// One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y), in float-float
+// and FP32 only.  paths != null: l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the
+// phase words of A_t and B_r.
+__global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *__restrict__ base0,
+                                                       const uint64_t *__restrict__ q0s, int64_t i0, int64_t cnt,
                                                        PhaseConst k, double *__restrict__ paths,
                                                        ulonglong2 *__restrict__ w_tx, ulonglong2 *__restrict__ w_rx,
                                                        int64_t stride, uint32_t *status) {
@@ -197,42 +307,46 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const double2 
   const int64_t j = blockIdx.y;
   if (li >= cnt) return;
   const int64_t i = i0 + li;
-  double pf[3] = {0, 0, 0}, pl[3] = {0, 0, 0}, inner = 0.0;
-  const bool ok = ray_hits<true>(g, i, j, pf, pl, inner);
+  ff ut[3] = {}, pl[3] = {}, inner = {0.f, 0.f};
+  const bool ok = ray_hits(g, i, j, ut, pl, inner);  // positions relative to ref_tx: ut = p_f - ref_tx
   if (!ok) atomicOr(status, kStatusBadGeometry);
-  const double ut[3] = {pf[0] - g.ref_tx[0], pf[1] - g.ref_tx[1], pf[2] - g.ref_tx[2]};
-  const double ur[3] = {pl[0] - g.ref_rx[0], pl[1] - g.ref_rx[1], pl[2] - g.ref_rx[2]};
-  const double st = sqrt_newton(ut[0] * ut[0] + ut[1] * ut[1] + ut[2] * ut[2]);
-  const double sr = sqrt_newton(ur[0] * ur[0] + ur[1] * ur[1] + ur[2] * ur[2]);
-  const double2 b0 = base0[i];
+  const ff ur[3] = {ff_add(pl[0], g.t2r[0]), ff_add(pl[1], g.t2r[1]), ff_add(pl[2], g.t2r[2])};
+  const ff st = ff_norm(ut), sr = ff_norm(ur);
+  const float4 b0 = base0[i];
   // Eq. 7 with the reference antennas: the traced length without its snapshot-0 antenna legs,
   // the stretch between the hits re-measured, and the two reference legs at snapshot j
-  const double a_ref = b0.x + inner + st;
-  const double b_ref = b0.y + sr;
-  const float stf = f32_of(st), srf = f32_of(sr);
+  const ff a_ref = ff_add(ff_add({b0.x, b0.y}, inner), st);
+  const ff b_ref = ff_add({b0.z, b0.w}, sr);
   if (paths) {
     const int nv = k.ntx * k.nrx;
     double *o = paths + (i * k.nc + j) * nv;
     for (int t = 0; t < k.ntx; ++t) {
-      const double a = a_ref + f64_of(leg_offset(ut, stf, g.tx[t]));
-      for (int r = 0; r < k.nrx; ++r) o[t * k.nrx + r] = ok ? a + (b_ref + f64_of(leg_offset(ur, srf, g.rx[r]))) : 0.0;
+      const ff a = ff_add_f(a_ref, leg_offset(ut, st.hi, g.tx[t]));
+      for (int r = 0; r < k.nrx; ++r) {
+        const ff l = ff_add(a, ff_add_f(b_ref, leg_offset(ur, sr.hi, g.rx[r])));
+        o[t * k.nrx + r] = ok ? f64_of(l.hi) + f64_of(l.lo) : 0.0;
+      }
     }
     return;
   }
-  const uint64_t q0 = frac_q64(f64_of(p0[i]) * kInv2Pi);
-  const uint64_t at_c = frac_q64(a_ref * k.fc_over_c) + q0, at_s = frac_q64(a_ref * k.step_per_m);
-  const uint64_t br_c = frac_q64(b_ref * k.fc_over_c), br_s = frac_q64(b_ref * k.step_per_m);
-  const float fc_f = k.fc_f, sp_f = k.sp_f;
+  const uint64_t at_c = q64_prod(a_ref, k.fc) + q0s[i], at_s = q64_prod(a_ref, k.sp);
+  const uint64_t br_c = q64_prod(b_ref, k.fc), br_s = q64_prod(b_ref, k.sp);
+  const float fc_f = k.fc.hi, sp_f = k.sp.hi;
   for (int t = 0; t < k.ntx; ++t) {
-    const float e = leg_offset(ut, stf, g.tx[t]);
+    const float e = leg_offset(ut, st.hi, g.tx[t]);
     w_tx[(j * k.ntx + t) * stride + li] =
         ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
   }
   for (int r = 0; r < k.nrx; ++r) {
-    const float e = leg_offset(ur, srf, g.rx[r]);
+    const float e = leg_offset(ur, sr.hi, g.rx[r]);
     w_rx[(j * k.nrx + r) * stride + li] =
         ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
   }
+}
+
+ff ff_host(double x) {
+  const float hi = static_cast<float>(x);
+  return {hi, static_cast<float>(x - static_cast<double>(hi))};
 }
 
 size_t round256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -257,7 +371,7 @@ struct SnapRun {
   GeomDev gd{};
   size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
   size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
-  size_t o_base0 = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
+  size_t o_base0 = 0, o_q0 = 0, o_vff = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
   size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0;
   int64_t cap = 0;
   ~SnapRun() {
@@ -325,6 +439,8 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   const size_t o_vert = take(vbytes), o_tri = take(12 * static_cast<size_t>(geom->n_triangles));
   const size_t o_tx = take(16 * static_cast<size_t>(g.ntx)), o_rx = take(16 * static_cast<size_t>(g.nrx));
   R.o_base0 = take(16 * un);
+  R.o_q0 = take(8 * un);
+  R.o_vff = take(vbytes);
   R.o_car = take(8 * up); R.o_nur = take(8 * up); R.o_nud = take(8 * up); R.o_nua = take(8 * up);
   R.o_amp = take(4 * up); R.o_cell = take(4 * up); R.o_en = take(8 * up); R.o_sd = take(8 * up);
   R.o_sr = take(8 * up); R.o_ntx = take(8 * up);
@@ -391,12 +507,14 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   cudaMemsetAsync(b + R.o_status, 0, 4, s);
   GeomDev &gd = R.gd;
   gd.vert = reinterpret_cast<const double *>(b + o_vert);
+  gd.vff = reinterpret_cast<const float2 *>(b + R.o_vff);
   gd.tri = reinterpret_cast<const int32_t *>(b + o_tri);
   gd.tx = reinterpret_cast<const float4 *>(b + o_tx);
   gd.rx = reinterpret_cast<const float4 *>(b + o_rx);
   for (int q = 0; q < 3; ++q) {
     gd.ref_tx[q] = geom->ref_tx[q];
     gd.ref_rx[q] = geom->ref_rx[q];
+    gd.t2r[q] = ff_host(geom->ref_tx[q] - geom->ref_rx[q]);
   }
   gd.off = reinterpret_cast<const int64_t *>(b + o_off);
   gd.htri = reinterpret_cast<const int32_t *>(b + o_ht);
@@ -411,20 +529,24 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
 }
 
 // the snapshot-0 terms of every ray (after snap_setup, on its stream); returns kernels launched
+// the float-float vertices and the per-ray snapshot-0 terms
 int launch_snapshot0(SnapRun &R) {
   if (R.n <= 0) return 0;
+  const int64_t n_val = 3 * static_cast<int64_t>(R.g->nc) * R.gd.n_vert;
+  const int64_t blocks = (n_val + 255) / 256 < 4096 ? (n_val + 255) / 256 : 4096;
+  split_vertices_kernel<<<static_cast<unsigned>(blocks), 256, 0, R.s>>>(
+      R.gd.vert, n_val, R.gd.ref_tx[0], R.gd.ref_tx[1], R.gd.ref_tx[2], reinterpret_cast<float2 *>(R.b + R.o_vff));
   snapshot0_kernel<<<static_cast<unsigned>((R.n + 127) / 128), 128, 0, R.s>>>(
-      R.gd, reinterpret_cast<const double *>(R.b + R.o_d), R.n, reinterpret_cast<double2 *>(R.b + R.o_base0),
+      R.gd, reinterpret_cast<const double *>(R.b + R.o_d), reinterpret_cast<const float *>(R.b + R.o_p0), R.n,
+      reinterpret_cast<float4 *>(R.b + R.o_base0), reinterpret_cast<uint64_t *>(R.b + R.o_q0),
       reinterpret_cast<uint32_t *>(R.b + R.o_status));
-  return 1;
+  return 2;
 }
 
 PhaseConst phase_const(const Derived &g) {
   PhaseConst k;
-  k.fc_over_c = g.fc / kC;
-  k.step_per_m = g.bw / (kC * static_cast<double>(g.ns));
-  k.fc_f = static_cast<float>(k.fc_over_c);
-  k.sp_f = static_cast<float>(k.step_per_m);
+  k.fc = ff_host(g.fc / kC);
+  k.sp = ff_host(g.bw / (kC * static_cast<double>(g.ns)));
   k.nc = g.nc;
   k.ntx = g.ntx;
   k.nrx = g.nrx;
@@ -454,8 +576,8 @@ extern "C" SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, co
   if (R.n > 0) {
     double *out = dev ? paths : reinterpret_cast<double *>(R.b + R.o_paths);
     const dim3 grid(static_cast<unsigned>((R.n + 127) / 128), static_cast<unsigned>(g.nc));
-    snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const double2 *>(R.b + R.o_base0),
-                                           reinterpret_cast<const float *>(R.b + R.o_p0), 0, R.n, phase_const(g),
+    snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const float4 *>(R.b + R.o_base0),
+                                           reinterpret_cast<const uint64_t *>(R.b + R.o_q0), 0, R.n, phase_const(g),
                                            out, nullptr, nullptr, 0, reinterpret_cast<uint32_t *>(R.b + R.o_status));
     if (!dev)
       cudaMemcpyAsync(paths, out, 8 * static_cast<size_t>(R.n) * g.nc * g.nv, cudaMemcpyDeviceToHost, R.s);
@@ -502,7 +624,8 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
   for (int64_t i0 = 0; i0 < R.n; i0 += R.chunk) {
     const int64_t cnt = R.n - i0 < R.chunk ? R.n - i0 : R.chunk;
     const dim3 grid(static_cast<unsigned>((cnt + 127) / 128), static_cast<unsigned>(g.nc));
-    snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const double2 *>(b + R.o_base0), in.p0, i0, cnt, k,
+    snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const float4 *>(b + R.o_base0),
+                                         reinterpret_cast<const uint64_t *>(b + R.o_q0), i0, cnt, k,
                                          nullptr, wt, wr, R.chunk, status);
     cudaEventRecord(ev[ei++], s);
     if (g.precision == SIM_PREC_FP32_DIRECT)
