@@ -109,9 +109,19 @@ int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *
                     cudaStream_t s);
 // virtual snapshots on tensor cores, one chunk of phase words (umma_taylor.cu): the per-tile
 // expansion, or the pair sum when the expansion's bound fails; workspace of
-// snap_tensor_workspace_bytes(g, chunk), pair_ws of pair_workspace_bytes(g, chunk)
+// snap_tensor_workspace_bytes(g, chunk), pair_ws of pair_workspace_bytes(g, chunk).  The
+// expansion's reference antennas are the central ones; `rec` holds, per (ray, chirp m) at
+// [m stride + ray], the step word S(m, t_c, r_c) and the largest and smallest signed
+// difference S(m, t, r) - S(m, t_c, r_c) over the antennas (Q0.64 units), which bound the
+// expansion's argument.
+inline int snap_ref_tx(const Derived &g) { return g.ntx / 2; }
+inline int snap_ref_rx(const Derived &g) { return g.nrx / 2; }
+struct SnapRec {
+  const uint64_t *s;
+  const int64_t *d_hi, *d_lo;
+};
 int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk);
-int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, int64_t stride,
+int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, SnapRec rec, int64_t stride,
                        const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
                        uint32_t *status, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);

@@ -66,6 +66,7 @@ struct PhaseConst {
   ff fc;  // f_c / c: carrier cycles per metre of path
   ff sp;  // B / (c N_s): beat cycles per sample per metre of path
   int nc, ntx, nrx;
+  int tc, rc;  // the tensor expansion's reference antennas (records below)
 };
 
 // x mod 1 as a Q0.64 phase, from the bits of x: x = +-m 2^(e - 1075) with m the 53-bit
@@ -297,12 +298,16 @@ __device__ __forceinline__ uint64_t q64_small(float x) {
 
 // One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y), in float-float
 // and FP32 only.  paths != null: l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the
-// phase words of A_t and B_r.
+// phase words of A_t and B_r, and, when rec_s != null, the record of (li, j) at j stride + li:
+// the step word S(j, t_c, r_c) of the reference antennas and the largest and smallest
+// S(j, t, r) - S(j, t_c, r_c), the sum of the transmitter's and the receiver's extremes.
 __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *__restrict__ base0,
                                                        const uint64_t *__restrict__ q0s, int64_t i0, int64_t cnt,
                                                        PhaseConst k, double *__restrict__ paths,
                                                        ulonglong2 *__restrict__ w_tx, ulonglong2 *__restrict__ w_rx,
-                                                       int64_t stride, uint32_t *status) {
+                                                       int64_t stride, uint64_t *__restrict__ rec_s,
+                                                       int64_t *__restrict__ rec_hi, int64_t *__restrict__ rec_lo,
+                                                       uint32_t *status) {
   const int64_t li = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t j = blockIdx.y;
   if (li >= cnt) return;
@@ -332,15 +337,33 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
   const uint64_t at_c = q64_prod(a_ref, k.fc) + q0s[i], at_s = q64_prod(a_ref, k.sp);
   const uint64_t br_c = q64_prod(b_ref, k.fc), br_s = q64_prod(b_ref, k.sp);
   const float fc_f = k.fc.hi, sp_f = k.sp.hi;
+  // step offsets of the reference antennas: the words' differences from them are the offsets'
+  const uint64_t otc = q64_small(leg_offset(ut, st.hi, g.tx[k.tc]) * sp_f);
+  const uint64_t orc = q64_small(leg_offset(ur, sr.hi, g.rx[k.rc]) * sp_f);
+  int64_t dt_hi = 0, dt_lo = 0, dr_hi = 0, dr_lo = 0;
   for (int t = 0; t < k.ntx; ++t) {
     const float e = leg_offset(ut, st.hi, g.tx[t]);
+    const uint64_t os = q64_small(e * sp_f);
+    const int64_t d = static_cast<int64_t>(os - otc);
+    dt_hi = max(dt_hi, d);
+    dt_lo = min(dt_lo, d);
     w_tx[(j * k.ntx + t) * stride + li] =
-        ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
+        ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + os) : make_ulonglong2(0, 0);
   }
   for (int r = 0; r < k.nrx; ++r) {
     const float e = leg_offset(ur, sr.hi, g.rx[r]);
+    const uint64_t os = q64_small(e * sp_f);
+    const int64_t d = static_cast<int64_t>(os - orc);
+    dr_hi = max(dr_hi, d);
+    dr_lo = min(dr_lo, d);
     w_rx[(j * k.nrx + r) * stride + li] =
-        ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + q64_small(e * sp_f)) : make_ulonglong2(0, 0);
+        ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + os) : make_ulonglong2(0, 0);
+  }
+  if (rec_s) {
+    const int64_t at = j * stride + li;
+    rec_s[at] = ok ? (at_s + otc) + (br_s + orc) : 0;
+    rec_hi[at] = ok ? dt_hi + dr_hi : 0;
+    rec_lo[at] = ok ? dt_lo + dr_lo : 0;
   }
 }
 
@@ -372,7 +395,7 @@ struct SnapRun {
   size_t o_d = 0, o_a = 0, o_v = 0, o_az = 0, o_el = 0, o_p0 = 0, o_obj = 0;
   size_t o_car = 0, o_nur = 0, o_nud = 0, o_nua = 0, o_amp = 0, o_cell = 0, o_en = 0, o_sd = 0, o_sr = 0, o_ntx = 0;
   size_t o_base0 = 0, o_q0 = 0, o_vff = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
-  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0;
+  size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0, o_rec = 0;
   int64_t cap = 0;
   ~SnapRun() {
     if (s) cudaStreamDestroy(s);
@@ -453,6 +476,10 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_tw = take(mode == 1 && chunk > 0 && g.precision != SIM_PREC_FP32_DIRECT
                     ? static_cast<size_t>(snap_tensor_workspace_bytes(g, chunk))
                     : 0);
+  // tensor-core precisions: the per-(ray, chirp) records that bound the expansion
+  R.o_rec = take(mode == 1 && chunk > 0 && g.precision != SIM_PREC_FP32_DIRECT
+                     ? 24 * static_cast<size_t>(chunk) * static_cast<size_t>(g.nc)
+                     : 0);
   R.o_tmp = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_spec = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
   R.o_lab = take(want_labels ? 4 * static_cast<size_t>(g.n_cell) : 0);
@@ -550,6 +577,8 @@ PhaseConst phase_const(const Derived &g) {
   k.nc = g.nc;
   k.ntx = g.ntx;
   k.nrx = g.nrx;
+  k.tc = snap_ref_tx(g);
+  k.rc = snap_ref_rx(g);
   return k;
 }
 
@@ -578,7 +607,8 @@ extern "C" SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, co
     const dim3 grid(static_cast<unsigned>((R.n + 127) / 128), static_cast<unsigned>(g.nc));
     snapshot_kernel<<<grid, 128, 0, R.s>>>(R.gd, reinterpret_cast<const float4 *>(R.b + R.o_base0),
                                            reinterpret_cast<const uint64_t *>(R.b + R.o_q0), 0, R.n, phase_const(g),
-                                           out, nullptr, nullptr, 0, reinterpret_cast<uint32_t *>(R.b + R.o_status));
+                                           out, nullptr, nullptr, 0, nullptr, nullptr, nullptr,
+                                           reinterpret_cast<uint32_t *>(R.b + R.o_status));
     if (!dev)
       cudaMemcpyAsync(paths, out, 8 * static_cast<size_t>(R.n) * g.nc * g.nv, cudaMemcpyDeviceToHost, R.s);
   }
@@ -621,18 +651,23 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
   if (R.n == 0) cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
   ulonglong2 *wt = reinterpret_cast<ulonglong2 *>(b + R.o_wt), *wr = reinterpret_cast<ulonglong2 *>(b + R.o_wr);
   const PhaseConst k = phase_const(g);
+  const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
+  const size_t rec_n = static_cast<size_t>(R.chunk) * static_cast<size_t>(g.nc);
+  uint64_t *rec_s = tensor ? reinterpret_cast<uint64_t *>(b + R.o_rec) : nullptr;
+  int64_t *rec_hi = tensor ? reinterpret_cast<int64_t *>(b + R.o_rec) + rec_n : nullptr;
+  int64_t *rec_lo = tensor ? reinterpret_cast<int64_t *>(b + R.o_rec) + 2 * rec_n : nullptr;
   for (int64_t i0 = 0; i0 < R.n; i0 += R.chunk) {
     const int64_t cnt = R.n - i0 < R.chunk ? R.n - i0 : R.chunk;
     const dim3 grid(static_cast<unsigned>((cnt + 127) / 128), static_cast<unsigned>(g.nc));
     snapshot_kernel<<<grid, 128, 0, s>>>(R.gd, reinterpret_cast<const float4 *>(b + R.o_base0),
                                          reinterpret_cast<const uint64_t *>(b + R.o_q0), i0, cnt, k,
-                                         nullptr, wt, wr, R.chunk, status);
+                                         nullptr, wt, wr, R.chunk, rec_s, rec_hi, rec_lo, status);
     cudaEventRecord(ev[ei++], s);
     if (g.precision == SIM_PREC_FP32_DIRECT)
       kernels += 1 + launch_pair_sum(g, wt, wr, rp.amp + i0, cnt, R.chunk, i0 > 0, sig, b + R.o_pw, nullptr, s);
     else
-      kernels += 1 + launch_snap_tensor(g, wt, wr, R.chunk, rp.amp + i0, cnt, i0 > 0, sig, b + R.o_tw, b + R.o_pw,
-                                        status, s);
+      kernels += 1 + launch_snap_tensor(g, wt, wr, SnapRec{rec_s, rec_hi, rec_lo}, R.chunk, rp.amp + i0, cnt, i0 > 0,
+                                        sig, b + R.o_tw, b + R.o_pw, status, s);
     cudaEventRecord(ev[ei++], s);
   }
   if (signal) cudaMemcpyAsync(signal, sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);

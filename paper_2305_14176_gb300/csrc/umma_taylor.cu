@@ -632,13 +632,18 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
   if (P == 0 && tdm) atomicOr(status, kStatusModelRange);
 }
 
-// Virtual snapshots: the largest |S - S_ref| over the chunk's rays and every row, S the
-// per-sample step of row (m, k = t N_rx + r) and S_ref the ray's reference step of that row's
-// 256-row tile (chirp m_c, antennas t_c, r_c), as signed Q0.64 words; and the amplitude maximum
-// (FP16 scaling).  One thread per (ray, chirp), consecutive threads on consecutive rays.
-__global__ void snap_stats(const ulonglong2 *__restrict__ w_tx, const ulonglong2 *__restrict__ w_rx, int64_t stride,
-                           const float *__restrict__ amp, int64_t cnt, int nc, int nv, int ntx, int nrx, int t_c,
-                           int r_c, bool want_amax, uint32_t *amax_bits, unsigned long long *d_max) {
+// Virtual snapshots: a bound on the largest |S - S_ref| over the chunk's rays and every row, S
+// the per-sample step of row (m, k = t N_rx + r) and S_ref the ray's reference step of that
+// row's 256-row tile (chirp m_c, antennas t_c, r_c), as signed Q0.64 words; and the amplitude
+// maximum (FP16 scaling).  It reads the phase-word kernel's record of each (ray, chirp):
+// s(m) = S(m, t_c, r_c) and the largest and smallest D(m, t, r) = S(m, t, r) - s(m) over the
+// antennas, which splits as D = D_tx(t) + D_rx(r), so its extremes are those of the two parts.
+// For a tile holding chirp m, S - S_ref = (s(m) - s(m_c)) + D lies between (s(m) - s(m_c)) plus
+// the smallest and plus the largest D; the bound is exact for chirps whose rows all fall in one
+// tile and at most the rest of their antennas' offsets above it for the others.  One thread per
+// (ray, chirp), consecutive threads on consecutive rays.
+__global__ void snap_stats(SnapRec rec, int64_t stride, const float *__restrict__ amp, int64_t cnt, int nc, int nv,
+                           bool want_amax, uint32_t *amax_bits, unsigned long long *d_max) {
   uint32_t ma = 0;
   unsigned long long md = 0;
   const int64_t total = cnt * nc;
@@ -647,20 +652,13 @@ __global__ void snap_stats(const ulonglong2 *__restrict__ w_tx, const ulonglong2
     const int m = static_cast<int>(e / cnt);
     const int64_t li = e - static_cast<int64_t>(m) * cnt;
     if (want_amax && m == 0) ma = max(ma, __float_as_uint(amp[li]));
-    int last_tile = -1;
-    uint64_t sref = 0;
-    for (int k = 0; k < nv; ++k) {
-      const int tile = (m * nv + k) >> 8;
-      if (tile != last_tile) {
-        last_tile = tile;
-        const int mc = min((tile * 256 + 128) / nv, nc - 1);
-        sref = w_tx[(static_cast<int64_t>(mc) * ntx + t_c) * stride + li].y +
-               w_rx[(static_cast<int64_t>(mc) * nrx + r_c) * stride + li].y;
-      }
-      const int t = k / nrx, r = k - t * nrx;
-      const uint64_t step = w_tx[(static_cast<int64_t>(m) * ntx + t) * stride + li].y +
-                            w_rx[(static_cast<int64_t>(m) * nrx + r) * stride + li].y;
-      md = max(md, signed_mag(step - sref));
+    const int64_t at = static_cast<int64_t>(m) * stride + li;
+    const uint64_t sm = rec.s[at], hi = static_cast<uint64_t>(rec.d_hi[at]), lo = static_cast<uint64_t>(rec.d_lo[at]);
+    const int t0 = (m * nv) >> 8, t1 = (m * nv + nv - 1) >> 8;
+    for (int tile = t0; tile <= t1; ++tile) {
+      const int mc = min((tile * 256 + 128) / nv, nc - 1);
+      const uint64_t base = sm - rec.s[static_cast<int64_t>(mc) * stride + li];
+      md = max(md, max(signed_mag(base + hi), signed_mag(base + lo)));
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -835,7 +833,7 @@ int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk) {
 // P from the chunk's largest |delta|; beyond the bound the direct pair sum runs instead (both
 // are launched, each returns at once when the other owns the chunk).  Adds to sig when
 // `accumulate`.
-int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, int64_t stride,
+int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, SnapRec rec, int64_t stride,
                        const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
                        uint32_t *status, cudaStream_t s) {
   if (!taylor_eligible(g) || cnt <= 0)
@@ -849,11 +847,10 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   unsigned long long *d_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
   uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
   unsigned long long *none = reinterpret_cast<unsigned long long *>(ws + kOffEpsTMax);  // stays 0
-  const int t_c = g.ntx / 2, r_c = g.nrx / 2;
+  const int t_c = snap_ref_tx(g), r_c = snap_ref_rx(g);
   int kernels = 0;
   cudaMemsetAsync(ws, 0, 32, s);
-  snap_stats<<<4 * sms_t(), 256, 0, s>>>(w_tx, w_rx, stride, amp, cnt, g.nc, g.nv, g.ntx, g.nrx, t_c, r_c, f16, amax,
-                                         d_max);
+  snap_stats<<<4 * sms_t(), 256, 0, s>>>(rec, stride, amp, cnt, g.nc, g.nv, f16, amax, d_max);
   // theta = 2 pi n_h max|delta|, delta in cycles per sample (the word times 2^-64)
   const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
   const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
