@@ -150,6 +150,24 @@ def cpu_oracle_rate(radar, rays, seconds: float = 10.0, seed: int = 17):
     return rate, n_pts, dt, oracle.threads(), idx, ref
 
 
+def cpu_snapshot_rate(radar, rays, hits, geom, seconds: float = 10.0, seed: int = 18):
+    """Contributions/s of the FP64 oracle of virtual snapshots (per-(ray, chirp, channel) Eq. 6 /
+    Eq. 7 paths, then the ray sum), on as many sampled output points of the frame as fill about
+    `seconds` of wall time on the host cores."""
+    import oracle
+    n_out = radar.n_virtual * radar.n_chirps * radar.n_samples
+    probe = scenegen.randint(seed, 1, 16, 0, n_out - 1).astype(np.int64)
+    t0 = time.perf_counter()
+    oracle.signal_geom_at(radar, rays, hits, geom, probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    n_pts = int(max(16, min(n_out, 16 * seconds / dt)))
+    idx = scenegen.randint(seed, 2, n_pts, 0, n_out - 1).astype(np.int64)
+    t0 = time.perf_counter()
+    ref = oracle.signal_geom_at(radar, rays, hits, geom, idx)
+    dt = time.perf_counter() - t0
+    return n_pts * rays.n / dt, n_pts, dt, oracle.threads(), idx, ref
+
+
 def result_error(radar, rays, sig_h, lab_h, idx, ref):
     """The frame's error against the FP64 oracle: normwise max and RMS relative error of the
     signal on the oracle's sampled output points, and whether every label matches."""
@@ -326,6 +344,15 @@ def run_snapshot_workload(args, rs, torch):
         step(host, tuple(h_out))
         if s >= args.warmup:
             e2e.append(time.perf_counter() - t0)
+    # the oracle leg: the FP64 snapshot oracle on a bounded sample of output points, timed on the
+    # host cores, and the last timed frame (still in sig, lab) against it
+    cpu, error = None, None
+    if not args.no_cpu_baseline:
+        rate, n_pts, dt, cores, idx, ref = cpu_snapshot_rate(radar, rays, hits, geom)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_pts} of {sig.numel() // 2} output points x {rays.n} rays, FP64 snapshot paths "
+                         f"and direct sum, {dt:.1f} s"}
+        error = result_error(radar, rays, sig.cpu().numpy(), lab.cpu().numpy(), idx, ref)
     dev_s = stages["total"] / 1e3
     sum_s = stages["ray_sum"] / 1e3
     if args.precision == "fp32":
@@ -355,7 +382,8 @@ def run_snapshot_workload(args, rs, torch):
                     "d2h_bytes_per_step": int(sum(v.numel() * v.element_size() for v in h_out)),
                     "ms_per_step": 1e3 * sum(e2e) / len(e2e),
                     "note": "synchronous call: includes its device allocation and input copies"},
-            "gpu_launches": kernels, "roofline": roof, "cpu_baseline": None, "clocks": clk.summary()}
+            "gpu_launches": kernels, "roofline": roof, "cpu_baseline": cpu, "error": error,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
