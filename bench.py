@@ -268,16 +268,49 @@ def run_batch_workload(args, rs, torch):
     cargs = ([c.ctx for c in ctxs], rays_s, metas, [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs])
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     times, kernels = [], 0
-    for s in range(args.warmup + args.steps):
+    for s in range(args.warmup):
         flush.zero_()
         torch.cuda.synchronize()
         rc, ms, kc = rs.sim_run_batch(*cargs)
         if rc != rs.SIM_OK:
             raise rs.SimError(rc, "sim_run_batch")
-        if s >= args.warmup:
+    with ClockSampler(0, args.clocks_csv) as clk:
+        for s in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            rc, ms, kc = rs.sim_run_batch(*cargs)
+            if rc != rs.SIM_OK:
+                raise rs.SimError(rc, "sim_run_batch")
             times.append(ms)
             kernels += kc
     dev_s = sum(times) / 1e3
+    # the oracle leg: four scenes spread over the batch, each at sampled signal points by the
+    # FP64 direct sum (about 10 s on the host cores in all) and its labels whole, against the
+    # last timed step's outputs
+    cpu, error = None, None
+    if not args.no_cpu_baseline:
+        picks = [0, len(scenes) // 3, 2 * len(scenes) // 3, len(scenes) - 1]
+        errs, pts, work, t_all, cores = [], 0, 0, 0.0, 0
+        for q in picks:
+            radar, rays = scenes[q]
+            rate, n_pts, dt, cores, idx, ref = cpu_oracle_rate(radar, rays, seconds=2.5, seed=30 + q)
+            errs.append(result_error(radar, rays, outs[q][1].cpu().numpy(), outs[q][2].cpu().numpy(), idx, ref))
+            pts += n_pts
+            work += n_pts * rays.n
+            t_all += dt
+        cpu = {"value": work / t_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{pts} output points of scenes {picks} x their rays, FP64 direct sum, {t_all:.1f} s"}
+        error = {"vs": "FP64 oracle", "points": pts, "scenes": picks,
+                 "max_rel": max(e["max_rel"] for e in errs), "rms_rel": max(e["rms_rel"] for e in errs),
+                 "labels_exact": all(e["labels_exact"] for e in errs)}
+    peaks, peak_src = _peaks()
+    achieved = 8.0 * contrib * len(times) / dev_s / 1e12
+    peak = float(peaks["bf16_tflops"])
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "the batch's whole step (persistent tensor-core launch, FFTs, labels)",
+            "peak_source": f"{peak_src} bf16 dense burst"}
+    if args.precision == "fp32":
+        roof = None
     line = {"metric": METRIC, "value": contrib * len(times) / dev_s, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
@@ -285,7 +318,8 @@ def run_batch_workload(args, rs, torch):
             "config": {"workload": "batch: 64 uneven scenes in one persistent graph-captured launch",
                        "rays_total": int(sum(r.n for _, r in scenes)), "contributions_per_step": contrib,
                        "precision": args.precision, "l2": "flushed (256 MB write) before each step"},
-            "frames_per_s": 64 * len(times) / dev_s, "gpu_launches": kernels}
+            "frames_per_s": 64 * len(times) / dev_s, "gpu_launches": kernels, "roofline": roof,
+            "cpu_baseline": cpu, "error": error, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     for c in ctxs:
         c.close()
