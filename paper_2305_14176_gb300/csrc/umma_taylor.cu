@@ -409,6 +409,12 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
       const int64_t ray0 = k_lo + static_cast<int64_t>(st) * RS;
       tstore<MODE>(s_rays[grp], gt, nxt);
       if (st + TGROUPS < n_stages) nxt = tfetch<MODE>(g, ray0 + TGROUPS * RS, RS, k_hi, gt, m_c);
+      // kSnap: this row's words of the group's stage after next (one line each, inside the row
+      // since that stage's first ray is below k_hi), pulled into L2 two group rounds ahead
+      if (MODE == kSnap && rc.valid && st + 2 * TGROUPS < n_stages) {
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rc.wt + ray0 + 2 * TGROUPS * RS));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(rc.wr + ray0 + 2 * TGROUPS * RS));
+      }
       const int valid = static_cast<int>(k_hi - ray0 < RS ? k_hi - ray0 : RS);
       tgroup_sync(grp);
       if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
