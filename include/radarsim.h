@@ -209,8 +209,10 @@ typedef struct {
 } sim_hits;
 
 /* Path lengths l(j, t, r) of every ray into paths, double[n][N_c][N_v] (k = t N_rx + r), host or
-   device.  The context gives N_c, n_tx, n_rx (any precision: paths are FP64) and must have no
-   TDM slot time.  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
+   device.  The context gives N_c, n_tx, n_rx (any precision: the paths do not depend on it)
+   and must have no TDM slot time.  The reference legs are carried in float-float arithmetic
+   (~48 bits, ~1e-12 m on a 100 m leg), the antenna offsets from them in FP32 (~3e-7 of the
+   offset).  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
    memory.  SIM_E_INVALID for bad arguments, a hit list or index out of range (checked before
    any access) or a ray failing sim_submit's checks. */
 SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hits *hits, const sim_geometry *geom,
