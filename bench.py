@@ -667,9 +667,9 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--p-img", type=float, default=0.002, help="serve: probability of an imaging frame")
     ap.add_argument("--imaging-rays", type=int, default=1_000_000)
-    ap.add_argument("--in-flight", type=int, default=3,
-                    help="e2e: frames submitted before the oldest is fetched (2: 5.16, 3: 5.03, 4: 5.00 ms per "
-                         "automotive frame)")
+    ap.add_argument("--in-flight", type=int, default=6,
+                    help="e2e: frames submitted before the oldest is fetched (2: 5.15, 3: 5.03, 4: 4.97, 6: 4.90 ms "
+                         "per automotive frame)")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
@@ -763,10 +763,9 @@ def main():
         if s >= args.warmup:
             e2e_times.append(dt)
     serial_max = max_over_ranks(sum(e2e_times), world, dist, dev)
-    # as a caller streams frames: two in flight (submit frame k + 1, then fetch frame k into the
-    # other set of pinned output buffers), so copies overlap the device work; L2 flushed
-    # before each submit
-    # one pinned output set per frame in flight (a set is reused only once its frame is fetched)
+    # as a caller streams frames: args.in_flight frames submitted before the oldest is fetched,
+    # each into its own set of pinned output buffers (a set is reused only once its frame is
+    # fetched), so copies overlap the device work; L2 flushed before each submit
     h_sets = [(h_spec, h_sig, h_lab)] + [tuple(torch.empty(x.shape, dtype=x.dtype).pin_memory()
                                               for x in (h_spec, h_sig, h_lab))
                                         for _ in range(max(1, args.in_flight) - 1)]
