@@ -60,6 +60,25 @@ def test_paths_match_oracle(device):
     assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-9   # the reference pair itself: no FP32 offset
 
 
+def test_paths_far_and_translated():
+    """Far targets (100-250 m) in a scene moved 2.9 km from the origin: the per-chirp legs are
+    float-float relative to the reference transmitter, so neither the range nor the absolute
+    position costs accuracy."""
+    radar = scenegen.radar_automotive(n_chirps=16, n_samples=32)
+    rays, hits, g0 = scenegen.moving_scene(22, radar, 300, bounce_frac=0.3, r_range=(100.0, 250.0))
+    shift = np.array([1500.0, -2500.0, 30.0])
+    geom = scenegen.Geometry(g0.vertices + shift, g0.triangles, g0.tx_pos + shift, g0.rx_pos + shift,
+                             g0.ref_tx + shift, g0.ref_rx + shift)
+    rc, got = snapshot(radar, rays, hits, geom, paths=True)
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    ref = oracle.paths(radar, rays, hits, geom)
+    assert ref.min() > 150.0                                    # round trips of 100 m and more
+    assert np.abs(got - ref).max() <= 2e-8
+    assert np.abs(got[:, :, 0] - ref[:, :, 0]).max() <= 1e-9
+    # the translation changes the oracle's FP64 rounding only
+    assert np.abs(ref - oracle.paths(radar, rays, hits, g0)).max() <= 1e-9
+
+
 PRECISIONS = [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16,
               rs.SIM_PREC_BF16]
 
