@@ -337,33 +337,38 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
   const uint64_t at_c = q64_prod(a_ref, k.fc) + q0s[i], at_s = q64_prod(a_ref, k.sp);
   const uint64_t br_c = q64_prod(b_ref, k.fc), br_s = q64_prod(b_ref, k.sp);
   const float fc_f = k.fc.hi, sp_f = k.sp.hi;
-  // step offsets of the reference antennas: the words' differences from them are the offsets'
-  const uint64_t otc = q64_small(leg_offset(ut, st.hi, g.tx[k.tc]) * sp_f);
-  const uint64_t orc = q64_small(leg_offset(ur, sr.hi, g.rx[k.rc]) * sp_f);
-  int64_t dt_hi = 0, dt_lo = 0, dr_hi = 0, dr_lo = 0;
+  // step offsets of the antennas relative to antenna 0 (their extremes, and the reference
+  // antenna's, give the records' offsets from the reference)
+  uint64_t ot0 = 0, or0 = 0;
+  int64_t dt_hi = 0, dt_lo = 0, dt_c = 0, dr_hi = 0, dr_lo = 0, dr_c = 0;
   for (int t = 0; t < k.ntx; ++t) {
     const float e = leg_offset(ut, st.hi, g.tx[t]);
     const uint64_t os = q64_small(e * sp_f);
-    const int64_t d = static_cast<int64_t>(os - otc);
+    if (t == 0) ot0 = os;
+    const int64_t d = static_cast<int64_t>(os - ot0);
     dt_hi = max(dt_hi, d);
     dt_lo = min(dt_lo, d);
+    if (t == k.tc) dt_c = d;
     w_tx[(j * k.ntx + t) * stride + li] =
         ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + os) : make_ulonglong2(0, 0);
   }
   for (int r = 0; r < k.nrx; ++r) {
     const float e = leg_offset(ur, sr.hi, g.rx[r]);
     const uint64_t os = q64_small(e * sp_f);
-    const int64_t d = static_cast<int64_t>(os - orc);
+    if (r == 0) or0 = os;
+    const int64_t d = static_cast<int64_t>(os - or0);
     dr_hi = max(dr_hi, d);
     dr_lo = min(dr_lo, d);
+    if (r == k.rc) dr_c = d;
     w_rx[(j * k.nrx + r) * stride + li] =
         ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + os) : make_ulonglong2(0, 0);
   }
   if (rec_s) {
     const int64_t at = j * stride + li;
+    const uint64_t otc = ot0 + static_cast<uint64_t>(dt_c), orc = or0 + static_cast<uint64_t>(dr_c);
     rec_s[at] = ok ? (at_s + otc) + (br_s + orc) : 0;
-    rec_hi[at] = ok ? dt_hi + dr_hi : 0;
-    rec_lo[at] = ok ? dt_lo + dr_lo : 0;
+    rec_hi[at] = ok ? (dt_hi - dt_c) + (dr_hi - dr_c) : 0;
+    rec_lo[at] = ok ? (dt_lo - dt_c) + (dr_lo - dr_c) : 0;
   }
 }
 
