@@ -64,10 +64,6 @@ template <bool SPLIT>
 __host__ __device__ constexpr int t_groups() {
   return SPLIT ? 3 : 4;
 }
-template <bool SPLIT>
-__host__ __device__ constexpr int t_threads() {
-  return t_groups<SPLIT>() * TGSIZE + 32 + TNDRAIN;
-}
 constexpr int TSUBST_SPLIT = 16;       // stages per accumulation chain at split precision
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
@@ -80,6 +76,19 @@ constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 2
 constexpr int kExact = 0;     // exact Eq. 2: per-ray words of the prep kernel
 constexpr int kExactTdm = 1;  // the same with TDM slot offsets
 constexpr int kSnap = 2;      // virtual snapshots: per-(ray, chirp, antenna) phase words
+
+// Snapshot mode at split precision folds the MMA issuer into the first drain warp: 16 warps,
+// so 128 registers a thread and no spills (measured 36.6 -> 34.4 ms per automotive snapshot
+// frame at FP16 hi + lo).  The other kernels keep a warp of their own for it, which measured
+// faster for them (the exact model at FP16 hi + lo 14.8 against 15.6 ms).
+template <bool SPLIT, int MODE>
+__host__ __device__ constexpr bool t_merged() {
+  return SPLIT && MODE == kSnap;
+}
+template <bool SPLIT, int MODE>
+__host__ __device__ constexpr int t_threads() {
+  return t_groups<SPLIT>() * TGSIZE + (t_merged<SPLIT, MODE>() ? 0 : 32) + TNDRAIN;
+}
 
 struct TArgs {
   RaysPrep p;
@@ -299,10 +308,45 @@ __host__ __device__ constexpr uint32_t t_stage_bytes(int bn) {
   return static_cast<uint32_t>(TBM * TKS * 2 * 2 + (bn / 4) * TKS * 2 * 2) * (SPLIT ? 2u : 1u);
 }
 
+// The MMAs of one stage for both CTAs of the pair: Re and Im of the M = 256 x N product over
+// the stage's 32 K slots, with the lo operand products at split precision (all K steps, or
+// only the first when the high-order terms go single pass).
+struct TIssue {
+  uint32_t idesc, ineg, lbo_a, lbo_x, a_half, x_half, lo, t_re, t_im;
+};
+template <bool SPLIT>
+__device__ __forceinline__ void t_issue_stage(const TIssue &w, uint32_t sb, bool first, bool lo_high) {
+  const uint32_t ar = sb, ai = sb + w.a_half, xr = sb + 2 * w.a_half, xi = xr + w.x_half;
+#pragma unroll
+  for (int kh = 0; kh < TKS / 16; ++kh) {
+    const uint32_t acc = (!first || kh > 0) ? 1u : 0u;
+    const uint32_t oa = kh * 2 * w.lbo_a, ox = kh * 2 * w.lbo_x;
+    const uint64_t dar = make_sdesc(ar + oa, w.lbo_a, 128), dai = make_sdesc(ai + oa, w.lbo_a, 128);
+    const uint64_t dxr = make_sdesc(xr + ox, w.lbo_x, 128), dxi = make_sdesc(xi + ox, w.lbo_x, 128);
+    mma_f16<true>(w.t_re, dar, dxr, w.idesc, acc);
+    mma_f16<true>(w.t_re, dai, dxi, w.ineg, 1u);
+    mma_f16<true>(w.t_im, dar, dxi, w.idesc, acc);
+    mma_f16<true>(w.t_im, dai, dxr, w.idesc, 1u);
+    if (SPLIT && (kh == 0 || lo_high)) {
+      const uint32_t lo = w.lo;
+      const uint64_t lar = make_sdesc(ar + lo + oa, w.lbo_a, 128), lai = make_sdesc(ai + lo + oa, w.lbo_a, 128);
+      const uint64_t lxr = make_sdesc(xr + lo + ox, w.lbo_x, 128), lxi = make_sdesc(xi + lo + ox, w.lbo_x, 128);
+      mma_f16<true>(w.t_re, dar, lxr, w.idesc, 1u);
+      mma_f16<true>(w.t_re, lar, dxr, w.idesc, 1u);
+      mma_f16<true>(w.t_re, dai, lxi, w.ineg, 1u);
+      mma_f16<true>(w.t_re, lai, dxi, w.ineg, 1u);
+      mma_f16<true>(w.t_im, dar, lxi, w.idesc, 1u);
+      mma_f16<true>(w.t_im, lar, dxi, w.idesc, 1u);
+      mma_f16<true>(w.t_im, dai, lxr, w.idesc, 1u);
+      mma_f16<true>(w.t_im, lai, dxr, w.idesc, 1u);
+    }
+  }
+}
+
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
 template <bool F16, bool SPLIT, int MODE>
-__global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs g) {
+__global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int TGROUPS = t_groups<SPLIT>();
   constexpr int TMMA_WARP = TGROUPS * TGSIZE / 32;
@@ -435,106 +479,120 @@ __global__ void __launch_bounds__(t_threads<SPLIT>(), 1) taylor_sum_kernel(TArgs
         tgroup_sync(grp);  // s_rays[grp] is rewritten next round
       }
     }
-  } else if (warp == TMMA_WARP) {
-    // ---------------- MMA issuer (CTA 0 issues for both; CTA 1 only waits for the end)
-    if (lane == 0 && rank != 0) {
-      if (!mbar_wait(done, 0)) failed = true;
-    } else if (lane == 0) {
-      const uint32_t sbase = smem_u32(base);
-      bool open = false;
-      const uint32_t idesc = make_idesc(F16, 2 * TBM, NC);
-      const uint32_t ineg = idesc | (1u << 14);  // negate B: Re S -= A_im B_im
-      const uint32_t lbo_a = TBM * 16, lbo_x = static_cast<uint32_t>(ncb) * 16;
-      const uint32_t a_half = TBM * TKS * 2, x_half = static_cast<uint32_t>(ncb) * TKS * 2;
-      const uint32_t lo = 2 * a_half + 2 * x_half;
-      const uint32_t t_re = tmem, t_im = tmem + static_cast<uint32_t>(NC);
-      for (int st = 0; st < n_stages; ++st) {
-        const int s = st % NST;
-        const int gc = st / SUBST;
-        const bool first = (st % SUBST) == 0;
-        if (first && gc > 0 && !mbar_wait(acce, (gc - 1) & 1)) {
-          failed = true;
-          break;
+  } else {
+    constexpr bool MERGED = t_merged<SPLIT, MODE>();
+    TIssue iw{};
+    iw.idesc = make_idesc(F16, 2 * TBM, NC);
+    iw.ineg = iw.idesc | (1u << 14);  // negate B: Re S -= A_im B_im
+    iw.lbo_a = TBM * 16;
+    iw.lbo_x = static_cast<uint32_t>(ncb) * 16;
+    iw.a_half = TBM * TKS * 2;
+    iw.x_half = static_cast<uint32_t>(ncb) * TKS * 2;
+    iw.lo = 2 * iw.a_half + 2 * iw.x_half;
+    iw.t_re = tmem;
+    iw.t_im = tmem + static_cast<uint32_t>(NC);
+    const uint32_t sbase = smem_u32(base);
+    if (!MERGED && warp == TMMA_WARP) {
+      // ---------------- MMA issuer warp (CTA 0 issues for both; CTA 1 only waits for the end)
+      if (lane == 0 && rank != 0) {
+        if (!mbar_wait(done, 0)) failed = true;
+      } else if (lane == 0) {
+        bool open = false;
+        for (int st = 0; st < n_stages; ++st) {
+          const int s = st % NST;
+          const int gc = st / SUBST;
+          const bool first = (st % SUBST) == 0;
+          if (first && gc > 0 && !mbar_wait(acce, (gc - 1) & 1)) {
+            failed = true;
+            break;
+          }
+          if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+            failed = true;
+            break;
+          }
+          tc_fence_after();
+          t_issue_stage<SPLIT>(iw, sbase + s * stage_bytes, first, lo_high);
+          open = true;
+          mma_commit<true>(empty0 + 8 * s);
+          if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
+            mma_commit<true>(accf);
+            open = false;
+          }
         }
-        if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+        if (open) mma_commit<true>(accf);
+        mma_commit<true>(done);  // fires in both CTAs once every issued MMA has completed
+        if (!mbar_wait(done, 0)) failed = true;
+      }
+    } else {
+      // ---------------- drain: TMEM lane quarter warp % 4; each finished chain is added in FP32
+      // to the running sum in tensor memory, the last one goes to this split's partial.  MERGED:
+      // lane 0 of the first drain warp in CTA 0 is the issuer; it issues each chain before its
+      // warp drains it (the next chain's first MMAs wait for the drain in either layout).
+      const bool issuer = MERGED && warp == TMMA_WARP && lane == 0 && rank == 0;
+      const int q = warp & 3;
+      const int grow = row0 + q * 32 + lane;
+      float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
+      const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      if (n_stages == 0 && grow < g.m_rows) {
+        for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      int st = 0;  // the merged issuer's next stage
+      for (int sub = 0; sub < n_sub; ++sub) {
+        if constexpr (MERGED) {
+          if (issuer && !failed) {
+            const int st_end = min(n_stages, (sub + 1) * SUBST);
+            for (; st < st_end; ++st) {
+              const int s = st % NST;
+              const bool first = (st % SUBST) == 0;
+              if (first && sub > 0 && !mbar_wait(acce, (sub - 1) & 1)) {
+                failed = true;
+                break;
+              }
+              if (!mbar_wait(full0 + 8 * s, (st / NST) & 1)) {
+                failed = true;
+                break;
+              }
+              tc_fence_after();
+              t_issue_stage<SPLIT>(iw, sbase + s * stage_bytes, first, lo_high);
+              mma_commit<true>(empty0 + 8 * s);
+            }
+            // complete once these MMAs are (after a failed wait too, so the drains end at once)
+            mma_commit<true>(accf);
+          }
+          __syncwarp();  // the tensor-memory loads below are warp-collective
+        }
+        if (!mbar_wait_sleep(accf, sub & 1)) {
           failed = true;
           break;
         }
         tc_fence_after();
-        const uint32_t sb = sbase + s * stage_bytes;
-        const uint32_t ar = sb, ai = sb + a_half, xr = sb + 2 * a_half, xi = xr + x_half;
+        const bool last = sub == n_sub - 1;
+        for (int c = 0; c < bn; c += 16) {
+          uint32_t h[16];
+          tmem_ld16(trow + static_cast<uint32_t>(c), h);
+          if (sub > 0) {
+            uint32_t r[16];
+            tmem_ld16(trow + TSUM_COL + static_cast<uint32_t>(c), r);
 #pragma unroll
-        for (int kh = 0; kh < TKS / 16; ++kh) {
-          const uint32_t acc = (!first || kh > 0) ? 1u : 0u;
-          const uint32_t oa = kh * 2 * lbo_a, ox = kh * 2 * lbo_x;
-          const uint64_t dar = make_sdesc(ar + oa, lbo_a, 128), dai = make_sdesc(ai + oa, lbo_a, 128);
-          const uint64_t dxr = make_sdesc(xr + ox, lbo_x, 128), dxi = make_sdesc(xi + ox, lbo_x, 128);
-          mma_f16<true>(t_re, dar, dxr, idesc, acc);
-          mma_f16<true>(t_re, dai, dxi, ineg, 1u);
-          mma_f16<true>(t_im, dar, dxi, idesc, acc);
-          mma_f16<true>(t_im, dai, dxr, idesc, 1u);
-          if (SPLIT && (kh == 0 || lo_high)) {
-            const uint64_t lar = make_sdesc(ar + lo + oa, lbo_a, 128), lai = make_sdesc(ai + lo + oa, lbo_a, 128);
-            const uint64_t lxr = make_sdesc(xr + lo + ox, lbo_x, 128), lxi = make_sdesc(xi + lo + ox, lbo_x, 128);
-            mma_f16<true>(t_re, dar, lxr, idesc, 1u);
-            mma_f16<true>(t_re, lar, dxr, idesc, 1u);
-            mma_f16<true>(t_re, dai, lxi, ineg, 1u);
-            mma_f16<true>(t_re, lai, dxi, ineg, 1u);
-            mma_f16<true>(t_im, dar, lxi, idesc, 1u);
-            mma_f16<true>(t_im, lar, dxi, idesc, 1u);
-            mma_f16<true>(t_im, dai, lxr, idesc, 1u);
-            mma_f16<true>(t_im, lai, dxr, idesc, 1u);
+            for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+          }
+          if (!last) {
+            tmem_st16(trow + TSUM_COL + static_cast<uint32_t>(c), h);
+          } else if (grow < g.m_rows) {
+#pragma unroll
+            for (int x = 0; x < 16; x += 4)
+              *reinterpret_cast<float4 *>(dst + c + x) = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]),
+                                                                     __uint_as_float(h[x + 2]), __uint_as_float(h[x + 3]));
           }
         }
-        open = true;
-        mma_commit<true>(empty0 + 8 * s);
-        if ((st % SUBST) == SUBST - 1 || st == n_stages - 1) {
-          mma_commit<true>(accf);
-          open = false;
-        }
+        if (!last) tmem_wait_st();
+        tc_fence_before();
+        mbar_arrive_cluster(acce_c);
       }
-      if (open) mma_commit<true>(accf);
-      mma_commit<true>(done);  // fires in both CTAs once every issued MMA has completed
-      if (!mbar_wait(done, 0)) failed = true;
-    }
-  } else {
-    // ---------------- drain: TMEM lane quarter warp % 4; each finished chain is added in FP32
-    // to the running sum in tensor memory, the last one goes to this split's partial.
-    const int q = warp & 3;
-    const int grow = row0 + q * 32 + lane;
-    float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
-    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
-    if (n_stages == 0 && grow < g.m_rows) {
-      for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    for (int sub = 0; sub < n_sub; ++sub) {
-      if (!mbar_wait_sleep(accf, sub & 1)) {
-        failed = true;
-        break;
+      if (MERGED && warp == TMMA_WARP && lane == 0) {
+        if (issuer) mma_commit<true>(done);  // fires in both CTAs once every issued MMA has completed
+        if (!mbar_wait(done, 0)) failed = true;
       }
-      tc_fence_after();
-      const bool last = sub == n_sub - 1;
-      for (int c = 0; c < bn; c += 16) {
-        uint32_t h[16];
-        tmem_ld16(trow + static_cast<uint32_t>(c), h);
-        if (sub > 0) {
-          uint32_t r[16];
-          tmem_ld16(trow + TSUM_COL + static_cast<uint32_t>(c), r);
-#pragma unroll
-          for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
-        }
-        if (!last) {
-          tmem_st16(trow + TSUM_COL + static_cast<uint32_t>(c), h);
-        } else if (grow < g.m_rows) {
-#pragma unroll
-          for (int x = 0; x < 16; x += 4)
-            *reinterpret_cast<float4 *>(dst + c + x) = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]),
-                                                                   __uint_as_float(h[x + 2]), __uint_as_float(h[x + 3]));
-        }
-      }
-      if (!last) tmem_wait_st();
-      tc_fence_before();
-      mbar_arrive_cluster(acce_c);
     }
   }
   if (failed) atomicOr(g.status, kStatusWaitLimit);
@@ -739,7 +797,7 @@ void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   }
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(2u * static_cast<unsigned>(sh.mt2 * sh.nt * sh.splits));
-  cfg.blockDim = dim3(t_threads<SPLIT>());
+  cfg.blockDim = dim3(t_threads<SPLIT, MODE>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
