@@ -259,8 +259,11 @@ typedef struct {
    <= 1.  Rays and meta: host or device, as for sim_submit.  Synchronous; allocates its own
    working memory outside the engine's budget.  Each span's rays are packed in ray order and
    summed alone (up to four spans at once, on their own streams), so a span costs its own ray
-   count and its part is bit for bit the scene of its rays alone; the parts of spans that
-   partition the rays add up to the whole scene (Eq. 5).
+   count and its part is the scene of its rays alone: bit for bit with SIM_PREC_FP32_DIRECT or
+   the exact model, and with the other precisions up to the regrouping of FP32 sums (a span's
+   tensor-core sum is split into fewer parts than a scene alone, since the spans share the
+   GPU: ~1e-6 of the norm at hi + lo, ~1e-5 single pass).  Repeated calls give the same bits.
+   The parts of spans that partition the rays add up to the whole scene (Eq. 5).
    Errors: SIM_E_INVALID (bad rule, missing meta a rule needs, bad ray), SIM_E_NOMEM,
    SIM_E_CUDA, SIM_E_DEVICE. */
 SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, int32_t n_spans,

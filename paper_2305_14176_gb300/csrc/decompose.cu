@@ -44,6 +44,11 @@ __device__ __forceinline__ bool in_span(const RuleDev &r, const int32_t *obj, co
 
 constexpr int kSpanBlock = 1024;  // rays per compaction block (one thread each)
 constexpr int kLanes = 4;         // spans summed concurrently (streams)
+// Each span's tensor-core sum plans one wave of CTAs (a scene alone plans four): the lanes share
+// the GPU, and a span's CTAs then take several times more rays each, with as many fewer split-K
+// partials to write and reduce.  Its workspace is sized by the same plan.
+constexpr float kSpanWaves = 0.5f;
+constexpr int64_t kSpanMinChunk = 8192;
 
 // cnt[h nb + b]: rays of block b in span h (grid nb x n_spans)
 __global__ void __launch_bounds__(kSpanBlock) span_count_kernel(const int32_t *__restrict__ obj,
@@ -320,7 +325,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   int64_t need = 0;  // ray-sum workspace of the largest span
   for (uint32_t nh : sizes)
     if (nh > 0)
-      need = std::max<int64_t>(need, tensor ? umma_workspace_bytes(g, static_cast<int64_t>(nh))
+      need = std::max<int64_t>(need, tensor ? umma_workspace_bytes(g, static_cast<int64_t>(nh), kSpanWaves, kSpanMinChunk)
                                             : direct_workspace_bytes(g, static_cast<int64_t>(nh)));
   const size_t l_prep = round256((exact ? 76 : 60) * up), l_ws = round256(static_cast<size_t>(need)),
                l_sig = round256(8 * static_cast<size_t>(g.n_sig));
@@ -366,7 +371,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
       float2 *ltmp = reinterpret_cast<float2 *>(lb + l_prep + l_ws + l_sig);
       span_gather_kernel<<<static_cast<unsigned>(nb), kSpanBlock, 0, sl>>>(rp, q, dobj, dmat, dhit, n, drules + h,
                                                                            boff + static_cast<int64_t>(h) * nb);
-      kernels += 1 + (tensor ? launch_umma_sum(g, q, nh, lsig, lb + l_prep, status, sl, nullptr)
+      kernels += 1 + (tensor ? launch_umma_sum(g, q, nh, lsig, lb + l_prep, status, sl, nullptr, kSpanWaves, kSpanMinChunk)
                              : launch_direct_sum(g, q, nh, lsig, lb + l_prep, sl));
       kernels += launch_fft(g, ctx->t, lsig, ltmp, x, sl);
       if (span_spectra && span_spectra[h])

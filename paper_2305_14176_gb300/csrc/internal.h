@@ -145,11 +145,14 @@ int64_t exact_tensor_workspace_bytes(const Derived &g, int64_t n);
 int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                         cudaStream_t s, cudaEvent_t after_main);
 // tensor-core ray sum: workspace bytes it needs and its launcher
-int64_t umma_workspace_bytes(const Derived &g, int64_t n);
+// `waves`: the plan's minimum waves of CTAs; `min_chunk` (> 0): at least that many rays per
+// split; launch_umma_sum takes the same values
+int64_t umma_workspace_bytes(const Derived &g, int64_t n, float waves = 4.f, int64_t min_chunk = 0);
 // `after_main` (may be null) is recorded on `s` right after the GEMM kernel, before the
 // split reduction, so the GEMM can be timed on its own stream.
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace,
-                    uint32_t *status, cudaStream_t s, cudaEvent_t after_main);
+                    uint32_t *status, cudaStream_t s, cudaEvent_t after_main, float waves = 4.f,
+                    int64_t min_chunk = 0);
 
 // ---- batched tensor-core ray sum (one persistent launch over several scenes)
 struct UmmaBatch {

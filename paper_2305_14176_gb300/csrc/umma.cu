@@ -663,18 +663,18 @@ int num_sms() {
 }
 
 // Tiles of 128 rows x bn columns; the rays split into `splits` chunks so that the CTAs fill
-// whole waves of the SMs (at least four waves) as evenly as possible.  Depends only on the
-// scene's own shape and ray count.
-Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits);
+// whole waves of the SMs (at least `waves`, four for a scene that has the GPU to itself) as
+// evenly as possible.  Depends only on the scene's own shape and ray count.
+Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits, float waves = 4.f, int64_t min_chunk = 0);
 
-Shape plan_shape(const Derived &g, int64_t n) {
+Shape plan_shape(const Derived &g, int64_t n, float waves = 4.f, int64_t min_chunk = 0) {
   Tuning tu{};
-  if (tuning_lookup(g, n, &tu) && tu.splits > 0) return plan_shape_forced(g, n, tu.splits);
-  return plan_shape_forced(g, n, 0);
+  if (waves == 4.f && min_chunk == 0 && tuning_lookup(g, n, &tu) && tu.splits > 0) return plan_shape_forced(g, n, tu.splits);
+  return plan_shape_forced(g, n, 0, waves, min_chunk);
 }
 
 // forced_splits > 0 replaces the wave-filling choice (autotuned tables, tuner trials)
-Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
+Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits, float waves, int64_t min_chunk) {
   Shape s;
   const int M = g.nv * g.nc;
   // single pass keeps no running sum in tensor memory, so its tiles can take 256 complex columns
@@ -687,7 +687,8 @@ Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
   const int sms = num_sms();
   const int64_t tiles = static_cast<int64_t>(s.mt) * s.nt;
   const int64_t max_splits = (n + KS - 1) / KS > 0 ? (n + KS - 1) / KS : 1;
-  const int64_t lo = (4 * sms + tiles - 1) / tiles;
+  const int64_t target = static_cast<int64_t>(waves * static_cast<float>(sms) + 0.5f);
+  const int64_t lo = std::max<int64_t>(1, (target + tiles - 1) / tiles);
   // idle fraction of the last wave, waste / (ctas + waste); smallest wins, ties to fewer splits
   int64_t best = lo, best_waste = -1, best_slots = 1;
   for (int64_t sp = lo; sp <= 3 * lo; ++sp) {
@@ -701,6 +702,8 @@ Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits) {
     }
   }
   int64_t splits = forced_splits > 0 ? forced_splits : best;
+  if (forced_splits <= 0 && min_chunk > 0 && splits > std::max<int64_t>(1, n / min_chunk))
+    splits = std::max<int64_t>(1, n / min_chunk);
   if (splits > max_splits) splits = max_splits;
   if (splits > 65535) splits = 65535;
   if (splits < 1) splits = 1;
@@ -789,16 +792,16 @@ void launch_gemm_dispatch(bool f16, bool split, bool fast, const Shape &sh, cons
 
 }  // namespace
 
-int64_t umma_workspace_bytes(const Derived &g, int64_t n) {
+int64_t umma_workspace_bytes(const Derived &g, int64_t n, float waves, int64_t min_chunk) {
   if (g.model == SIM_MODEL_EXACT) return exact_tensor_workspace_bytes(g, n);
-  const Shape sh = plan_shape(g, n);
+  const Shape sh = plan_shape(g, n, waves, min_chunk);
   return 256 + static_cast<int64_t>(sh.splits) * g.nv * g.nc * 2 * g.ns * 4;
 }
 
 int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
-                    cudaStream_t s, cudaEvent_t after_main) {
+                    cudaStream_t s, cudaEvent_t after_main, float waves, int64_t min_chunk) {
   if (g.model == SIM_MODEL_EXACT) return launch_exact_tensor(g, p, n, sig, workspace, status, s, after_main);
-  const Shape sh = plan_shape(g, n);
+  const Shape sh = plan_shape(g, n, waves, min_chunk);
   uint32_t *amax = static_cast<uint32_t *>(workspace);
   float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
   const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;
