@@ -160,7 +160,7 @@ int build_plan(int n, sim_ctx *const *ctxs, const sim_rays *rays, BatchPlan &p) 
     q.ck = take(4 * cap);
     q.cm = take(8 * cap);
     q.co = take(4 * cap);
-    q.ws = take(static_cast<size_t>(umma_workspace_bytes(g, r)));
+    q.ws = take(static_cast<size_t>(batch_workspace_bytes(g, r)));
     q.tables = take(ctxs[i]->table_bytes);
     p.bufs.push_back(q);
     p.gs.push_back(g);

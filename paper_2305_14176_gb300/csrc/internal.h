@@ -145,6 +145,10 @@ int64_t exact_tensor_workspace_bytes(const Derived &g, int64_t n);
 int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                         cudaStream_t s, cudaEvent_t after_main);
 // tensor-core ray sum: workspace bytes it needs and its launcher
+// A scene in a batch keeps the plan it has alone, so its results are the same bits.  Every step
+// of a batch (work list, workspace, split-K reduction) takes that plan from one function
+// (batch_workspace_bytes, umma_units_of, launch_umma_post).
+int64_t batch_workspace_bytes(const Derived &g, int64_t n);
 // `waves`: the plan's minimum waves of CTAs; `min_chunk` (> 0): at least that many rays per
 // split; launch_umma_sum takes the same values
 int64_t umma_workspace_bytes(const Derived &g, int64_t n, float waves = 4.f, int64_t min_chunk = 0);
