@@ -212,9 +212,11 @@ typedef struct {
    device.  The context gives N_c, n_tx, n_rx (any precision: the paths do not depend on it)
    and must have no TDM slot time.  The reference legs are carried in float-float arithmetic
    (~48 bits, ~1e-12 m on a 100 m leg), the antenna offsets from them in FP32 (~3e-7 of the
-   offset).  All arrays host or device (as for sim_submit).  Synchronous; allocates its own working
-   memory.  SIM_E_INVALID for bad arguments, a hit list or index out of range (checked before
-   any access) or a ray failing sim_submit's checks. */
+   offset).  All arrays host or device (as for sim_submit).  Synchronous.  Its working memory
+   stays in the context between calls (grown when a call needs more, freed by sim_destroy);
+   a call made while another one holds it allocates its own for its duration.
+   SIM_E_INVALID for bad arguments, a hit list or index out of range (checked before any
+   access) or a ray failing sim_submit's checks. */
 SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hits *hits, const sim_geometry *geom,
                                double *paths);
 
@@ -256,16 +258,16 @@ typedef struct {
    span_labels (nullable): int32[N_a][N_c][N_s], per cell the span h with the largest
    |X_h|^2 among spans with |X_h|^2 >= threshold^2 * max_{h, cells} |X_h|^2 (a binary
    segmentation of each span image; ties to the lower h), -1 if none passes.  0 <= threshold
-   <= 1.  Rays and meta: host or device, as for sim_submit.  Synchronous; allocates its own
-   working memory outside the engine's budget.  Each span's rays are packed in ray order and
-   summed alone (up to four spans at once, on their own streams), so a span costs its own ray
-   count and its part is the scene of its rays alone: bit for bit with SIM_PREC_FP32_DIRECT or
-   the exact model, and with the other precisions up to the regrouping of FP32 sums (a span's
-   tensor-core sum is split into fewer parts than a scene alone, since the spans share the
-   GPU: ~1e-6 of the norm at hi + lo, ~1e-5 single pass).  Repeated calls give the same bits.
-   The parts of spans that partition the rays add up to the whole scene (Eq. 5).
-   Errors: SIM_E_INVALID (bad rule, missing meta a rule needs, bad ray), SIM_E_NOMEM,
-   SIM_E_CUDA, SIM_E_DEVICE. */
+   <= 1. Rays and meta: host or device, as for sim_submit. Synchronous; its working memory,
+   outside the engine's budget, stays in the context between calls as for sim_snapshot_paths.
+   Each span's rays are packed in ray order and summed alone (up to four spans at once, on their
+   own streams), so a span costs its own ray count and its part is the scene of its rays alone:
+   bit for bit with SIM_PREC_FP32_DIRECT or the exact model, and with the other precisions up to
+   the regrouping of FP32 sums (a span's tensor-core sum is split into fewer parts than a scene
+   alone, since the spans share the GPU: ~1e-6 of the norm at hi + lo, ~1e-5 single pass).
+   Repeated calls give the same bits. The parts of spans that partition the rays add up to the
+   whole scene (Eq. 5). Errors: SIM_E_INVALID (bad rule, missing meta a rule needs, bad ray),
+   SIM_E_NOMEM, SIM_E_CUDA, SIM_E_DEVICE. */
 SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, int32_t n_spans,
                           const sim_span_rule *rules, void *const *span_spectra, int32_t *span_labels,
                           float threshold);

@@ -221,16 +221,13 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   const size_t o_status = take(256), o_max = take(256);
   const size_t o_spec = take(8 * static_cast<size_t>(g.n_cell) * static_cast<size_t>(n_spans));
   const size_t o_lab = take(4 * static_cast<size_t>(g.n_cell));
-  uint8_t *b = nullptr;
-  if (cudaMalloc(&b, off) != cudaSuccess) {
-    cudaGetLastError();
-    return SIM_E_NOMEM;
-  }
+  // the call's block and the lanes' blocks come from the context's scratch (kept between calls);
+  // both leases end after `finish` has waited for every stream
+  ScratchLease lease_b, lease_ws;
+  uint8_t *b = static_cast<uint8_t *>(lease_b.get(ctx->scratch[kSlotDecompose], off));
+  if (!b) return SIM_E_NOMEM;
   cudaStream_t s = nullptr;
-  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaFree(b);
-    return SIM_E_CUDA;
-  }
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SIM_E_CUDA;
   void *ws = nullptr;  // the lanes' blocks: packed prep, ray-sum workspace, signal, FFT scratch
   cudaStream_t lane_s[kLanes] = {};
   cudaEvent_t lane_done[kLanes] = {};
@@ -245,8 +242,6 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     }
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
-    if (ws) cudaFree(ws);
-    cudaFree(b);
     cudaGetLastError();
     return rc;
   };
@@ -330,12 +325,12 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   const size_t l_prep = round256((exact ? 76 : 60) * up), l_ws = round256(static_cast<size_t>(need)),
                l_sig = round256(8 * static_cast<size_t>(g.n_sig));
   const size_t lane_bytes = l_prep + l_ws + 2 * l_sig;  // prep, workspace, signal, FFT scratch
-  while (cudaMalloc(&ws, lane_bytes * static_cast<size_t>(lanes)) != cudaSuccess) {
-    cudaGetLastError();
-    ws = nullptr;
-    if (lanes == 1) return finish(SIM_E_NOMEM);
+  ws = lease_ws.get(ctx->scratch[kSlotDecomposeLanes], lane_bytes * static_cast<size_t>(lanes));
+  if (!ws && lanes > 1) {
     lanes = 1;
+    ws = lease_ws.get(ctx->scratch[kSlotDecomposeLanes], lane_bytes);
   }
+  if (!ws) return finish(SIM_E_NOMEM);
   for (int l = 1; l < lanes; ++l) {
     if (cudaStreamCreateWithFlags(&lane_s[l], cudaStreamNonBlocking) != cudaSuccess) return finish(SIM_E_CUDA);
     cudaStreamWaitEvent(lane_s[l], ev[1], 0);  // after prep and the span sizes

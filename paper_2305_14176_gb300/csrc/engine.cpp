@@ -521,6 +521,40 @@ void record_stage_ms(sim_ctx *c, const float *ms, int kernels) {
 }
 }  // namespace rs
 
+namespace rs {
+
+void *ScratchLease::get(ScratchSlot &slot, size_t bytes) {
+  if (!held_ && !own_ && slot.m.try_lock()) held_ = &slot;
+  if (held_) {
+    if (held_->bytes < bytes) {
+      if (held_->p) cudaFree(held_->p);
+      held_->p = nullptr;
+      held_->bytes = 0;
+      if (cudaMalloc(&held_->p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        held_->p = nullptr;
+        return nullptr;
+      }
+      held_->bytes = bytes;
+    }
+    return held_->p;
+  }
+  if (own_) cudaFree(own_);
+  own_ = nullptr;
+  if (cudaMalloc(&own_, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    own_ = nullptr;
+  }
+  return own_;
+}
+
+ScratchLease::~ScratchLease() {
+  if (own_) cudaFree(own_);
+  if (held_) held_->m.unlock();
+}
+
+}  // namespace rs
+
 extern "C" {
 
 const char *sim_status_string(int s) {
@@ -777,6 +811,11 @@ int sim_destroy(sim_ctx *c) {
   for (uint64_t t : mine) sim_fetch(c, t, nullptr, nullptr, nullptr, -1);
   while (c->live.load() > 0) std::this_thread::sleep_for(std::chrono::milliseconds(1));
   if (c->table_mem) cudaFree(c->table_mem);
+  for (auto &slot : c->scratch) {
+    std::lock_guard<std::mutex> lk(slot.m);  // a synchronous call still running ends first
+    if (slot.p) cudaFree(slot.p);
+    slot.p = nullptr;
+  }
   delete c;
   return SIM_OK;
 }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "radarsim.h"
 
@@ -213,6 +214,34 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
 }  // namespace rs
 
 // One radar configuration (the C ABI's opaque handle).
+namespace rs {
+// A context's device scratch for its synchronous calls (sim_decompose, sim_snapshot_*): grown on
+// demand and kept until sim_destroy, so that repeated calls neither allocate nor free device
+// memory (cudaFree waits for the whole device).  One call holds a slot at a time.
+struct ScratchSlot {
+  std::mutex m;
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+enum { kSlotDecompose = 0, kSlotDecomposeLanes = 1, kSlotSnapshot = 2, kSlots = 3 };
+// One call's use of a slot: the slot's buffer, grown to the size asked for, or, when another
+// call holds the slot, a buffer of this call's own.  Released (or freed) on destruction, which
+// must follow the last device work on it.  get() may be called again with a smaller size after
+// it returned null (out of memory).
+class ScratchLease {
+ public:
+  ScratchLease() = default;
+  ScratchLease(const ScratchLease &) = delete;
+  ScratchLease &operator=(const ScratchLease &) = delete;
+  ~ScratchLease();
+  void *get(ScratchSlot &slot, size_t bytes);
+
+ private:
+  ScratchSlot *held_ = nullptr;
+  void *own_ = nullptr;
+};
+}  // namespace rs
+
 struct sim_ctx {
   rs::Derived g;
   rs::Tables t;
@@ -221,5 +250,6 @@ struct sim_ctx {
   float last_ms[8] = {};
   int last_kernels = 0;
   std::atomic<int> live{0};   // tickets not yet fetched
+  rs::ScratchSlot scratch[rs::kSlots];
 };
 

@@ -402,9 +402,12 @@ struct SnapRun {
   size_t o_base0 = 0, o_q0 = 0, o_vff = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
   size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0, o_rec = 0;
   int64_t cap = 0;
+  ScratchLease lease;  // b: the context's snapshot scratch (kept between calls) or this call's own
   ~SnapRun() {
-    if (s) cudaStreamDestroy(s);
-    if (b) cudaFree(b);
+    if (s) {
+      cudaStreamSynchronize(s);  // nothing may still use b when the lease ends
+      cudaStreamDestroy(s);
+    }
   }
 };
 
@@ -493,11 +496,8 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_pk = take(8 * cap); R.o_pe = take(8 * cap); R.o_ck = take(4 * cap); R.o_cm = take(8 * cap);
   R.o_co = take(4 * cap);
   R.o_paths = take(mode == 0 && !paths_on_device ? 8 * un * g.nc * g.nv : 0);
-  if (cudaMalloc(&R.b, off) != cudaSuccess) {
-    cudaGetLastError();
-    R.b = nullptr;
-    return SIM_E_NOMEM;
-  }
+  R.b = static_cast<uint8_t *>(R.lease.get(ctx->scratch[kSlotSnapshot], off));
+  if (!R.b) return SIM_E_NOMEM;
   if (cudaStreamCreateWithFlags(&R.s, cudaStreamNonBlocking) != cudaSuccess) {
     R.s = nullptr;
     return SIM_E_CUDA;

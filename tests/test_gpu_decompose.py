@@ -135,3 +135,40 @@ def test_rules_needing_missing_meta_are_rejected():
         assert rs.sim_decompose(ctx.ctx, r, m, [rs.span_rule(object_id=1)], threshold=2.0) == rs.SIM_E_INVALID
     finally:
         ctx.close()
+
+
+def test_concurrent_calls_on_one_context():
+    """Four threads decompose on one context at once: one call holds the context's scratch,
+    the others allocate their own for their duration; every call gives the bits of a call made
+    alone, and a later call reuses the scratch."""
+    import threading
+    radar, rays, mat, hits = _scene(25, 3000)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT)
+    try:
+        arr = {k: np.ascontiguousarray(v) for k, v in dict(rays.arrays(), material_id=mat, n_hits=hits).items()}
+        r, m = rs.make_rays(arr, rays.n)
+        rules = [rs.span_rule(**q) for q in RULES]
+
+        def call():
+            out = [np.zeros(ctx.cube_shape + (2,), np.float32) for _ in rules]
+            lab = np.zeros(ctx.cube_shape, np.int32)
+            return rs.sim_decompose(ctx.ctx, r, m, rules, out, lab, 0.1), out, lab
+
+        rc0, ref, lab0 = call()
+        assert rc0 == rs.SIM_OK
+        results = [None] * 4
+
+        def worker(k):
+            results[k] = call()
+
+        threads = [threading.Thread(target=worker, args=(k,)) for k in range(4)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        for rc, out, lab in results + [call()]:
+            assert rc == rs.SIM_OK
+            assert all(np.array_equal(a, b) for a, b in zip(out, ref))
+            assert np.array_equal(lab, lab0)
+    finally:
+        ctx.close()
