@@ -576,10 +576,13 @@ def run_serve_workload(args, rs, torch):
     arrivals = arrivals[arrivals < args.duration]
     is_img = scenegen.uniform(4200, 2, arrivals.shape[0]) < args.p_img
     # warm-up: one of each kind
+    per_frame = {}
     for ctx, arr, nr in ((ctx_a, pools[0], args.rays), (ctx_i, img_arr, img_rays.n)):
         t = ctx.submit(arr, nr)
         assert ctx.fetch(t) == rs.SIM_OK
+        per_frame[id(ctx)] = rs.sim_last_kernel_count(ctx.ctx)  # kernels of one frame of this kind
     outstanding, lat, done_contrib, refused = [], [], [0], [0]
+    launches = [0]
     lock = threading.Lock()
     stop = [False]
     t0 = time.perf_counter()
@@ -600,10 +603,13 @@ def run_serve_workload(args, rs, torch):
                         outstanding.remove(it)
                         lat.append(now - t_arr)
                         done_contrib[0] += contrib
+                        launches[0] += per_frame[id(ctx)]
                     progressed = True
             if not progressed:
                 time.sleep(0.0001)
 
+    clk = ClockSampler(0, args.clocks_csv)
+    clk.__enter__()
     th = threading.Thread(target=fetcher)
     th.start()
     for k, ta in enumerate(arrivals):
@@ -624,6 +630,7 @@ def run_serve_workload(args, rs, torch):
     stop[0] = True
     th.join()
     wall = time.perf_counter() - t0
+    clk.__exit__(None, None, None)
     lat_ms = np.array(lat) * 1e3
     line = {"metric": METRIC, "value": done_contrib[0] / wall, "unit": UNIT, "n_gpus": 1,
             "steps": int(arrivals.shape[0]), "warmup": 2, "ms_per_step": float(np.median(lat_ms)) if lat else None,
@@ -636,7 +643,8 @@ def run_serve_workload(args, rs, torch):
                            "p99": float(np.percentile(lat_ms, 99)) if lat else None,
                            "max": float(lat_ms.max()) if lat else None},
             "completed": len(lat), "refused_busy": refused[0], "imaging_arrivals": int(is_img.sum()),
-            "frames_per_s": len(lat) / wall, "wall_s": wall}
+            "frames_per_s": len(lat) / wall, "wall_s": wall, "gpu_launches": launches[0],
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     ctx_a.close()
     ctx_i.close()
