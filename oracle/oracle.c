@@ -46,22 +46,14 @@ double orc_cos_rep(double x);
    in order */
 static double pattern_amp(const orc_radar *p, double a, double az, double el) {
   if (p->pattern_exp <= 0) return a;
-#if defined(ORC_MUTATION) && ORC_MUTATION == 9
-  const double c = orc_cos_rep(az) * orc_sin_rep(el);
-#else
   const double c = orc_cos_rep(az) * orc_cos_rep(el);
-#endif
   for (int e = 0; e < p->pattern_exp; ++e) a = a * c;
   return a;
 }
 
 /* transmitter of virtual channel k = tx N_rx + rx */
 static int64_t tx_of(const orc_radar *p, int64_t k) {
-#if defined(ORC_MUTATION) && ORC_MUTATION == 10
-  return k % p->n_rx;
-#else
   return k / p->n_rx;
-#endif
 }
 
 /* --------------------------------------------------------------- per-ray cycle counts */
@@ -95,20 +87,6 @@ static void ray_cycles_of(const orc_radar *p, const orc_rays *r, int64_t i, ray_
      in the exact model, n t eps_t to the range-migration product */
   o->nu_t = p->carrier_hz * (2.0 * v * p->tdm_slot_s) / ORC_C;
   o->eps_t = p->model == 1 ? mu * dt * (2.0 * v * p->tdm_slot_s) / ORC_C : 0.0;
-#if defined(ORC_MUTATION)
-  /* planted mistakes, compiled only by the pin-sensitivity test */
-#if ORC_MUTATION == 1
-  o->nu_a = spacing_wl(p) * sin(az);                              /* drops cos(el) */
-#elif ORC_MUTATION == 2
-  o->nu_d = -o->nu_d;                                             /* Doppler sign */
-#elif ORC_MUTATION == 3
-  o->nu_d = p->carrier_hz * (2.0 * v * p->sweep_time_s) / ORC_C;  /* T_c for T_d */
-#elif ORC_MUTATION == 4
-  o->nu_r = mu * dt * tau / 2.0;                                  /* one-way range */
-#elif ORC_MUTATION == 5
-  o->carrier = frac(p->carrier_hz * tau);                         /* drops phi0 */
-#endif
-#endif
   o->amp = pattern_amp(p, (double)r->amplitude[i], az, el);
 }
 
@@ -312,9 +290,6 @@ void orc_spectrum(const orc_radar *p, const double *signal, double *out, int nth
   orc_window(p, 1, wd);
   orc_window(p, 2, wa);
   double *tr = twiddles(ns), *td = twiddles(nc), *ta = twiddles(na);
-#if defined(ORC_MUTATION) && ORC_MUTATION == 8
-  for (int64_t t = 0; t < ns; ++t) wr[t] = 1.0;                   /* range window left out */
-#endif
   dft_ctx c0 = {p, signal, t1, wr, tr, 0};
   parallel_for(nv * nc, nthreads, dft_lines, &c0); /* range: along n */
   dft_ctx c1 = {p, t1, t2, wd, td, 1};
@@ -417,11 +392,7 @@ static void hit_position(const orc_geometry *g, int64_t j, int64_t h, double out
   const double u = (double)g->hit_u[h], v = (double)g->hit_v[h];
   const double w = 1.0 - u - v;
   for (int c = 0; c < 3; ++c) {
-#if defined(ORC_MUTATION) && ORC_MUTATION == 11
-    out[c] = w * V[3 * tri[0] + c] + v * V[3 * tri[1] + c] + u * V[3 * tri[2] + c];  /* u, v swapped */
-#else
     out[c] = w * V[3 * tri[0] + c] + u * V[3 * tri[1] + c] + v * V[3 * tri[2] + c];
-#endif
   }
 }
 
@@ -452,15 +423,9 @@ static double path_length(const orc_geometry *g, const orc_rays *r, int64_t i, i
   hit_position(g, 0, l, pl0);
   hit_position(g, j, f, pfj);
   hit_position(g, j, l, plj);
-#if defined(ORC_MUTATION) && ORC_MUTATION == 12
-  return r->range_rt_m[i] - distance3(pf0, g->ref_tx) + distance3(pfj, g->tx_pos + 3 * t) -
-         inner_length(g, i, 0) + inner_length(g, i, j) - distance3(pl0, g->ref_rx) +
-         distance3(plj, g->rx_pos + 3 * t);                       /* receiver leg to the transmitter */
-#else
   return r->range_rt_m[i] - distance3(pf0, g->ref_tx) + distance3(pfj, g->tx_pos + 3 * t) -
          inner_length(g, i, 0) + inner_length(g, i, j) - distance3(pl0, g->ref_rx) +
          distance3(plj, g->rx_pos + 3 * rx);
-#endif
 }
 
 typedef struct {
@@ -606,11 +571,7 @@ double orc_cos_rep(double x) {
    q_x = floor(x + 0.5) reduced into [0, N_x); cell = (q_a N_c + q_d) N_s + q_r;
    energy = min(rint(a^2 2^32), 2^41). */
 static int64_t bin_of(double x, int64_t n) {
-#if defined(ORC_MUTATION) && ORC_MUTATION == 6
-  int64_t q = (int64_t)floor(x);                                  /* truncating bins */
-#else
   int64_t q = (int64_t)floor(x + 0.5);
-#endif
   q %= n;
   if (q < 0) q += n;
   return q;
@@ -696,11 +657,7 @@ void orc_labels(const orc_radar *p, const orc_rays *r, const int32_t *object_id,
   int64_t best_e = -1;
   for (int64_t t = 0; t < m; ++t) {
     if (t == 0 || cell[t] != cell[t - 1]) best_e = -1;
-#if defined(ORC_MUTATION) && ORC_MUTATION == 7
-    if (e[t] >= best_e) {                                         /* ties to the largest id */
-#else
     if (e[t] > best_e) {
-#endif
       best_e = e[t];
       labels[cell[t]] = obj[t];
     }
