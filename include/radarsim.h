@@ -381,9 +381,11 @@ SIM_API int sim_selftest_umma_pair(int32_t f16, int32_t n, int64_t k, const void
    the whole cube, 8 N_v N_c N_s bytes, must also fit beside the 72 bytes per ray of
    per-ray data, 88 in the exact model (the automotive 12 x 256 x 512 cube does; a 192 x 512 x 1024 imaging
    cube does not).  The exact model runs here per chirp on the tensor-core precisions, a
-   form without the TDM slot term, so the exact model with tdm_slot_s > 0 on a tensor-core
-   precision is refused.  Beyond a limit, with host pointers, or in that case it returns
-   SIM_E_INVALID before launching anything.
+   form without the TDM slot term that keeps one FP32 cube per split of its rays: the
+   exact model with tdm_slot_s > 0 on a tensor-core precision is refused, and so is an
+   exact-model scene whose splits do not fit beside its per-ray data.  Beyond a limit,
+   with pointers that are not device memory of the current device, or in those cases it
+   returns SIM_E_INVALID before launching anything.
    The first call on each device looks up the array's device address (set-up); make
    that first call before any stream capture.  Every call on a device shares the one
    array and finds the previous call's contents in it (the call clears what must start

@@ -40,13 +40,16 @@ int scratch_on_current_device(uint8_t **out) {
   return SIM_OK;
 }
 
-bool on_device(const void *p) {
+// device (or managed) memory that the current device's kernels can address: memory of another
+// GPU is refused, since without peer access a kernel here would fault on it
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -54,19 +57,23 @@ bool on_device(const void *p) {
 extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const sim_rays *rays, void *signal_c64,
                                           void *stream) {
   using namespace rs;
+  // an error left by an unrelated earlier call must not be reported as this call's
+  cudaGetLastError();
   Derived g;
   int rc = derive_radar(params, &g);
   if (rc != SIM_OK) return rc;
   if (!rays || !signal_c64) return SIM_E_INVALID;
   const int64_t n = rays->n;
   if (n < 0 || n > kMaxRays || n > g.max_rays) return SIM_E_INVALID;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SIM_E_CUDA;
   if (n > 0) {
     const void *arr[6] = {rays->range_rt_m, rays->amplitude, rays->radial_velocity_mps, rays->azimuth_rad,
                           rays->elevation_rad, rays->phase0_rad};
     for (const void *a : arr)
-      if (!a || !on_device(a)) return SIM_E_INVALID;
+      if (!a || !on_device(a, dev)) return SIM_E_INVALID;
   }
-  if (!on_device(signal_c64)) return SIM_E_INVALID;
+  if (!on_device(signal_c64, dev)) return SIM_E_INVALID;
   uint8_t *scr = nullptr;
   rc = scratch_on_current_device(&scr);
   if (rc != SIM_OK) return rc;
@@ -98,8 +105,11 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   // the tensor-core path needs room for at least one FP32 partial of the whole cube
   const int64_t one_split = 256 + 8 * g.n_sig;
   if (g.precision != SIM_PREC_FP32_DIRECT && one_split > ws_bytes) return SIM_E_INVALID;
-  // the per-chirp exact form used here has no TDM slot term
-  if (g.model == SIM_MODEL_EXACT && g.precision != SIM_PREC_FP32_DIRECT && g.tslot != 0.0) return SIM_E_INVALID;
+  if (g.model == SIM_MODEL_EXACT && g.precision != SIM_PREC_FP32_DIRECT) {
+    // the per-chirp exact form used here has no TDM slot term, and its split partials (one
+    // FP32 cube each) must fit the scratch left after the per-ray data
+    if (g.tslot != 0.0 || exact_workspace_bytes(g, n) > ws_bytes) return SIM_E_INVALID;
+  }
 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   float2 *sig = static_cast<float2 *>(signal_c64);
