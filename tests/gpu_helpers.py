@@ -4,16 +4,36 @@ import torch
 
 from paper_2305_14176_gb300 import radarsim as rs
 
-# Normwise tolerances (max |err| / max |ref|, and RMS) per ray-sum arithmetic.
-# FP32 and split precision: 1e-5.  Single-pass operands carry their format's rounding:
-# each real operand component is rounded to 8 (BF16) or 11 (FP16) significand bits,
-# a relative error of at most 2^-9 (2^-12); two operands per term and errors adding in
-# quadrature over incoherent rays give an RMS near 2^-9 (2^-12) and a maximum of about
-# twice that, so the bounds below are 1.5x (RMS) and 3x (max) the unit roundoff.
+# Each ray-sum arithmetic's stated target, normwise (max |err| / max |ref|, and RMS): 1e-5 for
+# the FP32 direct sum and for split precision (hi + lo operands), 2e-3 for single-pass BF16/FP16.
+TARGET = {rs.SIM_PREC_FP32_DIRECT: 1e-5, rs.SIM_PREC_BF16_SPLIT: 1e-5, rs.SIM_PREC_FP16_SPLIT: 1e-5,
+          rs.SIM_PREC_BF16: 2e-3, rs.SIM_PREC_FP16: 2e-3}
+
+# The bounds the tests assert.  FP32 and split precision assert their target.  Single-pass FP16
+# asserts a bound tighter than its target, from its rounding: each real operand component keeps
+# 11 significand bits, a relative error of at most 2^-12; two operands per term and errors adding
+# in quadrature over incoherent rays give an RMS near 2^-12 and a maximum of about twice that,
+# so 3 x 2^-12 (max) and 1.5 x 2^-12 (RMS), both below 2e-3.
+# Single-pass BF16 MISSES its 2e-3 target on frames of many rays: with 8 significand bits per
+# component the same argument gives ~2^-9 = 1.95e-3 per term, and the automotive frame measures
+# 2.5e-3 max and 2.3e-3 RMS.  Its tests assert only that rounding bound (3 x 2^-9 max,
+# 1.5 x 2^-9 RMS) and carry "misses-2e-3-target" in their names (see `prec_params`).
 TOL = {rs.SIM_PREC_FP32_DIRECT: 1e-5, rs.SIM_PREC_BF16_SPLIT: 1e-5, rs.SIM_PREC_FP16_SPLIT: 1e-5,
        rs.SIM_PREC_BF16: 3 * 2.0 ** -9, rs.SIM_PREC_FP16: 3 * 2.0 ** -12}
 TOL_RMS = {rs.SIM_PREC_FP32_DIRECT: 1e-5, rs.SIM_PREC_BF16_SPLIT: 1e-5, rs.SIM_PREC_FP16_SPLIT: 1e-5,
            rs.SIM_PREC_BF16: 1.5 * 2.0 ** -9, rs.SIM_PREC_FP16: 1.5 * 2.0 ** -12}
+MEETS_TARGET = {p: TOL[p] <= TARGET[p] and TOL_RMS[p] <= TARGET[p] for p in TARGET}
+
+PREC_ID = {rs.SIM_PREC_FP32_DIRECT: "fp32", rs.SIM_PREC_BF16_SPLIT: "bf16_split",
+           rs.SIM_PREC_FP16_SPLIT: "fp16_split", rs.SIM_PREC_FP16: "fp16",
+           rs.SIM_PREC_BF16: "bf16-single-pass-misses-2e-3-target"}
+
+
+def prec_params(*precisions):
+    """pytest parameters for precisions, named so that a variant that misses its stated target
+    says so in every test id it appears in."""
+    import pytest
+    return [pytest.param(p, id=PREC_ID[p]) for p in precisions]
 
 
 def to_c(x: torch.Tensor) -> np.ndarray:

@@ -8,7 +8,7 @@ import torch
 import oracle
 import scenegen
 from paper_2305_14176_gb300 import radarsim as rs
-from gpu_helpers import TOL, rel_max, run, to_c
+from gpu_helpers import TOL, prec_params, rel_max, run, to_c
 
 pytestmark = pytest.mark.gpu
 
@@ -20,7 +20,7 @@ def _outputs(ctx):
     return spec, sig, lab
 
 
-@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16])
+@pytest.mark.parametrize("precision", prec_params(rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_BF16))
 def test_batch_equals_alone_bitwise_and_replays(precision):
     scenes = scenegen.batch_scenes(seed=3000, n_scenes=10, ray_scale=0.05)
     scenes.append(scenegen.tiny_scene(seed=3))

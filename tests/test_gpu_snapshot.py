@@ -8,7 +8,7 @@ import torch
 import oracle
 import scenegen
 from paper_2305_14176_gb300 import radarsim as rs
-from gpu_helpers import TOL, TOL_RMS, rel_max, rel_rms, to_c
+from gpu_helpers import TOL, TOL_RMS, prec_params, rel_max, rel_rms, to_c
 
 pytestmark = pytest.mark.gpu
 
@@ -79,8 +79,8 @@ def test_paths_far_and_translated():
     assert np.abs(ref - oracle.paths(radar, rays, hits, g0)).max() <= 1e-9
 
 
-PRECISIONS = [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16,
-              rs.SIM_PREC_BF16]
+PRECISIONS = prec_params(rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16,
+                         rs.SIM_PREC_BF16)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
