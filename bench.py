@@ -38,9 +38,44 @@ import numpy as np  # noqa: E402
 
 import scenegen  # noqa: E402
 
-# DRAM bytes (read + write) of one ray-sum launch on this workload, from the ncu captures
-# summarised in profiles/umma_sum_kernel_automotive_{fp16split,bf16}.md; None where not captured.
-TRAFFIC_BYTES = {"fp16_split": 194.95e6, "bf16": 195.40e6}
+# DRAM bytes (read + write) per ray-sum launch come from ncu captures listed in this table, one
+# row per (kernel, precision, rays) with the hash of the kernel's sources at capture time; a row
+# whose hash no longer matches the sources is stale and gives no traffic figure.
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "traffic_captures.md")
+KERNEL_SOURCES = {"umma_sum_kernel": ["umma.cu", "tcgen05.cuh"],
+                  "taylor_sum_kernel": ["umma_taylor.cu", "tcgen05.cuh"]}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """First 16 hex digits of the SHA-256 of the kernel's source files, in order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2305_14176_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def captured_traffic(kernel: str, precision: str, rays: int):
+    """(bytes per launch, note) from the capture table; bytes is None when no capture of the
+    current sources exists for this kernel, precision and ray count."""
+    if not os.path.exists(TRAFFIC_TABLE):
+        return None, "no capture table"
+    want = kernel_source_hash(kernel)
+    stale = False
+    for line in open(TRAFFIC_TABLE):
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) < 6 or cells[0] != kernel:
+            continue
+        try:
+            prec, n, nbytes, sha = cells[1], int(cells[2]), float(cells[3]), cells[4]
+        except ValueError:
+            continue
+        if prec == precision and n == rays:
+            if sha == want:
+                return nbytes, f"ncu capture of sources {sha}"
+            stale = True
+    return None, ("kernel sources changed since the last capture" if stale else "not captured")
 
 METRIC = "ray-sample contributions/s"
 UNIT = "contributions/s"
@@ -360,6 +395,39 @@ def single_pass_variant(rs, torch, radar, dev_in, n, contrib, flush, peaks, step
                          "kernel": "umma_sum_kernel"}}
 
 
+def direct_variant(rs, torch, radar, dev_in, n, contrib, flush, steps=5, warmup=3):
+    """The same frame through the plain FP32 direct sum (one sin/cos per ray and thread, then a
+    phasor recurrence), timed the same way: the baseline the tensor-core path is measured
+    against at equal accuracy.  Returns the figures and the last frame's signal and labels."""
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
+    dev = dev_in["range_rt_m"].device
+    spec = torch.empty(ctx.cube_shape + (2,), dtype=torch.float32, device=dev)
+    sig = torch.empty(ctx.signal_shape + (2,), dtype=torch.float32, device=dev)
+    lab = torch.empty(ctx.cube_shape, dtype=torch.int32, device=dev)
+    totals, mains, kernels = [], [], 0
+    for s in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        rc = ctx.fetch(ctx.submit(dev_in, n), spec, sig, lab)
+        if rc != rs.SIM_OK:
+            raise rs.SimError(rc, "sim_fetch")
+        if s >= warmup:
+            st = rs.sim_last_stage_ms(ctx.ctx)
+            totals.append(st["total"])
+            mains.append(st["ray_sum"])
+            kernels += rs.sim_last_kernel_count(ctx.ctx)
+    ctx.close()
+    main_s = statistics.mean(mains) / 1e3
+    achieved = contrib / main_s / 1e12
+    out = {"value": contrib * steps / (sum(totals) / 1e3), "unit": UNIT, "dtype": "f32",
+           "ms_per_step": sum(totals) / steps, "ray_sum_ms": 1e3 * main_s, "steps": steps, "warmup": warmup,
+           "gpu_launches": kernels,
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": DIRECT_PEAK_TCONTRIB, "unit": "Tcontrib/s",
+                        "frac": achieved / DIRECT_PEAK_TCONTRIB, "kernel": "direct_sum_kernel",
+                        "peak_source": "FP32 pipe, 6 operations per contribution at the maximum SM clock"}}
+    return out, sig.cpu().numpy(), lab.cpu().numpy()
+
+
 def run_snapshot_workload(args, rs, torch):
     """Virtual snapshots (Eq. 6) and Eq. 7 antenna paths: a seeded moving-box scene at the
     automotive radar size (12 channels x 256 chirps x 512 samples), per-(ray, chirp, channel)
@@ -555,29 +623,35 @@ def run_decompose_workload(args, rs, torch):
     return 0
 
 
-def run_serve_workload(args, rs, torch):
-    """Poisson arrivals (seeded trace) of automotive frames and, with probability p_img,
-    imaging frames, through sim_submit/sim_fetch; latency = result ready - arrival."""
+def serve_run(rs, prec, rate, duration, n_rays, p_img=0.0, imaging_rays=1_000_000, clocks_csv=None, seed=4200):
+    """Poisson arrivals (seeded trace) at `rate` per second for `duration` seconds of automotive
+    frames (`n_rays` rays) and, with probability p_img, imaging frames, through
+    sim_submit/sim_fetch from host arrays; latency = result ready to fetch - arrival.  Returns
+    the statistics and the clock record of the run."""
     import threading
-    prec = rs.PRECISION_NAMES[args.precision]
     auto_radar = scenegen.radar_automotive()
-    auto_pool = [scenegen.automotive_scene(seed=4000 + i, n_rays=args.rays)[1] for i in range(4)]
-    img_radar, img_rays = scenegen.imaging_scene(seed=4100, n_rays=args.imaging_rays)
+    auto_pool = [scenegen.automotive_scene(seed=4000 + i, n_rays=n_rays)[1] for i in range(4)]
     ctx_a = rs.Context(auto_radar, precision=prec)
-    ctx_i = rs.Context(img_radar, precision=prec)
     pools = [{k: np.ascontiguousarray(v) for k, v in r.arrays().items()} for r in auto_pool]
-    img_arr = {k: np.ascontiguousarray(v) for k, v in img_rays.arrays().items()}
-    c_auto = args.rays * auto_radar.n_virtual * auto_radar.n_chirps * auto_radar.n_samples
-    c_img = img_rays.n * img_radar.n_virtual * img_radar.n_chirps * img_radar.n_samples
+    c_auto = n_rays * auto_radar.n_virtual * auto_radar.n_chirps * auto_radar.n_samples
+    kinds = [(ctx_a, pools[0], n_rays)]
+    ctx_i, img_arr, img_n, c_img = None, None, 0, 0
+    if p_img > 0:
+        img_radar, img_rays = scenegen.imaging_scene(seed=4100, n_rays=imaging_rays)
+        ctx_i = rs.Context(img_radar, precision=prec)
+        img_arr = {k: np.ascontiguousarray(v) for k, v in img_rays.arrays().items()}
+        img_n = img_rays.n
+        c_img = img_n * img_radar.n_virtual * img_radar.n_chirps * img_radar.n_samples
+        kinds.append((ctx_i, img_arr, img_n))
     # seeded arrival trace
-    n_arr = int(args.rate * args.duration * 1.5) + 16
-    gaps = -np.log(1.0 - scenegen.uniform(4200, 1, n_arr)) / args.rate
+    n_arr = int(rate * duration * 1.5) + 16
+    gaps = -np.log(1.0 - scenegen.uniform(seed, 1, n_arr)) / rate
     arrivals = np.cumsum(gaps)
-    arrivals = arrivals[arrivals < args.duration]
-    is_img = scenegen.uniform(4200, 2, arrivals.shape[0]) < args.p_img
+    arrivals = arrivals[arrivals < duration]
+    is_img = scenegen.uniform(seed, 2, arrivals.shape[0]) < p_img
     # warm-up: one of each kind
     per_frame = {}
-    for ctx, arr, nr in ((ctx_a, pools[0], args.rays), (ctx_i, img_arr, img_rays.n)):
+    for ctx, arr, nr in kinds:
         t = ctx.submit(arr, nr)
         assert ctx.fetch(t) == rs.SIM_OK
         per_frame[id(ctx)] = rs.sim_last_kernel_count(ctx.ctx)  # kernels of one frame of this kind
@@ -585,7 +659,6 @@ def run_serve_workload(args, rs, torch):
     launches = [0]
     lock = threading.Lock()
     stop = [False]
-    t0 = time.perf_counter()
 
     def fetcher():
         while True:
@@ -605,11 +678,14 @@ def run_serve_workload(args, rs, torch):
                         done_contrib[0] += contrib
                         launches[0] += per_frame[id(ctx)]
                     progressed = True
+                elif rc != rs.SIM_E_NOT_READY:
+                    raise rs.SimError(rc, "sim_fetch")
             if not progressed:
                 time.sleep(0.0001)
 
-    clk = ClockSampler(0, args.clocks_csv)
+    clk = ClockSampler(0, clocks_csv or os.path.join(tempfile.gettempdir(), "serve_clocks.csv"))
     clk.__enter__()
+    t0 = time.perf_counter()
     th = threading.Thread(target=fetcher)
     th.start()
     for k, ta in enumerate(arrivals):
@@ -617,7 +693,7 @@ def run_serve_workload(args, rs, torch):
         if ta > now:
             time.sleep(ta - now)
         img = bool(is_img[k])
-        ctx, arr, nr, cc = (ctx_i, img_arr, img_rays.n, c_img) if img else (ctx_a, pools[k % 4], args.rays, c_auto)
+        ctx, arr, nr, cc = (ctx_i, img_arr, img_n, c_img) if img else (ctx_a, pools[k % 4], n_rays, c_auto)
         try:
             ticket = ctx.submit(arr, nr)
         except rs.SimError as e:
@@ -631,23 +707,36 @@ def run_serve_workload(args, rs, torch):
     th.join()
     wall = time.perf_counter() - t0
     clk.__exit__(None, None, None)
+    for ctx, _, _ in kinds:
+        ctx.close()
     lat_ms = np.array(lat) * 1e3
-    line = {"metric": METRIC, "value": done_contrib[0] / wall, "unit": UNIT, "n_gpus": 1,
-            "steps": int(arrivals.shape[0]), "warmup": 2, "ms_per_step": float(np.median(lat_ms)) if lat else None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
-            "data": "synthetic",
-            "config": {"workload": f"serve: Poisson {args.rate}/s for {args.duration}s, automotive frames "
-                                   f"({args.rays} rays) + imaging frames ({img_rays.n} rays, p={args.p_img})",
-                       "precision": args.precision},
+    return {"value": done_contrib[0] / wall, "unit": UNIT,
             "latency_ms": {"p50": float(np.percentile(lat_ms, 50)) if lat else None,
                            "p99": float(np.percentile(lat_ms, 99)) if lat else None,
                            "max": float(lat_ms.max()) if lat else None},
-            "completed": len(lat), "refused_busy": refused[0], "imaging_arrivals": int(is_img.sum()),
-            "frames_per_s": len(lat) / wall, "wall_s": wall, "gpu_launches": launches[0],
-            "clocks": clk.summary()}
+            "arrivals": int(arrivals.shape[0]), "completed": len(lat), "refused_busy": refused[0],
+            "imaging_arrivals": int(is_img.sum()), "frames_per_s": len(lat) / wall, "wall_s": wall,
+            "gpu_launches": launches[0], "clocks": clk.summary(),
+            "imaging_rays": img_n if p_img > 0 else None}
+
+
+def run_serve_workload(args, rs, torch):
+    """Poisson arrivals (seeded trace) of automotive frames and, with probability p_img,
+    imaging frames, through sim_submit/sim_fetch; latency = result ready - arrival."""
+    r = serve_run(rs, rs.PRECISION_NAMES[args.precision], args.rate, args.duration, args.rays, args.p_img,
+                  args.imaging_rays, args.clocks_csv)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": r["arrivals"], "warmup": 2,
+            "ms_per_step": r["latency_ms"]["p50"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": f"serve: Poisson {args.rate}/s for {args.duration}s, automotive frames "
+                                   f"({args.rays} rays) + imaging frames ({r['imaging_rays']} rays, p={args.p_img})",
+                       "precision": args.precision},
+            "latency_ms": r["latency_ms"], "completed": r["completed"], "refused_busy": r["refused_busy"],
+            "imaging_arrivals": r["imaging_arrivals"], "frames_per_s": r["frames_per_s"], "wall_s": r["wall_s"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
-    ctx_a.close()
-    ctx_i.close()
     return 0
 
 
@@ -675,6 +764,11 @@ def main():
     ap.add_argument("--duration", type=float, default=5.0, help="serve: seconds of arrivals")
     ap.add_argument("--p-img", type=float, default=0.002, help="serve: probability of an imaging frame")
     ap.add_argument("--imaging-rays", type=int, default=1_000_000)
+    ap.add_argument("--no-direct", action="store_true", help="automotive: skip the FP32 direct-sum leg")
+    ap.add_argument("--direct-steps", type=int, default=5)
+    ap.add_argument("--no-serve", action="store_true", help="automotive: skip the serving-latency leg")
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=2.0)
     ap.add_argument("--in-flight", type=int, default=6,
                     help="e2e: frames submitted before the oldest is fetched (2: 5.15, 3: 5.03, 4: 4.97, 6: 4.90 ms "
                          "per automotive frame)")
@@ -811,11 +905,11 @@ def main():
         achieved = flops / main_s / 1e12
         peak = float(peaks["bf16_tflops"])
         exact = args.model == "exact"
+        kname = "taylor_sum_kernel" if exact else "umma_sum_kernel"
+        traffic, traffic_note = captured_traffic(kname, args.precision, n)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": TRAFFIC_BYTES.get(args.precision) if n == 200_000 and not exact else None,
-                "kernel": "taylor_sum_kernel" if exact else "umma_sum_kernel",
-                "peak_source": f"{peak_src} bf16 dense burst"}
+                "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_note,
+                "kernel": kname, "peak_source": f"{peak_src} bf16 dense burst"}
         # context: the measured power-capped (seconds-long) GEMM rate, the regime of the timed loop
         # when the clock record shows sw_power_cap; `frac` above stays against the burst peak
         sustained = float(peaks.get("bf16_tflops_sustained", 0.0))
@@ -866,6 +960,22 @@ def main():
     }
     if args.precision.endswith("_split") and args.model == "separable" and world == 1:
         line["single_pass_fp16"] = single_pass_variant(rs, torch, radar, dev_in, n, contrib, flush, peaks)
+    if args.precision != "fp32" and args.model == "separable" and world == 1 and not args.no_direct:
+        # the metric's comparison: the plain FP32 direct sum on the same frame, its error on the
+        # same sampled points, and how many times faster the headline arithmetic is
+        d, d_sig, d_lab = direct_variant(rs, torch, radar, dev_in, n, contrib, flush, steps=args.direct_steps)
+        if want_cpu:
+            d["error"] = result_error(radar, rays, d_sig, d_lab, idx, ref)
+        d["headline_speedup"] = d["ms_per_step"] / line["ms_per_step"]
+        d["headline_ray_sum_speedup"] = d["ray_sum_ms"] / (1e3 * main_s)
+        line["direct_fp32"] = d
+    if world == 1 and not args.no_serve:
+        # the metric's latency: Poisson arrivals of automotive frames through submit / fetch
+        line["serve"] = serve_run(rs, prec, args.serve_rate, args.serve_seconds, n,
+                                  clocks_csv=args.clocks_csv + ".serve")
+        line["serve"]["config"] = (f"Poisson {args.serve_rate}/s for {args.serve_seconds} s, automotive frames "
+                                   f"({n} rays) from host arrays, {args.precision}; latency = arrival to "
+                                   "result ready to fetch")
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
