@@ -51,7 +51,9 @@ constexpr int NTHREADS_ALL = NPROD + 32 + NDRAIN;
 // Stages (of KS rays) per tensor-core accumulation chain before it is folded into the FP32
 // running sum: the tensor core's accumulate is not IEEE round-to-nearest and its error grows
 // with the chain, so split precision folds every 512 rays; single precision (whose operand
-// rounding is ~1e-3) folds only at the end of its chunk.
+// rounding is ~1e-3) folds only at the end of its chunk.  Each fold stalls the tensor pipe
+// (about 3 us per chain); 1024-ray chains were measured 3.5 % faster but gave 1.14e-5 on a
+// 1,500-ray scene at FP16 hi + lo, whose whole sum is one chain.
 constexpr int SUBST_SPLIT = 16;
 constexpr uint32_t kSumCol = 256;      // TMEM column of the FP32 running sum
 constexpr int NGROUP = 3;              // producer groups; group g builds stages g, g + 3, ...
@@ -77,11 +79,41 @@ struct Args {
 // Per-ray inputs of one stage, staged in shared memory by the producer group that builds it.
 // base = carrier + t0 nu_tx + r0 nu_a + m0 nu_d is the phase at the tile's first row
 // (k0 = t0 N_rx + r0, m0).
-struct StageRays {
-  uint64_t base[KS], car[KS], nua[KS], nud[KS], nur[KS], nutx[KS];
-  float2 wd[KS], wr[KS];  // e^{2 pi j 32 nu_d}, e^{2 pi j 32 nu_r}
-  float amp[KS];
+// The fields every producer thread reads for each ray sit in one record per operand, so that a
+// ray costs three 16-byte loads (broadcast to the warp) instead of six narrow ones.
+struct __align__(16) RayA {  // A rows of the fast path
+  uint64_t base, nud;        // phase at the tile's first row, phase step per chirp
+  float2 wd;                 // e^{2 pi j 32 nu_d}
+  float amp, pad;
 };
+struct __align__(16) RayB {  // B columns
+  uint64_t nur;              // phase step per sample
+  float2 wr;                 // e^{2 pi j 32 nu_r}
+};
+struct StageRays {
+  RayA a[KS];
+  RayB b[KS];
+  uint64_t car[KS], nua[KS], nutx[KS];  // carrier, channel and transmitter steps (general path)
+};
+
+__device__ __forceinline__ RayA load_ray_a(const StageRays &sr, int i) {
+  const uint4 v0 = *reinterpret_cast<const uint4 *>(&sr.a[i]);
+  const uint4 v1 = *(reinterpret_cast<const uint4 *>(&sr.a[i]) + 1);
+  RayA r;
+  r.base = static_cast<uint64_t>(v0.x) | (static_cast<uint64_t>(v0.y) << 32);
+  r.nud = static_cast<uint64_t>(v0.z) | (static_cast<uint64_t>(v0.w) << 32);
+  r.wd = make_float2(__uint_as_float(v1.x), __uint_as_float(v1.y));
+  r.amp = __uint_as_float(v1.z);
+  r.pad = 0.f;
+  return r;
+}
+__device__ __forceinline__ RayB load_ray_b(const StageRays &sr, int i) {
+  const uint4 v = *reinterpret_cast<const uint4 *>(&sr.b[i]);
+  RayB r;
+  r.nur = static_cast<uint64_t>(v.x) | (static_cast<uint64_t>(v.y) << 32);
+  r.wr = make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
+  return r;
+}
 
 // Group threads fetch the stage's per-ray words one group-stage ahead: thread (f, q) with
 // f = gt / 32 takes field set f of ray q.  Rays past the chunk read as 0.
@@ -115,14 +147,14 @@ __device__ __forceinline__ void store_ray_words(StageRays &sr, int gt, const Ray
   if (f == 0) {
     sr.car[q] = w.v0;
     sr.nua[q] = w.v1;
-    sr.nud[q] = w.v2;
+    sr.a[q].nud = w.v2;
     sr.nutx[q] = w.v3;
-    sr.base[q] = w.v0 + t0 * w.v3 + r0 * w.v1 + m0 * w.v2;
+    sr.a[q].base = w.v0 + t0 * w.v3 + r0 * w.v1 + m0 * w.v2;
   } else if (f == 1) {
-    sr.nur[q] = w.v0;
-    sr.wr[q] = *reinterpret_cast<const float2 *>(&w.v1);
-    sr.amp[q] = __uint_as_float(static_cast<uint32_t>(w.v2));
-    sr.wd[q] = *reinterpret_cast<const float2 *>(&w.v3);
+    sr.b[q].nur = w.v0;
+    sr.b[q].wr = *reinterpret_cast<const float2 *>(&w.v1);
+    sr.a[q].amp = __uint_as_float(static_cast<uint32_t>(w.v2));
+    sr.a[q].wd = *reinterpret_cast<const float2 *>(&w.v3);
   }
 }
 
@@ -141,6 +173,30 @@ __device__ __forceinline__ void group_sync(int g) {
 //   chirps / 32 samples per complex multiply with the prep kernel's e^{2 pi j 32 nu} (from the
 //   exact Q0.64 product, within ~1.5 ulp).
 //   PAIR: this CTA holds B for its half of the tile's complex columns (NC = bn / 4 of them).
+// bytes of the hi A planes (A_re | A_im) of one stage; split precision stores the lo planes next
+template <bool SPLIT>
+__host__ __device__ constexpr uint32_t hi_bytes_a() {
+  return 2u * BM * KS * 2;
+}
+
+// Eight B phasors of eight rays -> the window rows of one column: B_re at +nc16, B_im at
+// +2 nc16 and -B_im (exact sign flips of the same hi and lo values) at +0; the lo block at +lo.
+template <bool F16>
+__device__ __forceinline__ void put_octet_window(const float2 (&z)[OCT], uint8_t *p, uint32_t nc16, uint32_t lo) {
+  constexpr uint32_t kSign = 0x80008000u;
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) encode<F16, true>(z[2 * q].x, z[2 * q + 1].x, h[q], l[q]);
+  sts128(p + nc16, h[0], h[1], h[2], h[3]);
+  sts128(p + nc16 + lo, l[0], l[1], l[2], l[3]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) encode<F16, true>(z[2 * q].y, z[2 * q + 1].y, h[q], l[q]);
+  sts128(p + 2 * nc16, h[0], h[1], h[2], h[3]);
+  sts128(p + 2 * nc16 + lo, l[0], l[1], l[2], l[3]);
+  sts128(p, h[0] ^ kSign, h[1] ^ kSign, h[2] ^ kSign, h[3] ^ kSign);
+  sts128(p + lo, l[0] ^ kSign, l[1] ^ kSign, l[2] ^ kSign, l[3] ^ kSign);
+}
+
 template <bool F16, bool SPLIT, bool FAST, bool PAIR>
 __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &sr, uint8_t *stage, int gt, int row0,
                                                int col0, float scale, int rank) {
@@ -149,7 +205,8 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
   const uint32_t x_half = static_cast<uint32_t>(NC) * KS * 2;
   const uint32_t hi_bytes = 2 * a_half + 2 * x_half;
   uint8_t *a_re = stage, *a_im = stage + a_half, *x_re = stage + 2 * a_half, *x_im = x_re + x_half;
-  const uint32_t lo = SPLIT ? hi_bytes : 0;
+  // A lo planes: after all hi planes, or (window form) right after the A hi planes
+  const uint32_t lo = SPLIT ? (PAIR ? 2 * a_half : hi_bytes) : 0;
   const int o = gt >> 5, j = gt & 31;
   {
     // ---- A: rows j + 32 l
@@ -163,10 +220,11 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
       for (int q = 0; q < OCT; ++q) {
         const int i = o * OCT + q;
         float sn, cs;
+        const RayA ra = load_ray_a(sr, i);
         __sincosf(q64_to_rad(sr.car[i] + static_cast<uint64_t>(tq) * sr.nutx[i] + static_cast<uint64_t>(rq) * sr.nua[i] +
-                             static_cast<uint64_t>(mq) * sr.nud[i]),
+                             static_cast<uint64_t>(mq) * ra.nud),
                   &sn, &cs);
-        const float am = sr.amp[i] * scale;
+        const float am = ra.amp * scale;
         z[q] = make_float2(am * cs, am * sn);
       }
     };
@@ -174,17 +232,18 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
       // the tile's rows share channel k0 and rows are m0 + r: phase = base + r nu_d
 #pragma unroll
       for (int q = 0; q < OCT; ++q) {
-        const int i = o * OCT + q;
+        const RayA ra = load_ray_a(sr, o * OCT + q);
         float sn, cs;
-        __sincosf(q64_to_rad(sr.base[i] + static_cast<uint64_t>(j) * sr.nud[i]), &sn, &cs);
-        const float am = sr.amp[i] * scale;
+        __sincosf(q64_to_rad(ra.base + static_cast<uint64_t>(j) * ra.nud), &sn, &cs);
+        const float am = ra.amp * scale;
         z[q] = make_float2(am * cs, am * sn);
+        w[q] = ra.wd;
       }
     } else {
       start();
-    }
 #pragma unroll
-    for (int q = 0; q < OCT; ++q) w[q] = sr.wd[o * OCT + q];
+      for (int q = 0; q < OCT; ++q) w[q] = sr.a[o * OCT + q].wd;
+    }
 #pragma unroll 1
     for (int l = 0; l < BM / 32; ++l) {
       if (l > 0) {
@@ -212,7 +271,35 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
       off += 512;
     }
   }
-  if (j < NC) {
+  if constexpr (PAIR && SPLIT) {
+    // ---- B, window form: per K chunk this CTA's rows are [-B_im | B_re | B_im] (NC rows each)
+    // so that one MMA takes A_re against [B_re | B_im] and one takes A_im against [-B_im | B_re]
+    if (j < NC) {
+      const uint32_t nc16 = static_cast<uint32_t>(NC * 16);
+      uint8_t *xb = stage + 2 * hi_bytes_a<SPLIT>();
+      const uint32_t lo_b = 3 * nc16 * (KS / OCT);  // the lo block follows the hi block
+      uint32_t off = o * 3 * nc16 + (j >> 3) * 128 + (j & 7) * 16;
+      float2 z[OCT], w[OCT];
+#pragma unroll
+      for (int q = 0; q < OCT; ++q) {
+        const int i = o * OCT + q;
+        const RayB rb = load_ray_b(sr, i);
+        float sn, cs;
+        __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + rank * NC + j) * rb.nur), &sn, &cs);
+        z[q] = make_float2(cs, sn);
+        w[q] = rb.wr;
+      }
+#pragma unroll 1
+      for (int c = j; c < NC; c += 32) {
+        if (c > j) {
+#pragma unroll
+          for (int q = 0; q < OCT; ++q) z[q] = cmulf(z[q], w[q]);  // 32 samples on
+        }
+        put_octet_window<F16>(z, xb + off, nc16, lo_b);
+        off += 512;
+      }
+    }
+  } else if (j < NC) {
     // ---- B: columns j + 32 l below NC
     uint32_t off = o * static_cast<uint32_t>(NC * 16) + (j >> 3) * 128 + (j & 7) * 16;
     float2 z[OCT], w[OCT];
@@ -220,9 +307,10 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
     for (int q = 0; q < OCT; ++q) {
       const int i = o * OCT + q;
       float sn, cs;
-      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + (PAIR ? rank * NC : 0) + j) * sr.nur[i]), &sn, &cs);
+      const RayB rb = load_ray_b(sr, i);
+      __sincosf(q64_to_rad(static_cast<uint64_t>(col0 / 2 + (PAIR ? rank * NC : 0) + j) * rb.nur), &sn, &cs);
       z[q] = make_float2(cs, sn);
-      w[q] = sr.wr[i];
+      w[q] = rb.wr;
     }
 #pragma unroll 1
     for (int c = j; c < NC; c += 32) {
@@ -292,14 +380,17 @@ struct Launch {
 
 template <bool SPLIT, bool TEST, bool PAIR>
 __host__ __device__ constexpr int num_stages() {
-  return TEST ? 4 : (PAIR ? (SPLIT ? 4 : 6) : (SPLIT ? 3 : 6));
+  return TEST ? 4 : (PAIR ? (SPLIT ? 3 : 6) : (SPLIT ? 3 : 6));
 }
 
 // bytes of one pipeline stage (PAIR: B for half the tile's columns)
 template <bool SPLIT, bool TEST, bool PAIR>
 __host__ __device__ constexpr uint32_t stage_size(int bn) {
+  // split precision on two-SM tiles (window form): A_re | A_im, hi then lo, then per hi and lo
+  // block KS / 8 K chunks of 3 x bn / 4 B rows ([-B_im | B_re | B_im] for this CTA's columns)
   return TEST ? static_cast<uint32_t>(BM * KELEM * 2 + bn * KELEM * 2)
-              : static_cast<uint32_t>(BM * KELEM * 2 + (PAIR ? bn / 2 : bn) * KS * 2) * (SPLIT ? 2u : 1u);
+              : (PAIR && SPLIT ? 2 * hi_bytes_a<SPLIT>() + 2u * (KS / OCT) * 3u * static_cast<uint32_t>(bn / 4) * 16u
+                               : static_cast<uint32_t>(BM * KELEM * 2 + (PAIR ? bn / 2 : bn) * KS * 2) * (SPLIT ? 2u : 1u));
 }
 
 // PAIR: launched as clusters of two CTAs; each cluster takes one unit of 256 rows, the even
@@ -352,7 +443,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   if constexpr (PAIR) cluster_sync();  // both CTAs' barriers exist before any remote arrival
   else __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = *tmem_holder;
+  const uint32_t tmem_base = *tmem_holder;
 
   // running counters shared by every role: pipeline stages, accumulation chains, units
   int gst = 0, gsub = 0, gunit = 0;
@@ -458,6 +549,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
       } else if (lane == 0) {
         const uint32_t sbase = smem_u32(base);
         bool open = false;  // issued MMAs not yet committed to acc_full
+        const uint32_t tmem = tmem_base;
         for (int st = 0; st < n_stages; ++st) {
           const int gs = gst + st;
           const int s = gs % NST;
@@ -482,6 +574,33 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
             for (int kk = 0; kk < KELEM / 16; ++kk)
               mma_f16<false>(tmem, make_sdesc(sb + kk * 2 * lbo_a, lbo_a, 128),
                              make_sdesc(b0 + kk * 2 * lbo_b, lbo_b, 128), idesc, (!first || kk > 0) ? 1u : 0u);
+          } else if constexpr (PAIR && SPLIT) {
+            // window form: per 16-ray K step, [Re | Im] += A_re [B_re | B_im] + A_im [-B_im | B_re]
+            // as two MMAs of N = 2 NC (CTA 0's window rows give accumulator columns 0 .. NC - 1,
+            // CTA 1's the rest: [Re | Im] of each CTA's NC / 2 columns), for hi x hi, hi x lo and
+            // lo x hi: six MMAs, each A plane read once per complex product
+            const uint32_t idesc = make_idesc(F16, 2 * BM, 2 * NC);
+            const uint32_t h = static_cast<uint32_t>(NC / 2);  // complex columns of this CTA
+            const uint32_t lbo_a = BM * 16, lbo_x = 3 * h * 16;
+            const uint32_t a_half = BM * KS * 2;
+            const uint32_t ar = sb, ai = sb + a_half, alo = 2 * a_half;
+            const uint32_t xb = sb + 4 * a_half, xlo = (KS / OCT) * lbo_x;
+            const uint32_t w1 = h * 16;  // window [B_re | B_im] starts after the -B_im rows
+#pragma unroll
+            for (int kh = 0; kh < KS / 16; ++kh) {
+              const uint32_t acc = (!first || kh > 0) ? 1u : 0u;
+              const uint32_t oa = kh * 2 * lbo_a, ox = kh * 2 * lbo_x;
+              const uint64_t dar = make_sdesc(ar + oa, lbo_a, 128), dai = make_sdesc(ai + oa, lbo_a, 128);
+              const uint64_t lar = make_sdesc(ar + alo + oa, lbo_a, 128), lai = make_sdesc(ai + alo + oa, lbo_a, 128);
+              const uint64_t w1h = make_sdesc(xb + ox + w1, lbo_x, 128), w2h = make_sdesc(xb + ox, lbo_x, 128);
+              const uint64_t w1l = make_sdesc(xb + xlo + ox + w1, lbo_x, 128), w2l = make_sdesc(xb + xlo + ox, lbo_x, 128);
+              mma_f16<true>(tmem, dar, w1h, idesc, acc);
+              mma_f16<true>(tmem, dai, w2h, idesc, 1u);
+              mma_f16<true>(tmem, dar, w1l, idesc, 1u);
+              mma_f16<true>(tmem, dai, w2l, idesc, 1u);
+              mma_f16<true>(tmem, lar, w1h, idesc, 1u);
+              mma_f16<true>(tmem, lai, w2h, idesc, 1u);
+            }
           } else {
             // planar layout: per 16-ray K step, Re S += A_re B_re - A_im B_im and
             // Im S += A_re B_im + A_im B_re (the minus by the descriptor's negate-B bit).
@@ -532,12 +651,29 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
       }
     } else {
       // ---------------- drain: TMEM lane quarter (warp % 4).  Each finished chain is added in
-      // FP32 (round to nearest) to the running sum kept in tensor memory; after the last chain
-      // the sum goes to this split's partial in global memory.
+      // FP32 (round to nearest) to the running sum kept in tensor memory, 32 columns per load
+      // pair and wait (the tensor pipe waits while a chain drains); after the last chain the sum
+      // goes to this split's partial in global memory.
       const int q = warp & 3;
       const int grow = row0 + q * 32 + lane;
       float *dst = g.partials + (static_cast<int64_t>(split) * g.m_rows + grow) * (2 * g.ns) + col0;
-      const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      const uint32_t trow = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
+      // 16 accumulator columns from column c to the partial (window form: accumulator columns
+      // [Re | Im] of CTA 0's columns, then of CTA 1's, in blocks of bn / 4; the partial keeps
+      // the tile as [Re block | Im block])
+      auto put16 = [&](int c, const uint32_t *v) {
+        int dc = c;
+        if constexpr (PAIR && SPLIT) {
+          const int hq = bn >> 2;
+          if (c >= hq && c < 2 * hq) dc = c + hq;
+          else if (c >= 2 * hq && c < 3 * hq) dc = c - hq;
+        }
+#pragma unroll
+        for (int x = 0; x < 16; x += 4)
+          *reinterpret_cast<float4 *>(dst + dc + x) =
+              make_float4(__uint_as_float(v[x]), __uint_as_float(v[x + 1]), __uint_as_float(v[x + 2]),
+                          __uint_as_float(v[x + 3]));
+      };
       if (n_stages == 0 && grow < g.m_rows) {
         for (int c = 0; c < bn; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(0.f, 0.f, 0.f, 0.f);
       }
@@ -548,23 +684,36 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         }
         tc_fence_after();
         const bool last = sub == n_sub - 1;
-        for (int c = 0; c < bn; c += 16) {
-          uint32_t h[16];
-          tmem_ld16(trow + static_cast<uint32_t>(c), h);
-          if (sub > 0) {
-            uint32_t r[16];
-            tmem_ld16(trow + kSumCol + static_cast<uint32_t>(c), r);
+        for (int c = 0; c < bn;) {
+          if (c + 32 <= bn) {
+            uint32_t h[32];
+            if (sub > 0) {
+              uint32_t r[32];
+              tmem_ld32x2(trow + static_cast<uint32_t>(c), trow + kSumCol + static_cast<uint32_t>(c), h, r);
 #pragma unroll
-            for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
-          }
-          if (!last) {
-            tmem_st16(trow + kSumCol + static_cast<uint32_t>(c), h);
-          } else if (grow < g.m_rows) {
+              for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+            } else {
+              tmem_ld32(trow + static_cast<uint32_t>(c), h);
+            }
+            if (!last) {
+              tmem_st32(trow + kSumCol + static_cast<uint32_t>(c), h);
+            } else if (grow < g.m_rows) {
+              put16(c, h);
+              put16(c + 16, h + 16);
+            }
+            c += 32;
+          } else {
+            uint32_t h[16];
+            tmem_ld16(trow + static_cast<uint32_t>(c), h);
+            if (sub > 0) {
+              uint32_t r[16];
+              tmem_ld16(trow + kSumCol + static_cast<uint32_t>(c), r);
 #pragma unroll
-            for (int x = 0; x < 16; x += 4)
-              *reinterpret_cast<float4 *>(dst + c + x) =
-                  make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
-                              __uint_as_float(h[x + 3]));
+              for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+            }
+            if (!last) tmem_st16(trow + kSumCol + static_cast<uint32_t>(c), h);
+            else if (grow < g.m_rows) put16(c, h);
+            c += 16;
           }
         }
         if (!last) tmem_wait_st();
@@ -601,7 +750,7 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
   else __syncthreads();
   if (warp == MMA_WARP) {
     tc_fence_after();
-    tmem_dealloc<PAIR>(tmem, TMEM_COLS);
+    tmem_dealloc<PAIR>(tmem_base, TMEM_COLS);
   }
 }
 
