@@ -279,6 +279,13 @@ SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *me
    Must be called before the first sim_create; SIM_E_INVALID afterwards. */
 SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int32_t max_queue);
 
+/* Device bytes the engine holds for one submitted scene of n_rays rays on this context (its
+   inputs, per-ray data, signal, spectrum, labels, label tables and ray-sum workspace): the
+   amount the memory budget of sim_engine_configure is charged while the scene is admitted,
+   for callers that plan a budget.  Not a compute call; the result follows the current tuning
+   table.  Errors: SIM_E_INVALID (null pointers, n_rays < 0 or above the context's max_rays). */
+SIM_API int sim_scene_bytes(const sim_ctx *ctx, int64_t n_rays, int64_t *bytes);
+
 /* Per-stage device time in milliseconds of the most recently fetched ticket of
    this context, from CUDA events on the stream the scene ran on: [0] ingest
    copies, [1] per-ray prep, [2] ray-sum main kernel, [3] ray-sum split reduction,

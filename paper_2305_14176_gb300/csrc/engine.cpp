@@ -607,6 +607,13 @@ int sim_create(const sim_radar_params *params, sim_ctx **out) {
   return SIM_OK;
 }
 
+int sim_scene_bytes(const sim_ctx *c, int64_t n_rays, int64_t *bytes) {
+  if (!c || !bytes || n_rays < 0 || n_rays > c->g.max_rays) return SIM_E_INVALID;
+  const bool want_labels = (c->g.outputs & SIM_OUT_LABELS) != 0;
+  *bytes = static_cast<int64_t>(make_plan(c->g, n_rays, want_labels && n_rays > 0).total);
+  return SIM_OK;
+}
+
 int sim_submit(sim_ctx *c, const sim_rays *rays, const sim_meta *meta, uint64_t *ticket_out) {
   if (!c || !rays || !ticket_out) return SIM_E_INVALID;
   const int64_t n = rays->n;

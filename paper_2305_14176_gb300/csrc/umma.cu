@@ -361,19 +361,58 @@ __device__ __forceinline__ void copy_stage(const Args &g, uint8_t *a_hi, uint8_t
 }
 
 // One work unit: a 128-row x bn-column tile of one scene summed over one chunk of its rays.
+// One work unit: one tile of one scene summed over rays [k_lo, k_hi) into partial `split`.
 struct Unit {
   int scene, tile_m, tile_n, split;
+  int64_t k_lo, k_hi;
 };
 
-// A launch of the ray-sum kernel: either one scene whose units are decoded from the CTA
-// index (one unit per CTA), or a persistent batch whose CTAs take units from a work list
-// (longest first) through an atomic counter.
+// Stream-K plan of a scene (split precision): its T tiles x S stages of rays form W = T S
+// stage-units in tile order (tile t = tile_n mt + tile_m); program c of C takes the contiguous
+// range [c W / C, (c + 1) W / C), cut at tile boundaries into pieces.  Piece slot = c minus the
+// program holding the tile's first stage, so a tile's pieces are slots 0 .. p_t - 1 in ray
+// order.  The plan depends only on the scene's own shape and the program count.
+struct StreamK {
+  int64_t w, s;  // stage-units and stages per tile; w = 0: no stream-K plan
+  int c, mt;     // programs, tile rows (the tile order's stride)
+};
+
+// program holding stage-unit x: the largest j with floor(j W / C) <= x
+__host__ __device__ inline int64_t sk_program_of(const StreamK &k, int64_t x) {
+  return ((x + 1) * k.c + k.w - 1) / k.w - 1;
+}
+// pieces of tile t
+__host__ __device__ inline int sk_pieces(const StreamK &k, int64_t t) {
+  return static_cast<int>(sk_program_of(k, (t + 1) * k.s - 1) - sk_program_of(k, t * k.s) + 1);
+}
+// piece `idx` of program c (tile, ray range, slot); false once the program has no more
+__host__ __device__ inline bool sk_piece(const StreamK &k, int64_t n_rays, int c, int idx, Unit &u) {
+  int64_t pos = static_cast<int64_t>(c) * k.w / k.c;
+  const int64_t end = static_cast<int64_t>(c + 1) * k.w / k.c;
+  for (int q = 0; q < idx && pos < end; ++q) pos = (pos / k.s + 1) * k.s < end ? (pos / k.s + 1) * k.s : end;
+  if (pos >= end) return false;
+  const int64_t t = pos / k.s;
+  const int64_t hi = (t + 1) * k.s < end ? (t + 1) * k.s : end;
+  u.scene = 0;
+  u.split = static_cast<int>(c - sk_program_of(k, t * k.s));
+  u.tile_n = static_cast<int>(t / k.mt);
+  u.tile_m = static_cast<int>(t - static_cast<int64_t>(u.tile_n) * k.mt);
+  u.k_lo = (pos - t * k.s) * KS;
+  u.k_hi = (hi - t * k.s) * KS < n_rays ? (hi - t * k.s) * KS : n_rays;
+  return true;
+}
+
+// A launch of the ray-sum kernel: one scene whose units are decoded from the CTA index (one
+// split unit per CTA, or with a stream-K plan the pieces of one program per CTA), or a
+// persistent batch whose CTAs take units from a work list (longest first) through an atomic
+// counter.
 struct Launch {
   Args inline_scene;     // used when `scenes` is null
   const Args *scenes;    // per-scene arguments in device memory, or null
   const Unit *units;     // work list in device memory, or null (decode from inline_scene)
   int n_units;
   int mt, nt;            // tiles of the inline scene (for decoding)
+  StreamK sk;            // the inline scene's stream-K plan (sk.w = 0: split units)
   unsigned *counter;     // persistent mode: next unit to take (zeroed before the launch)
   int bn_layout;         // B rows the shared-memory stages are laid out for (max bn)
 };
@@ -471,29 +510,38 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
       __syncthreads();
     }
   }
+  // inline stream-K: this CTA (pair) is program `prog` and runs its pieces 0, 1, ...
+  const int prog = u;
+  if (!L.units && L.sk.w > 0) u = 0;
   while (u < L.n_units) {
     if (threadIdx.x == 0) {
       if (L.units) {
         s_unit = L.units[u];
+      } else if (L.sk.w > 0) {
+        const int64_t kt = TEST ? L.inline_scene.test_k / 2 : L.inline_scene.n_rays;
+        if (!sk_piece(L.sk, kt, prog, u, s_unit)) s_unit.scene = -1;
       } else {
         const int per = L.mt * L.nt;
+        const Args &a = L.inline_scene;
+        const int64_t kt = TEST ? a.test_k / 2 : a.n_rays;
         s_unit.scene = 0;
         s_unit.split = u / per;
         s_unit.tile_n = (u - s_unit.split * per) / L.mt;
         s_unit.tile_m = u - s_unit.split * per - s_unit.tile_n * L.mt;
+        s_unit.k_lo = static_cast<int64_t>(s_unit.split) * a.chunk;
+        s_unit.k_hi = s_unit.k_lo + a.chunk < kt ? s_unit.k_lo + a.chunk : kt;
       }
-      s_args = L.scenes ? L.scenes[s_unit.scene] : L.inline_scene;
+      if (s_unit.scene >= 0) s_args = L.scenes ? L.scenes[s_unit.scene] : L.inline_scene;
     }
     __syncthreads();
+    if (s_unit.scene < 0) break;  // the program's pieces are done (uniform across the CTA pair)
     const Args &g = s_args;
     const int bn = g.bn;
     const int NC = bn >> 1;
     const int row0 = (PAIR ? 2 * s_unit.tile_m + static_cast<int>(rank) : s_unit.tile_m) * BM;
     const int col0 = s_unit.tile_n * bn;  // real column; complex n0 = col0 / 2
     const int split = s_unit.split;
-    const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
-    const int64_t k_total = TEST ? g.test_k / 2 : g.n_rays;  // rays (K pairs)
-    const int64_t k_hi = k_lo + g.chunk < k_total ? k_lo + g.chunk : k_total;
+    const int64_t k_lo = s_unit.k_lo, k_hi = s_unit.k_hi;
     const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + KS - 1) / KS) : 0;
     const int SUBST = SPLIT ? SUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
     const int n_sub = (n_stages + SUBST - 1) / SUBST;
@@ -732,7 +780,25 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
     tc_fence_before();
     __syncthreads();  // every role is done with this unit (and with s_args)
     tc_fence_after();
-    if (!L.counter) break;
+    if (!L.counter) {
+      if (L.units || L.sk.w == 0) break;
+      // the program's next piece; a CTA pair stops together when either CTA has aborted
+      if constexpr (PAIR) {
+        if (rank != 0 && threadIdx.x == 0 && s_abort) st_cluster_u32(cluster_addr(smem_u32(&s_peer_abort), 0), 1u);
+        cluster_sync();
+        if (rank == 0 && threadIdx.x == 0) {
+          const int v = (s_abort || s_peer_abort) ? 1 : 0;
+          s_next = v;
+          st_cluster_u32(cluster_addr(smem_u32(&s_next), 1), static_cast<uint32_t>(v));
+        }
+        cluster_sync();
+        if (s_next) break;
+      } else {
+        if (s_abort) break;
+      }
+      ++u;
+      continue;
+    }
     if constexpr (PAIR) {
       u = pair_next();  // both CTAs stop together
     } else {
@@ -758,9 +824,11 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
 //   sig[row][n] = sum_s (P_s[row][t bn + nl], P_s[row][t bn + bn/2 + nl]) / scale,
 //   t = n / (bn/2), nl = n % (bn/2).
 // A thread takes four consecutive samples (16-byte loads; bn / 2 and N_s are multiples of 16).
+// With a stream-K plan (sk.w > 0) tile t has sk_pieces(t) partials instead of `splits`;
+// tile_rows is the rows of a tile (256 for two-SM tiles).
 template <bool F16>
 __global__ void reduce_partials(const float *__restrict__ part, int splits, int64_t m_rows, int ns, int bn,
-                                float2 *__restrict__ sig, const uint32_t *amax_bits) {
+                                float2 *__restrict__ sig, const uint32_t *amax_bits, StreamK sk, int tile_rows) {
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
   const int64_t n_q = m_rows * ns / 4;
   const int64_t plane = m_rows * 2 * ns;
@@ -772,8 +840,9 @@ __global__ void reduce_partials(const float *__restrict__ part, int splits, int6
     const int t = n / half, nl = n - t * half;
     const float *p = part + row * 2 * ns + t * bn + nl;
     float4 re = *reinterpret_cast<const float4 *>(p), im = *reinterpret_cast<const float4 *>(p + half);
+    const int n_split = sk.w > 0 ? sk_pieces(sk, static_cast<int64_t>(t) * sk.mt + row / tile_rows) : splits;
 #pragma unroll 6
-    for (int s = 1; s < splits; ++s) {
+    for (int s = 1; s < n_split; ++s) {
       const float4 a = *reinterpret_cast<const float4 *>(p + s * plane);
       const float4 b = *reinterpret_cast<const float4 *>(p + s * plane + half);
       re.x += a.x; re.y += a.y; re.z += a.z; re.w += a.w;
@@ -797,8 +866,9 @@ __global__ void amax_kernel(const float *__restrict__ amp, int64_t n, uint32_t *
 int g_num_sms = 0;
 
 struct Shape {
-  int mt, nt, splits, bn;
+  int mt, nt, splits, bn;  // splits: partials per tile (with stream-K the most any tile has)
   int64_t chunk;
+  StreamK sk;              // sk.w > 0: stream-K plan
 };
 
 int num_sms() {
@@ -816,15 +886,44 @@ int num_sms() {
 // evenly as possible.  Depends only on the scene's own shape and ray count.
 Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits, float waves = 4.f, int64_t min_chunk = 0);
 
-Shape plan_shape(const Derived &g, int64_t n, float waves = 4.f, int64_t min_chunk = 0) {
+// Two-SM tiles (M = 256 over a CTA pair, each CTA building B for half the columns) when the
+// tile has at least 32 complex columns; the split-K chunks are those of the one-SM tiling.
+bool use_pair(const Shape &sh) { return sh.bn >= 64; }
+
+// Split precision on a GPU to itself: one program per SM (pair), each summing a contiguous run
+// of the scene's (tile, ray stage) work, at least one accumulation chain long.  A tile then
+// has at most a few partials (three on the automotive frame, against 19 split units), and a
+// CTA switches tiles once or twice instead of once per split.
+Shape with_stream_k(Shape s, int64_t n) {
+  const bool pair = use_pair(s);
+  const int mtp = pair ? (s.mt + 1) / 2 : s.mt;
+  const int64_t tiles = static_cast<int64_t>(mtp) * s.nt;
+  const int64_t stages = (n + KS - 1) / KS;
+  const int64_t w = tiles * stages;
+  const int64_t programs = pair ? num_sms() / 2 : num_sms();
+  StreamK k{w, stages, static_cast<int>(std::max<int64_t>(1, std::min(programs, w / SUBST_SPLIT))), mtp};
+  int pmax = 1;
+  for (int64_t t = 0; t < tiles; ++t) pmax = std::max(pmax, sk_pieces(k, t));
+  s.sk = k;
+  s.splits = pmax;
+  s.chunk = stages * KS;
+  return s;
+}
+
+// allow_sk: a scene planned for the whole GPU with split precision and no tuned entry takes the
+// stream-K plan
+Shape plan_shape(const Derived &g, int64_t n, float waves = 4.f, int64_t min_chunk = 0, bool allow_sk = true) {
   Tuning tu{};
   if (waves == 4.f && min_chunk == 0 && tuning_lookup(g, n, &tu) && tu.splits > 0) return plan_shape_forced(g, n, tu.splits);
-  return plan_shape_forced(g, n, 0, waves, min_chunk);
+  const Shape s = plan_shape_forced(g, n, 0, waves, min_chunk);
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  if (allow_sk && split && waves == 4.f && min_chunk == 0 && n > 0) return with_stream_k(s, n);
+  return s;
 }
 
 // forced_splits > 0 replaces the wave-filling choice (autotuned tables, tuner trials)
 Shape plan_shape_forced(const Derived &g, int64_t n, int forced_splits, float waves, int64_t min_chunk) {
-  Shape s;
+  Shape s{};
   const int M = g.nv * g.nc;
   // single pass keeps no running sum in tensor memory, so its tiles can take 256 complex columns
   // (Re and Im blocks fill all 512 TMEM columns); split precision tiles take 128
@@ -898,9 +997,13 @@ void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
   L.nt = sh.nt;
   L.n_units = L.mt * sh.nt * sh.splits;
   L.bn_layout = sh.bn;
+  L.sk = sh.sk;
+  // stream-K: one CTA (pair) per program, each running its pieces; n_units only bounds the loop
+  const unsigned ctas = sh.sk.w > 0 ? static_cast<unsigned>(sh.sk.c) : static_cast<unsigned>(L.n_units);
+  if (sh.sk.w > 0) L.n_units = 0x7fffffff;
   if constexpr (PAIR) {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(2u * static_cast<unsigned>(L.n_units));
+    cfg.gridDim = dim3(2u * ctas);
     cfg.blockDim = dim3(NTHREADS_ALL);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
@@ -913,13 +1016,9 @@ void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, L);
   } else {
-    umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR><<<L.n_units, NTHREADS_ALL, sm, s>>>(L);
+    umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR><<<ctas, NTHREADS_ALL, sm, s>>>(L);
   }
 }
-
-// Two-SM tiles (M = 256 over a CTA pair, each CTA building B for half the columns) when the
-// tile has at least 32 complex columns; the split-K chunks are those of the one-SM tiling.
-bool use_pair(const Shape &sh) { return sh.bn >= 64; }
 
 // FAST: every tile's 128 rows lie in one channel (N_c a multiple of 128); the general kernel
 // gives the same bits on such scenes, only with more work per row
@@ -978,8 +1077,10 @@ int launch_umma_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *
   if (after_main) cudaEventRecord(after_main, s);
   const int rb = 4 * num_sms();
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
-  if (f16) reduce_partials<true><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
-  else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  if (f16) reduce_partials<true><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax, sh.sk,
+                                                    use_pair(sh) ? 2 * BM : BM);
+  else reduce_partials<false><<<rb, 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax, sh.sk,
+                                                     use_pair(sh) ? 2 * BM : BM);
   ++kernels;
   return kernels;
 }
@@ -1033,8 +1134,10 @@ int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig,
   a.status = status;
   launch_gemm_dispatch(f16, split, (g.nc % BM) == 0, sh, a, s);
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
-  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
-  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                sh.sk, use_pair(sh) ? 2 * BM : BM);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                 sh.sk, use_pair(sh) ? 2 * BM : BM);
   return sh.splits;
 }
 
@@ -1054,9 +1157,30 @@ int64_t batch_workspace_bytes(const Derived &g, int64_t n) {
   return 256 + static_cast<int64_t>(sh.splits) * g.nv * g.nc * 2 * g.ns * 4;
 }
 
+// the scene's work units in its standalone plan: stream-K pieces, or tiles x splits
+template <typename F>
+void for_each_unit(const Shape &sh, int64_t n, F &&f) {
+  const int mt = use_pair(sh) ? (sh.mt + 1) / 2 : sh.mt;
+  if (sh.sk.w > 0) {
+    for (int c = 0; c < sh.sk.c; ++c) {
+      Unit u{};
+      for (int idx = 0; sk_piece(sh.sk, n, c, idx, u); ++idx) f(u);
+    }
+    return;
+  }
+  for (int sp = 0; sp < sh.splits; ++sp) {
+    const int64_t k_lo = static_cast<int64_t>(sp) * sh.chunk;
+    const int64_t k_hi = std::min<int64_t>(k_lo + sh.chunk, n);
+    for (int tn = 0; tn < sh.nt; ++tn)
+      for (int tm = 0; tm < mt; ++tm) f(Unit{0, tm, tn, sp, k_lo, std::max(k_hi, k_lo)});
+  }
+}
+
 int64_t umma_units_of(const Derived &g, int64_t n) {
   const Shape sh = batch_shape(g, n);
-  return static_cast<int64_t>(sh.mt) * sh.nt * sh.splits;
+  int64_t k = 0;
+  for_each_unit(sh, n, [&](const Unit &) { ++k; });
+  return k;
 }
 
 int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *ps, const int64_t *ns,
@@ -1097,15 +1221,11 @@ int prepare_umma_batch(int n_scenes, const Derived *const *gs, const RaysPrep *p
     const bool pair = use_pair(sh);
     int &bmax = pair ? bn_max : bn_max1;
     if (sh.bn > bmax) bmax = sh.bn;
-    const int mt = pair ? (sh.mt + 1) / 2 : sh.mt;
-    for (int sp = 0; sp < sh.splits; ++sp) {
-      const int64_t rays = std::min<int64_t>(sh.chunk, ns[i] - sp * sh.chunk);
-      for (int tn = 0; tn < sh.nt; ++tn)
-        for (int tm = 0; tm < mt; ++tm) {
-          (pair ? units : units1).push_back(Unit{i, tm, tn, sp});
-          (pair ? cost : cost1).push_back(std::max<int64_t>(rays, 0) * sh.bn);
-        }
-    }
+    for_each_unit(sh, ns[i], [&](Unit u) {
+      u.scene = i;
+      (pair ? units : units1).push_back(u);
+      (pair ? cost : cost1).push_back((u.k_hi - u.k_lo) * sh.bn);
+    });
   }
   // longest first (stable: ties keep scene, split, tile order)
   auto longest_first = [](const std::vector<Unit> &u, const std::vector<int64_t> &c) {
@@ -1233,8 +1353,10 @@ int launch_umma_post(const Derived &g, int64_t n, float2 *sig, void *workspace, 
   uint32_t *amax = static_cast<uint32_t *>(workspace);
   float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
-  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
-  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                sh.sk, use_pair(sh) ? 2 * BM : BM);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                 sh.sk, use_pair(sh) ? 2 * BM : BM);
   return 1;
 }
 
@@ -1245,7 +1367,7 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
     if (g.tslot != 0.0 || exact_workspace_bytes(g, n) > ws_bytes) return -1;
     return launch_exact_sum(g, p, n, sig, workspace, status, s, nullptr);
   }
-  Shape sh = plan_shape(g, n);
+  Shape sh = plan_shape(g, n, 4.f, 0, false);  // split units: their count is capped to the scratch
   const int64_t per_split = static_cast<int64_t>(g.nv) * g.nc * 2 * g.ns * 4;
   const int64_t fit = (ws_bytes - 256) / per_split;
   if (fit < 1) return -1;
@@ -1282,8 +1404,10 @@ int launch_umma_sum_in(const Derived &g, RaysPrep p, int64_t n, float2 *sig, voi
   launch_gemm_dispatch(f16, split, (g.nc % BM) == 0, sh, a, s);
   ++kernels;
   const int64_t m_rows = static_cast<int64_t>(g.nv) * g.nc;
-  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
-  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax);
+  if (f16) reduce_partials<true><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                sh.sk, use_pair(sh) ? 2 * BM : BM);
+  else reduce_partials<false><<<4 * num_sms(), 256, 0, s>>>(partials, sh.splits, m_rows, g.ns, sh.bn, sig, amax,
+                                                                 sh.sk, use_pair(sh) ? 2 * BM : BM);
   ++kernels;
   return kernels;
 }
@@ -1297,7 +1421,7 @@ extern "C" SIM_API int sim_selftest_umma(int32_t f16, int32_t m, int32_t n, int6
   if (m < 1 || n < 32 || (n & 15) || n > 512 || k < 2 || (k & 1) || !a || !b || !d || (f16 & ~3)) return SIM_E_INVALID;
   const bool negate = (f16 & 2) != 0;
   f16 &= 1;
-  Shape sh;
+  Shape sh{};
   sh.bn = n < 256 ? n : 256;
   if (n % sh.bn) return SIM_E_INVALID;
   sh.mt = (m + BM - 1) / BM;

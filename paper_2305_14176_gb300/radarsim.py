@@ -95,6 +95,7 @@ def _load() -> ctypes.CDLL:
     lib.sim_submit.argtypes = [P, ctypes.POINTER(sim_rays), ctypes.POINTER(sim_meta), U64P]
     lib.sim_fetch.argtypes = [P, ctypes.c_uint64, P, P, P, I32]
     lib.sim_destroy.argtypes = [P]
+    lib.sim_scene_bytes.argtypes = [P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.sim_status_string.argtypes = [ctypes.c_int]
     lib.sim_status_string.restype = ctypes.c_char_p
     lib.sim_engine_configure.argtypes = [I64, I32, I32]
@@ -153,6 +154,15 @@ def sim_status_string(code: int) -> str:
 
 def sim_engine_configure(memory_budget_bytes: int = 0, slots: int = 4, max_queue: int = 64) -> int:
     return lib.sim_engine_configure(int(memory_budget_bytes), int(slots), int(max_queue))
+
+
+def sim_scene_bytes(ctx, n_rays: int) -> int:
+    """Device bytes one admitted scene of n_rays rays holds on this context."""
+    b = ctypes.c_int64(0)
+    rc = lib.sim_scene_bytes(ctx, int(n_rays), ctypes.byref(b))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_scene_bytes")
+    return int(b.value)
 
 
 def sim_create(params: sim_radar_params) -> ctypes.c_void_p:

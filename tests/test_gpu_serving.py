@@ -62,8 +62,10 @@ _ADMISSION = textwrap.dedent("""
     import scenegen
     from paper_2305_14176_gb300 import radarsim as rs
     torch.cuda.init()
-    # budget for about two automotive scenes of 20k rays, at most 3 queued
-    assert rs.sim_engine_configure(int(1.5 * 260e6), 4, 3) == rs.SIM_OK
+    # budget for one and a half automotive scenes of 20k rays (their size from the engine's own
+    # plan, measured in another process), at most 3 queued
+    one = {one}
+    assert rs.sim_engine_configure(int(1.5 * one), 4, 3) == rs.SIM_OK
     radar, rays = scenegen.automotive_scene(seed=9, n_rays=20_000)
     ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT)
     assert rs.sim_engine_configure(0, 4, 3) == rs.SIM_E_INVALID  # too late: engine running
@@ -94,8 +96,24 @@ _ADMISSION = textwrap.dedent("""
 """)
 
 
+_SCENE_BYTES = textwrap.dedent("""
+    import sys
+    sys.path.insert(0, {root!r})
+    import scenegen
+    from paper_2305_14176_gb300 import radarsim as rs
+    radar, rays = scenegen.automotive_scene(seed=9, n_rays=20_000)
+    ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT)
+    print(rs.sim_scene_bytes(ctx.ctx, rays.n))
+""")
+
+
 def test_admission_by_memory_budget():
-    src = _ADMISSION.format(root=ROOT)
+    r = subprocess.run([sys.executable, "-c", _SCENE_BYTES.format(root=ROOT)], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr
+    one = int(r.stdout.strip().splitlines()[-1])
+    assert 50e6 < one < 400e6, one
+    src = _ADMISSION.format(root=ROOT, one=one)
     r = subprocess.run([sys.executable, "-c", src], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and "admission ok" in r.stdout, r.stdout + r.stderr
 
