@@ -64,7 +64,13 @@ template <bool SPLIT>
 __host__ __device__ constexpr int t_groups() {
   return SPLIT ? 3 : 4;
 }
-constexpr int TSUBST_SPLIT = 16;       // stages per accumulation chain at split precision
+// Stages per accumulation chain at split precision.  The tensor core's accumulate is not
+// round-to-nearest, so a chain is folded into the FP32 running sum after a bounded number of
+// MMAs into its accumulator: 192, as in the separable kernel's 512-ray chains.  A stage adds 12
+// MMAs to each accumulator block when every term keeps its lo operands (16 stages) and 8 when
+// the high-order terms go single pass (24 stages); each fold stalls the tensor pipe.
+constexpr int TSUBST_SPLIT = 16;
+constexpr int TSUBST_SPLIT_LOW = 24;
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
 constexpr int kMaxDynSmemT = 232448 - 8192;
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
   const int64_t k_lo = static_cast<int64_t>(split) * g.chunk;
   const int64_t k_hi = k_lo + g.chunk < g.n_rays ? k_lo + g.chunk : g.n_rays;
   const int n_stages = k_hi > k_lo ? static_cast<int>((k_hi - k_lo + RS - 1) / RS) : 0;
-  const int SUBST = SPLIT ? TSUBST_SPLIT : (n_stages > 0 ? n_stages : 1);
+  const int SUBST = SPLIT ? (lo_high ? TSUBST_SPLIT : TSUBST_SPLIT_LOW) : (n_stages > 0 ? n_stages : 1);
   const int n_sub = (n_stages + SUBST - 1) / SUBST;
   bool failed = false;
 
@@ -567,22 +573,48 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
         }
         tc_fence_after();
         const bool last = sub == n_sub - 1;
-        for (int c = 0; c < bn; c += 16) {
-          uint32_t h[16];
-          tmem_ld16(trow + static_cast<uint32_t>(c), h);
-          if (sub > 0) {
-            uint32_t r[16];
-            tmem_ld16(trow + TSUM_COL + static_cast<uint32_t>(c), r);
+        // 32 columns per load pair and wait where the tile allows (the tensor pipe waits while
+        // a chain drains), 16 at the tail
+        for (int c = 0; c < bn;) {
+          if (c + 32 <= bn) {
+            uint32_t h[32];
+            if (sub > 0) {
+              uint32_t r[32];
+              tmem_ld32x2(trow + static_cast<uint32_t>(c), trow + TSUM_COL + static_cast<uint32_t>(c), h, r);
 #pragma unroll
-            for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
-          }
-          if (!last) {
-            tmem_st16(trow + TSUM_COL + static_cast<uint32_t>(c), h);
-          } else if (grow < g.m_rows) {
+              for (int x = 0; x < 32; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+            } else {
+              tmem_ld32(trow + static_cast<uint32_t>(c), h);
+            }
+            if (!last) {
+              tmem_st32(trow + TSUM_COL + static_cast<uint32_t>(c), h);
+            } else if (grow < g.m_rows) {
 #pragma unroll
-            for (int x = 0; x < 16; x += 4)
-              *reinterpret_cast<float4 *>(dst + c + x) = make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]),
-                                                                     __uint_as_float(h[x + 2]), __uint_as_float(h[x + 3]));
+              for (int x = 0; x < 32; x += 4)
+                *reinterpret_cast<float4 *>(dst + c + x) =
+                    make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
+                                __uint_as_float(h[x + 3]));
+            }
+            c += 32;
+          } else {
+            uint32_t h[16];
+            tmem_ld16(trow + static_cast<uint32_t>(c), h);
+            if (sub > 0) {
+              uint32_t r[16];
+              tmem_ld16(trow + TSUM_COL + static_cast<uint32_t>(c), r);
+#pragma unroll
+              for (int x = 0; x < 16; ++x) h[x] = __float_as_uint(__uint_as_float(h[x]) + __uint_as_float(r[x]));
+            }
+            if (!last) {
+              tmem_st16(trow + TSUM_COL + static_cast<uint32_t>(c), h);
+            } else if (grow < g.m_rows) {
+#pragma unroll
+              for (int x = 0; x < 16; x += 4)
+                *reinterpret_cast<float4 *>(dst + c + x) =
+                    make_float4(__uint_as_float(h[x]), __uint_as_float(h[x + 1]), __uint_as_float(h[x + 2]),
+                                __uint_as_float(h[x + 3]));
+            }
+            c += 16;
           }
         }
         if (!last) tmem_wait_st();
