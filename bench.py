@@ -135,6 +135,17 @@ class ClockSampler:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+        # the sampler is live before the timed region starts: wait (at most 2 s) for its first row
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < 2.0:
+            if self.proc.poll() is not None:
+                break
+            try:
+                if os.path.getsize(self.path) > 0:
+                    break
+            except OSError:
+                pass
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *a):
