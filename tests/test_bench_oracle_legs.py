@@ -50,3 +50,19 @@ def test_decompose_leg_samples_each_span_at_its_rays_bins():
         assert set(c.tolist()) <= set(oracle.bins(radar, sub)["cell"].tolist())
         spec = oracle.spectrum(radar, oracle.signal(radar, sub))
         assert np.allclose(ref, spec.reshape(-1)[c], rtol=0, atol=1e-9 * np.abs(spec).max())
+
+
+def test_traffic_comes_only_from_a_capture_of_the_current_sources(tmp_path, monkeypatch):
+    """roofline.traffic is read from the capture table row whose source hash matches the
+    kernel's current sources; a row captured from other sources gives no figure."""
+    import bench
+    cur = bench.kernel_source_hash("umma_sum_kernel")
+    table = tmp_path / "traffic.md"
+    table.write_text("| kernel | precision | rays | bytes | sources | note |\n|---|---|---|---|---|---|\n"
+                     f"| umma_sum_kernel | fp16_split | 200000 | 12345 | {cur} | current |\n"
+                     "| umma_sum_kernel | bf16 | 200000 | 999 | 0000000000000000 | stale |\n")
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", str(table))
+    assert bench.captured_traffic("umma_sum_kernel", "fp16_split", 200000)[0] == 12345
+    assert bench.captured_traffic("umma_sum_kernel", "fp16_split", 100000)[0] is None
+    nbytes, note = bench.captured_traffic("umma_sum_kernel", "bf16", 200000)
+    assert nbytes is None and "changed" in note
