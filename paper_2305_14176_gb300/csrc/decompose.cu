@@ -274,7 +274,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   cudaMemcpyAsync(b + o_rules, hrules.data(), sizeof(RuleDev) * hrules.size(), cudaMemcpyHostToDevice, s);
   uint32_t *status = reinterpret_cast<uint32_t *>(b + o_status);
   uint32_t *pmax = reinterpret_cast<uint32_t *>(b + o_max);
-  cudaMemsetAsync(status, 0, 4, s);
+  cudaMemsetAsync(status, 0, 8, s);  // status bits and route mask
   cudaMemsetAsync(pmax, 0, 4, s);
   RaysIn in{reinterpret_cast<const double *>(b + o_d), reinterpret_cast<const float *>(b + o_a),
             reinterpret_cast<const float *>(b + o_v), reinterpret_cast<const float *>(b + o_az),
@@ -399,13 +399,13 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
       cudaMemcpyAsync(span_labels, dlab, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDeviceToHost, s);
   }
   cudaEventRecord(ev[3], s);
-  uint32_t st = 0;
-  cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
+  uint32_t st[2] = {0, 0};  // status bits, route mask
+  cudaMemcpyAsync(st, status, 8, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);
   const bool launch_ok = cudaGetLastError() == cudaSuccess;
   if (e != cudaSuccess || !launch_ok) return finish(SIM_E_CUDA);
-  if (st & (kStatusBadRay | kStatusModelRange)) return finish(SIM_E_INVALID);
-  if (st) return finish(SIM_E_DEVICE);
+  if (st[0] & (kStatusBadRay | kStatusModelRange)) return finish(SIM_E_INVALID);
+  if (st[0]) return finish(SIM_E_DEVICE);
   // stage times as sim_last_stage_ms reports them: prep (with the span sizes), the spans'
   // packing, ray sums and FFTs together (they overlap on the lanes), labels, and the whole
   // call on the device's clock (with the read-back of the span sizes)
@@ -415,6 +415,6 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     return ms;
   };
   float ms[7] = {0, el(0, 1), el(1, 2), 0, 0, el(2, 3), el(0, 3)};
-  record_stage_ms(ctx, ms, kernels);
+  record_stage_ms(ctx, ms, kernels, st[1]);
   return finish(SIM_OK);
 }

@@ -187,11 +187,10 @@ __global__ void __launch_bounds__(128) direct_sum_kernel(RaysPrep p, int64_t n_r
   }
 }
 
-// gate (may be null) holding 4 or 8: a tensor-core expansion computed the chunk instead
+// gate (may be null) holding a term count: a tensor-core expansion computed the chunk instead
 __device__ __forceinline__ bool gated_off(const uint32_t *gate) {
   if (!gate) return false;
-  const uint32_t v = *gate;
-  return v == 4u || v == 8u;
+  return expansion_terms(*gate);
 }
 
 // sig += parts[0] + parts[1] + ... in part order

@@ -513,11 +513,12 @@ int upload_tables(sim_ctx *c) {
 int rs::derive_radar(const sim_radar_params *p, Derived *g) { return derive(p, g); }
 
 namespace rs {
-void record_stage_ms(sim_ctx *c, const float *ms, int kernels) {
+void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route) {
   Engine &e = engine();
   std::lock_guard<std::mutex> lk(e.mu);
   for (int i = 0; i < kNumEvents; ++i) c->last_ms[i] = ms[i];
   c->last_kernels = kernels;
+  c->last_route = route;
 }
 }  // namespace rs
 
@@ -762,7 +763,7 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
   cudaStream_t s = e.egress[ticket % e.egress.size()];
   lk.unlock();
 
-  uint32_t status = 0;
+  uint32_t st[2] = {0, 0};  // status bits, route mask
   cudaError_t sync_rc = j->device_error;
   if (j->launch_error == SIM_OK && j->block) {
     const Derived &g = c->g;
@@ -770,7 +771,7 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
     if (spectrum) cudaMemcpyAsync(spectrum, j->block + p.spec, 8 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
     if (signal) cudaMemcpyAsync(signal, j->block + p.sig, 8 * static_cast<size_t>(g.n_sig), cudaMemcpyDefault, s);
     if (labels) cudaMemcpyAsync(labels, j->block + p.labels, 4 * static_cast<size_t>(g.n_cell), cudaMemcpyDefault, s);
-    cudaMemcpyAsync(&status, j->block + p.status, 4, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(st, j->block + p.status, 8, cudaMemcpyDeviceToHost, s);
     const cudaError_t cr = cudaStreamSynchronize(s);
     if (sync_rc == cudaSuccess) sync_rc = cr;
   }
@@ -779,6 +780,7 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
     std::lock_guard<std::mutex> g2(e.mu);
     for (int i = 0; i < kNumEvents; ++i) c->last_ms[i] = j->ms[i];
     c->last_kernels = j->kernels;
+    c->last_route = st[0] == 0 && sync_rc == cudaSuccess ? st[1] : 0u;
     e.used -= static_cast<int64_t>(j->plan.total);
     c->live--;
     e.cv.notify_all();
@@ -787,8 +789,8 @@ int sim_fetch(sim_ctx *c, uint64_t ticket, void *spectrum, void *signal, int32_t
   delete j;
   if (launch_error != SIM_OK) return launch_error;
   if (sync_rc != cudaSuccess) return SIM_E_CUDA;
-  if (status & (kStatusBadRay | kStatusModelRange)) return SIM_E_INVALID;
-  if (status) return SIM_E_DEVICE;
+  if (st[0] & (kStatusBadRay | kStatusModelRange)) return SIM_E_INVALID;
+  if (st[0]) return SIM_E_DEVICE;
   return SIM_OK;
 }
 
@@ -840,6 +842,14 @@ int sim_last_kernel_count(sim_ctx *c, int32_t *count) {
   Engine &e = engine();
   std::lock_guard<std::mutex> lk(e.mu);
   *count = c->last_kernels;
+  return SIM_OK;
+}
+
+int sim_last_expansion_terms(sim_ctx *c, uint32_t *mask) {
+  if (!c || !mask) return SIM_E_INVALID;
+  Engine &e = engine();
+  std::lock_guard<std::mutex> lk(e.mu);
+  *mask = c->last_route;
   return SIM_OK;
 }
 

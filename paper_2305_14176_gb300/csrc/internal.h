@@ -13,7 +13,9 @@ namespace rs {
 
 constexpr double kC = 299792458.0;  // speed of light, m/s
 
-// device status word bits (written by kernels with atomicOr, read at fetch)
+// device status word bits (written by kernels with atomicOr, read at fetch).  A scene's status
+// block is 256 bytes: word 0 holds these bits, word 1 the route mask of the expansion's term
+// chooser (bit P for a P-term chunk, bit 0 for one handed to the per-chirp or pair-sum form).
 enum : uint32_t {
   kStatusBadRay = 1u,        // a ray failed validation in the prep kernel
   kStatusHashFull = 2u,      // a label hash probe ran past its limit
@@ -23,6 +25,11 @@ enum : uint32_t {
   kStatusModelRange = 32u,   // exact model with TDM slots on tensor cores: the range migration is
                              // beyond the per-tile expansion's bound (reported as invalid rays)
 };
+
+// Term counts P the per-tile expansion (umma_taylor.cu) is built for.  Its term chooser writes
+// one of them, or 0 when none meets the bound; the per-chirp and pair-sum kernels then own the
+// scene, and each kernel of either route returns at once when the other one owns it.
+__host__ __device__ inline bool expansion_terms(uint32_t p) { return p == 4u || p == 6u || p == 8u; }
 
 // Radar constants derived on the host in FP64 from sim_radar_params.
 struct Derived {
@@ -97,8 +104,9 @@ int launch_ingest(const IngestArgs &x, int64_t n, cudaStream_t s);
 // lets the rays go in parts that fill the SMs
 int64_t direct_workspace_bytes(const Derived &g, int64_t n);
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, cudaStream_t s);
-// store a synchronous call's stage times (7 entries, the sim_last_stage_ms order) and kernel count
-void record_stage_ms(sim_ctx *c, const float *ms, int kernels);
+// store a synchronous call's stage times (7 entries, the sim_last_stage_ms order), kernel count
+// and route mask (status word 1)
+void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route);
 // direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase
 // words (base, per-sample step): w_tx[(m N_tx + t) stride + i], w_rx[(m N_rx + r) stride + i]
 // `workspace` (may be null: one ray part) of pair_workspace_bytes(g, n) lets the rays go in
@@ -249,6 +257,7 @@ struct sim_ctx {
   size_t table_bytes = 0;
   float last_ms[8] = {};
   int last_kernels = 0;
+  uint32_t last_route = 0;    // route mask of the last fetched scene (sim_last_expansion_terms)
   std::atomic<int> live{0};   // tickets not yet fetched
   rs::ScratchSlot scratch[rs::kSlots];
 };

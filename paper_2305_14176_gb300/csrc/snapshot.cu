@@ -402,6 +402,7 @@ struct SnapRun {
   size_t o_base0 = 0, o_q0 = 0, o_vff = 0, o_status = 0, o_wt = 0, o_wr = 0, o_sig = 0, o_tmp = 0, o_spec = 0, o_lab = 0, o_paths = 0;
   size_t o_pk = 0, o_pe = 0, o_ck = 0, o_cm = 0, o_co = 0, o_pw = 0, o_tw = 0, o_rec = 0;
   int64_t cap = 0;
+  uint32_t route = 0;  // the route mask read back by snap_finish
   ScratchLease lease;  // b: the context's snapshot scratch (kept between calls) or this call's own
   ~SnapRun() {
     if (s) {
@@ -536,7 +537,7 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   offsets(rxp, geom->ref_rx, erx);
   cudaMemcpyAsync(b + o_tx, etx.data(), 4 * etx.size(), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(b + o_rx, erx.data(), 4 * erx.size(), cudaMemcpyHostToDevice, s);
-  cudaMemsetAsync(b + R.o_status, 0, 4, s);
+  cudaMemsetAsync(b + R.o_status, 0, 8, s);  // status bits and route mask
   GeomDev &gd = R.gd;
   gd.vert = reinterpret_cast<const double *>(b + o_vert);
   gd.vff = reinterpret_cast<const float2 *>(b + R.o_vff);
@@ -588,12 +589,13 @@ PhaseConst phase_const(const Derived &g) {
 }
 
 int snap_finish(SnapRun &R) {
-  uint32_t st = 0;
-  cudaMemcpyAsync(&st, R.b + R.o_status, 4, cudaMemcpyDeviceToHost, R.s);
+  uint32_t st[2] = {0, 0};  // status bits, route mask
+  cudaMemcpyAsync(st, R.b + R.o_status, 8, cudaMemcpyDeviceToHost, R.s);
   const cudaError_t e = cudaStreamSynchronize(R.s);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
-  if (st & (kStatusBadRay | kStatusBadGeometry)) return SIM_E_INVALID;
-  return st ? SIM_E_DEVICE : SIM_OK;
+  if (st[0] & (kStatusBadRay | kStatusBadGeometry)) return SIM_E_INVALID;
+  R.route = st[1];
+  return st[0] ? SIM_E_DEVICE : SIM_OK;
 }
 
 }  // namespace
@@ -708,7 +710,7 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
     ms[4] = span(prev, prev + 1);
     ms[5] = span(prev + 1, prev + 2);
     ms[6] = span(0, prev + 2);
-    record_stage_ms(ctx, ms, kernels);
+    record_stage_ms(ctx, ms, kernels, R.route);
   }
   for (auto &e : ev) cudaEventDestroy(e);
   return rc;

@@ -49,14 +49,13 @@ struct XArgs {
   float *partials;          // [split][N_v][N_c][N_s] complex64
   const uint32_t *amax_bits;
   uint32_t *status;
-  const uint32_t *gate;     // may be null; when it holds 4 or 8 the expanded kernel owns the scene
+  const uint32_t *gate;     // may be null; when it holds a term count the expanded kernel owns the scene
 };
 
 // the expanded tensor-core kernel (umma_taylor.cu) has taken the scene
 __device__ __forceinline__ bool gated_off(const uint32_t *gate) {
   if (!gate) return false;
-  const uint32_t v = *gate;
-  return v == 4u || v == 8u;
+  return expansion_terms(*gate);
 }
 
 struct XStage {               // per-ray words of one stage

@@ -20,7 +20,7 @@
 // joins the coupling the same way: the shifts take n_c t' eps_t (rows) and n t_c eps_t
 // (columns), and x = 2 pi n' (m' eps + t' eps_t).
 //
-// P is 4 or 8, the smaller one whose bound theta^P / P!, theta = 2 pi n_h (max|eps| m_h +
+// P is 4, 6 or 8, the smallest whose bound theta^P / P!, theta = 2 pi n_h (max|eps| m_h +
 // max|eps_t| t_h), is at most 1e-6 for
 // the hi + lo precisions (1e-5 single pass, whose operand rounding is ~3e-4); a device kernel
 // takes it from the scene's largest |eps|, so no host round trip is needed.  When even P = 8
@@ -30,17 +30,19 @@
 // The per-chirp form has no slot term, so with TDM slots P = 0 is an error instead (a status
 // bit reported as invalid rays).
 //
-// At the hi + lo precisions the terms of order p >= P / 2 (the second 16-slot K step of every
-// stage) are at most theta^(P/2) / (P/2)! of the ray's amplitude, so single-pass operand
-// rounding (<= 2u relative, u = 2^-11 FP16, 2^-8 BF16) adds at most that times 2u; when the
-// device finds this below 2e-6 those terms skip their lo operands and the hi x lo MMAs (8 MMA
-// units per stage instead of 12 at P = 4).
+// At the hi + lo precisions the second 16-slot K step of every stage holds only terms of order
+// p >= P / 2 (at P = 6 term 3 of the stage's first ray falls in the first K step and keeps its
+// lo operands), each at most theta^(P/2) / (P/2)! of the ray's amplitude, so single-pass
+// operand rounding (<= 2u relative, u = 2^-11 FP16, 2^-8 BF16) adds at most that times 2u; when
+// the device finds this below 2e-6 that K step skips its lo operands and the hi x lo MMAs (8
+// MMA units per stage instead of 12).
 //
 // Pipeline, tensor-core issue and drain are those of the separable kernel's two-SM form: CTA
 // pairs (cta_group::2, M = 256), planar K (Re S += A_re B_re - A_im B_im, Im S += A_re B_im +
 // A_im B_re, split precision adds the hi / lo cross terms), FP32 running sum in tensor memory
 // every 512 K slots at split precision, FP32 partials per ray chunk added by a second kernel.
-// A stage holds 32 K slots: 32 / P rays times P terms, slot = p (32 / P) + q.  Every mbarrier
+// A stage holds 32 K slots: RS = floor(32 / P) rays times P terms, slot = p RS + q, and at P = 6
+// two zero slots (5 rays: 0.8 K steps of MMAs per ray against 1.0 at P = 8).  Every mbarrier
 // wait is bounded; a wait that runs out sets a status bit and the CTA drains and returns.
 #include <cuda_runtime.h>
 
@@ -72,7 +74,7 @@ __host__ __device__ constexpr int t_groups() {
 constexpr int TSUBST_SPLIT = 16;
 constexpr int TSUBST_SPLIT_LOW = 24;
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
-constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4
+constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4 (5 at P = 6, 4 at P = 8)
 constexpr int kMaxDynSmemT = 232448 - 8192;
 // workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64), whether the
 // high-order K step keeps its lo operands (u32), largest |eps_t| (u64)
@@ -202,6 +204,8 @@ struct ColCtx {
 
 // One stage of operands: A row gt (all 32 slots) and this thread's B column octets, in the
 // no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
+// Slot s = p RS + q holds term p of the stage's ray q; with RS = floor(32 / P) rays per stage the
+// slots from P RS on (two at P = 6) are zero on both sides.
 // kSnap: rays li0 + q, q < valid, of the chunk are present; the rest read as silent.
 template <bool F16, bool SPLIT, int MODE, int P>
 __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
@@ -209,7 +213,7 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
                                                int valid) {
   constexpr bool TDM = MODE == kExactTdm;
   constexpr int RS = TKS / P;   // rays per stage
-  constexpr int TPO = P / 4;    // terms per octet
+  static_assert(RS <= TMAX_RAYS && P * RS <= TKS, "stage slots");
   const uint32_t a_half = TBM * TKS * 2;
   const uint32_t x_half = static_cast<uint32_t>(ncb) * TKS * 2;
   const uint32_t lo = SPLIT ? 2 * a_half + 2 * x_half : 0;
@@ -251,16 +255,15 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
     for (int o = 0; o < 4; ++o) {
       float2 z[OCT];
 #pragma unroll
-      for (int tt = 0; tt < TPO; ++tt) {
-        const int p = o * TPO + tt;
+      for (int e = 0; e < OCT; ++e) {
+        const int sl = o * OCT + e, p = sl / RS, q = sl % RS;  // compile-time after unrolling
+        z[e] = p < P ? t[q] : make_float2(0.f, 0.f);
+        if (q == RS - 1 && p + 1 < P) {
+          const float inv = 1.f / static_cast<float>(p + 1);
 #pragma unroll
-        for (int q = 0; q < RS; ++q) z[tt * RS + q] = t[q];
-        if (p + 1 < P) {
-          const float inv = 1.f / static_cast<float>(p + 1);  // compile-time after unrolling
-#pragma unroll
-          for (int q = 0; q < RS; ++q) {
-            const float f = x[q] * inv;  // t <- t (j x) / (p + 1)
-            t[q] = make_float2(-t[q].y * f, t[q].x * f);
+          for (int r = 0; r < RS; ++r) {
+            const float f = x[r] * inv;  // t <- t (j x) / (p + 1): term p + 1
+            t[r] = make_float2(-t[r].y * f, t[r].x * f);
           }
         }
       }
@@ -290,12 +293,12 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
       if (!((cc.octets >> o) & 1)) continue;
       float2 z[OCT];
 #pragma unroll
-      for (int tt = 0; tt < TPO; ++tt) {
-        float u = 1.f;  // (n' / n_h)^p, p = o TPO + tt (a compile-time count of products)
+      for (int e = 0; e < OCT; ++e) {
+        const int sl = o * OCT + e, p = sl / RS, q = sl % RS;
+        float u = 1.f;  // (n' / n_h)^p (a compile-time count of products)
 #pragma unroll
-        for (int e = 0; e < o * TPO + tt; ++e) u *= cc.u;
-#pragma unroll
-        for (int q = 0; q < RS; ++q) z[tt * RS + q] = make_float2(b[q].x * u, b[q].y * u);
+        for (int k = 0; k < p; ++k) u *= cc.u;
+        z[e] = p < P ? make_float2(b[q].x * u, b[q].y * u) : make_float2(0.f, 0.f);
       }
       const uint32_t off = o * static_cast<uint32_t>(ncb) * 16 + off0;
       if (o < 2 || lo_high) put_octet<F16, SPLIT>(z, x_re + off, x_im + off, x_re + lo + off, x_im + lo + off);
@@ -351,14 +354,20 @@ __device__ __forceinline__ void t_issue_stage(const TIssue &w, uint32_t sb, bool
 
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
-template <bool F16, bool SPLIT, int MODE>
+// PT: the term count this instance is built for (it returns at once for another one), or 0 for
+// every term count behind a branch per stage.  Split precision launches one instance per term
+// count, whose producers then fit their registers without spills (exact model, FP16 hi + lo
+// automotive frame: 13.95 ms against 14.53 with the branch); single pass keeps the branch
+// (5.8 against 6.0 ms).
+template <bool F16, bool SPLIT, int MODE, int PT>
 __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int TGROUPS = t_groups<SPLIT>();
   constexpr int TMMA_WARP = TGROUPS * TGSIZE / 32;
   __shared__ TStage s_rays[TMAX_GROUPS];
   const uint32_t P = *g.terms;
-  if (P != 4u && P != 8u) return;  // the per-chirp kernel owns this scene (both CTAs return)
+  // another instance, or the per-chirp kernel, owns this scene (both CTAs return)
+  if (PT == 0 ? !expansion_terms(P) : P != static_cast<uint32_t>(PT)) return;
   const bool lo_high = !SPLIT || *g.lo_high != 0u;
   constexpr int NST = t_stages<SPLIT>();
   constexpr uint32_t TMEM_COLS = 512;
@@ -472,8 +481,12 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
         break;
       }
       uint8_t *st_base = base + s * stage_bytes;
-      if (P == 4u)
+      if constexpr (PT != 0)
+        produce_taylor<F16, SPLIT, MODE, PT>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+      else if (P == 4u)
         produce_taylor<F16, SPLIT, MODE, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+      else if (P == 6u)
+        produce_taylor<F16, SPLIT, MODE, 6>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       else
         produce_taylor<F16, SPLIT, MODE, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       fence_proxy_async();  // this thread's stores, visible to the tensor core
@@ -646,8 +659,7 @@ template <bool F16>
 __global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv, int nc, int ns, int bn,
                               float2 *__restrict__ sig, const uint32_t *amax_bits, const uint32_t *terms,
                               int accumulate) {
-  const uint32_t P = *terms;
-  if (P != 4u && P != 8u) return;
+  if (!expansion_terms(*terms)) return;
   const float inv = F16 ? 1.f / amp_scale<true>(amax_bits) : 1.f;
   const int64_t m_rows = static_cast<int64_t>(nv) * nc;
   const int64_t n_q = m_rows * ns / 4;
@@ -718,14 +730,18 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
                              uint32_t *lo_high, double xs_m, double xs_t, double tol, double two_u, double tol_lo,
                              bool tdm, uint32_t *status) {
   const double th = static_cast<double>(*eps_max) * xs_m + static_cast<double>(*eps_t_max) * xs_t;
-  const double t2 = th * th, t4 = t2 * t2;
+  const double t2 = th * th, t3 = t2 * th, t4 = t2 * t2;
   uint32_t P = 0;
   if (t4 / 24.0 <= tol) P = 4;
+  else if (t3 * t3 / 720.0 <= tol) P = 6;
   else if (t4 * t4 / 40320.0 <= tol) P = 8;
   *terms = P;
-  const double high = P == 4 ? t2 / 2.0 : t4 / 24.0;  // largest term of the second K step
+  // bound of term P / 2, the lowest order in the second K step (at P = 6 slot 15, term 3 of the
+  // stage's first ray, sits in the first K step and keeps its lo operands)
+  const double high = P == 4 ? t2 / 2.0 : (P == 6 ? t3 / 6.0 : t4 / 24.0);
   *lo_high = (two_u > 0.0 && high * two_u > tol_lo) ? 1u : 0u;
   if (P == 0 && tdm) atomicOr(status, kStatusModelRange);
+  atomicOr(status + 1, P ? (1u << P) : 1u);  // the route mask read back at fetch
 }
 
 // Virtual snapshots: a bound on the largest |S - S_ref| over the chunk's rays and every row, S
@@ -817,13 +833,13 @@ TShape plan_taylor(const Derived &g, int64_t n) {
 // the expansion needs two-SM tiles of at least 32 complex columns
 bool taylor_eligible(const Derived &g) { return g.ns >= 32; }
 
-template <bool F16, bool SPLIT, int MODE>
-void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
+template <bool F16, bool SPLIT, int MODE, int PT>
+void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
   const size_t smem =
       t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(sh.bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          kMaxDynSmemT);
     attr = true;
   }
@@ -839,13 +855,27 @@ void launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE>, a);
+  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE, PT>, a);
+}
+
+// the instances of one precision and mode; returns the number of launches
+template <bool F16, bool SPLIT, int MODE>
+int launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
+  if constexpr (SPLIT) {
+    launch_taylor_p<F16, SPLIT, MODE, 4>(sh, a, s);
+    launch_taylor_p<F16, SPLIT, MODE, 6>(sh, a, s);
+    launch_taylor_p<F16, SPLIT, MODE, 8>(sh, a, s);
+    return 3;
+  } else {
+    launch_taylor_p<F16, SPLIT, MODE, 0>(sh, a, s);
+    return 1;
+  }
 }
 
 template <int MODE>
-void launch_taylor_mode(bool f16, bool split, const TShape &sh, const TArgs &a, cudaStream_t s) {
-  if (f16) split ? launch_taylor<true, true, MODE>(sh, a, s) : launch_taylor<true, false, MODE>(sh, a, s);
-  else split ? launch_taylor<false, true, MODE>(sh, a, s) : launch_taylor<false, false, MODE>(sh, a, s);
+int launch_taylor_mode(bool f16, bool split, const TShape &sh, const TArgs &a, cudaStream_t s) {
+  if (f16) return split ? launch_taylor<true, true, MODE>(sh, a, s) : launch_taylor<true, false, MODE>(sh, a, s);
+  return split ? launch_taylor<false, true, MODE>(sh, a, s) : launch_taylor<false, false, MODE>(sh, a, s);
 }
 
 }  // namespace
@@ -900,9 +930,7 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.terms = terms;
   a.lo_high = lo_high;
   a.status = status;
-  if (tdm) launch_taylor_mode<kExactTdm>(f16, split, sh, a, s);
-  else launch_taylor_mode<kExact>(f16, split, sh, a, s);
-  ++kernels;
+  kernels += tdm ? launch_taylor_mode<kExactTdm>(f16, split, sh, a, s) : launch_taylor_mode<kExact>(f16, split, sh, a, s);
   // the per-chirp kernel, which returns at once unless P = 0 (it has no slot term: not with TDM)
   if (!tdm) kernels += launch_exact_main(g, p, n, workspace, status, s, terms);
   if (after_main) cudaEventRecord(after_main, s);
@@ -975,7 +1003,7 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   a.terms = terms;
   a.lo_high = lo_high;
   a.status = status;
-  launch_taylor_mode<kSnap>(f16, split, sh, a, s);
+  kernels += launch_taylor_mode<kSnap>(f16, split, sh, a, s);
   const int rb = 4 * sms_t();
   if (f16)
     taylor_reduce<true><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms,
@@ -983,7 +1011,7 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   else
     taylor_reduce<false><<<rb, 256, 0, s>>>(a.partials, sh.splits, g.nv, g.nc, g.ns, sh.bn, sig, amax, terms,
                                             accumulate ? 1 : 0);
-  kernels += 2;
+  ++kernels;
   // the direct pair sum, which returns at once unless P = 0
   kernels += launch_pair_sum(g, w_tx, w_rx, amp, cnt, stride, accumulate, sig, pair_ws, terms, s);
   return kernels;

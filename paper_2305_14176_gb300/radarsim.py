@@ -101,6 +101,7 @@ def _load() -> ctypes.CDLL:
     lib.sim_engine_configure.argtypes = [I64, I32, I32]
     lib.sim_last_stage_ms.argtypes = [P, ctypes.POINTER(ctypes.c_float), I32]
     lib.sim_last_kernel_count.argtypes = [P, ctypes.POINTER(ctypes.c_int32)]
+    lib.sim_last_expansion_terms.argtypes = [P, ctypes.POINTER(ctypes.c_uint32)]
     lib.sim_selftest_umma.argtypes = [I32, I32, I32, I64, P, P, P, P]
     lib.sim_selftest_umma_pair.argtypes = [I32, I32, I64, P, P, P, P]
     lib.sim_selftest_wait.argtypes = [I32, ctypes.POINTER(ctypes.c_int32), P]
@@ -121,7 +122,8 @@ def _load() -> ctypes.CDLL:
     for f in ("sim_autotune", "sim_tuning_save", "sim_tuning_load", "sim_tuning_clear", "sim_tuning_count"):
         getattr(lib, f).restype = ctypes.c_int
     for f in ("sim_create", "sim_submit", "sim_fetch", "sim_destroy", "sim_engine_configure",
-              "sim_last_stage_ms", "sim_last_kernel_count", "sim_selftest_umma", "sim_raysum_noalloc"):
+              "sim_last_stage_ms", "sim_last_kernel_count", "sim_last_expansion_terms", "sim_selftest_umma",
+              "sim_raysum_noalloc"):
         getattr(lib, f).restype = ctypes.c_int
     return lib
 
@@ -317,6 +319,17 @@ def sim_last_kernel_count(ctx) -> int:
     if rc != SIM_OK:
         raise SimError(rc, "sim_last_kernel_count")
     return int(c.value)
+
+
+def sim_last_expansion_terms(ctx) -> set:
+    """The route mask of sim_last_expansion_terms as a set: the term counts P (4, 6, 8) the
+    last scene's chunks expanded with, and 0 for a chunk that took the per-chirp or pair-sum
+    form; empty when no ray sum chose a term count."""
+    m = ctypes.c_uint32()
+    rc = lib.sim_last_expansion_terms(ctx, ctypes.byref(m))
+    if rc != SIM_OK:
+        raise SimError(rc, "sim_last_expansion_terms")
+    return {b for b in range(32) if (m.value >> b) & 1}
 
 
 # ------------------------------------------------------------------ marshalling helpers

@@ -338,7 +338,7 @@ def test_tdm_slot_offsets(precision, shape):
 @pytest.mark.parametrize("shape", [(64, 32, 3, 4, 16, 30.0), (128, 64, 4, 2, 8, 30.0), (64, 32, 3, 4, 16, 5.0)])
 def test_tdm_exact_model(precision, shape):
     """Exact Eq. 2 with TDM slot offsets on every path: on tensor cores the slot term n t eps_t
-    joins the per-tile expansion (transmitters about their centre); eight terms at 30 m/s, four
+    joins the per-tile expansion (transmitters about their centre); six terms at 30 m/s, four
     at 5 m/s."""
     ns, nc, ntx, nrx, na, v_max = shape
     radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na,
@@ -348,9 +348,12 @@ def test_tdm_exact_model(precision, shape):
     ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
     try:
         rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
+        route = rs.sim_last_expansion_terms(ctx.ctx)
     finally:
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    # the FP32 direct sum chooses no term count
+    assert route == (set() if precision == rs.SIM_PREC_FP32_DIRECT else {6 if v_max == 30.0 else 4})
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
     assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
@@ -417,9 +420,10 @@ def test_exact_model_tensor_core(precision):
 @pytest.mark.parametrize("case", ["narrow_tile", "beyond_expansion", "short_chirp"])
 def test_exact_model_tensor_core_regimes(precision, case):
     """The exact model's per-tile expansion of the range-migration phase in its edge regimes:
-    the narrowest two-SM tile (32 samples, 16 columns of B per CTA, 43 chirps per tile: eight
+    the narrowest two-SM tile (32 samples, 16 columns of B per CTA, 43 chirps per tile: six
     terms); a velocity whose migration phase no eight-term expansion bounds (the device hands
-    the scene to the per-chirp kernel); and 16 samples (per-chirp kernel chosen on the host)."""
+    the scene to the per-chirp kernel); and 16 samples (per-chirp kernel chosen on the host,
+    no term choice)."""
     ns, nc, ntx, nrx, na, v_max = {"narrow_tile": (32, 16, 1, 3, 4, 15.0),
                                    "beyond_expansion": (64, 32, 1, 4, 16, 2000.0),
                                    "short_chirp": (16, 32, 2, 2, 4, 15.0)}[case]
@@ -429,9 +433,11 @@ def test_exact_model_tensor_core_regimes(precision, case):
     ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
     try:
         rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
+        route = rs.sim_last_expansion_terms(ctx.ctx)
     finally:
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    assert route == {"narrow_tile": {6}, "beyond_expansion": {0}, "short_chirp": set()}[case]
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
     assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
@@ -445,7 +451,7 @@ def test_exact_model_tensor_core_regimes(precision, case):
 def test_exact_model_tensor_core_size_extremes(precision, shape):
     """The expansion at the edges of the radar sizes: 4096 samples (16 column tiles of 256),
     two chirps with one channel (the tile's rows are mostly past M), and 512 chirps of four
-    channels (64 chirps per 256-row tile, eight terms)."""
+    channels (64 chirps per 256-row tile, six terms)."""
     ns, nc, ntx, nrx, na = shape
     radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na, model=1)
     rays = scenegen.uniform_rays(seed=ns + nc, n=150, n_objects=3, v_max=15.0)
@@ -457,6 +463,32 @@ def test_exact_model_tensor_core_size_extremes(precision, shape):
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     assert rel_max(sig, ref) <= TOL[precision] and rel_rms(sig, ref) <= TOL_RMS[precision]
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
+@pytest.mark.parametrize("precision", prec_params(rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16,
+                                                   rs.SIM_PREC_FP16))
+@pytest.mark.parametrize("v_max,terms", [(3.0, 4), (15.0, 6), (35.0, 8), (2000.0, 0)])
+def test_exact_model_each_term_count(precision, v_max, terms):
+    """Every route of the exact model's term choice (Sec. II-A, Eq. 2): the velocity sets the
+    expansion variable theta = 2 pi n_h max|eps| m_h (0.042, 0.21, 0.49, 28 on this radar of
+    64 samples and 4 channels), so the device picks four, six (five rays and two zero K slots
+    per stage) or eight terms, or hands the scene to the per-chirp kernel (0).  At six terms
+    FP16 hi + lo runs the second K step single pass and BF16 hi + lo keeps its lo operands."""
+    radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=32, n_tx=1, n_rx=4, n_angle=16, model=1)
+    rays = scenegen.uniform_rays(seed=90 + int(v_max) % 97, n=517, n_objects=4, v_max=v_max)
+    ref = oracle.signal(radar, rays)
+    ctx = rs.Context(radar, precision=precision, model=rs.SIM_MODEL_EXACT)
+    try:
+        rc, sig, spec, lab = run(radar, rays, precision, ctx=ctx)
+        route = rs.sim_last_expansion_terms(ctx.ctx)
+    finally:
+        ctx.close()
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    assert route == {terms}
+    tol, trms = TOL[precision], TOL_RMS[precision]
+    assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
     assert np.array_equal(lab, oracle.labels(radar, rays))
 
 

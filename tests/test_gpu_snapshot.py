@@ -24,7 +24,9 @@ def _arrays(rays, hits, geom, device):
     return a
 
 
-def snapshot(radar, rays, hits, geom, device=True, paths=False, outputs=None, precision=rs.SIM_PREC_FP32_DIRECT):
+def snapshot(radar, rays, hits, geom, device=True, paths=False, outputs=None, precision=rs.SIM_PREC_FP32_DIRECT,
+             routes=None):
+    """routes (a list, optional) receives the call's expansion route (sim_last_expansion_terms)."""
     outputs = outputs or (rs.SIM_OUT_SIGNAL | rs.SIM_OUT_SPECTRUM | rs.SIM_OUT_LABELS)
     ctx = rs.Context(radar, precision=precision, outputs=outputs)
     try:
@@ -42,6 +44,8 @@ def snapshot(radar, rays, hits, geom, device=True, paths=False, outputs=None, pr
         lab = torch.zeros(ctx.cube_shape, dtype=torch.int32, device="cuda")
         rc = rs.sim_snapshot_run(ctx.ctx, r, m, h, g, spec, sig, lab)
         torch.cuda.synchronize()
+        if routes is not None:
+            routes.append(rs.sim_last_expansion_terms(ctx.ctx))
         return rc, to_c(sig), to_c(spec), lab.cpu().numpy()
     finally:
         ctx.close()
@@ -87,12 +91,17 @@ PRECISIONS = prec_params(rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT, rs.SIM
 @pytest.mark.parametrize("shape", [(32, 16, 3, 4, 16), (64, 8, 1, 4, 16), (16, 4, 2, 3, 8), (128, 64, 2, 2, 4)])
 def test_signal_spectrum_labels_match_oracle(shape, precision):
     """Every precision: FP32 sums directly; the tensor-core precisions expand each tile about
-    its centre with each row's own phase words (N_s = 16 is summed directly at any precision)."""
+    its centre with each row's own phase words (N_s = 16 is summed directly at any precision).
+    The scenes' largest 2 pi n_h |S - S_ref| (0.25, 0.14, -, 0.54) take six, six, no and eight
+    expansion terms."""
     ns, nc, ntx, nrx, na = shape
     radar = scenegen.Radar(77e9, 1e9, 51.2e-6, 60e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na)
     rays, hits, geom = scenegen.moving_scene(ns + nc, radar, 333, n_objects=5, bounce_frac=0.3)
-    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision)
+    routes = []
+    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision, routes=routes)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    terms = {32: {6}, 64: {6}, 16: set(), 128: {8}}[ns]
+    assert routes == [set() if precision == rs.SIM_PREC_FP32_DIRECT else terms]
     ref = oracle.signal_geom(radar, rays, hits, geom)
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
@@ -109,8 +118,13 @@ def test_automotive_size_in_two_chunks_sampled(precision):
     second chunk adds to the first, on tensor cores too)."""
     radar = scenegen.radar_automotive()
     rays, hits, geom = scenegen.moving_scene(1234, radar, 45_000, n_objects=20)
-    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision)
+    routes = []
+    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision, routes=routes)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    if precision == rs.SIM_PREC_FP32_DIRECT:
+        assert routes == [set()]
+    else:  # each chunk picks its own term count; these road-speed boxes need at most six
+        assert routes[0] and routes[0] <= {4, 6}
     idx = scenegen.randint(1234, 9, 384, 0, sig.size - 1).astype(np.int64)
     ref = oracle.signal_geom_at(radar, rays, hits, geom, idx)
     assert rel_max(sig.reshape(-1)[idx], ref) <= 1e-5
