@@ -404,8 +404,8 @@ SIM_API int sim_selftest_umma_pair(int32_t f16, int32_t n, int64_t k, const void
    exact-model scene whose splits do not fit beside its per-ray data.  Beyond a limit,
    with pointers that are not device memory of the current device, or in those cases it
    returns SIM_E_INVALID before launching anything.
-   The first call on each device looks up the array's device address (set-up); make
-   that first call before any stream capture.  Every call on a device shares the one
+   The first call on each device also looks up the array's device address (set-up).
+   Every call on a device shares the one
    array and finds the previous call's contents in it (the call clears what must start
    at zero), so calls whose work overlaps on the GPU, from several streams or host
    threads, race: serialise them.
