@@ -219,6 +219,7 @@ extern "C" SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_
                                      void *const *spectra, void *const *signals, int32_t *const *labels,
                                      float *device_ms, int32_t *kernel_count) {
   if (n < 1 || n > 4096 || !ctxs || !rays) return SIM_E_INVALID;
+  launches_begin();
   for (int i = 0; i < n; ++i) {
     const sim_ctx *c = ctxs[i];
     if (!c) return SIM_E_INVALID;
@@ -310,7 +311,7 @@ extern "C" SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_
     cudaEventElapsedTime(device_ms, g_ev0, g_ev1);
   }
   if (kernel_count) *kernel_count = plan->kernels;
-  if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (!launches_ok()) return SIM_E_CUDA;
   uint32_t any = 0;
   for (uint32_t v : status) any |= v;
   if (any & kStatusBadRay) return SIM_E_INVALID;

@@ -181,6 +181,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
                                      const sim_span_rule *rules, void *const *span_spectra, int32_t *span_labels,
                                      float threshold) {
   if (!ctx || !rays || !rules || n_spans < 1 || n_spans > 64) return SIM_E_INVALID;
+  launches_begin();
   if (!(threshold >= 0.f && threshold <= 1.f)) return SIM_E_INVALID;
   const Derived &g = ctx->g;
   const int64_t n = rays->n;
@@ -402,7 +403,7 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
   uint32_t st[2] = {0, 0};  // status bits, route mask
   cudaMemcpyAsync(st, status, 8, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);
-  const bool launch_ok = cudaGetLastError() == cudaSuccess;
+  const bool launch_ok = launches_ok();
   if (e != cudaSuccess || !launch_ok) return finish(SIM_E_CUDA);
   if (st[0] & (kStatusBadRay | kStatusModelRange)) return finish(SIM_E_INVALID);
   if (st[0]) return finish(SIM_E_DEVICE);

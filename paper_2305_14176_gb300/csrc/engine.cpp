@@ -179,6 +179,7 @@ int start_engine_locked(Engine &e);
 // Launch a scene on its slot: ingest copies, prep, ray sum, FFTs, labels.
 // `src` holds the caller's pointers (or the host copy's).  Returns a SIM status.
 int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
+  launches_begin();
   Slot &sl = e.slots[j->slot];
   cudaStream_t s = sl.stream;
   const Derived &g = j->ctx->g;
@@ -257,7 +258,7 @@ int launch_job(Engine &e, Job *j, const sim_rays &src, const int32_t *src_obj) {
   if (labels) cudaStreamWaitEvent(s, sl.lab[1], 0);  // join: the scene ends when its labels do
   cudaEventRecord(sl.ev[6], s);
   j->kernels = kernels;
-  if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (!launches_ok()) return SIM_E_CUDA;
   return SIM_OK;
 }
 
@@ -513,6 +514,19 @@ int upload_tables(sim_ctx *c) {
 int rs::derive_radar(const sim_radar_params *p, Derived *g) { return derive(p, g); }
 
 namespace rs {
+namespace {
+thread_local cudaError_t t_launch_error = cudaSuccess;
+}
+void note_launch(cudaError_t e) {
+  if (e != cudaSuccess && t_launch_error == cudaSuccess) t_launch_error = e;
+}
+void launches_begin() { t_launch_error = cudaSuccess; }
+bool launches_ok() {
+  const bool ok = cudaGetLastError() == cudaSuccess && t_launch_error == cudaSuccess;
+  t_launch_error = cudaSuccess;
+  return ok;
+}
+
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route) {
   Engine &e = engine();
   std::lock_guard<std::mutex> lk(e.mu);

@@ -177,9 +177,9 @@ int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp
 int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec,
                     cudaStream_t s, const Tuning &tu) {
   if (!g_attr_done) {
-    cudaFuncSetAttribute(fft_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(fft_doppler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
-    cudaFuncSetAttribute(fft_angle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    note_launch(cudaFuncSetAttribute(fft_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    note_launch(cudaFuncSetAttribute(fft_doppler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
+    note_launch(cudaFuncSetAttribute(fft_angle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     g_attr_done = true;
   }
   // range: rows of N_s, about 2048 points per block

@@ -104,6 +104,14 @@ int launch_ingest(const IngestArgs &x, int64_t n, cudaStream_t s);
 // lets the rays go in parts that fill the SMs
 int64_t direct_workspace_bytes(const Derived &g, int64_t n);
 int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, cudaStream_t s);
+// Launch calls that hand back their error instead of leaving it for cudaGetLastError
+// (cudaLaunchKernelEx, cudaFuncSetAttribute) report it through note_launch.  A call clears the
+// record with launches_begin() before its first launch, and its final check takes
+// launches_ok(), which also reads and clears cudaGetLastError: a launch the runtime refused
+// fails the call instead of leaving its outputs unwritten.  The record is per host thread.
+void note_launch(cudaError_t e);
+void launches_begin();
+bool launches_ok();
 // store a synchronous call's stage times (7 entries, the sim_last_stage_ms order), kernel count
 // and route mask (status word 1)
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route);

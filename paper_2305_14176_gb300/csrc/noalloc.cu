@@ -59,6 +59,7 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   using namespace rs;
   // an error left by an unrelated earlier call must not be reported as this call's
   cudaGetLastError();
+  launches_begin();
   Derived g;
   int rc = derive_radar(params, &g);
   if (rc != SIM_OK) return rc;
@@ -126,7 +127,7 @@ extern "C" SIM_API int sim_raysum_noalloc(const sim_radar_params *params, const 
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return SIM_E_CUDA;
-  if (cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (!launches_ok()) return SIM_E_CUDA;
   if (st & kStatusBadRay) return SIM_E_INVALID;
   return st ? SIM_E_DEVICE : SIM_OK;
 }

@@ -417,6 +417,7 @@ struct SnapRun {
 int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, const sim_hits *hits,
                const sim_geometry *geom, int mode, bool want_spec, bool want_labels, bool paths_on_device) {
   if (!ctx || !rays || !hits || !geom) return SIM_E_INVALID;
+  launches_begin();
   const Derived &g = ctx->g;
   R.g = &g;
   if (g.tslot != 0.0) return SIM_E_INVALID;  // snapshots exist at j T_d only
@@ -592,7 +593,7 @@ int snap_finish(SnapRun &R) {
   uint32_t st[2] = {0, 0};  // status bits, route mask
   cudaMemcpyAsync(st, R.b + R.o_status, 8, cudaMemcpyDeviceToHost, R.s);
   const cudaError_t e = cudaStreamSynchronize(R.s);
-  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (e != cudaSuccess || !launches_ok()) return SIM_E_CUDA;
   if (st[0] & (kStatusBadRay | kStatusBadGeometry)) return SIM_E_INVALID;
   R.route = st[1];
   return st[0] ? SIM_E_DEVICE : SIM_OK;

@@ -104,6 +104,7 @@ using namespace rs;
 
 extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *out) {
   if (!ctx || n_rays < 1 || n_rays > ctx->g.max_rays) return SIM_E_INVALID;
+  launches_begin();
   const Derived &g = ctx->g;
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
   // the table holds separable-model choices; the exact model's tiles are planned on their own
@@ -200,7 +201,7 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   cudaEventDestroy(e1);
   cudaStreamDestroy(s);
   cudaFree(b);
-  if (err != cudaSuccess || cudaGetLastError() != cudaSuccess) return SIM_E_CUDA;
+  if (err != cudaSuccess || !launches_ok()) return SIM_E_CUDA;
   {
     std::lock_guard<std::mutex> lk(g_tmu);
     g_table[key_of(g, n_rays)] = best;

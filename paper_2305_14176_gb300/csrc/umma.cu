@@ -978,8 +978,9 @@ template <bool F16, bool SPLIT, bool TEST, bool FAST, bool PAIR>
 void set_smem_attr() {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, SPLIT || !PAIR ? 256 : 512, PAIR)));
+    note_launch(cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, SPLIT || !PAIR ? 256 : 512, PAIR))));
     attr = true;
   }
 }
@@ -1014,7 +1015,7 @@ void launch_gemm(const Shape &sh, const Args &a, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, L);
+    note_launch(cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>, L));
   } else {
     umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR><<<ctas, NTHREADS_ALL, sm, s>>>(L);
   }
@@ -1293,7 +1294,7 @@ void launch_persistent(const Launch &L, size_t sm, cudaStream_t s) {
     at[0].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, false, FAST, true>, L);
+    note_launch(cudaLaunchKernelEx(&cfg, umma_sum_kernel<F16, SPLIT, false, FAST, true>, L));
   } else {
     umma_sum_kernel<F16, SPLIT, false, FAST, false><<<std::min(L.n_units, num_sms()), NTHREADS_ALL, sm, s>>>(L);
   }

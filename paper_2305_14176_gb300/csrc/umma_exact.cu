@@ -462,7 +462,8 @@ int launch_exact_main(const Derived &g, RaysPrep p, int64_t n, void *workspace, 
   const unsigned grid = static_cast<unsigned>(static_cast<int64_t>(g.nc) * sh.mtiles * sh.ktiles * sh.splits);
 #define RS_EXACT(F, SP)                                                                                      \
   do {                                                                                                       \
-    cudaFuncSetAttribute(exact_sum_kernel<F, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDynSmemX); \
+    note_launch(cudaFuncSetAttribute(exact_sum_kernel<F, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                     kMaxDynSmemX));                                                       \
     exact_sum_kernel<F, SP><<<grid, XTHREADS, smem, s>>>(a);                                                 \
   } while (0)
   if (f16) {

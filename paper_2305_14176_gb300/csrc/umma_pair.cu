@@ -198,15 +198,16 @@ extern "C" SIM_API int sim_selftest_umma_pair(int32_t f16, int32_t n, int64_t k,
   if (cudaMalloc(&status, 4) != cudaSuccess) return SIM_E_NOMEM;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaMemsetAsync(status, 0, 4, s);
+  rs::launches_begin();
   const size_t smem = static_cast<size_t>(128 * PK * 2 + (n / 2) * PK * 2);
-  cudaFuncSetAttribute(pair_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  rs::note_launch(cudaFuncSetAttribute(pair_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   pair_tile_kernel<<<2, PT, smem, s>>>(static_cast<const uint16_t *>(a), static_cast<const uint16_t *>(b), d, n, k,
                                        f16, status);
-  const cudaError_t le = cudaGetLastError();
+  const bool launched = rs::launches_ok();
   uint32_t st = 0;
   cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s);
   const cudaError_t e = cudaStreamSynchronize(s);
   cudaFree(status);
-  if (le != cudaSuccess || e != cudaSuccess) return SIM_E_CUDA;
+  if (!launched || e != cudaSuccess) return SIM_E_CUDA;
   return st ? SIM_E_DEVICE : SIM_OK;
 }

@@ -75,7 +75,6 @@ constexpr int TSUBST_SPLIT = 16;
 constexpr int TSUBST_SPLIT_LOW = 24;
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4 (5 at P = 6, 4 at P = 8)
-constexpr int kMaxDynSmemT = 232448 - 8192;
 // workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64), whether the
 // high-order K step keeps its lo operands (u32), largest |eps_t| (u64)
 constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 24, kHeader = 256;
@@ -833,14 +832,20 @@ TShape plan_taylor(const Derived &g, int64_t n) {
 // the expansion needs two-SM tiles of at least 32 complex columns
 bool taylor_eligible(const Derived &g) { return g.ns >= 32; }
 
+// dynamic shared memory of a launch: the stages of tiles bn columns wide and the barriers
+template <bool SPLIT>
+constexpr size_t t_smem(int bn) {
+  return t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
+}
+
 template <bool F16, bool SPLIT, int MODE, int PT>
 void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
-  const size_t smem =
-      t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(sh.bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
+  const size_t smem = t_smem<SPLIT>(sh.bn);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         kMaxDynSmemT);
+    // the widest tile's need (plan_taylor caps bn at 256 split, 512 single pass)
+    note_launch(cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(t_smem<SPLIT>(SPLIT ? 256 : 512))));
     attr = true;
   }
   cudaLaunchConfig_t cfg{};
@@ -855,7 +860,7 @@ void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE, PT>, a);
+  note_launch(cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE, PT>, a));
 }
 
 // the instances of one precision and mode; returns the number of launches
