@@ -51,6 +51,22 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t a, uint32_t parity, uint6
 __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
   return mbar_wait_for(a, parity, kWaitLimitNs);
 }
+// Named barrier `id` over `count` threads that also ORs `p` across them: every participant gets
+// true when any of them passed true.  A producer group decides together whether to leave its
+// stage loop, so that no thread is left waiting at the group's next named barrier for one that
+// gave up on a pipeline wait.
+__device__ __forceinline__ bool bar_any(int id, int count, bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred pi, po;\n\t"
+      "setp.ne.u32 pi, %1, 0;\n\t"
+      "bar.red.or.pred po, %2, %3, pi;\n\t"
+      "selp.u32 %0, 1, 0, po;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(p)), "r"(id), "r"(count)
+      : "memory");
+  return r != 0u;
+}
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

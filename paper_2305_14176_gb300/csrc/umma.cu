@@ -174,7 +174,6 @@ __device__ __forceinline__ void group_sync(int g) {
 //   exact Q0.64 product, within ~1.5 ulp).
 //   PAIR: this CTA holds B for its half of the tile's complex columns (NC = bn / 4 of them).
 // bytes of the hi A planes (A_re | A_im) of one stage; split precision stores the lo planes next
-template <bool SPLIT>
 __host__ __device__ constexpr uint32_t hi_bytes_a() {
   return 2u * BM * KS * 2;
 }
@@ -276,7 +275,7 @@ __device__ __forceinline__ void produce_planar(const Args &g, const StageRays &s
     // so that one MMA takes A_re against [B_re | B_im] and one takes A_im against [-B_im | B_re]
     if (j < NC) {
       const uint32_t nc16 = static_cast<uint32_t>(NC * 16);
-      uint8_t *xb = stage + 2 * hi_bytes_a<SPLIT>();
+      uint8_t *xb = stage + 2 * hi_bytes_a();
       const uint32_t lo_b = 3 * nc16 * (KS / OCT);  // the lo block follows the hi block
       uint32_t off = o * 3 * nc16 + (j >> 3) * 128 + (j & 7) * 16;
       float2 z[OCT], w[OCT];
@@ -428,7 +427,7 @@ __host__ __device__ constexpr uint32_t stage_size(int bn) {
   // split precision on two-SM tiles (window form): A_re | A_im, hi then lo, then per hi and lo
   // block KS / 8 K chunks of 3 x bn / 4 B rows ([-B_im | B_re | B_im] for this CTA's columns)
   return TEST ? static_cast<uint32_t>(BM * KELEM * 2 + bn * KELEM * 2)
-              : (PAIR && SPLIT ? 2 * hi_bytes_a<SPLIT>() + 2u * (KS / OCT) * 3u * static_cast<uint32_t>(bn / 4) * 16u
+              : (PAIR && SPLIT ? 2 * hi_bytes_a() + 2u * (KS / OCT) * 3u * static_cast<uint32_t>(bn / 4) * 16u
                                : static_cast<uint32_t>(BM * KELEM * 2 + (PAIR ? bn / 2 : bn) * KS * 2) * (SPLIT ? 2u : 1u));
 }
 
@@ -562,9 +561,11 @@ __global__ void __launch_bounds__(NTHREADS_ALL, 1) umma_sum_kernel(Launch L) {
         if constexpr (!TEST) {
           store_ray_words(s_rays[grp], gt, nxt, t0, r0, m0);
           if (st + NGROUP < n_stages) nxt = fetch_ray_words(g, ray0 + NGROUP * KS, k_hi, gt);
-          group_sync(grp);
         }
-        if (gs >= NST && !mbar_wait(empty0 + 8 * s, ((gs / NST) - 1) & 1)) {
+        // the stage slot is free, and the group's ray words are visible; a wait that ran out
+        // in any thread takes the whole group out of the loop
+        const bool slot_ok = gs < NST || mbar_wait(empty0 + 8 * s, ((gs / NST) - 1) & 1);
+        if (bar_any(grp + 1, GSIZE, !slot_ok)) {
           failed = true;
           break;
         }

@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(XTHREADS, 1) exact_sum_kernel(XArgs g) {
       const int s = st % nst;
       xstore(s_rays[grp], gt, nxt);
       if (st + XGROUPS < n_stages) nxt = xfetch(g, k_lo + static_cast<int64_t>(st + XGROUPS) * XK, k_hi, gt, mu);
-      xgroup_sync(grp);
-      if (st >= nst && !mbar_wait(empty0 + 8 * s, ((st / nst) - 1) & 1)) {
+      // the stage slot is free, and the group's ray words are visible; a wait that ran out in
+      // any thread takes the whole group out of the loop
+      const bool slot_ok = st < nst || mbar_wait(empty0 + 8 * s, ((st / nst) - 1) & 1);
+      if (bar_any(grp + 1, XGSIZE, !slot_ok)) {
         failed = true;
         break;
       }

@@ -474,8 +474,10 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
         asm volatile("prefetch.global.L2 [%0];" ::"l"(rc.wr + ray0 + 2 * TGROUPS * RS));
       }
       const int valid = static_cast<int>(k_hi - ray0 < RS ? k_hi - ray0 : RS);
-      tgroup_sync(grp);
-      if (st >= NST && !mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1)) {
+      // the stage slot is free, and the group's ray words are visible; a wait that ran out in
+      // any thread takes the whole group out of the loop
+      const bool slot_ok = st < NST || mbar_wait(empty0 + 8 * s, ((st / NST) - 1) & 1);
+      if (bar_any(grp + 1, TGSIZE, !slot_ok)) {
         failed = true;
         break;
       }
