@@ -354,12 +354,18 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     return q;
   };
   float2 *spectra = reinterpret_cast<float2 *>(b + o_spec);
-  int next = 0;
-  for (int h = 0; h < n_spans; ++h) {
+  // lanes by longest span first, each span to the lane with the fewest rays so far (a span's
+  // bits do not depend on its lane)
+  std::vector<int> order(static_cast<size_t>(n_spans));
+  for (int h = 0; h < n_spans; ++h) order[static_cast<size_t>(h)] = h;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return sizes[x] > sizes[y]; });
+  std::vector<int64_t> lane_rays(static_cast<size_t>(lanes), 0);
+  for (int h : order) {
     const int64_t nh = sizes[h];
     float2 *x = spectra + static_cast<int64_t>(h) * g.n_cell;
     if (nh > 0) {
-      const int l = next++ % lanes;
+      const int l = static_cast<int>(std::min_element(lane_rays.begin(), lane_rays.end()) - lane_rays.begin());
+      lane_rays[static_cast<size_t>(l)] += nh;
       cudaStream_t sl = lane_s[l];
       uint8_t *lb = static_cast<uint8_t *>(ws) + static_cast<size_t>(l) * lane_bytes;
       const RaysPrep q = lane_prep(l);
