@@ -394,9 +394,8 @@ extern "C" SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const s
     power_max_kernel<<<1024, 256, 0, s>>>(spectra, all, pmax);
     int32_t *dlab = nullptr;
     cudaPointerAttributes at;
-    const bool dev_out = cudaPointerGetAttributes(&at, span_labels) == cudaSuccess &&
+    const bool dev_out = handled_call([&] { return cudaPointerGetAttributes(&at, span_labels); }) == cudaSuccess &&
                          (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
     if (dev_out) dlab = span_labels;
     else dlab = reinterpret_cast<int32_t *>(b + o_lab);
     const float t2 = threshold * threshold;

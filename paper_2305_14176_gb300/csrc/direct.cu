@@ -286,13 +286,14 @@ int pair_row_threads(int ns) { return ns <= 64 ? ns : (ns / 32 > 64 ? ns / 32 : 
 namespace {
 template <int NPT>
 int resident_blocks(int threads) {
-  static int per_sm = 0;
-  if (per_sm == 0 &&
-      (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, direct_sum_kernel<NPT>, threads, 0) != cudaSuccess ||
-       per_sm <= 0)) {
-    cudaGetLastError();
-    per_sm = 1;
-  }
+  static const int per_sm = [threads] {
+    int r = 0;
+    return handled_call([&] {
+             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, direct_sum_kernel<NPT>, threads, 0);
+           }) == cudaSuccess && r > 0
+               ? r
+               : 1;
+  }();
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
@@ -356,15 +357,16 @@ int pair_parts(const Derived &g, int64_t n) {
   const int64_t rows = static_cast<int64_t>(g.nv) * g.nc;
   const int threads = pair_row_threads(g.ns);
   int per_sm = 0;
-  switch (g.ns / threads) {  // resident blocks of the instance this shape launches
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<1>, threads, 0); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<2>, threads, 0); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<4>, threads, 0); break;
-    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<8>, threads, 0); break;
-    case 16: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<16>, threads, 0); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<32>, threads, 0); break;
-  }
-  cudaGetLastError();
+  handled_call([&] {
+    switch (g.ns / threads) {  // resident blocks of the instance this shape launches
+      case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<1>, threads, 0);
+      case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<2>, threads, 0);
+      case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<4>, threads, 0);
+      case 8: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<8>, threads, 0);
+      case 16: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<16>, threads, 0);
+      default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_sum_kernel<32>, threads, 0);
+    }
+  });
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;

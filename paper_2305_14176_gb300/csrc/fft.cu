@@ -156,8 +156,6 @@ __global__ void __launch_bounds__(256) fft_angle_kernel(const float2 *__restrict
   }
 }
 
-bool g_attr_done = false;
-
 // the largest power of two <= x, at least 2
 int pow2_floor_min2(int x) {
   int p = 2;
@@ -176,12 +174,12 @@ int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp
 
 int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec,
                     cudaStream_t s, const Tuning &tu) {
-  if (!g_attr_done) {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     note_launch(cudaFuncSetAttribute(fft_range_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     note_launch(cudaFuncSetAttribute(fft_doppler_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
     note_launch(cudaFuncSetAttribute(fft_angle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024));
-    g_attr_done = true;
-  }
+  });
   // range: rows of N_s, about 2048 points per block
   const int64_t rows = static_cast<int64_t>(g.nv) * g.nc;
   int points = tu.fft_range_points > 0 ? tu.fft_range_points : 2048;

@@ -112,6 +112,30 @@ int launch_direct_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void
 void note_launch(cudaError_t e);
 void launches_begin();
 bool launches_ok();
+// Runs a runtime call whose failure is expected and handled (a pointer or occupancy query) in
+// the middle of a pipeline: its own error is cleared, and an earlier launch's error that the
+// thread's last-error slot held is kept in the launch record instead of being lost with it.
+template <class F>
+cudaError_t handled_call(F f) {
+  const cudaError_t prior = cudaGetLastError();
+  const cudaError_t rc = f();
+  if (rc != cudaSuccess) cudaGetLastError();
+  note_launch(prior);
+  return rc;
+}
+// Runs f() once per device for the flag `done` (bit d: done on device d).  Function attributes
+// such as the dynamic shared-memory size belong to a device's context, so each device the
+// process launches on needs its own call; several host threads may arrive at once, and f() may
+// then run more than once, which setting an attribute allows.
+template <class F>
+void once_per_device(std::atomic<uint64_t> &done, F f) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const uint64_t bit = dev >= 0 && dev < 64 ? (1ull << dev) : 0ull;
+  if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return;
+  f();
+  if (bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
+}
 // store a synchronous call's stage times (7 entries, the sim_last_stage_ms order), kernel count
 // and route mask (status word 1)
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route);

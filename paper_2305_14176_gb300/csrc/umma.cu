@@ -864,8 +864,6 @@ __global__ void amax_kernel(const float *__restrict__ amp, int64_t n, uint32_t *
   if ((threadIdx.x & 31) == 0) atomicMax(amax_bits, m);
 }
 
-int g_num_sms = 0;
-
 struct Shape {
   int mt, nt, splits, bn;  // splits: partials per tile (with stream-K the most any tile has)
   int64_t chunk;
@@ -873,13 +871,12 @@ struct Shape {
 };
 
 int num_sms() {
-  if (g_num_sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g_num_sms <= 0)
-      g_num_sms = 148;
-  }
-  return g_num_sms;
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 148;
+  }();
+  return sms;
 }
 
 // Tiles of 128 rows x bn columns; the rays split into `splits` chunks so that the CTAs fill
@@ -977,13 +974,12 @@ constexpr int kMaxDynSmem = 232448 - 8192;  // 227 KB per block, less the kernel
 
 template <bool F16, bool SPLIT, bool TEST, bool FAST, bool PAIR>
 void set_smem_attr() {
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     note_launch(cudaFuncSetAttribute(umma_sum_kernel<F16, SPLIT, TEST, FAST, PAIR>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      TEST ? kMaxDynSmem : static_cast<int>(smem_bytes(SPLIT, SPLIT || !PAIR ? 256 : 512, PAIR))));
-    attr = true;
-  }
+  });
 }
 
 // one scene, one unit per CTA (PAIR: per cluster of two CTAs, units of 256 rows)

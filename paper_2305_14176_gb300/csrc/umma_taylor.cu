@@ -788,12 +788,11 @@ __global__ void snap_stats(SnapRec rec, int64_t stride, const float *__restrict_
 }
 
 int sms_t() {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 148;
-  }
+    return cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0 ? n : 148;
+  }();
   return sms;
 }
 
@@ -846,13 +845,12 @@ constexpr size_t t_smem(int bn) {
 template <bool F16, bool SPLIT, int MODE, int PT>
 void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
   const size_t smem = t_smem<SPLIT>(sh.bn);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> done{0};
+  once_per_device(done, [] {
     // the widest tile's need (plan_taylor caps bn at 256 split, 512 single pass)
     note_launch(cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(t_smem<SPLIT>(SPLIT ? 256 : 512))));
-    attr = true;
-  }
+  });
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(2u * static_cast<unsigned>(sh.mt2 * sh.nt * sh.splits));
   cfg.blockDim = dim3(t_threads<SPLIT, MODE>());
