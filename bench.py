@@ -244,6 +244,15 @@ def cpu_decompose_rate(radar, rays, ids, seconds: float = 10.0, seed: int = 19):
     return rate, per, dt, oracle.threads(), cells, refs
 
 
+def expansion_names(bits):
+    """The route bits of sim_last_expansion_terms by name: 'taylor4', 'chebyshev6', ... and
+    'per-chirp' (or pair sum, for snapshots) for a chunk beyond the expansion's bound."""
+    out = []
+    for b in sorted(bits):
+        out.append("per-chirp" if b == 0 else (f"chebyshev{b - 16}" if b > 16 else f"taylor{b}"))
+    return out
+
+
 def result_error(radar, rays, sig_h, lab_h, idx, ref):
     """The frame's error against the FP64 oracle: normwise max and RMS relative error of the
     signal on the oracle's sampled output points, and whether every label matches."""
@@ -479,7 +488,7 @@ def run_snapshot_workload(args, rs, torch):
             for k, v in rs.sim_last_stage_ms(ctx.ctx).items():
                 stages[k] = stages.get(k, 0.0) + v
             kernels += rs.sim_last_kernel_count(ctx.ctx)
-    terms = sorted(rs.sim_last_expansion_terms(ctx.ctx))
+    terms = expansion_names(rs.sim_last_expansion_terms(ctx.ctx))
     e2e = []
     for s in range(args.warmup + args.steps):
         flush.zero_()
@@ -518,7 +527,7 @@ def run_snapshot_workload(args, rs, torch):
             "config": {"workload": "virtual snapshots: moving boxes, Eq. 6 hit update + Eq. 7 antenna paths, "
                                    "12 virtual ch x 256 chirps x 512 samples",
                        "rays": rays.n, "hits": int(hits.offset[-1]), "triangles": int(geom.triangles.shape[0]),
-                       "precision": args.precision, "expansion_terms": terms,
+                       "precision": args.precision, "expansion": terms,
                        "l2": "flushed (256 MB write) before each step"},
             "stage_ms_mean": {k: v / args.steps for k, v in stages.items()},
             "e2e": {"value": contrib * len(e2e) / sum(e2e), "unit": UNIT,
@@ -855,7 +864,7 @@ def main():
             kernels += rs.sim_last_kernel_count(ctx.ctx)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
-    terms = sorted(rs.sim_last_expansion_terms(ctx.ctx))
+    terms = expansion_names(rs.sim_last_expansion_terms(ctx.ctx))
     # the last timed frame's outputs, for its error against the oracle (outside the timed region)
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     sig_h = sig.cpu().numpy() if want_cpu else None
@@ -959,7 +968,7 @@ def main():
                    "n_samples": radar.n_samples, "n_angle": radar.n_angle, "precision": args.precision,
                    "outputs": "signal+spectrum+labels", "l2": "flushed (256 MB write) before each step",
                    "parallelism": f"replicas x{world}"}
-        | ({"expansion_terms": terms} if args.model == "exact" else {}),
+        | ({"expansion": terms} if args.model == "exact" else {}),
         "frames_per_s": args.steps * world / dev_s_max,
         "stage_ms_mean": {k: v / args.steps for k, v in stages_sum.items()},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

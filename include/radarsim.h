@@ -308,8 +308,9 @@ SIM_API int sim_last_kernel_count(sim_ctx *ctx, int32_t *count);
    range-migration term) or of virtual snapshots (Sec. II-D and II-E, Eq. 6 and 7) took in the
    most recently fetched ticket of this context (or the last sim_snapshot_run or sim_decompose
    on it), as a bit mask over its ray chunks and spans: bit P (P = 4, 6 or 8) when one ran the
-   per-tile Taylor expansion of the coupling phase with P terms; bit 0 when one lay beyond the
-   expansion's bound and ran the per-chirp product (snapshots: the direct pair sum).  0 when no
+   per-tile expansion of the coupling phase with P Taylor terms, bit 16 + P with P Chebyshev
+   (Jacobi-Anger) terms; bit 0 when one lay beyond the expansion's bound and ran the per-chirp
+   product (snapshots: the direct pair sum).  0 when no
    ray sum chose a term count (the separable model, SIM_PREC_FP32_DIRECT, fewer than 32
    samples, no ray) and after a failed sim_fetch; a failed sim_snapshot_run or sim_decompose
    leaves it, like the stage times, as it was.  Errors: SIM_E_INVALID (null pointer). */

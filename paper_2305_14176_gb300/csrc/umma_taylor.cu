@@ -76,8 +76,9 @@ constexpr int TSUBST_SPLIT_LOW = 24;
 constexpr uint32_t TSUM_COL = 256;     // TMEM column of the running sum
 constexpr int TMAX_RAYS = 8;           // rays per stage at P = 4 (5 at P = 6, 4 at P = 8)
 // workspace header: amplitude maximum (u32 bits), P (u32), largest |eps| (u64), whether the
-// high-order K step keeps its lo operands (u32), largest |eps_t| (u64)
-constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 24, kHeader = 256;
+// high-order K step keeps its lo operands (u32), largest |eps_t| (u64), the expansion's form
+// (u32: 0 Taylor, 1 Chebyshev)
+constexpr size_t kOffTerms = 4, kOffEpsMax = 8, kOffLoHigh = 16, kOffEpsTMax = 24, kOffForm = 32, kHeader = 256;
 
 // what the rows and columns are synthesised from
 constexpr int kExact = 0;     // exact Eq. 2: per-ray words of the prep kernel
@@ -114,6 +115,7 @@ struct TArgs {
   const uint32_t *amax_bits;
   const uint32_t *terms;  // P chosen on the device; 0: the per-chirp kernel owns the scene
   const uint32_t *lo_high;  // split precision: 0 when the terms p >= P/2 go single pass
+  const uint32_t *form;     // 0: Taylor terms, 1: Chebyshev (Jacobi-Anger) terms
   uint32_t *status;
 };
 
@@ -201,12 +203,52 @@ struct ColCtx {
   bool active;
 };
 
+// Chebyshev form of the coupling factor (Jacobi-Anger): for real x and t in [-1, 1],
+//   e^{j x t} = J_0(x) + 2 sum_{p>=1} j^p J_p(x) T_p(t),
+// truncated after P terms with remainder at most 2 sum_{p>=P} |J_p(x)| <= 2 (|x|/2)^P / P! /
+// (1 - |x| / (2 (P + 1))), using |J_p(x)| <= (|x|/2)^p / p!.  That is 2^(P-1) times below the
+// Taylor bound, so a given tolerance is met with fewer terms.  Rows take eps_p j^p J_p(x),
+// columns T_p(n' / n_h).  J_p(x) = (x/2)^p / p! S_p(-x^2/4), S_p(w) = sum_k w^k / (k! (p+1)_k),
+// summed to k = K: K = 2, 4, 6 for P = 4, 6, 8 leaves < 5e-8 of the largest J_p at the largest
+// x each P is chosen for (0.21, 0.78, 1.62 at the single-pass tolerance).
+__host__ __device__ constexpr int chebyshev_series_terms(int P) { return P <= 4 ? 2 : (P <= 6 ? 4 : 6); }
+__host__ __device__ constexpr float ja_coef(int p, int k) {
+  double c = 1.0;
+  for (int i = 1; i <= k; ++i) c /= static_cast<double>(i) * static_cast<double>(p + i);
+  return static_cast<float>(c);
+}
+template <int K>
+__device__ __forceinline__ float ja_series(int p, float w) {  // S_p(w) by Horner; p compile-time after unrolling
+  float s = ja_coef(p, K);
+#pragma unroll
+  for (int k = K - 1; k >= 0; --k) s = fmaf(s, w, ja_coef(p, k));
+  return s;
+}
+__device__ __forceinline__ float2 rot_i(float2 v, int p) {  // v j^p
+  switch (p & 3) {
+    case 0: return v;
+    case 1: return make_float2(-v.y, v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    default: return make_float2(v.y, -v.x);
+  }
+}
+__device__ __forceinline__ float chebyshev_t(int p, float u) {  // T_p(u) by the three-term recurrence
+  float t0 = 1.f, t1 = u;
+  if (p == 0) return 1.f;
+  for (int k = 1; k < p; ++k) {
+    const float t2 = 2.f * u * t1 - t0;
+    t0 = t1;
+    t1 = t2;
+  }
+  return t1;
+}
+
 // One stage of operands: A row gt (all 32 slots) and this thread's B column octets, in the
 // no-swizzle K-major core-matrix layout of the separable kernel (octet o = K chunk o).
 // Slot s = p RS + q holds term p of the stage's ray q; with RS = floor(32 / P) rays per stage the
 // slots from P RS on (two at P = 6) are zero on both sides.
 // kSnap: rays li0 + q, q < valid, of the chunk are present; the rest read as silent.
-template <bool F16, bool SPLIT, int MODE, int P>
+template <bool F16, bool SPLIT, int MODE, int P, bool CH>
 __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage, int gt, int ncb, const RowCtx &rc,
                                                const ColCtx &cc, float scale, bool lo_high, int64_t li0,
                                                int valid) {
@@ -220,6 +262,7 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
   {
     float2 t[RS];
     float x[RS];
+    float h[RS];  // CH: eps_p (x / 2)^p / p! of the current term
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
@@ -249,6 +292,10 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
         if constexpr (TDM) x[q] += rc.xt * static_cast<float>(static_cast<int64_t>(sr.epst[q]));
       }
     }
+    if constexpr (CH) {
+#pragma unroll
+      for (int q = 0; q < RS; ++q) h[q] = 1.f;
+    }
     uint32_t off = (gt >> 3) * 128 + (gt & 7) * 16;
 #pragma unroll
     for (int o = 0; o < 4; ++o) {
@@ -256,13 +303,29 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
       for (int e = 0; e < OCT; ++e) {
         const int sl = o * OCT + e, p = sl / RS, q = sl % RS;  // compile-time after unrolling
-        z[e] = p < P ? t[q] : make_float2(0.f, 0.f);
-        if (q == RS - 1 && p + 1 < P) {
-          const float inv = 1.f / static_cast<float>(p + 1);
+        if constexpr (CH) {
+          // t i^p eps_p J_p(x), J_p(x) = (x / 2)^p / p! S_p(-x^2 / 4)
+          if (p < P) {
+            const float c = h[q] * ja_series<chebyshev_series_terms(P)>(p, -0.25f * x[q] * x[q]);
+            const float2 v = rot_i(t[q], p);
+            z[e] = make_float2(v.x * c, v.y * c);
+          } else {
+            z[e] = make_float2(0.f, 0.f);
+          }
+          if (q == RS - 1 && p + 1 < P) {
+            const float f = (p == 0 ? 1.f : 0.5f) / static_cast<float>(p + 1);  // eps_{p+1} / eps_p / 2 / (p + 1)
 #pragma unroll
-          for (int r = 0; r < RS; ++r) {
-            const float f = x[r] * inv;  // t <- t (j x) / (p + 1): term p + 1
-            t[r] = make_float2(-t[r].y * f, t[r].x * f);
+            for (int r = 0; r < RS; ++r) h[r] *= x[r] * f;
+          }
+        } else {
+          z[e] = p < P ? t[q] : make_float2(0.f, 0.f);
+          if (q == RS - 1 && p + 1 < P) {
+            const float inv = 1.f / static_cast<float>(p + 1);
+#pragma unroll
+            for (int r = 0; r < RS; ++r) {
+              const float f = x[r] * inv;  // t <- t (j x) / (p + 1): term p + 1
+              t[r] = make_float2(-t[r].y * f, t[r].x * f);
+            }
           }
         }
       }
@@ -294,9 +357,13 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
       for (int e = 0; e < OCT; ++e) {
         const int sl = o * OCT + e, p = sl / RS, q = sl % RS;
-        float u = 1.f;  // (n' / n_h)^p (a compile-time count of products)
+        float u = 1.f;  // Taylor: (n' / n_h)^p; CH: T_p(n' / n_h) (a compile-time count of steps)
+        if constexpr (CH) {
+          u = chebyshev_t(p, cc.u);
+        } else {
 #pragma unroll
-        for (int k = 0; k < p; ++k) u *= cc.u;
+          for (int k = 0; k < p; ++k) u *= cc.u;
+        }
         z[e] = p < P ? make_float2(b[q].x * u, b[q].y * u) : make_float2(0.f, 0.f);
       }
       const uint32_t off = o * static_cast<uint32_t>(ncb) * 16 + off0;
@@ -353,20 +420,23 @@ __device__ __forceinline__ void t_issue_stage(const TIssue &w, uint32_t sb, bool
 
 // Launched as clusters of two CTAs; cluster u takes unit u = (split, tile_n, tile_m), the even
 // CTA holding rows 0..127 of the 256-row tile and issuing the M = 256 MMAs.
-// PT: the term count this instance is built for (it returns at once for another one), or 0 for
-// every term count behind a branch per stage.  Split precision launches one instance per term
-// count, whose producers then fit their registers without spills (exact model, FP16 hi + lo
-// automotive frame: 13.95 ms against 14.53 with the branch); single pass keeps the branch
-// (5.8 against 6.0 ms).
-template <bool F16, bool SPLIT, int MODE, int PT>
+// PT, CH: the term count and form (Taylor, Chebyshev) this instance is built for (it returns at
+// once for another choice), or PT = 0 for every choice behind a branch per stage.  Split
+// precision launches one instance per choice, whose producers then fit their registers without
+// spills (exact model, FP16 hi + lo automotive frame: 13.95 ms against 14.53 with the branch);
+// single pass keeps the branch (5.8 against 6.0 ms).  The chooser takes Taylor terms only at
+// P = 4 (fewer operations per slot than Chebyshev terms at the same count) and Chebyshev terms
+// wherever they need fewer terms than Taylor's.
+template <bool F16, bool SPLIT, int MODE, int PT, bool CH>
 __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel(TArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int TGROUPS = t_groups<SPLIT>();
   constexpr int TMMA_WARP = TGROUPS * TGSIZE / 32;
   __shared__ TStage s_rays[TMAX_GROUPS];
   const uint32_t P = *g.terms;
+  const bool cheb = *g.form != 0u;
   // another instance, or the per-chirp kernel, owns this scene (both CTAs return)
-  if (PT == 0 ? !expansion_terms(P) : P != static_cast<uint32_t>(PT)) return;
+  if (PT == 0 ? (!expansion_terms(P) || cheb != CH) : (P != static_cast<uint32_t>(PT) || cheb != CH)) return;
   const bool lo_high = !SPLIT || *g.lo_high != 0u;
   constexpr int NST = t_stages<SPLIT>();
   constexpr uint32_t TMEM_COLS = 512;
@@ -486,13 +556,14 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
       }
       uint8_t *st_base = base + s * stage_bytes;
       if constexpr (PT != 0)
-        produce_taylor<F16, SPLIT, MODE, PT>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+        produce_taylor<F16, SPLIT, MODE, (PT != 0 ? PT : 4), CH>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high,
+                                                                 ray0, valid);
       else if (P == 4u)
-        produce_taylor<F16, SPLIT, MODE, 4>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+        produce_taylor<F16, SPLIT, MODE, 4, CH>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       else if (P == 6u)
-        produce_taylor<F16, SPLIT, MODE, 6>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+        produce_taylor<F16, SPLIT, MODE, 6, CH>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       else
-        produce_taylor<F16, SPLIT, MODE, 8>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
+        produce_taylor<F16, SPLIT, MODE, 8, CH>(s_rays[grp], st_base, gt, ncb, rc, cc, scale, lo_high, ray0, valid);
       fence_proxy_async();  // this thread's stores, visible to the tensor core
       if constexpr (ONE_ARRIVE) {
         tgroup_sync(grp);  // the group's stores are done and s_rays[grp] is free again
@@ -730,22 +801,45 @@ __global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__res
 // (xs_m, xs_t: the factors of the two word maxima); at split precision (two_u = twice the unit
 // roundoff) the terms p >= P/2 drop their lo operands when theta^(P/2) / (P/2)! * two_u <= tol_lo.
 // With TDM slots there is no per-chirp fallback: P = 0 raises the model-range status bit.
+// bound of the Chebyshev remainder after P terms at |x| <= th (see chebyshev_series_terms)
+__device__ double chebyshev_bound(double th, int P) {
+  double b = 2.0;
+  for (int p = 1; p <= P; ++p) b *= 0.5 * th / p;
+  const double g = 1.0 - th / (2.0 * (P + 1));
+  return g > 0.0 ? b / g : 1e300;
+}
+// The expansion: Taylor terms when four of them meet tol, else the fewest Chebyshev terms (4, 6,
+// 8) that do, else none (P = 0).  lo_high: whether the second K step, which holds only terms of
+// order >= P/2, keeps its lo operands (its largest term times 2u above tol_lo).
 __global__ void choose_terms(const unsigned long long *eps_max, const unsigned long long *eps_t_max, uint32_t *terms,
-                             uint32_t *lo_high, double xs_m, double xs_t, double tol, double two_u, double tol_lo,
-                             bool tdm, uint32_t *status) {
+                             uint32_t *form, uint32_t *lo_high, double xs_m, double xs_t, double tol, double two_u,
+                             double tol_lo, bool tdm, uint32_t *status) {
   const double th = static_cast<double>(*eps_max) * xs_m + static_cast<double>(*eps_t_max) * xs_t;
-  const double t2 = th * th, t3 = t2 * th, t4 = t2 * t2;
-  uint32_t P = 0;
-  if (t4 / 24.0 <= tol) P = 4;
-  else if (t3 * t3 / 720.0 <= tol) P = 6;
-  else if (t4 * t4 / 40320.0 <= tol) P = 8;
+  const double t2 = th * th, t4 = t2 * t2;
+  uint32_t P = 0, ch = 0;
+  if (t4 / 24.0 <= tol) {
+    P = 4;
+  } else {
+    for (int c = 4; c <= 8 && P == 0; c += 2)
+      if (chebyshev_bound(th, c) <= tol) {
+        P = static_cast<uint32_t>(c);
+        ch = 1;
+      }
+  }
   *terms = P;
-  // bound of term P / 2, the lowest order in the second K step (at P = 6 slot 15, term 3 of the
-  // stage's first ray, sits in the first K step and keeps its lo operands)
-  const double high = P == 4 ? t2 / 2.0 : (P == 6 ? t3 / 6.0 : t4 / 24.0);
+  *form = ch;
+  // largest term of the second K step: Taylor th^2 / 2 at P = 4; Chebyshev 2 (th/2)^(P/2) /
+  // (P/2)! (at P = 6 slot 15, term 3 of the stage's first ray, sits in the first K step and keeps
+  // its lo operands)
+  double high = t2 / 2.0;
+  if (ch) {
+    high = 2.0;
+    for (uint32_t p = 1; p <= P / 2; ++p) high *= 0.5 * th / p;
+  }
   *lo_high = (two_u > 0.0 && high * two_u > tol_lo) ? 1u : 0u;
   if (P == 0 && tdm) atomicOr(status, kStatusModelRange);
-  atomicOr(status + 1, P ? (1u << P) : 1u);  // the route mask read back at fetch
+  // the route mask read back at fetch: bit P (Taylor), bit 16 + P (Chebyshev), bit 0 (none)
+  atomicOr(status + 1, P ? (1u << (P + (ch ? 16u : 0u))) : 1u);
 }
 
 // Virtual snapshots: a bound on the largest |S - S_ref| over the chunk's rays and every row, S
@@ -842,13 +936,13 @@ constexpr size_t t_smem(int bn) {
   return t_stages<SPLIT>() * static_cast<size_t>(t_stage_bytes<SPLIT>(bn)) + 8 * (2 * t_stages<SPLIT>() + 3) + 16;
 }
 
-template <bool F16, bool SPLIT, int MODE, int PT>
+template <bool F16, bool SPLIT, int MODE, int PT, bool CH>
 void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
   const size_t smem = t_smem<SPLIT>(sh.bn);
   static std::atomic<uint64_t> done{0};
   once_per_device(done, [] {
     // the widest tile's need (plan_taylor caps bn at 256 split, 512 single pass)
-    note_launch(cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    note_launch(cudaFuncSetAttribute(taylor_sum_kernel<F16, SPLIT, MODE, PT, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(t_smem<SPLIT>(SPLIT ? 256 : 512))));
   });
   cudaLaunchConfig_t cfg{};
@@ -863,20 +957,22 @@ void launch_taylor_p(const TShape &sh, const TArgs &a, cudaStream_t s) {
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  note_launch(cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE, PT>, a));
+  note_launch(cudaLaunchKernelEx(&cfg, taylor_sum_kernel<F16, SPLIT, MODE, PT, CH>, a));
 }
 
 // the instances of one precision and mode; returns the number of launches
 template <bool F16, bool SPLIT, int MODE>
 int launch_taylor(const TShape &sh, const TArgs &a, cudaStream_t s) {
   if constexpr (SPLIT) {
-    launch_taylor_p<F16, SPLIT, MODE, 4>(sh, a, s);
-    launch_taylor_p<F16, SPLIT, MODE, 6>(sh, a, s);
-    launch_taylor_p<F16, SPLIT, MODE, 8>(sh, a, s);
-    return 3;
+    launch_taylor_p<F16, SPLIT, MODE, 4, false>(sh, a, s);
+    launch_taylor_p<F16, SPLIT, MODE, 4, true>(sh, a, s);
+    launch_taylor_p<F16, SPLIT, MODE, 6, true>(sh, a, s);
+    launch_taylor_p<F16, SPLIT, MODE, 8, true>(sh, a, s);
+    return 4;
   } else {
-    launch_taylor_p<F16, SPLIT, MODE, 0>(sh, a, s);
-    return 1;
+    launch_taylor_p<F16, SPLIT, MODE, 0, false>(sh, a, s);  // Taylor terms
+    launch_taylor_p<F16, SPLIT, MODE, 0, true>(sh, a, s);   // Chebyshev terms
+    return 2;
   }
 }
 
@@ -907,18 +1003,19 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
   unsigned long long *eps_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
   uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
+  uint32_t *form = reinterpret_cast<uint32_t *>(ws + kOffForm);
   unsigned long long *eps_t_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsTMax);
   const bool tdm = g.tslot != 0.0;
   const int t_c = g.ntx / 2, t_h = std::max(t_c, g.ntx - 1 - t_c);  // |t - t_c| <= t_h
   int kernels = 0;
-  cudaMemsetAsync(ws, 0, 32, s);
+  cudaMemsetAsync(ws, 0, 64, s);
   exact_stats<<<2 * sms_t(), 256, 0, s>>>(p.amp, p.eps, p.eps_t, n, f16, amax, eps_max, eps_t_max);
   // theta = 2 pi n_h (max|eps| m_h + max|eps_t| t_h) with eps in cycles (the word times 2^-64)
   const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
   // unit roundoff 2^-11 (FP16), 2^-8 (BF16); single pass has no lo operands to drop
   const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
-  choose_terms<<<1, 1, 0, s>>>(eps_max, eps_t_max, terms, lo_high, xs * sh.mh, xs * t_h, split ? 1e-6 : 1e-5, two_u,
-                               2e-6, tdm, status);
+  choose_terms<<<1, 1, 0, s>>>(eps_max, eps_t_max, terms, form, lo_high, xs * sh.mh, xs * t_h, split ? 1e-6 : 1e-5,
+                               two_u, 2e-6, tdm, status);
   kernels += 2;
   TArgs a{};
   a.p = p;
@@ -937,6 +1034,7 @@ int launch_exact_tensor(const Derived &g, RaysPrep p, int64_t n, float2 *sig, vo
   a.amax_bits = amax;
   a.terms = terms;
   a.lo_high = lo_high;
+  a.form = form;
   a.status = status;
   kernels += tdm ? launch_taylor_mode<kExactTdm>(f16, split, sh, a, s) : launch_taylor_mode<kExact>(f16, split, sh, a, s);
   // the per-chirp kernel, which returns at once unless P = 0 (it has no slot term: not with TDM)
@@ -978,15 +1076,17 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   uint32_t *terms = reinterpret_cast<uint32_t *>(ws + kOffTerms);
   unsigned long long *d_max = reinterpret_cast<unsigned long long *>(ws + kOffEpsMax);
   uint32_t *lo_high = reinterpret_cast<uint32_t *>(ws + kOffLoHigh);
+  uint32_t *form = reinterpret_cast<uint32_t *>(ws + kOffForm);
   unsigned long long *none = reinterpret_cast<unsigned long long *>(ws + kOffEpsTMax);  // stays 0
   const int t_c = snap_ref_tx(g), r_c = snap_ref_rx(g);
   int kernels = 0;
-  cudaMemsetAsync(ws, 0, 32, s);
+  cudaMemsetAsync(ws, 0, 64, s);
   snap_stats<<<4 * sms_t(), 256, 0, s>>>(rec, stride, amp, cnt, g.nc, g.nv, f16, amax, d_max);
   // theta = 2 pi n_h max|delta|, delta in cycles per sample (the word times 2^-64)
   const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
   const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
-  choose_terms<<<1, 1, 0, s>>>(d_max, none, terms, lo_high, xs, 0.0, split ? 1e-6 : 1e-5, two_u, 2e-6, false, status);
+  choose_terms<<<1, 1, 0, s>>>(d_max, none, terms, form, lo_high, xs, 0.0, split ? 1e-6 : 1e-5, two_u, 2e-6, false,
+                               status);
   kernels += 2;
   TArgs a{};
   a.w_tx = w_tx;
@@ -1010,6 +1110,7 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   a.amax_bits = amax;
   a.terms = terms;
   a.lo_high = lo_high;
+  a.form = form;
   a.status = status;
   kernels += launch_taylor_mode<kSnap>(f16, split, sh, a, s);
   const int rb = 4 * sms_t();

@@ -322,9 +322,9 @@ def sim_last_kernel_count(ctx) -> int:
 
 
 def sim_last_expansion_terms(ctx) -> set:
-    """The route mask of sim_last_expansion_terms as a set: the term counts P (4, 6, 8) the
-    last scene's chunks expanded with, and 0 for a chunk that took the per-chirp or pair-sum
-    form; empty when no ray sum chose a term count."""
+    """The route mask of sim_last_expansion_terms as a set of its bits: P for a chunk expanded
+    with P Taylor terms, 16 + P with P Chebyshev terms (P = 4, 6, 8), 0 for a chunk that took
+    the per-chirp or pair-sum form; empty when no ray sum chose an expansion."""
     m = ctypes.c_uint32()
     rc = lib.sim_last_expansion_terms(ctx, ctypes.byref(m))
     if rc != SIM_OK:

@@ -338,8 +338,8 @@ def test_tdm_slot_offsets(precision, shape):
 @pytest.mark.parametrize("shape", [(64, 32, 3, 4, 16, 30.0), (128, 64, 4, 2, 8, 30.0), (64, 32, 3, 4, 16, 5.0)])
 def test_tdm_exact_model(precision, shape):
     """Exact Eq. 2 with TDM slot offsets on every path: on tensor cores the slot term n t eps_t
-    joins the per-tile expansion (transmitters about their centre); six terms at 30 m/s, four
-    at 5 m/s."""
+    joins the per-tile expansion (transmitters about their centre); at 30 m/s six Chebyshev terms
+    (four single pass on the narrower case), at 5 m/s four Taylor terms."""
     ns, nc, ntx, nrx, na, v_max = shape
     radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na,
                   tdm_slot_s=9.1e-6, model=1)
@@ -352,8 +352,10 @@ def test_tdm_exact_model(precision, shape):
     finally:
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
-    # the FP32 direct sum chooses no term count
-    assert route == (set() if precision == rs.SIM_PREC_FP32_DIRECT else {6 if v_max == 30.0 else 4})
+    # the FP32 direct sum chooses no term count; route bits: P Taylor, 16 + P Chebyshev terms
+    split = precision in (rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT)
+    expect = {(64, 30.0): {22} if split else {20}, (128, 30.0): {22}, (64, 5.0): {4}}[(ns, v_max)]
+    assert route == (set() if precision == rs.SIM_PREC_FP32_DIRECT else expect)
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
     assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
@@ -421,7 +423,7 @@ def test_exact_model_tensor_core(precision):
 def test_exact_model_tensor_core_regimes(precision, case):
     """The exact model's per-tile expansion of the range-migration phase in its edge regimes:
     the narrowest two-SM tile (32 samples, 16 columns of B per CTA, 43 chirps per tile: six
-    terms); a velocity whose migration phase no eight-term expansion bounds (the device hands
+    Chebyshev terms); a velocity whose migration phase no eight-term expansion bounds (the device hands
     the scene to the per-chirp kernel); and 16 samples (per-chirp kernel chosen on the host,
     no term choice)."""
     ns, nc, ntx, nrx, na, v_max = {"narrow_tile": (32, 16, 1, 3, 4, 15.0),
@@ -437,7 +439,7 @@ def test_exact_model_tensor_core_regimes(precision, case):
     finally:
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
-    assert route == {"narrow_tile": {6}, "beyond_expansion": {0}, "short_chirp": set()}[case]
+    assert route == {"narrow_tile": {22}, "beyond_expansion": {0}, "short_chirp": set()}[case]
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
     assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol
@@ -468,13 +470,16 @@ def test_exact_model_tensor_core_size_extremes(precision, shape):
 
 @pytest.mark.parametrize("precision", prec_params(rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_BF16,
                                                    rs.SIM_PREC_FP16))
-@pytest.mark.parametrize("v_max,terms", [(3.0, 4), (15.0, 6), (35.0, 8), (2000.0, 0)])
-def test_exact_model_each_term_count(precision, v_max, terms):
-    """Every route of the exact model's term choice (Sec. II-A, Eq. 2): the velocity sets the
-    expansion variable theta = 2 pi n_h max|eps| m_h (0.042, 0.21, 0.49, 28 on this radar of
-    64 samples and 4 channels), so the device picks four, six (five rays and two zero K slots
-    per stage) or eight terms, or hands the scene to the per-chirp kernel (0).  At six terms
-    FP16 hi + lo runs the second K step single pass and BF16 hi + lo keeps its lo operands."""
+@pytest.mark.parametrize("v_max,split_route,single_route", [(3.0, 4, 4), (7.0, 20, 4), (25.0, 22, 22), (70.0, 24, 24),
+                                                          (2000.0, 0, 0)])
+def test_exact_model_each_term_count(precision, v_max, split_route, single_route):
+    """Every route of the exact model's expansion (Sec. II-A, Eq. 2): the velocity sets the
+    expansion variable theta = 2 pi n_h max|eps| m_h (0.042, 0.099, 0.35, 0.99, 28 on this
+    radar of 64 samples and 4 channels).  The device takes four Taylor terms where they meet
+    the tolerance (route bit 4), else the fewest Chebyshev (Jacobi-Anger) terms that do: four,
+    six (five rays and two zero K slots per stage) or eight (bits 20, 22, 24), else the
+    per-chirp kernel (bit 0).  The single-pass tolerance is ten times looser, so 7 m/s still
+    takes Taylor terms there."""
     radar = Radar(77e9, 512e6, 25.6e-6, 40e-6, n_samples=64, n_chirps=32, n_tx=1, n_rx=4, n_angle=16, model=1)
     rays = scenegen.uniform_rays(seed=90 + int(v_max) % 97, n=517, n_objects=4, v_max=v_max)
     ref = oracle.signal(radar, rays)
@@ -485,7 +490,8 @@ def test_exact_model_each_term_count(precision, v_max, terms):
     finally:
         ctx.close()
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
-    assert route == {terms}
+    split = precision in (rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT)
+    assert route == {split_route if split else single_route}
     tol, trms = TOL[precision], TOL_RMS[precision]
     assert rel_max(sig, ref) <= tol and rel_rms(sig, ref) <= trms
     assert rel_max(spec, oracle.spectrum(radar, ref)) <= tol

@@ -93,14 +93,16 @@ def test_signal_spectrum_labels_match_oracle(shape, precision):
     """Every precision: FP32 sums directly; the tensor-core precisions expand each tile about
     its centre with each row's own phase words (N_s = 16 is summed directly at any precision).
     The scenes' largest 2 pi n_h |S - S_ref| (0.25, 0.14, -, 0.54) take six, six, no and eight
-    expansion terms."""
+    Chebyshev terms at hi + lo (route bits 22, 22, -, 24), and six, four, no and six single
+    pass."""
     ns, nc, ntx, nrx, na = shape
     radar = scenegen.Radar(77e9, 1e9, 51.2e-6, 60e-6, n_samples=ns, n_chirps=nc, n_tx=ntx, n_rx=nrx, n_angle=na)
     rays, hits, geom = scenegen.moving_scene(ns + nc, radar, 333, n_objects=5, bounce_frac=0.3)
     routes = []
     rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision, routes=routes)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
-    terms = {32: {6}, 64: {6}, 16: set(), 128: {8}}[ns]
+    split = precision in (rs.SIM_PREC_BF16_SPLIT, rs.SIM_PREC_FP16_SPLIT)
+    terms = ({32: {22}, 64: {22}, 16: set(), 128: {24}} if split else {32: {22}, 64: {20}, 16: set(), 128: {22}})[ns]
     assert routes == [set() if precision == rs.SIM_PREC_FP32_DIRECT else terms]
     ref = oracle.signal_geom(radar, rays, hits, geom)
     tol, trms = TOL[precision], TOL_RMS[precision]
@@ -123,8 +125,8 @@ def test_automotive_size_in_two_chunks_sampled(precision):
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
     if precision == rs.SIM_PREC_FP32_DIRECT:
         assert routes == [set()]
-    else:  # each chunk picks its own term count; these road-speed boxes need at most six
-        assert routes[0] and routes[0] <= {4, 6}
+    else:  # each chunk picks its own expansion; these road-speed boxes need four terms
+        assert routes[0] and routes[0] <= {4, 20}
     idx = scenegen.randint(1234, 9, 384, 0, sig.size - 1).astype(np.int64)
     ref = oracle.signal_geom_at(radar, rays, hits, geom, idx)
     assert rel_max(sig.reshape(-1)[idx], ref) <= 1e-5
