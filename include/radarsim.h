@@ -275,7 +275,8 @@ SIM_API int sim_decompose(sim_ctx *ctx, const sim_rays *rays, const sim_meta *me
 /* ---- engine controls and measurement (not part of the paper's method) ---- */
 
 /* Device-memory budget of the engine in bytes (0 = default: 90 % of the free
-   memory when the engine starts) and the number of concurrent slots (streams).
+   memory when the engine starts), the number of concurrent slots (streams; 2 unless
+   configured) and the queue length (64 unless configured).
    Must be called before the first sim_create; SIM_E_INVALID afterwards. */
 SIM_API int sim_engine_configure(int64_t memory_budget_bytes, int32_t slots, int32_t max_queue);
 
