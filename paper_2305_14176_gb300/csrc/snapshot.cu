@@ -17,10 +17,12 @@
 // f_c l / c plus the start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m)
 // of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
 // antennas take N_c (N_tx + N_rx) 16 bytes per ray, so rays go through in chunks that keep
-// them within 2 GiB (three chunks for 200,000 rays at the automotive size).  A chunk's split of
-// rays then carries ~110 MB of words, which the four column tiles that read them find in L2:
-// FP16 hi + lo frame 26.4 ms with 1 GiB, 25.7 ms with 2 GiB, 26.1 ms with 4 GiB, 27.8 ms in
-// one chunk; single pass 13.3, 12.6, 12.4 and 12.8 ms.
+// them within 3 GiB (two chunks for 200,000 rays at the automotive size).  The chunk size was
+// measured: FP16 hi + lo frame 26.4 ms with 1 GiB chunks, 25.9 with 1.5, 25.6 with 2, 25.4 with
+// 3, 26.1 with 4 GiB and 27.8 ms in one chunk; single pass 13.3, 12.8, 12.6, 12.3, 12.4 and
+// 12.8 ms.  Smaller chunks keep the words one split of rays carries, which the four column
+// tiles of a row tile all read, closer to the L2's size; larger ones pay the per-chunk
+// statistics, term choice and reduction fewer times.
 //
 // The reference paths need ~48 bits (f_c l / c is ~10^4 cycles, wanted to ~10^-9): the hit
 // positions, the legs to the two reference antennas s = |p - x_ref| and the reference phase
@@ -44,7 +46,7 @@ using namespace rs;
 namespace {
 
 constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;
-constexpr size_t kWordBudget = size_t{2} << 30;
+constexpr size_t kWordBudget = size_t{3} << 30;
 
 // Float-float numbers x = hi + lo with |lo| <= ulp(hi) / 2, about 48 significant bits
 struct ff {
