@@ -850,25 +850,27 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
 // antennas, which splits as D = D_tx(t) + D_rx(r), so its extremes are those of the two parts.
 // For a tile holding chirp m, S - S_ref = (s(m) - s(m_c)) + D lies between (s(m) - s(m_c)) plus
 // the smallest and plus the largest D; the bound is exact for chirps whose rows all fall in one
-// tile and at most the rest of their antennas' offsets above it for the others.  One thread per
-// (ray, chirp), consecutive threads on consecutive rays.
+// tile and at most the rest of their antennas' offsets above it for the others.  Chirps stride
+// over the grid's y, rays over its x (consecutive threads on consecutive rays), so no thread
+// divides to find its chirp.
 __global__ void snap_stats(SnapRec rec, int64_t stride, const float *__restrict__ amp, int64_t cnt, int nc, int nv,
                            bool want_amax, uint32_t *amax_bits, unsigned long long *d_max) {
   uint32_t ma = 0;
   unsigned long long md = 0;
-  const int64_t total = cnt * nc;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int m = static_cast<int>(e / cnt);
-    const int64_t li = e - static_cast<int64_t>(m) * cnt;
-    if (want_amax && m == 0) ma = max(ma, __float_as_uint(amp[li]));
-    const int64_t at = static_cast<int64_t>(m) * stride + li;
-    const uint64_t sm = rec.s[at], hi = static_cast<uint64_t>(rec.d_hi[at]), lo = static_cast<uint64_t>(rec.d_lo[at]);
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int m = blockIdx.y; m < nc; m += gridDim.y) {
     const int t0 = (m * nv) >> 8, t1 = (m * nv + nv - 1) >> 8;
-    for (int tile = t0; tile <= t1; ++tile) {
-      const int mc = min((tile * 256 + 128) / nv, nc - 1);
-      const uint64_t base = sm - rec.s[static_cast<int64_t>(mc) * stride + li];
-      md = max(md, max(signed_mag(base + hi), signed_mag(base + lo)));
+    const uint64_t *srow = rec.s + static_cast<int64_t>(m) * stride;
+    const int64_t *hrow = rec.d_hi + static_cast<int64_t>(m) * stride;
+    const int64_t *lrow = rec.d_lo + static_cast<int64_t>(m) * stride;
+    for (int64_t li = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; li < cnt; li += step) {
+      if (want_amax && m == 0) ma = max(ma, __float_as_uint(amp[li]));
+      const uint64_t sm = srow[li], hi = static_cast<uint64_t>(hrow[li]), lo = static_cast<uint64_t>(lrow[li]);
+      for (int tile = t0; tile <= t1; ++tile) {
+        const int mc = min((tile * 256 + 128) / nv, nc - 1);
+        const uint64_t base = sm - rec.s[static_cast<int64_t>(mc) * stride + li];
+        md = max(md, max(signed_mag(base + hi), signed_mag(base + lo)));
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1081,7 +1083,8 @@ int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong
   const int t_c = snap_ref_tx(g), r_c = snap_ref_rx(g);
   int kernels = 0;
   cudaMemsetAsync(ws, 0, 64, s);
-  snap_stats<<<4 * sms_t(), 256, 0, s>>>(rec, stride, amp, cnt, g.nc, g.nv, f16, amax, d_max);
+  snap_stats<<<dim3(2u * static_cast<unsigned>(sms_t()), static_cast<unsigned>(std::min(g.nc, 4))), 256, 0, s>>>(
+      rec, stride, amp, cnt, g.nc, g.nv, f16, amax, d_max);
   // theta = 2 pi n_h max|delta|, delta in cycles per sample (the word times 2^-64)
   const double xs = 6.283185307179586 * (sh.bn / 4) * 5.421010862427522e-20;
   const double two_u = split ? (f16 ? 9.765625e-4 : 7.8125e-3) : 0.0;
