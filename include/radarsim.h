@@ -89,7 +89,7 @@ extern "C" {
 #define SIM_MODEL_EXACT 1         /* Eq. 2 with mu t (tau_i(j) - tau_i(0)): phase + n m eps_i,
                                      eps_i = B 2 v_i T_d / (c N_s); any precision.  The tensor-core
                                      precisions expand the coupling about each output tile's centre
-                                     (4 or 8 Taylor terms, truncation <= 1e-6 of a contribution at
+                                     (4 Taylor or 4, 6, 8 Chebyshev terms, truncation <= 1e-6 of a contribution at
                                      hi + lo, 1e-5 single pass); a scene beyond that bound runs per
                                      chirp instead.  With tdm_slot_s > 0 they need n_samples >= 32,
                                      and a scene beyond the bound is reported as SIM_E_INVALID. */
@@ -227,9 +227,10 @@ SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hit
    sim_fetch (labels from the rays' analytic cells of d, v, az, el).  Any of spectrum,
    signal, labels may be NULL (not all); spectrum and labels need the context's outputs
    bit.  Same context limits, memory and errors as sim_snapshot_paths.  Rays go in chunks
-   whose phase words fit 1 GiB.  SIM_PREC_FP32_DIRECT sums each chunk directly; the
+   whose phase words fit 3 GiB.  SIM_PREC_FP32_DIRECT sums each chunk directly; the
    tensor-core precisions expand each tile's coupling of samples and rows about its centre,
-   the exact-model expansion with every row's own phase words (4 or 8 terms, truncation
+   the exact-model expansion with every row's own phase words (4 Taylor or 4, 6, 8
+   Chebyshev terms, truncation
    <= 1e-6 of a contribution at hi + lo, 1e-5 single pass, chosen on the device per chunk).
    A chunk beyond that bound, or N_s < 32, is summed directly in FP32. */
 SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, const sim_meta *meta, const sim_hits *hits,

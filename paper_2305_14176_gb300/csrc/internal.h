@@ -144,7 +144,8 @@ void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route);
 // `workspace` (may be null: one ray part) of pair_workspace_bytes(g, n) lets the rays go in
 // parts that fill the SMs
 int64_t pair_workspace_bytes(const Derived &g, int64_t n);
-// `gate` (device word, may be null) holding 4 or 8 makes both of its kernels return at once
+// `gate` (device word, may be null) holding a term count (expansion_terms) makes both of its
+// kernels return at once
 int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
                     int64_t stride, bool accumulate, float2 *sig, void *workspace, const uint32_t *gate,
                     cudaStream_t s);
@@ -174,7 +175,7 @@ int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, L
 int64_t exact_workspace_bytes(const Derived &g, int64_t n);
 int launch_exact_sum(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                      cudaStream_t s, cudaEvent_t after_main);
-// its two halves; `gate` (device word, may be null) holding 4 or 8 makes both return at once
+// its two halves; `gate` (device word, may be null) holding a term count makes both return at once
 int launch_exact_main(const Derived &g, RaysPrep p, int64_t n, void *workspace, uint32_t *status, cudaStream_t s,
                       const uint32_t *gate);
 int launch_exact_reduce(const Derived &g, int64_t n, float2 *sig, void *workspace, cudaStream_t s,

@@ -7,24 +7,26 @@
 //   n m eps = n_c m' eps + n m_c eps + n' m' eps.
 // The first two terms are exact per-tile shifts of the chirp and sample frequencies; only
 // e^{2 pi j n' m' eps} still couples rows and columns, and over a tile |m'| <= m_h, |n'| <= n_h
-// are small, so it is replaced by its Taylor polynomial of P terms,
-//   e^{j x} = sum_{p<P} (j x)^p / p! + R,   |R| <= |x|^P / P!,   x = 2 pi eps m' n'.
-// Each term is separable, (j 2 pi eps m' n_h)^p / p! on the row side times (n' / n_h)^p on the
-// column side, so the tile is one complex product over K = P x rays:
+// are small, so e^{j x t}, x = 2 pi eps m' n_h (row) and t = n' / n_h in [-1, 1) (column), is
+// replaced by a separable series of P terms: Taylor,
+//   e^{j x t} = sum_{p<P} (j x)^p / p! t^p + R,   |R| <= |x|^P / P!,
+// or Chebyshev (Jacobi-Anger, see chebyshev_series_terms), eps_p j^p J_p(x) times T_p(t), whose
+// remainder is 2^(P-1) times smaller.  The tile is one complex product over K = P x rays:
 //   S[row, n] = sum_{i, p} A_p[row, i] B_p[i, n]
-//   A_p[row, i] = a_i e^{2 pi j (phi + t nu_tx + r nu_a + m nu_d + n_c m' eps)} (j x_row,i)^p / p!
-//   B_p[i, n]   = e^{2 pi j n (nu_r + m_c eps)} (n' / n_h)^p,      x_row,i = 2 pi eps_i m' n_h
+//   A_p[row, i] = a_i e^{2 pi j (phi + t nu_tx + r nu_a + m nu_d + n_c m' eps)} c_p(x_row,i)
+//   B_p[i, n]   = e^{2 pi j n (nu_r + m_c eps)} b_p(n' / n_h),      x_row,i = 2 pi eps_i m' n_h
+// with c_p(x) = (j x)^p / p!, b_p(t) = t^p (Taylor) or c_p(x) = eps_p j^p J_p(x), b_p = T_p.
 // Rows are chirp-major (row = m N_v + k), so a 256-row tile spans only about 256 / N_v chirps,
 // and each synthesised value serves a whole 256 x NC tile instead of N_v channels.
 // With TDM slot offsets the phase also holds n t eps_t (transmitter t); with t = t_c + t' it
 // joins the coupling the same way: the shifts take n_c t' eps_t (rows) and n t_c eps_t
 // (columns), and x = 2 pi n' (m' eps + t' eps_t).
 //
-// P is 4, 6 or 8, the smallest whose bound theta^P / P!, theta = 2 pi n_h (max|eps| m_h +
-// max|eps_t| t_h), is at most 1e-6 for
-// the hi + lo precisions (1e-5 single pass, whose operand rounding is ~3e-4); a device kernel
-// takes it from the scene's largest |eps|, so no host round trip is needed.  When even P = 8
-// would not meet the bound (velocities far beyond road traffic), P = 0 is written and the
+// The device takes four Taylor terms when their bound theta^4 / 4!, theta = 2 pi n_h (max|eps|
+// m_h + max|eps_t| t_h), is at most 1e-6 at the hi + lo precisions (1e-5 single pass, whose
+// operand rounding is ~3e-4), else the fewest Chebyshev terms (4, 6, 8) that meet it; a device
+// kernel takes theta from the scene's largest |eps|, so no host round trip is needed.  When even
+// eight terms would not meet the bound (velocities far beyond road traffic), P = 0 is written and the
 // per-chirp kernel of umma_exact.cu, launched behind this one, computes the scene instead: each
 // of the two kernels (and its reduction) returns at once when the other one owns the scene.
 // The per-chirp form has no slot term, so with TDM slots P = 0 is an error instead (a status
@@ -32,8 +34,9 @@
 //
 // At the hi + lo precisions the second 16-slot K step of every stage holds only terms of order
 // p >= P / 2 (at P = 6 term 3 of the stage's first ray falls in the first K step and keeps its
-// lo operands), each at most theta^(P/2) / (P/2)! of the ray's amplitude, so single-pass
-// operand rounding (<= 2u relative, u = 2^-11 FP16, 2^-8 BF16) adds at most that times 2u; when
+// lo operands), each at most theta^(P/2) / (P/2)! of the ray's amplitude (Chebyshev: 2 (theta /
+// 2)^(P/2) / (P/2)!), so single-pass operand rounding (<= 2u relative, u = 2^-11 FP16, 2^-8
+// BF16) adds at most that times 2u; when
 // the device finds this below 2e-6 that K step skips its lo operands and the hi x lo MMAs (8
 // MMA units per stage instead of 12).
 //
