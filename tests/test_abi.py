@@ -64,3 +64,19 @@ def test_null_arguments():
     assert rs.sim_engine_configure(0, 0, 8) == rs.SIM_E_INVALID
     assert rs.lib.sim_selftest_wait(0, None, None) == rs.SIM_E_INVALID
     assert rs.lib.sim_selftest_wait(2000, None, None) == rs.SIM_E_INVALID
+    mask = ctypes.c_uint32(7)
+    assert rs.lib.sim_last_expansion_terms(None, ctypes.byref(mask)) == rs.SIM_E_INVALID
+    assert mask.value == 7  # untouched
+    count = ctypes.c_int32(-1)
+    assert rs.lib.sim_last_kernel_count(None, ctypes.byref(count)) == rs.SIM_E_INVALID
+    assert rs.lib.sim_scene_bytes(None, 10, None) == rs.SIM_E_INVALID
+
+
+def test_expansion_route_names():
+    """The bench's names for the route bits of sim_last_expansion_terms: P for Taylor terms,
+    16 + P for Chebyshev terms, 0 for the per-chirp (or pair-sum) route."""
+    import bench
+    assert bench.expansion_names({4}) == ["taylor4"]
+    assert bench.expansion_names({20, 22, 24}) == ["chebyshev4", "chebyshev6", "chebyshev8"]
+    assert bench.expansion_names({0, 4}) == ["per-chirp", "taylor4"]
+    assert bench.expansion_names(set()) == []
