@@ -154,7 +154,7 @@ def sim_status_string(code: int) -> str:
     return lib.sim_status_string(int(code)).decode()
 
 
-def sim_engine_configure(memory_budget_bytes: int = 0, slots: int = 4, max_queue: int = 64) -> int:
+def sim_engine_configure(memory_budget_bytes: int = 0, slots: int = 2, max_queue: int = 64) -> int:
     return lib.sim_engine_configure(int(memory_budget_bytes), int(slots), int(max_queue))
 
 
