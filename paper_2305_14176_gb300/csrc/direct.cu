@@ -210,13 +210,13 @@ __global__ void add_parts_kernel(float2 *__restrict__ sig, const float2 *__restr
 
 // The same sum with phase words per (ray, chirp, transmitter) and (ray, chirp, receiver):
 // row (k = tx N_rx + rx, m) takes base = wt.x + wr.x and step = wt.y + wr.y, wt =
-// w_tx[(m N_tx + tx) stride + i], wr = w_rx[(m N_rx + rx) stride + i] (Q0.64, wrap-exact
-// sums).  With `accumulate` the row is added to what sig holds (rays in several chunks).  Ray
+// w_tx[(m N_tx + tx) stride + i], wr = w_rx[(m N_rx + rx) stride + i] (Q0.32, wrap-exact
+// sums, staged as the upper halves of Q0.64 phases).  With `accumulate` the row is added to what sig holds (rays in several chunks).  Ray
 // part blockIdx.y > 0 (rays [y part_len, ...)) writes its row to parts[(y - 1) n_sig + ...]
 // instead, added in order afterwards.
 template <int NPT>
-__global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restrict__ w_tx,
-                                                       const ulonglong2 *__restrict__ w_rx,
+__global__ void __launch_bounds__(128) pair_sum_kernel(const uint2 *__restrict__ w_tx,
+                                                       const uint2 *__restrict__ w_rx,
                                                        const float *__restrict__ amp, int64_t n_rays, int64_t stride,
                                                        int64_t part_len, int nc, int ns, int ntx, int nrx,
                                                        int accumulate, float2 *__restrict__ sig,
@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
   const int row = blockIdx.x;
   const int k = row / nc, m = row % nc;
   const int tx = k / nrx, rx = k - tx * nrx;
-  const ulonglong2 *wt = w_tx + (static_cast<int64_t>(m) * ntx + tx) * stride;
-  const ulonglong2 *wr = w_rx + (static_cast<int64_t>(m) * nrx + rx) * stride;
+  const uint2 *wt = w_tx + (static_cast<int64_t>(m) * ntx + tx) * stride;
+  const uint2 *wr = w_rx + (static_cast<int64_t>(m) * nrx + rx) * stride;
   const int t = threadIdx.x;
   const uint64_t T = blockDim.x;
   float tot_re[NPT], tot_im[NPT];
@@ -240,8 +240,8 @@ __global__ void __launch_bounds__(128) pair_sum_kernel(const ulonglong2 *__restr
     const int cnt = static_cast<int>(hi - c0 < kChunk ? hi - c0 : kChunk);
     __syncthreads();
     for (int i = t; i < cnt; i += blockDim.x) {
-      const ulonglong2 a = wt[c0 + i], b = wr[c0 + i];
-      stage_ray(st, i, a.x + b.x, a.y + b.y, amp[c0 + i], T);
+      const uint2 a = wt[c0 + i], b = wr[c0 + i];
+      stage_ray(st, i, static_cast<uint64_t>(a.x + b.x) << 32, static_cast<uint64_t>(a.y + b.y) << 32, amp[c0 + i], T);
     }
     if (t == 0) stage_pad(st, cnt);
     __syncthreads();
@@ -380,7 +380,7 @@ int64_t pair_workspace_bytes(const Derived &g, int64_t n) {
   return static_cast<int64_t>(pair_parts(g, n) - 1) * 8 * g.n_sig;
 }
 
-int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
+int launch_pair_sum(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, const float *amp, int64_t n,
                     int64_t stride, bool accumulate, float2 *sig, void *workspace, const uint32_t *gate,
                     cudaStream_t s) {
   const int rows = g.nv * g.nc;

@@ -139,23 +139,23 @@ void once_per_device(std::atomic<uint64_t> &done, F f) {
 // store a synchronous call's stage times (7 entries, the sim_last_stage_ms order), kernel count
 // and route mask (status word 1)
 void record_stage_ms(sim_ctx *c, const float *ms, int kernels, uint32_t route);
-// direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.64 phase
+// direct sum over per-(ray, chirp, transmitter) and per-(ray, chirp, receiver) Q0.32 phase
 // words (base, per-sample step): w_tx[(m N_tx + t) stride + i], w_rx[(m N_rx + r) stride + i]
 // `workspace` (may be null: one ray part) of pair_workspace_bytes(g, n) lets the rays go in
 // parts that fill the SMs
 int64_t pair_workspace_bytes(const Derived &g, int64_t n);
 // `gate` (device word, may be null) holding a term count (expansion_terms) makes both of its
 // kernels return at once
-int launch_pair_sum(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, const float *amp, int64_t n,
+int launch_pair_sum(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, const float *amp, int64_t n,
                     int64_t stride, bool accumulate, float2 *sig, void *workspace, const uint32_t *gate,
                     cudaStream_t s);
 // virtual snapshots on tensor cores, one chunk of phase words (umma_taylor.cu): the per-tile
 // expansion, or the pair sum when the expansion's bound fails; workspace of
 // snap_tensor_workspace_bytes(g, chunk), pair_ws of pair_workspace_bytes(g, chunk).  The
 // expansion's reference antennas are the central ones; `rec` holds, per (ray, chirp m) at
-// [m stride + ray], the step word S(m, t_c, r_c) and the largest and smallest signed
-// difference S(m, t, r) - S(m, t_c, r_c) over the antennas (Q0.64 units), which bound the
-// expansion's argument.
+// [m stride + ray], the step S(m, t_c, r_c) and the largest and smallest signed difference
+// S(m, t, r) - S(m, t_c, r_c) over the antennas, in Q0.64 units before the words' rounding to
+// Q0.32, which bound the expansion's argument.
 inline int snap_ref_tx(const Derived &g) { return g.ntx / 2; }
 inline int snap_ref_rx(const Derived &g) { return g.nrx / 2; }
 struct SnapRec {
@@ -163,7 +163,7 @@ struct SnapRec {
   const int64_t *d_hi, *d_lo;
 };
 int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk);
-int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, SnapRec rec, int64_t stride,
+int launch_snap_tensor(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, SnapRec rec, int64_t stride,
                        const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
                        uint32_t *status, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);

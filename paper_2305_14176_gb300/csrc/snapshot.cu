@@ -13,16 +13,20 @@
 // not separable over chirps and channels: it runs on the direct-sum path (FP32) or, at the
 // tensor-core precisions, through the per-tile expansion of umma_taylor.cu with each row's own
 // phase words (the direct sum remains that path's fallback, gated on the device).  One thread per
-// (ray, chirp) computes A_t and B_r and stores them as Q0.64 phase words (carrier
-// f_c l / c plus the start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m)
-// of the sum adds the transmitter's and the receiver's word.  The words of all chirps and
-// antennas take N_c (N_tx + N_rx) 16 bytes per ray, so rays go through in chunks that keep
-// them within 3 GiB (two chunks for 200,000 rays at the automotive size).  The chunk size was
-// measured: FP16 hi + lo frame 26.4 ms with 1 GiB chunks, 25.9 with 1.5, 25.6 with 2, 25.4 with
-// 3, 26.1 with 4 GiB and 27.8 ms in one chunk; single pass 13.3, 12.8, 12.6, 12.3, 12.4 and
-// 12.8 ms.  Smaller chunks keep the words one split of rays carries, which the four column
-// tiles of a row tile all read, closer to the L2's size; larger ones pay the per-chunk
-// statistics, term choice and reduction fewer times.
+// (ray, chirp) computes A_t and B_r and stores them as phase words (carrier f_c l / c plus the
+// start phase, per-sample step B l / (c N_s)); the row (k = t N_rx + r, m) of the sum adds the
+// transmitter's and the receiver's word.  The words are formed in Q0.64 and stored rounded to
+// Q0.32 (a uint2 per word): a row's phase at sample n is off by at most n 2^-32 cycles from
+// the two roundings of its step (7.5e-7 rad at n = 512, 6e-6 at n = 4096, against the carrier
+// phase's own FP32 resolution of ~2^-25 cycles), and half the bytes are read and written.  The
+// words of all chirps and antennas take N_c (N_tx + N_rx) 8 bytes per ray, so rays go through
+// in chunks that keep them within 3 GiB (224,512 rays at the automotive size: 200,000 rays in
+// one chunk).  The chunk size was measured (automotive frame, 200,000 rays): FP16 hi + lo 20.43
+// ms with 1 GiB chunks, 20.14 with 1.5, 20.12 with 2 and 19.82 with 3 GiB; single pass 10.45,
+// 10.25, 10.23 and 10.01 ms.  With 16-byte Q0.64 words the same frame took 25.4 ms at best
+// (3 GiB chunks, two of them) and 27.8 ms in one 5.3 GiB chunk: smaller chunks keep the words
+// one split of rays carries, which the four column tiles of a row tile all read, closer to the
+// L2's size; larger ones pay the per-chunk statistics, term choice and reduction fewer times.
 //
 // The reference paths need ~48 bits (f_c l / c is ~10^4 cycles, wanted to ~10^-9): the hit
 // positions, the legs to the two reference antennas s = |p - x_ref| and the reference phase
@@ -32,7 +36,7 @@
 // antenna at x_ref + e differs from the reference leg by |u - e| - |u| = (|e|^2 - 2 u.e) /
 // (|u - e| + |u|), u = p - x_ref, a few centimetres for a compact array: that difference is
 // taken in FP32 (relative error ~2^-22, so ~5 nm for e = 2 cm, 8e-6 rad of carrier phase)
-// and added to the words as Q0.64.
+// and added to the words in Q0.64 before their rounding.
 #include <cuda_runtime.h>
 
 #include <math.h>
@@ -301,6 +305,11 @@ __device__ __forceinline__ uint64_t q64_small(float x) {
   return static_cast<uint64_t>(static_cast<uint32_t>(__float2int_rn(f * 4294967296.0f))) << 32;
 }
 
+// a Q0.64 phase rounded to the nearest Q0.32 word (modulo one cycle)
+__device__ __forceinline__ uint32_t q32_of(uint64_t q) {
+  return static_cast<uint32_t>((q + (uint64_t{1} << 31)) >> 32);
+}
+
 // One thread per (ray li of the chunk starting at i0, snapshot j = blockIdx.y), in float-float
 // and FP32 only.  paths != null: l(j, t, r) into paths[(i N_c + j) N_v + t N_rx + r]; else the
 // phase words of A_t and B_r, and, when rec_s != null, the record of (li, j) at j stride + li:
@@ -309,7 +318,7 @@ __device__ __forceinline__ uint64_t q64_small(float x) {
 __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *__restrict__ base0,
                                                        const uint64_t *__restrict__ q0s, int64_t i0, int64_t cnt,
                                                        PhaseConst k, double *__restrict__ paths,
-                                                       ulonglong2 *__restrict__ w_tx, ulonglong2 *__restrict__ w_rx,
+                                                       uint2 *__restrict__ w_tx, uint2 *__restrict__ w_rx,
                                                        int64_t stride, uint64_t *__restrict__ rec_s,
                                                        int64_t *__restrict__ rec_hi, int64_t *__restrict__ rec_lo,
                                                        uint32_t *status) {
@@ -355,7 +364,7 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
     dt_lo = min(dt_lo, d);
     if (t == k.tc) dt_c = d;
     w_tx[(j * k.ntx + t) * stride + li] =
-        ok ? make_ulonglong2(at_c + q64_small(e * fc_f), at_s + os) : make_ulonglong2(0, 0);
+        ok ? make_uint2(q32_of(at_c + q64_small(e * fc_f)), q32_of(at_s + os)) : make_uint2(0, 0);
   }
   for (int r = 0; r < k.nrx; ++r) {
     const float e = leg_offset(ur, sr.hi, g.rx[r]);
@@ -366,7 +375,7 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
     dr_lo = min(dr_lo, d);
     if (r == k.rc) dr_c = d;
     w_rx[(j * k.nrx + r) * stride + li] =
-        ok ? make_ulonglong2(br_c + q64_small(e * fc_f), br_s + os) : make_ulonglong2(0, 0);
+        ok ? make_uint2(q32_of(br_c + q64_small(e * fc_f)), q32_of(br_s + os)) : make_uint2(0, 0);
   }
   if (rec_s) {
     const int64_t at = j * stride + li;
@@ -456,12 +465,12 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.H = H;
 
   const size_t un = static_cast<size_t>(n), up = (un + 31) / 32 * 32, uh = static_cast<size_t>(H);
-  const size_t per_ray_words = 16 * static_cast<size_t>(g.nc) * static_cast<size_t>(g.ntx + g.nrx);
+  const size_t per_ray_words = 8 * static_cast<size_t>(g.nc) * static_cast<size_t>(g.ntx + g.nrx);
   int64_t chunk = 0;
   if (mode == 1 && n > 0) {
     chunk = static_cast<int64_t>(kWordBudget / per_ray_words) / 256 * 256;
     if (chunk < 256) chunk = 256;
-    if (chunk > n) chunk = n;
+    if (chunk > n) chunk = (n + 1) / 2 * 2;  // the word rows' stride stays even (16-byte pairs)
   }
   R.chunk = chunk;
   const size_t vbytes = 24 * static_cast<size_t>(g.nc) * static_cast<size_t>(geom->n_vertices);
@@ -483,8 +492,8 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   R.o_amp = take(4 * up); R.o_cell = take(4 * up); R.o_en = take(8 * up); R.o_sd = take(8 * up);
   R.o_sr = take(8 * up); R.o_ntx = take(8 * up);
   R.o_status = take(256);
-  R.o_wt = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.ntx : 0);
-  R.o_wr = take(mode == 1 ? 16 * static_cast<size_t>(chunk) * g.nc * g.nrx : 0);
+  R.o_wt = take(mode == 1 ? 8 * static_cast<size_t>(chunk) * g.nc * g.ntx : 0);
+  R.o_wr = take(mode == 1 ? 8 * static_cast<size_t>(chunk) * g.nc * g.nrx : 0);
   R.o_sig = take(mode == 1 ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_pw = take(mode == 1 && chunk > 0 ? static_cast<size_t>(pair_workspace_bytes(g, chunk)) : 0);  // ray parts
   // tensor-core precisions: the expansion's header and split-K partials
@@ -662,7 +671,7 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
   cudaEventRecord(ev[ei++], s);
   float2 *sig = reinterpret_cast<float2 *>(b + R.o_sig);
   if (R.n == 0) cudaMemsetAsync(sig, 0, 8 * static_cast<size_t>(g.n_sig), s);
-  ulonglong2 *wt = reinterpret_cast<ulonglong2 *>(b + R.o_wt), *wr = reinterpret_cast<ulonglong2 *>(b + R.o_wr);
+  uint2 *wt = reinterpret_cast<uint2 *>(b + R.o_wt), *wr = reinterpret_cast<uint2 *>(b + R.o_wr);
   const PhaseConst k = phase_const(g);
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
   const size_t rec_n = static_cast<size_t>(R.chunk) * static_cast<size_t>(g.nc);

@@ -243,6 +243,10 @@ __device__ __forceinline__ void encode(float x, float y, uint32_t &hi, uint32_t 
 __device__ __forceinline__ float q64_to_rad(uint64_t p) {
   return static_cast<float>(static_cast<int32_t>(p >> 32)) * 1.46291807926715968e-09f;  // 2 pi / 2^32
 }
+// the same for a Q0.32 phase
+__device__ __forceinline__ float q32_to_rad(uint32_t p) {
+  return static_cast<float>(static_cast<int32_t>(p)) * 1.46291807926715968e-09f;
+}
 
 template <bool F16>
 __device__ __forceinline__ float amp_scale(const uint32_t *amax_bits) {

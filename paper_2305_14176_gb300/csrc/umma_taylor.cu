@@ -103,9 +103,9 @@ __host__ __device__ constexpr int t_threads() {
 
 struct TArgs {
   RaysPrep p;
-  // kSnap: phase words (base, per-sample step) w_tx[(m N_tx + t) stride + i],
+  // kSnap: Q0.32 phase words (base, per-sample step) w_tx[(m N_tx + t) stride + i],
   // w_rx[(m N_rx + r) stride + i] of the chunk's rays, their amplitudes, the reference antennas
-  const ulonglong2 *w_tx, *w_rx;
+  const uint2 *w_tx, *w_rx;
   int64_t stride;
   const float *samp;
   int ntx, r_c;
@@ -136,7 +136,7 @@ struct TWords {
 
 // thread gt < rays of the stage fetches its ray's words (rays past the chunk read as 0).
 // kSnap: the ray's reference per-sample step (the tile's centre chirp m_c, antennas t_c, r_c),
-// kept in `nur`, and its amplitude.
+// a Q0.32 word kept in the low half of `nur`, and its amplitude.
 template <int MODE>
 __device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays, int64_t k_hi, int gt, int m_c) {
   TWords w{0, 0, 0, 0, 0, 0, 0, 0.f};
@@ -144,7 +144,7 @@ __device__ __forceinline__ TWords tfetch(const TArgs &g, int64_t ray0, int rays,
   if constexpr (MODE == kSnap) {
     if (gt < rays && ray < k_hi) {
       w.nur = g.w_tx[(static_cast<int64_t>(m_c) * g.ntx + g.t_c) * g.stride + ray].y +
-              g.w_rx[(static_cast<int64_t>(m_c) * g.nrx + g.r_c) * g.stride + ray].y;
+              g.w_rx[(static_cast<int64_t>(m_c) * g.nrx + g.r_c) * g.stride + ray].y;  // modulo 2^32
       w.amp = g.samp[ray];
     }
     return w;
@@ -193,8 +193,8 @@ struct RowCtx {
   int32_t ncm, nct;         // n_c m', n_c t' (|n_c m'| < 2^23)
   float xm, xt;             // 2 pi m' n_h 2^-64, 2 pi t' n_h 2^-64: x = xm eps_i + xt eps_t,i (words)
   bool valid;
-  // kSnap: the row's phase-word rows, n_c, and 2 pi n_h 2^-64 (x = xs delta_i, words)
-  const ulonglong2 *wt, *wr;
+  // kSnap: the row's phase-word rows, n_c, and 2 pi n_h 2^-32 (x = xs delta_i, Q0.32 words)
+  const uint2 *wt, *wr;
   uint32_t n_c;
   float xs;
 };
@@ -266,23 +266,49 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
     float2 t[RS];
     float x[RS];
     float h[RS];  // CH: eps_p (x / 2)^p / p! of the current term
+    // kSnap: the row's words of the stage's rays, two rays per 16-byte load when RS is even (the
+    // stage's first ray is then even and the row stride is even, so each pair is aligned; a pair
+    // whose first ray is present lies inside the row, its second ray is masked below if absent)
+    uint2 wa[RS], wb[RS];
+    if constexpr (MODE == kSnap) {
+      if constexpr (RS % 2 == 0) {
+#pragma unroll
+        for (int q = 0; q < RS; q += 2) {
+          uint4 u = make_uint4(0u, 0u, 0u, 0u), v = make_uint4(0u, 0u, 0u, 0u);
+          if (rc.valid && q < valid) {
+            u = *reinterpret_cast<const uint4 *>(rc.wt + li0 + q);
+            v = *reinterpret_cast<const uint4 *>(rc.wr + li0 + q);
+          }
+          wa[q] = make_uint2(u.x, u.y);
+          wa[q + 1] = make_uint2(u.z, u.w);
+          wb[q] = make_uint2(v.x, v.y);
+          wb[q + 1] = make_uint2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < RS; ++q) {
+          const bool live = rc.valid && q < valid;
+          wa[q] = live ? rc.wt[li0 + q] : make_uint2(0u, 0u);
+          wb[q] = live ? rc.wr[li0 + q] : make_uint2(0u, 0u);
+        }
+      }
+    }
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
       if constexpr (MODE == kSnap) {
         // base C and per-sample step S of this row's path, delta = S - S_ref (a small signed
-        // word): phase C + n_c delta, expansion variable x = 2 pi n_h delta
+        // word): phase C + n_c delta, expansion variable x = 2 pi n_h delta (Q0.32, wrapping)
         const bool live = rc.valid && q < valid;
-        uint64_t c = 0, d = 0;
+        uint32_t c = 0, d = 0;
         if (live) {
-          const ulonglong2 a = rc.wt[li0 + q], b = rc.wr[li0 + q];
-          c = a.x + b.x;
-          d = a.y + b.y - sr.nur[q];
+          c = wa[q].x + wb[q].x;
+          d = wa[q].y + wb[q].y - static_cast<uint32_t>(sr.nur[q]);
         }
-        __sincosf(q64_to_rad(c + static_cast<uint64_t>(rc.n_c) * d), &sn, &cs);
+        __sincosf(q32_to_rad(c + rc.n_c * d), &sn, &cs);
         const float am = live ? sr.amp[q] * scale : 0.f;
         t[q] = make_float2(am * cs, am * sn);
-        x[q] = rc.xs * static_cast<float>(static_cast<int64_t>(d));
+        x[q] = rc.xs * static_cast<float>(static_cast<int32_t>(d));
       } else {
         uint64_t ph = sr.car[q] + static_cast<uint64_t>(rc.tx) * sr.nutx[q] + static_cast<uint64_t>(rc.rx) * sr.nua[q] +
                       static_cast<uint64_t>(rc.m) * sr.nud[q] +
@@ -342,14 +368,13 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
 #pragma unroll
     for (int q = 0; q < RS; ++q) {
       float sn, cs;
-      uint64_t ph;
       if constexpr (MODE == kSnap) {
-        ph = static_cast<uint64_t>(cc.n) * sr.nur[q];  // the ray's reference step
+        __sincosf(q32_to_rad(cc.n * static_cast<uint32_t>(sr.nur[q])), &sn, &cs);  // the ray's reference step
       } else {
-        ph = static_cast<uint64_t>(cc.n) * sr.nur[q] + static_cast<uint64_t>(cc.nmc) * sr.eps[q];
+        uint64_t ph = static_cast<uint64_t>(cc.n) * sr.nur[q] + static_cast<uint64_t>(cc.nmc) * sr.eps[q];
         if constexpr (TDM) ph += static_cast<uint64_t>(cc.ntc) * sr.epst[q];
+        __sincosf(q64_to_rad(ph), &sn, &cs);
       }
-      __sincosf(q64_to_rad(ph), &sn, &cs);
       b[q] = make_float2(cs, sn);
     }
     const uint32_t off0 = (cc.c >> 3) * 128 + (cc.c & 7) * 16;
@@ -515,7 +540,7 @@ __global__ void __launch_bounds__(t_threads<SPLIT, MODE>(), 1) taylor_sum_kernel
       rc.nct = n_c * tp;
       rc.xt = static_cast<float>(tp) * static_cast<float>(n_h) * 3.40612158008655459e-19f;
       rc.n_c = static_cast<uint32_t>(n_c);
-      rc.xs = static_cast<float>(n_h) * 3.40612158008655459e-19f;
+      rc.xs = static_cast<float>(n_h) * 1.46291807926715968e-09f;  // 2 pi 2^-32
       rc.wt = rc.wr = nullptr;
       if (MODE == kSnap && rc.valid) {
         rc.wt = g.w_tx + (static_cast<int64_t>(m) * g.ntx + t) * g.stride;
@@ -848,7 +873,8 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
 // Virtual snapshots: a bound on the largest |S - S_ref| over the chunk's rays and every row, S
 // the per-sample step of row (m, k = t N_rx + r) and S_ref the ray's reference step of that
 // row's 256-row tile (chirp m_c, antennas t_c, r_c), as signed Q0.64 words; and the amplitude
-// maximum (FP16 scaling).  It reads the phase-word kernel's record of each (ray, chirp):
+// maximum (FP16 scaling).  The kernel's delta is formed from four words rounded to Q0.32, so
+// it may exceed the unrounded one by up to four half units: 2^33 in Q0.64 is added to the bound.  It reads the phase-word kernel's record of each (ray, chirp):
 // s(m) = S(m, t_c, r_c) and the largest and smallest D(m, t, r) = S(m, t, r) - s(m) over the
 // antennas, which splits as D = D_tx(t) + D_rx(r), so its extremes are those of the two parts.
 // For a tile holding chirp m, S - S_ref = (s(m) - s(m_c)) + D lies between (s(m) - s(m_c)) plus
@@ -882,7 +908,7 @@ __global__ void snap_stats(SnapRec rec, int64_t stride, const float *__restrict_
   }
   if ((threadIdx.x & 31) == 0) {
     if (want_amax) atomicMax(amax_bits, ma);
-    atomicMax(d_max, md);
+    atomicMax(d_max, md + (1ull << 33));
   }
 }
 
@@ -1068,7 +1094,7 @@ int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk) {
 // P from the chunk's largest |delta|; beyond the bound the direct pair sum runs instead (both
 // are launched, each returns at once when the other owns the chunk).  Adds to sig when
 // `accumulate`.
-int launch_snap_tensor(const Derived &g, const ulonglong2 *w_tx, const ulonglong2 *w_rx, SnapRec rec, int64_t stride,
+int launch_snap_tensor(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, SnapRec rec, int64_t stride,
                        const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
                        uint32_t *status, cudaStream_t s) {
   if (!taylor_eligible(g) || cnt <= 0)

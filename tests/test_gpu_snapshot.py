@@ -116,10 +116,11 @@ def test_signal_spectrum_labels_match_oracle(shape, precision):
 
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT])
 def test_automotive_size_in_two_chunks_sampled(precision):
-    """256 chirps x 512 samples x 12 channels; 120,000 rays need two chunks of phase words (the
-    second chunk adds to the first, on tensor cores too)."""
+    """256 chirps x 512 samples x 12 channels; 240,000 rays need two chunks of phase words
+    (224,512 rays fill the 3 GiB of a chunk; the second chunk adds to the first, on tensor cores
+    too)."""
     radar = scenegen.radar_automotive()
-    rays, hits, geom = scenegen.moving_scene(1234, radar, 120_000, n_objects=20)
+    rays, hits, geom = scenegen.moving_scene(1234, radar, 240_000, n_objects=20)
     routes = []
     rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision, routes=routes)
     assert rc == rs.SIM_OK, rs.sim_status_string(rc)
