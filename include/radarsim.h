@@ -227,7 +227,7 @@ SIM_API int sim_snapshot_paths(sim_ctx *ctx, const sim_rays *rays, const sim_hit
    sim_fetch (labels from the rays' analytic cells of d, v, az, el).  Any of spectrum,
    signal, labels may be NULL (not all); spectrum and labels need the context's outputs
    bit.  Same context limits, memory and errors as sim_snapshot_paths.  Rays go in chunks
-   whose phase words fit 3 GiB.  SIM_PREC_FP32_DIRECT sums each chunk directly; the
+   whose phase words (8 bytes per ray, chirp and antenna) fit 3 GiB.  SIM_PREC_FP32_DIRECT sums each chunk directly; the
    tensor-core precisions expand each tile's coupling of samples and rows about its centre,
    the exact-model expansion with every row's own phase words (4 Taylor or 4, 6, 8
    Chebyshev terms, truncation
