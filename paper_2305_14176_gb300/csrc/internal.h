@@ -154,13 +154,13 @@ int launch_pair_sum(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, cons
 // snap_tensor_workspace_bytes(g, chunk), pair_ws of pair_workspace_bytes(g, chunk).  The
 // expansion's reference antennas are the central ones; `rec` holds, per (ray, chirp m) at
 // [m stride + ray], the step S(m, t_c, r_c) and the largest and smallest signed difference
-// S(m, t, r) - S(m, t_c, r_c) over the antennas, in Q0.64 units before the words' rounding to
-// Q0.32, which bound the expansion's argument.
+// S(m, t, r) - S(m, t_c, r_c) over the antennas, as the Q0.32 words hold them, which bound
+// the expansion's argument.
 inline int snap_ref_tx(const Derived &g) { return g.ntx / 2; }
 inline int snap_ref_rx(const Derived &g) { return g.nrx / 2; }
 struct SnapRec {
-  const uint64_t *s;
-  const int64_t *d_hi, *d_lo;
+  const uint32_t *s;
+  const int32_t *d_hi, *d_lo;
 };
 int64_t snap_tensor_workspace_bytes(const Derived &g, int64_t chunk);
 int launch_snap_tensor(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, SnapRec rec, int64_t stride,

@@ -298,11 +298,17 @@ __device__ __forceinline__ float leg_offset(const ff u[3], float s, float4 e) {
   return num / den;
 }
 
-// a small cycle count as a Q0.64 phase: only x - rint(x), exact and within +-1/2, counts, so
-// a 32-bit conversion of it times 2^32 gives the word's upper half
-__device__ __forceinline__ uint64_t q64_small(float x) {
+// a small cycle count as a Q0.32 phase: only x - rint(x), exact and within +-1/2, counts, so a
+// 32-bit conversion of it times 2^32 gives the word (f 2^32 is exact, its rounding the only one)
+__device__ __forceinline__ uint32_t q32_small(float x) {
   const float f = x - rintf(x);
-  return static_cast<uint64_t>(static_cast<uint32_t>(__float2int_rn(f * 4294967296.0f))) << 32;
+  return static_cast<uint32_t>(__float2int_rn(f * 4294967296.0f));
+}
+
+// a signed offset sum kept within int32 (antennas far enough apart to reach it give a bound the
+// expansion refuses)
+__device__ __forceinline__ int32_t sat32(int64_t x) {
+  return static_cast<int32_t>(x > INT32_MAX ? INT32_MAX : (x < -INT32_MAX ? -INT32_MAX : x));
 }
 
 // a Q0.64 phase rounded to the nearest Q0.32 word (modulo one cycle)
@@ -319,8 +325,8 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
                                                        const uint64_t *__restrict__ q0s, int64_t i0, int64_t cnt,
                                                        PhaseConst k, double *__restrict__ paths,
                                                        uint2 *__restrict__ w_tx, uint2 *__restrict__ w_rx,
-                                                       int64_t stride, uint64_t *__restrict__ rec_s,
-                                                       int64_t *__restrict__ rec_hi, int64_t *__restrict__ rec_lo,
+                                                       int64_t stride, uint32_t *__restrict__ rec_s,
+                                                       int32_t *__restrict__ rec_hi, int32_t *__restrict__ rec_lo,
                                                        uint32_t *status) {
   const int64_t li = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   const int64_t j = blockIdx.y;
@@ -348,41 +354,44 @@ __global__ void __launch_bounds__(128) snapshot_kernel(GeomDev g, const float4 *
     }
     return;
   }
-  const uint64_t at_c = q64_prod(a_ref, k.fc) + q0s[i], at_s = q64_prod(a_ref, k.sp);
-  const uint64_t br_c = q64_prod(b_ref, k.fc), br_s = q64_prod(b_ref, k.sp);
+  // the four reference words rounded once: an antenna's offset is a whole number of Q0.32
+  // units (q32_small), so its word is the rounded reference plus that offset, exactly
+  const uint32_t at_c = q32_of(q64_prod(a_ref, k.fc) + q0s[i]), at_s = q32_of(q64_prod(a_ref, k.sp));
+  const uint32_t br_c = q32_of(q64_prod(b_ref, k.fc)), br_s = q32_of(q64_prod(b_ref, k.sp));
   const float fc_f = k.fc.hi, sp_f = k.sp.hi;
   // step offsets of the antennas relative to antenna 0 (their extremes, and the reference
   // antenna's, give the records' offsets from the reference)
-  uint64_t ot0 = 0, or0 = 0;
-  int64_t dt_hi = 0, dt_lo = 0, dt_c = 0, dr_hi = 0, dr_lo = 0, dr_c = 0;
-  for (int t = 0; t < k.ntx; ++t) {
+  uint32_t ot0 = 0, or0 = 0;
+  int32_t dt_hi = 0, dt_lo = 0, dt_c = 0, dr_hi = 0, dr_lo = 0, dr_c = 0;
+  uint2 *wt = w_tx + j * k.ntx * stride + li;
+  for (int t = 0; t < k.ntx; ++t, wt += stride) {
     const float e = leg_offset(ut, st.hi, g.tx[t]);
-    const uint64_t os = q64_small(e * sp_f);
+    const uint32_t os = q32_small(e * sp_f);
     if (t == 0) ot0 = os;
-    const int64_t d = static_cast<int64_t>(os - ot0);
+    const int32_t d = static_cast<int32_t>(os - ot0);
     dt_hi = max(dt_hi, d);
     dt_lo = min(dt_lo, d);
     if (t == k.tc) dt_c = d;
-    w_tx[(j * k.ntx + t) * stride + li] =
-        ok ? make_uint2(q32_of(at_c + q64_small(e * fc_f)), q32_of(at_s + os)) : make_uint2(0, 0);
+    *wt = ok ? make_uint2(at_c + q32_small(e * fc_f), at_s + os) : make_uint2(0u, 0u);
   }
-  for (int r = 0; r < k.nrx; ++r) {
+  uint2 *wr = w_rx + j * k.nrx * stride + li;
+  for (int r = 0; r < k.nrx; ++r, wr += stride) {
     const float e = leg_offset(ur, sr.hi, g.rx[r]);
-    const uint64_t os = q64_small(e * sp_f);
+    const uint32_t os = q32_small(e * sp_f);
     if (r == 0) or0 = os;
-    const int64_t d = static_cast<int64_t>(os - or0);
+    const int32_t d = static_cast<int32_t>(os - or0);
     dr_hi = max(dr_hi, d);
     dr_lo = min(dr_lo, d);
     if (r == k.rc) dr_c = d;
-    w_rx[(j * k.nrx + r) * stride + li] =
-        ok ? make_uint2(q32_of(br_c + q64_small(e * fc_f)), q32_of(br_s + os)) : make_uint2(0, 0);
+    *wr = ok ? make_uint2(br_c + q32_small(e * fc_f), br_s + os) : make_uint2(0u, 0u);
   }
   if (rec_s) {
+    // the words' own units: S(m, t, r) - S(m, t_c, r_c) of the stored words is exactly the
+    // recorded D, and s(m) is the stored reference pair's sum
     const int64_t at = j * stride + li;
-    const uint64_t otc = ot0 + static_cast<uint64_t>(dt_c), orc = or0 + static_cast<uint64_t>(dr_c);
-    rec_s[at] = ok ? (at_s + otc) + (br_s + orc) : 0;
-    rec_hi[at] = ok ? (dt_hi - dt_c) + (dr_hi - dr_c) : 0;
-    rec_lo[at] = ok ? (dt_lo - dt_c) + (dr_lo - dr_c) : 0;
+    rec_s[at] = ok ? (at_s + ot0 + static_cast<uint32_t>(dt_c)) + (br_s + or0 + static_cast<uint32_t>(dr_c)) : 0u;
+    rec_hi[at] = ok ? sat32(static_cast<int64_t>(dt_hi) - dt_c + static_cast<int64_t>(dr_hi) - dr_c) : 0;
+    rec_lo[at] = ok ? sat32(static_cast<int64_t>(dt_lo) - dt_c + static_cast<int64_t>(dr_lo) - dr_c) : 0;
   }
 }
 
@@ -470,7 +479,7 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
   if (mode == 1 && n > 0) {
     chunk = static_cast<int64_t>(kWordBudget / per_ray_words) / 256 * 256;
     if (chunk < 256) chunk = 256;
-    if (chunk > n) chunk = (n + 1) / 2 * 2;  // the word rows' stride stays even (16-byte pairs)
+    if (chunk > n) chunk = (n + 3) / 4 * 4;  // row strides of four: 16-byte word pairs, record quads
   }
   R.chunk = chunk;
   const size_t vbytes = 24 * static_cast<size_t>(g.nc) * static_cast<size_t>(geom->n_vertices);
@@ -502,7 +511,7 @@ int snap_setup(SnapRun &R, sim_ctx *ctx, const sim_rays *rays, const sim_meta *m
                     : 0);
   // tensor-core precisions: the per-(ray, chirp) records that bound the expansion
   R.o_rec = take(mode == 1 && chunk > 0 && g.precision != SIM_PREC_FP32_DIRECT
-                     ? 24 * static_cast<size_t>(chunk) * static_cast<size_t>(g.nc)
+                     ? 12 * static_cast<size_t>(chunk) * static_cast<size_t>(g.nc)
                      : 0);
   R.o_tmp = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_sig) : 0);
   R.o_spec = take(mode == 1 && want_spec ? 8 * static_cast<size_t>(g.n_cell) : 0);
@@ -675,9 +684,9 @@ extern "C" SIM_API int sim_snapshot_run(sim_ctx *ctx, const sim_rays *rays, cons
   const PhaseConst k = phase_const(g);
   const bool tensor = g.precision != SIM_PREC_FP32_DIRECT;
   const size_t rec_n = static_cast<size_t>(R.chunk) * static_cast<size_t>(g.nc);
-  uint64_t *rec_s = tensor ? reinterpret_cast<uint64_t *>(b + R.o_rec) : nullptr;
-  int64_t *rec_hi = tensor ? reinterpret_cast<int64_t *>(b + R.o_rec) + rec_n : nullptr;
-  int64_t *rec_lo = tensor ? reinterpret_cast<int64_t *>(b + R.o_rec) + 2 * rec_n : nullptr;
+  uint32_t *rec_s = tensor ? reinterpret_cast<uint32_t *>(b + R.o_rec) : nullptr;
+  int32_t *rec_hi = tensor ? reinterpret_cast<int32_t *>(b + R.o_rec) + rec_n : nullptr;
+  int32_t *rec_lo = tensor ? reinterpret_cast<int32_t *>(b + R.o_rec) + 2 * rec_n : nullptr;
   for (int64_t i0 = 0; i0 < R.n; i0 += R.chunk) {
     const int64_t cnt = R.n - i0 < R.chunk ? R.n - i0 : R.chunk;
     const dim3 grid(static_cast<unsigned>((cnt + 127) / 128), static_cast<unsigned>(g.nc));

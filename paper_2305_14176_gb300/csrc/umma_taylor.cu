@@ -800,6 +800,9 @@ __global__ void taylor_reduce(const float *__restrict__ part, int splits, int nv
 __device__ __forceinline__ unsigned long long signed_mag(uint64_t e) {
   return static_cast<int64_t>(e) < 0 ? ~e + 1ull : e;  // |signed Q0.64 word|
 }
+__device__ __forceinline__ uint32_t signed_mag32(uint32_t e) {
+  return static_cast<int32_t>(e) < 0 ? ~e + 1u : e;  // |signed Q0.32 word|
+}
 
 // amplitude maximum (FP16 scaling) and largest |eps| and |eps_t| of the scene
 __global__ void exact_stats(const float *__restrict__ amp, const uint64_t *__restrict__ eps,
@@ -872,43 +875,59 @@ __global__ void choose_terms(const unsigned long long *eps_max, const unsigned l
 
 // Virtual snapshots: a bound on the largest |S - S_ref| over the chunk's rays and every row, S
 // the per-sample step of row (m, k = t N_rx + r) and S_ref the ray's reference step of that
-// row's 256-row tile (chirp m_c, antennas t_c, r_c), as signed Q0.64 words; and the amplitude
-// maximum (FP16 scaling).  The kernel's delta is formed from four words rounded to Q0.32, so
-// it may exceed the unrounded one by up to four half units: 2^33 in Q0.64 is added to the bound.  It reads the phase-word kernel's record of each (ray, chirp):
+// row's 256-row tile (chirp m_c, antennas t_c, r_c), from the signed Q0.32 words, returned in
+// Q0.64 units with 2^33 (two word units) added as a margin; and the amplitude maximum (FP16
+// scaling).  It reads the phase-word kernel's record of each (ray, chirp):
 // s(m) = S(m, t_c, r_c) and the largest and smallest D(m, t, r) = S(m, t, r) - s(m) over the
 // antennas, which splits as D = D_tx(t) + D_rx(r), so its extremes are those of the two parts.
 // For a tile holding chirp m, S - S_ref = (s(m) - s(m_c)) + D lies between (s(m) - s(m_c)) plus
 // the smallest and plus the largest D; the bound is exact for chirps whose rows all fall in one
 // tile and at most the rest of their antennas' offsets above it for the others.  Chirps stride
-// over the grid's y, rays over its x (consecutive threads on consecutive rays), so no thread
-// divides to find its chirp.
+// over the grid's y, groups of four rays over its x (16-byte loads: the stride and the chunk's
+// first ray are multiples of four; lanes past cnt are masked), so no thread divides to find its
+// chirp.
 __global__ void snap_stats(SnapRec rec, int64_t stride, const float *__restrict__ amp, int64_t cnt, int nc, int nv,
                            bool want_amax, uint32_t *amax_bits, unsigned long long *d_max) {
-  uint32_t ma = 0;
-  unsigned long long md = 0;
+  uint32_t ma = 0, md = 0;
+  const int64_t quads = (cnt + 3) / 4;
   const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
   for (int m = blockIdx.y; m < nc; m += gridDim.y) {
     const int t0 = (m * nv) >> 8, t1 = (m * nv + nv - 1) >> 8;
-    const uint64_t *srow = rec.s + static_cast<int64_t>(m) * stride;
-    const int64_t *hrow = rec.d_hi + static_cast<int64_t>(m) * stride;
-    const int64_t *lrow = rec.d_lo + static_cast<int64_t>(m) * stride;
-    for (int64_t li = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; li < cnt; li += step) {
-      if (want_amax && m == 0) ma = max(ma, __float_as_uint(amp[li]));
-      const uint64_t sm = srow[li], hi = static_cast<uint64_t>(hrow[li]), lo = static_cast<uint64_t>(lrow[li]);
+    const uint4 *srow = reinterpret_cast<const uint4 *>(rec.s + static_cast<int64_t>(m) * stride);
+    const uint4 *hrow = reinterpret_cast<const uint4 *>(rec.d_hi + static_cast<int64_t>(m) * stride);
+    const uint4 *lrow = reinterpret_cast<const uint4 *>(rec.d_lo + static_cast<int64_t>(m) * stride);
+    for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < quads; q += step) {
+      const int64_t live = cnt - 4 * q;  // lanes e < live hold rays
+      const uint4 s4 = srow[q], h4 = hrow[q], l4 = lrow[q];
+      const uint32_t sm[4] = {s4.x, s4.y, s4.z, s4.w}, hi[4] = {h4.x, h4.y, h4.z, h4.w},
+                     lo[4] = {l4.x, l4.y, l4.z, l4.w};
+      if (want_amax && m == 0) {
+        const uint4 a4 = reinterpret_cast<const uint4 *>(amp)[q];  // amplitudes are >= 0
+        const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e < live) ma = max(ma, av[e]);
+      }
       for (int tile = t0; tile <= t1; ++tile) {
         const int mc = min((tile * 256 + 128) / nv, nc - 1);
-        const uint64_t base = sm - rec.s[static_cast<int64_t>(mc) * stride + li];
-        md = max(md, max(signed_mag(base + hi), signed_mag(base + lo)));
+        const uint4 c4 = reinterpret_cast<const uint4 *>(rec.s + static_cast<int64_t>(mc) * stride)[q];
+        const uint32_t sc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint32_t base = sm[e] - sc[e];
+          if (e < live) md = max(md, max(signed_mag32(base + hi[e]), signed_mag32(base + lo[e])));
+        }
       }
     }
   }
+  unsigned long long md64 = (static_cast<unsigned long long>(md) << 32) + (1ull << 33);  // Q0.64 units
   for (int o = 16; o > 0; o >>= 1) {
     ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
-    md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+    md64 = max(md64, __shfl_xor_sync(0xffffffffu, md64, o));
   }
   if ((threadIdx.x & 31) == 0) {
     if (want_amax) atomicMax(amax_bits, ma);
-    atomicMax(d_max, md + (1ull << 33));
+    atomicMax(d_max, md64);
   }
 }
 
