@@ -167,6 +167,12 @@ int launch_snap_tensor(const Derived &g, const uint2 *w_tx, const uint2 *w_rx, S
                        const float *amp, int64_t cnt, bool accumulate, float2 *sig, void *workspace, void *pair_ws,
                        uint32_t *status, cudaStream_t s);
 int launch_fft(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec, cudaStream_t s);
+// The same passes for many cubes of one shape held in spectrum slots of n_cell elements: the
+// range pass of one signal into the first n_sig elements of its slot, then the Doppler and angle
+// passes in place over `count` consecutive slots at once (the same arithmetic per cube, so the
+// same bits as launch_fft).
+int launch_fft_range_into(const Derived &g, const Tables &t, const float2 *sig, float2 *slot, cudaStream_t s);
+int launch_fft_planes(const Derived &g, const Tables &t, float2 *slots, int count, cudaStream_t s);
 int launch_labels(const Derived &g, RaysPrep p, const int32_t *obj, int64_t n, LabelScratch sc,
                   int32_t *labels, uint32_t *status, cudaStream_t s);
 

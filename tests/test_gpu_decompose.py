@@ -164,6 +164,31 @@ def test_span_part_is_the_scene_of_its_rays(precision, model, n_rays):
         ctx.close()
 
 
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT])
+def test_host_and_device_spectra_give_the_same_bits(precision):
+    """Spectra copied to host memory and to device memory, empty spans included, carry the same
+    bits, and so do the labels."""
+    radar, rays, mat, hits = _scene(26, 6000)
+    ctx = rs.Context(radar, precision=precision)
+    try:
+        arr = {k: np.ascontiguousarray(v) for k, v in dict(rays.arrays(), material_id=mat, n_hits=hits).items()}
+        r, m = rs.make_rays(arr, rays.n)
+        rules = [rs.span_rule(**q) for q in RULES] + [rs.span_rule(object_id=9)]  # the last one is empty
+        host = [np.full(ctx.cube_shape + (2,), np.nan, np.float32) for _ in rules]
+        lab_h = np.full(ctx.cube_shape, -7, np.int32)
+        assert rs.sim_decompose(ctx.ctx, r, m, rules, host, lab_h, 0.1) == rs.SIM_OK
+        dev = [torch.full(ctx.cube_shape + (2,), float("nan"), dtype=torch.float32, device="cuda") for _ in rules]
+        lab_d = torch.full(ctx.cube_shape, -7, dtype=torch.int32, device="cuda")
+        assert rs.sim_decompose(ctx.ctx, r, m, rules, dev, lab_d, 0.1) == rs.SIM_OK
+        torch.cuda.synchronize()
+        for x, y in zip(host, dev):
+            assert np.array_equal(x, y.cpu().numpy())
+        assert not host[-1].any()
+        assert np.array_equal(lab_h, lab_d.cpu().numpy())
+    finally:
+        ctx.close()
+
+
 def test_rules_needing_missing_meta_are_rejected():
     radar, rays, mat, hits = _scene(23, 100)
     ctx = rs.Context(radar, precision=rs.SIM_PREC_FP32_DIRECT)
