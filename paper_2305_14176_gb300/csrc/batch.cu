@@ -1,10 +1,13 @@
 // sim_run_batch: many scenes, possibly of different radar configurations, as one device
 // pipeline (see include/radarsim.h).
 //
-//   per scene: per-ray prep (+ amplitude maximum for FP16)
+//   per scene: per-ray prep (+ amplitude maximum for FP16), then its labels
 //   all scenes: ONE persistent tensor-core launch; CTAs take (scene, tile, split) units
 //               longest first from an atomic work list
-//   per scene: split reduction, windowed FFTs, labels
+//   per scene: split reduction, windowed FFTs
+//
+// The per-scene stages go to eight side streams (graph branches), so the scenes' small kernels
+// overlap one another and the labels overlap the persistent launch.
 //
 // Each scene's units are exactly those of its single-scene launch, and a unit's result does
 // not depend on which CTA runs it, so every scene gives the same bits in the batch as alone.
@@ -60,6 +63,13 @@ std::map<Key, std::unique_ptr<BatchPlan>> g_plans;
 cudaStream_t g_stream = nullptr;
 cudaEvent_t g_ev0 = nullptr, g_ev1 = nullptr;
 constexpr size_t kMaxPlans = 4;
+// Per-scene stages run on kBranches side streams (branches of the captured graph), scene i on
+// branch i % kBranches, so the small kernels of different scenes overlap each other and the
+// labels overlap the persistent launch; the main stream forks before the preps and joins
+// before and after the persistent launch.
+constexpr int kBranches = 8;
+cudaStream_t g_branch[kBranches] = {};
+cudaEvent_t g_fork = nullptr, g_gemm = nullptr, g_pre[kBranches] = {}, g_post[kBranches] = {};
 
 Key key_of(int n, sim_ctx *const *ctxs, const sim_rays *rays) {
   Key k;
@@ -71,15 +81,19 @@ Key key_of(int n, sim_ctx *const *ctxs, const sim_rays *rays) {
   return k;
 }
 
-// the stages of one batch on stream s; returns the number of kernels launched
+// the stages of one batch, forked from and joined back into stream s; returns the number of
+// kernels launched
 int enqueue(BatchPlan &p, cudaStream_t s) {
   uint8_t *b = p.block;
   const int n = static_cast<int>(p.gs.size());
   uint32_t *status = reinterpret_cast<uint32_t *>(b + p.status_off);
   int kernels = 0;
   cudaMemsetAsync(status, 0, 4 * static_cast<size_t>(n), s);
+  cudaEventRecord(g_fork, s);
+  for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(g_branch[k], g_fork, 0);
   std::vector<RaysPrep> preps(static_cast<size_t>(n));
   for (int i = 0; i < n; ++i) {
+    cudaStream_t bs = g_branch[i % kBranches];
     const SceneBufs &q = p.bufs[static_cast<size_t>(i)];
     const Derived &g = p.gs[static_cast<size_t>(i)];
     const bool lab = g.outputs & SIM_OUT_LABELS;
@@ -94,26 +108,42 @@ int enqueue(BatchPlan &p, cudaStream_t s) {
                 reinterpret_cast<float2 *>(b + q.step_r), nullptr, reinterpret_cast<uint64_t *>(b + q.nu_tx),
                 nullptr};
     preps[static_cast<size_t>(i)] = rp;
-    kernels += launch_prep(g, in, p.ns[static_cast<size_t>(i)], rp, status + i, s);
-    kernels += launch_umma_pre(g, rp, p.ns[static_cast<size_t>(i)], b + q.ws, s);
+    kernels += launch_prep(g, in, p.ns[static_cast<size_t>(i)], rp, status + i, bs);
+    kernels += launch_umma_pre(g, rp, p.ns[static_cast<size_t>(i)], b + q.ws, bs);
   }
-  kernels += launch_umma_batch(p.ub, s);
+  for (int k = 0; k < kBranches; ++k) {
+    cudaEventRecord(g_pre[k], g_branch[k]);
+    cudaStreamWaitEvent(s, g_pre[k], 0);
+  }
+  // the labels need only the prep: they run beside the persistent launch
   for (int i = 0; i < n; ++i) {
     const SceneBufs &q = p.bufs[static_cast<size_t>(i)];
     const Derived &g = p.gs[static_cast<size_t>(i)];
-    float2 *sig = reinterpret_cast<float2 *>(b + q.sig);
-    kernels += launch_umma_post(g, p.ns[static_cast<size_t>(i)], sig, b + q.ws, s);
-    if (g.outputs & SIM_OUT_SPECTRUM)
-      kernels += launch_fft(g, p.tables[static_cast<size_t>(i)], sig, reinterpret_cast<float2 *>(b + q.tmp),
-                            reinterpret_cast<float2 *>(b + q.spec), s);
     if (g.outputs & SIM_OUT_LABELS) {
       LabelScratch sc{reinterpret_cast<uint64_t *>(b + q.pk), reinterpret_cast<uint64_t *>(b + q.pe),
                       reinterpret_cast<uint32_t *>(b + q.ck), reinterpret_cast<uint64_t *>(b + q.cm),
                       reinterpret_cast<uint32_t *>(b + q.co), q.cap};
       kernels += launch_labels(g, preps[static_cast<size_t>(i)], reinterpret_cast<const int32_t *>(b + q.obj),
                                p.ns[static_cast<size_t>(i)], sc, reinterpret_cast<int32_t *>(b + q.labels),
-                               status + i, s);
+                               status + i, g_branch[i % kBranches]);
     }
+  }
+  kernels += launch_umma_batch(p.ub, s);
+  cudaEventRecord(g_gemm, s);
+  for (int k = 0; k < kBranches; ++k) cudaStreamWaitEvent(g_branch[k], g_gemm, 0);
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t bs = g_branch[i % kBranches];
+    const SceneBufs &q = p.bufs[static_cast<size_t>(i)];
+    const Derived &g = p.gs[static_cast<size_t>(i)];
+    float2 *sig = reinterpret_cast<float2 *>(b + q.sig);
+    kernels += launch_umma_post(g, p.ns[static_cast<size_t>(i)], sig, b + q.ws, bs);
+    if (g.outputs & SIM_OUT_SPECTRUM)
+      kernels += launch_fft(g, p.tables[static_cast<size_t>(i)], sig, reinterpret_cast<float2 *>(b + q.tmp),
+                            reinterpret_cast<float2 *>(b + q.spec), bs);
+  }
+  for (int k = 0; k < kBranches; ++k) {
+    cudaEventRecord(g_post[k], g_branch[k]);
+    cudaStreamWaitEvent(s, g_post[k], 0);
   }
   return kernels;
 }
@@ -237,9 +267,18 @@ extern "C" SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_
   }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_stream) {
-    if (cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&g_ev0) != cudaSuccess || cudaEventCreate(&g_ev1) != cudaSuccess)
+    bool ok = cudaStreamCreateWithFlags(&g_stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreate(&g_ev0) == cudaSuccess && cudaEventCreate(&g_ev1) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g_fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&g_gemm, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kBranches && ok; ++k)
+      ok = cudaStreamCreateWithFlags(&g_branch[k], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaEventCreateWithFlags(&g_pre[k], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&g_post[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      g_stream = nullptr;  // a later call tries again
       return SIM_E_CUDA;
+    }
   }
   cudaStream_t s = g_stream;
   const Key key = key_of(n, ctxs, rays);
