@@ -337,14 +337,15 @@ SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_rays *rays,
 
 /* ---- autotuner ----
    sim_autotune times, on the device and with synthetic rays of the context's shape,
-   the tensor-core ray sum at several split-K counts and the FFT passes at several tile
-   widths, and stores the fastest choice in a process-wide table keyed by (N_v, N_c,
+   the tensor-core ray sum in its built-in plan and at several split-K counts and the FFT
+   passes at several tile widths, and stores the fastest choice in a process-wide table keyed by (N_v, N_c,
    N_s, N_a, precision, ceil(log2 n_rays)).  Every later launch of that shape uses it
    (single scenes, batches, sim_raysum_noalloc), so tune before serving: results of one
    shape stay bit-identical for as long as the table does.  out (nullable) receives the
    choice and its timings.  Errors: SIM_E_INVALID, SIM_E_NOMEM, SIM_E_CUDA. */
 typedef struct {
-  int32_t splits;            /* split-K count of the ray sum (0: FP32 direct, not tuned) */
+  int32_t splits;            /* split-K count of the ray sum (0: the built-in plan, which at hi + lo
+                                precisions divides the work stream-K; FP32 direct is not tuned) */
   int32_t fft_range_points;  /* points per block of the range FFT (0: built-in choice) */
   int32_t fft_doppler_strip; /* samples per block of the Doppler FFT (0: built-in) */
   int32_t fft_angle_strip;   /* (m, n) positions per block of the angle FFT (0: built-in) */

@@ -242,10 +242,13 @@ bool tuning_lookup(const Derived &g, int64_t n, Tuning *t);
 // FFTs with explicit tile choices (zeros: heuristic)
 int launch_fft_with(const Derived &g, const Tables &t, const float2 *sig, float2 *tmp, float2 *spec,
                     cudaStream_t s, const Tuning &tu);
-// tensor-core ray sum with a forced split count (autotuner); workspace sized for it
+// tensor-core ray sum with a forced split count (autotuner), or with splits = 0 the plan a
+// scene takes without a table entry (stream-K at split precision); workspace sized for it
 int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                            cudaStream_t s, int splits);
 int64_t umma_workspace_bytes_splits(const Derived &g, int splits);
+// partial slots of that built-in plan (its workspace is umma_workspace_bytes_splits of them)
+int umma_builtin_splits(const Derived &g, int64_t n);
 // the split counts the tuner tries for a shape (heuristic first)
 int umma_split_candidates(const Derived &g, int64_t n, int *out, int max_out);
 

@@ -111,7 +111,7 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   if (tensor && g.model == SIM_MODEL_EXACT) return SIM_E_INVALID;
   int cand[16];
   const int nc = tensor ? umma_split_candidates(g, n_rays, cand, 16) : 0;
-  int max_splits = 1;
+  int max_splits = tensor ? umma_builtin_splits(g, n_rays) : 1;
   for (int i = 0; i < nc; ++i) max_splits = cand[i] > max_splits ? cand[i] : max_splits;
   const size_t un = static_cast<size_t>((n_rays + 31) / 32 * 32);
   const size_t prep_bytes = un * 72;
@@ -158,7 +158,8 @@ extern "C" SIM_API int sim_autotune(sim_ctx *ctx, int64_t n_rays, sim_tuning *ou
   Tuning best{};
   float best_sum = 0.f;
   if (tensor) {
-    best_sum = 1e30f;
+    // the built-in plan first (splits = 0 keeps it): a forced count must beat it
+    best_sum = time_min(s, e0, e1, [&] { launch_umma_sum_splits(g, rp, n_rays, sig, ws, status, s, 0); });
     for (int i = 0; i < nc; ++i) {
       const int sp = cand[i];
       const float ms = time_min(s, e0, e1, [&] { launch_umma_sum_splits(g, rp, n_rays, sig, ws, status, s, sp); });

@@ -1109,9 +1109,18 @@ int64_t umma_workspace_bytes_splits(const Derived &g, int splits) {
   return 256 + static_cast<int64_t>(splits) * g.nv * g.nc * 2 * g.ns * 4;
 }
 
+// the plan a scene takes with no table entry (stream-K at split precision)
+Shape builtin_shape(const Derived &g, int64_t n) {
+  const Shape s = plan_shape_forced(g, n, 0);
+  const bool split = g.precision == SIM_PREC_BF16_SPLIT || g.precision == SIM_PREC_FP16_SPLIT;
+  return split && n > 0 ? with_stream_k(s, n) : s;
+}
+
+int umma_builtin_splits(const Derived &g, int64_t n) { return builtin_shape(g, n).splits; }
+
 int launch_umma_sum_splits(const Derived &g, RaysPrep p, int64_t n, float2 *sig, void *workspace, uint32_t *status,
                            cudaStream_t s, int splits) {
-  const Shape sh = plan_shape_forced(g, n, splits);
+  const Shape sh = splits > 0 ? plan_shape_forced(g, n, splits) : builtin_shape(g, n);
   uint32_t *amax = static_cast<uint32_t *>(workspace);
   float *partials = reinterpret_cast<float *>(static_cast<uint8_t *>(workspace) + 256);
   const bool f16 = g.precision == SIM_PREC_FP16 || g.precision == SIM_PREC_FP16_SPLIT;

@@ -1,5 +1,6 @@
-"""Autotuner on the device: it picks a valid launch shape, later runs use it, and the
-results still match the oracle and repeat bit for bit."""
+"""Autotuner on the device: it picks a valid launch shape (the built-in plan or a forced
+split count), later runs use it, and the results still match the oracle and repeat bit for
+bit."""
 import numpy as np
 import pytest
 
@@ -17,7 +18,9 @@ def test_autotune_then_run():
     ctx = rs.Context(radar, precision=rs.SIM_PREC_FP16_SPLIT)
     try:
         t = rs.sim_autotune(ctx.ctx, rays.n)
-        assert t.splits >= 1 and t.ray_sum_ms > 0 and t.fft_ms > 0
+        # 0 keeps the built-in plan (stream-K at hi + lo), timed first; a forced split count
+        # is stored only when it beat that plan
+        assert t.splits >= 0 and t.ray_sum_ms > 0 and t.fft_ms > 0
         assert rs.sim_tuning_count() == 1
         rc1, s1, x1, l1 = run(radar, rays, rs.SIM_PREC_FP16_SPLIT, ctx=ctx)
         rc2, s2, x2, l2 = run(radar, rays, rs.SIM_PREC_FP16_SPLIT, ctx=ctx)

@@ -114,6 +114,24 @@ def test_signal_spectrum_labels_match_oracle(shape, precision):
     assert rc == rs.SIM_OK and np.array_equal(sig_h, sig)
 
 
+@pytest.mark.parametrize("precision", [rs.SIM_PREC_FP16_SPLIT, rs.SIM_PREC_FP16])
+def test_fast_boxes_take_the_pair_sum(precision):
+    """Boxes at up to 3 km/s move a path by ~4 m across a 256-row tile's eleven chirps: the
+    steps' spread 2 pi n_h |S - S_ref| is ~40 rad, far beyond eight Chebyshev terms, so the
+    chunk's bound sends it to the FP32 pair sum (route bit 0) and the result is the FP32
+    path's."""
+    radar = scenegen.radar_automotive(n_chirps=16, n_samples=64)
+    rays, hits, geom = scenegen.moving_scene(27, radar, 300, n_objects=4, bounce_frac=0.3, v_max=3000.0)
+    routes = []
+    rc, sig, spec, lab = snapshot(radar, rays, hits, geom, precision=precision, routes=routes)
+    assert rc == rs.SIM_OK, rs.sim_status_string(rc)
+    assert routes == [{0}]
+    ref = oracle.signal_geom(radar, rays, hits, geom)
+    assert rel_max(sig, ref) <= TOL[rs.SIM_PREC_FP32_DIRECT] and rel_rms(sig, ref) <= TOL_RMS[rs.SIM_PREC_FP32_DIRECT]
+    assert rel_max(spec, oracle.spectrum(radar, ref)) <= TOL[rs.SIM_PREC_FP32_DIRECT]
+    assert np.array_equal(lab, oracle.labels(radar, rays))
+
+
 @pytest.mark.parametrize("precision", [rs.SIM_PREC_FP32_DIRECT, rs.SIM_PREC_FP16_SPLIT])
 def test_automotive_size_in_two_chunks_sampled(precision):
     """256 chirps x 512 samples x 12 channels; 240,000 rays need two chunks of phase words
