@@ -35,8 +35,9 @@
 // relative to the reference transmitter) and once per ray (the snapshot-0 terms of Eq. 7).  An
 // antenna at x_ref + e differs from the reference leg by |u - e| - |u| = (|e|^2 - 2 u.e) /
 // (|u - e| + |u|), u = p - x_ref, a few centimetres for a compact array: that difference is
-// taken in FP32 (relative error ~2^-22, so ~5 nm for e = 2 cm, 8e-6 rad of carrier phase)
-// and added to the words in Q0.64 before their rounding.
+// taken in FP32, by its series in (|e|^2 - 2 u.e) / |u|^2 where that is small (relative error
+// ~2^-22, so ~5 nm for e = 2 cm, 8e-6 rad of carrier phase), and added to the words in Q0.64
+// before their rounding.
 #include <cuda_runtime.h>
 
 #include <math.h>
