@@ -247,6 +247,14 @@ __device__ __forceinline__ float q64_to_rad(uint64_t p) {
 __device__ __forceinline__ float q32_to_rad(uint32_t p) {
   return static_cast<float>(static_cast<int32_t>(p)) * 1.46291807926715968e-09f;
 }
+// The signed value of a 64-bit word in FP32 from its two 32-bit halves (a 64-bit integer
+// conversion runs on this GPU's FP64 pipe): two roundings, so an absolute error of at most
+// 2^7 plus 2^-23 of the value, for quantities that need no more (the expansion variable x; a
+// phasor step, whose error a recurrence multiplies, keeps the correctly rounded conversion).
+__device__ __forceinline__ float s64_to_f32(uint64_t w) {
+  return fmaf(static_cast<float>(static_cast<int32_t>(w >> 32)), 4294967296.0f,
+              static_cast<float>(static_cast<uint32_t>(w)));
+}
 
 template <bool F16>
 __device__ __forceinline__ float amp_scale(const uint32_t *amax_bits) {

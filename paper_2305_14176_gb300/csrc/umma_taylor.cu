@@ -317,8 +317,8 @@ __device__ __forceinline__ void produce_taylor(const TStage &sr, uint8_t *stage,
         __sincosf(q64_to_rad(ph), &sn, &cs);
         const float am = rc.valid ? sr.amp[q] * scale : 0.f;
         t[q] = make_float2(am * cs, am * sn);
-        x[q] = rc.xm * static_cast<float>(static_cast<int64_t>(sr.eps[q]));
-        if constexpr (TDM) x[q] += rc.xt * static_cast<float>(static_cast<int64_t>(sr.epst[q]));
+        x[q] = rc.xm * s64_to_f32(sr.eps[q]);
+        if constexpr (TDM) x[q] += rc.xt * s64_to_f32(sr.epst[q]);
       }
     }
     if constexpr (CH) {
