@@ -1,8 +1,8 @@
 // K_a: per-ray prep in FP64 (arXiv 2305.14176, Sec. II-A Eqs. 1-3, Sec. II-E Eq. 7).
 //
 // For every ray: validate it, range-reduce its phase increments to Q0.64 fixed point
-// (the one step whose accuracy needs FP64: f_c d / c is up to ~1e5 cycles), and compute
-// its label cell and fixed-point energy.  All FP64 arithmetic uses explicit _rn
+// (the one step whose accuracy needs FP64: f_c d / c is up to ~1e5 cycles; the reduction mod 1
+// works on the FP64 product's bits), and compute its label cell and fixed-point energy.  All FP64 arithmetic uses explicit _rn
 // intrinsics so no multiply-add is contracted: the bin coordinates follow a fixed
 // operation order and are reproducible bit for bit.
 #include <math.h>
@@ -17,7 +17,6 @@ __device__ constexpr double kP1 = 0x1.921fb54442d18p+0;
 __device__ constexpr double kP2 = 0x1.1a62633145c07p-54;
 __device__ constexpr double kTwoOverPi = 0x1.45f306dc9c883p-1;
 __device__ constexpr double kInv2Pi = 0x1.45f306dc9c883p-3;  // 1 / (2 pi)
-__device__ constexpr double kTwo64 = 18446744073709551616.0;
 
 // Taylor series of sin on [-pi/4, pi/4] through r^17, Horner in r^2 with fused multiply-adds
 __device__ __forceinline__ double poly_sin(double r) {
@@ -62,9 +61,23 @@ __device__ __forceinline__ double sin_or_cos(double x, bool want_cos) {
   }
 }
 
+// x mod 1 as a Q0.64 phase, from the bits of x on the integer pipes (this GPU's FP64 pipe is
+// the prep's limit): x = +-m 2^(e - 1075) with m the 53-bit significand, so x 2^64 mod 2^64 =
+// +-m 2^(e - 1011) mod 2^64, rounded to nearest when the shift is to the right; zero,
+// subnormal and non-finite x give 0 (the validated inputs give none of those but zero).
 __device__ __forceinline__ uint64_t frac_q64(double x) {
-  const double f = __dsub_rn(x, floor(x));  // exact, in [0, 1)
-  return __double2ull_rn(__dmul_rn(f, kTwo64));
+  const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x));
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  if (e == 0 || e == 0x7ff) return 0;
+  const uint64_t m = (b & 0xfffffffffffffull) | (uint64_t{1} << 52);
+  const int sh = e - 1011;
+  uint64_t q = 0;
+  if (sh >= 0) {
+    if (sh < 64) q = m << sh;
+  } else if (sh > -64) {
+    q = (m + (uint64_t{1} << (-sh - 1))) >> -sh;
+  }
+  return (b >> 63) ? uint64_t{0} - q : q;
 }
 
 // e^{2 pi j 32 q} for a Q0.64 phase increment q.  The exact Q0.64 product p = 32 q splits into
@@ -94,6 +107,10 @@ __device__ __forceinline__ int64_t bin_of(double x, int64_t n) {
 struct PrepConst {
   int pattern_exp;
   double fc, bw, td, tslot, nc_d, ka;
+  // phase-word constants (no bin depends on them): f_c / c, 2 f_c T_slot / c, and the
+  // range-migration words' 2 B T_d / (c N_s) and 2 B T_slot / (c N_s), each one FP64 product
+  // per ray instead of a division
+  double fc_c, nut_v, eps_v, epst_v;
   uint64_t nrx;
   double inv_ns, inv_nc, inv_na;
   int64_t ns, nc, na;
@@ -144,20 +161,16 @@ __global__ void __launch_bounds__(256) prep_kernel(PrepConst k, RaysIn in, int64
   out.nu_a[i] = nu_a;
   // TDM-MIMO: transmitter t fires chirp j at j T_d + t T_slot, so its phase gains t nu_t with
   // nu_t = 2 v f_c T_slot / c; channel k = t N_rx + r then has phase t (N_rx nu_a + nu_t) + r nu_a
-  const uint64_t nu_t = k.tslot > 0.0
-                            ? frac_q64(__ddiv_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, vd), k.fc), k.tslot), kC))
-                            : 0ull;
+  const uint64_t nu_t = k.tslot > 0.0 ? frac_q64(__dmul_rn(vd, k.nut_v)) : 0ull;
   out.nu_tx[i] = k.nrx * nu_a + nu_t;
   if (out.eps) {
     // exact Eq. 2: mu t_n (tau_i(j) - tau_i(0)) = n j B (2 v T_d) / (c N_s) cycles
-    out.eps[i] = frac_q64(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(k.bw, __dmul_rn(2.0, vd)), k.td), kC), k.inv_ns));
+    out.eps[i] = frac_q64(__dmul_rn(vd, k.eps_v));
     // and with TDM slots n t B (2 v T_slot) / (c N_s)
-    out.eps_t[i] =
-        frac_q64(__dmul_rn(__ddiv_rn(__dmul_rn(__dmul_rn(k.bw, __dmul_rn(2.0, vd)), k.tslot), kC), k.inv_ns));
+    out.eps_t[i] = frac_q64(__dmul_rn(vd, k.epst_v));
   }
   // carrier phase f_c tau (Eq. 1, Eq. 2) plus the ray's start phase
-  out.carrier[i] = frac_q64(__ddiv_rn(__dmul_rn(k.fc, d), kC)) +
-                   frac_q64(__dmul_rn(static_cast<double>(p0), kInv2Pi));
+  out.carrier[i] = frac_q64(__dmul_rn(d, k.fc_c)) + frac_q64(__dmul_rn(static_cast<double>(p0), kInv2Pi));
   out.amp[i] = static_cast<float>(aa);
   const int64_t cell = (bin_of(x_a, k.na) * k.nc + bin_of(x_d, k.nc)) * k.ns + bin_of(x_r, k.ns);
   out.cell[i] = static_cast<int32_t>(cell);
@@ -200,6 +213,10 @@ int launch_prep(const Derived &g, RaysIn in, int64_t n, RaysPrep out, uint32_t *
   k.td = g.td;
   k.nc_d = static_cast<double>(g.nc);
   k.ka = g.ka;
+  k.fc_c = g.fc / kC;
+  k.nut_v = 2.0 * g.fc * g.tslot / kC;
+  k.eps_v = 2.0 * g.bw * g.td / (kC * g.ns);
+  k.epst_v = 2.0 * g.bw * g.tslot / (kC * g.ns);
   k.inv_ns = 1.0 / g.ns;
   k.inv_nc = 1.0 / g.nc;
   k.inv_na = 1.0 / g.na;
