@@ -275,8 +275,21 @@ extern "C" SIM_API int sim_run_batch(int32_t n, sim_ctx *const *ctxs, const sim_
       ok = cudaStreamCreateWithFlags(&g_branch[k], cudaStreamNonBlocking) == cudaSuccess &&
            cudaEventCreateWithFlags(&g_pre[k], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&g_post[k], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-      g_stream = nullptr;  // a later call tries again
+    if (!ok) {  // release what was made; a later call tries again
+      for (int k = 0; k < kBranches; ++k) {
+        if (g_branch[k]) cudaStreamDestroy(g_branch[k]);
+        if (g_pre[k]) cudaEventDestroy(g_pre[k]);
+        if (g_post[k]) cudaEventDestroy(g_post[k]);
+        g_branch[k] = nullptr;
+        g_pre[k] = g_post[k] = nullptr;
+      }
+      for (cudaEvent_t *e : {&g_ev0, &g_ev1, &g_fork, &g_gemm}) {
+        if (*e) cudaEventDestroy(*e);
+        *e = nullptr;
+      }
+      if (g_stream) cudaStreamDestroy(g_stream);
+      g_stream = nullptr;
+      cudaGetLastError();
       return SIM_E_CUDA;
     }
   }
